@@ -1,0 +1,165 @@
+/*
+ * swig.h -- C-ABI of libswig, a GB300-native (sm_103a) Slice-within-Gibbs
+ * nested sampler for compact-binary gravitational-wave parameter estimation.
+ *
+ * The calls follow the paper's statement of the problem: set data, PSDs,
+ * detectors and prior; run nested sampling; return posterior samples and the
+ * log-evidence.  Citations are to "Ab Initio Real-Time Gravitational-Wave
+ * Parameter Estimation" (arXiv 2607.28265) by section / equation / table.
+ *
+ * Conventions for every call:
+ *   - Every function returns SWIG_OK (0) or a negative SWIG_E_* code and never
+ *     throws; swig_last_error() gives a message for the last failure on a
+ *     context (valid until the next call on that context).
+ *   - Host arrays passed in are COPIED; the caller keeps ownership.  Output
+ *     buffers are caller-allocated.
+ *   - "_dev" variants take device pointers (to memory of the context's device)
+ *     and a cudaStream_t passed as void*; they enqueue work and return without
+ *     synchronising unless stated.
+ *   - A context is not thread-safe; distinct contexts may be used concurrently.
+ *   - The 13-vector theta has slots, in order:
+ *       0 Mc [Msun] (detector-frame chirp mass), 1 q = m2/m1 <= 1,
+ *       2 chi1, 3 chi2 (aligned dimensionless spins), 4 Lambda1, 5 Lambda2,
+ *       6 d_L [Mpc], 7 iota [rad], 8 psi [rad], 9 RA [rad], 10 Dec [rad],
+ *       11 t_c [s] (relative to the reference time), 12 phi_c [rad].
+ */
+#ifndef SWIG_H
+#define SWIG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define SWIG_OK 0
+#define SWIG_E_ARG (-1)      /* invalid argument (null pointer, size, range) */
+#define SWIG_E_STATE (-2)    /* call out of order (e.g. run before data)     */
+#define SWIG_E_NOMEM (-3)    /* host or device allocation failed             */
+#define SWIG_E_CUDA (-4)     /* CUDA runtime error                           */
+#define SWIG_E_TIMEOUT (-5)  /* a bounded device wait expired                */
+#define SWIG_E_NUMERIC (-6)  /* non-finite or non-positive input values      */
+
+/* ---- enumerations ------------------------------------------------------ */
+#define SWIG_N_PARAMS 13
+#define SWIG_MAX_DET 4
+
+enum swig_prior_kind {       /* Table I prior families, on [lo, hi]          */
+  SWIG_PRIOR_UNIFORM = 0,    /* p(x) = const                                 */
+  SWIG_PRIOR_SINE = 1,       /* p(x) ~ sin x   (inclination)                 */
+  SWIG_PRIOR_COSINE = 2,     /* p(x) ~ cos x   (declination)                 */
+  SWIG_PRIOR_POWER2 = 3      /* p(x) ~ x^2     (luminosity distance)         */
+};
+enum swig_param_mode {
+  SWIG_MODE_SAMPLE = 0,      /* sampled by the Gibbs kernel                  */
+  SWIG_MODE_FIXED = 1,       /* held at `value`                              */
+  SWIG_MODE_MARG = 2         /* marginalised analytically (phi_c only)       */
+};
+enum swig_likelihood { SWIG_LIKE_FULL = 0, SWIG_LIKE_HET = 1 };
+enum swig_precision { SWIG_PREC_FP64 = 0, SWIG_PREC_MIXED = 1 };
+enum swig_proposal { SWIG_PROPOSAL_COV = 0, SWIG_PROPOSAL_LEARNED = 1 };
+
+/* One slot of the 13-vector: prior family and bounds (Table I), mode, and the
+ * Gibbs block it belongs to (Sec. 3.2; blocks are swept in increasing id). */
+typedef struct swig_param {
+  int kind;
+  double lo, hi;
+  int mode;
+  double value;
+  int block;
+} swig_param;
+
+/* Sampler hyper-parameters (Table II): live points m, deletions k per
+ * iteration, Gibbs sweeps M, slice steps per dimension of each block, the
+ * termination threshold on log Z_live - log Z_dead (Sec. 3.2: -3). */
+typedef struct swig_sampler_cfg {
+  int nlive;
+  int nrep;
+  int sweeps;
+  int steps_per_dim;
+  uint64_t seed;
+  int likelihood;       /* swig_likelihood */
+  int precision;        /* swig_precision  */
+  int proposal;         /* swig_proposal   */
+  int het_bins;         /* heterodyned bins (SWIG_LIKE_HET)              */
+  int het_spacing;      /* 0 = equal maximum phase change, 1 = geometric */
+  double dlogz;         /* termination threshold, e.g. -3                */
+  int max_iter;         /* safety cap on outer iterations                */
+  double het_fiducial[SWIG_N_PARAMS]; /* theta of the reference waveform  */
+} swig_sampler_cfg;
+
+typedef struct swig_result {
+  double logz, logz_err, info, ess, wall_s;
+  int64_t n_dead, n_iter, n_evals, n_sweep_evals;
+  int status;
+} swig_result;
+
+typedef struct swig_ctx swig_ctx;  /* opaque; owned by the library */
+
+/* ---- context ----------------------------------------------------------- */
+/* Create a context bound to CUDA device `cuda_device`.  *out is set on success. */
+int swig_create(swig_ctx** out, int cuda_device);
+/* Free the context and every device buffer it owns.  NULL is a no-op. */
+void swig_destroy(swig_ctx* ctx);
+/* Message for the last failure on ctx ("" if none).  NULL ctx gives the
+ * message of the last failed swig_create in this thread. */
+const char* swig_last_error(const swig_ctx* ctx);
+
+/* ---- problem definition (Sec. 3.1) ------------------------------------- */
+/* Frequency grid f_k = k df for k = ceil(f_min/df) .. floor(f_max/df), both
+ * ends inclusive.  Requires 0 < f_min < f_max, df > 0, at most 2^22 bins. */
+int swig_set_grid(swig_ctx* ctx, double f_min, double f_max, double df);
+/* Detector `idx` (0 <= idx < SWIG_MAX_DET; detectors must be set
+ * contiguously from 0): vertex position [m] and unit arm vectors in the
+ * Earth-fixed frame.  The detector tensor is D = (x x^T - y y^T) / 2. */
+int swig_set_detector(swig_ctx* ctx, int idx, const double vertex_m[3],
+                      const double x_arm[3], const double y_arm[3]);
+/* Greenwich mean sidereal time [rad] at the reference time (fixes the Earth's
+ * orientation for antenna patterns and delays; Sec. 4.1). */
+int swig_set_time_ref(swig_ctx* ctx, double gmst_rad);
+/* Frequency-domain strain of detector `det` on the grid: n complex values as
+ * 2n doubles (re, im interleaved), time origin at the reference time.
+ * n must equal the number of grid bins.  Non-finite values -> SWIG_E_NUMERIC. */
+int swig_set_data(swig_ctx* ctx, int det, const double* re_im, int64_t n);
+/* One-sided noise PSD S_n(f) [1/Hz] of detector `det` on the grid (n values,
+ * all finite and > 0, else SWIG_E_NUMERIC). */
+int swig_set_psd(swig_ctx* ctx, int det, const double* psd, int64_t n);
+/* Prior: exactly SWIG_N_PARAMS slots (Table I).  Requires lo < hi for sampled
+ * slots; only phi_c may be SWIG_MODE_MARG (closed-form phase marginalisation,
+ * Sec. 3.1). */
+int swig_set_prior(swig_ctx* ctx, const swig_param* params, int n_params);
+/* Sampler configuration (Table II); validated here (nlive > nrep >= 1, ...). */
+int swig_set_sampler(swig_ctx* ctx, const swig_sampler_cfg* cfg);
+
+/* ---- likelihood (Eq. 2) ------------------------------------------------- */
+/* logL(theta) = -1/2 sum_i <d_i - h_i | d_i - h_i>_i (Eq. 2, without the
+ * constant normalisation), or, when phi_c is SWIG_MODE_MARG, the phase-
+ * marginalised form log I0(|Z|) - 1/2 sum <h|h> - 1/2 sum <d|d> (Sec. 3.1).
+ * theta: n x 13 doubles (row-major, host).  out_logl: n doubles (host).
+ * Precision and likelihood type follow the sampler configuration (FULL and
+ * MIXED if none was set).  n == 0 is a no-op; n > 2^20 -> SWIG_E_ARG. */
+int swig_loglike_batch(swig_ctx* ctx, const double* theta, int64_t n, double* out_logl);
+/* Same with device pointers on the context's device, enqueued on `stream`
+ * (cudaStream_t).  Uses the context's scratch buffers, so calls on one
+ * context must not overlap. */
+int swig_loglike_batch_dev(swig_ctx* ctx, const double* theta_dev, int64_t n,
+                           double* out_logl_dev, void* stream);
+
+/* ---- prior transform (Table I) ---------------------------------------- */
+/* Map n unit-cube points (n x n_sampled doubles, sampled slots in slot order)
+ * to full 13-vectors theta (n x 13). */
+int swig_prior_transform(swig_ctx* ctx, const double* u, int64_t n, double* theta);
+
+/* ---- nested sampling (Sec. 2.2, 2.3, 3.2) ------------------------------ */
+/* Run nested sampling to termination on the device. */
+int swig_run(swig_ctx* ctx, swig_result* out);
+/* Dead points of the last run (theta n x 13, logL, log-weight normalised so
+ * that logsumexp(logw) = log Z).  With cap == 0 only *n_out is set. */
+int swig_get_samples(swig_ctx* ctx, double* theta, double* logl, double* logw,
+                     int64_t cap, int64_t* n_out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SWIG_H */

@@ -18,10 +18,15 @@ import math
 
 import numpy as np
 
-from swig_inputs import (C_SI, IDX, MODE_FIXED, MODE_MARG, MPC_M, MTSUN_S, N_PARAMS,
-                         PRIOR_COSINE, PRIOR_POWER2, PRIOR_SINE, PRIOR_UNIFORM)
+from swig_inputs import (C_SI, IDX, MODE_FIXED, MODE_MARG, N_PARAMS, PRIOR_COSINE, PRIOR_POWER2,
+                         PRIOR_SINE, PRIOR_UNIFORM)
 
 EULER_GAMMA = 0.57721566490153286061
+# G M_sun / c^3 [s] from the IAU 2015 (Resolution B3) nominal solar mass
+# parameter G M_sun = 1.3271244e20 m^3 s^-2, and the parsec-based Mpc [m].
+GM_SUN_SI = 1.3271244e20
+MTSUN_S = GM_SUN_SI / C_SI**3
+MPC_M = 3.0856775814913673e22
 
 
 # --------------------------------------------------------------------------

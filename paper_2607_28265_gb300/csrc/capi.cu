@@ -1,0 +1,595 @@
+// C-ABI of libswig: context management, problem definition, host-side FP64
+// preparation (data weighting, tile planning) and the likelihood entry points.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "context.h"
+#include "device_common.cuh"
+#include "kernels.h"
+#include "swig.h"
+
+using namespace swig;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+int fail(swig_ctx* c, int code, const std::string& msg) {
+  if (c) c->err = msg;
+  return code;
+}
+
+#define CUDA_TRY(ctx, call)                                                              \
+  do {                                                                                  \
+    cudaError_t e_ = (call);                                                            \
+    if (e_ != cudaSuccess) {                                                            \
+      return fail((ctx), e_ == cudaErrorMemoryAllocation ? SWIG_E_NOMEM : SWIG_E_CUDA,  \
+                  std::string(#call) + ": " + cudaGetErrorString(e_));                  \
+    }                                                                                   \
+  } while (0)
+
+template <typename T>
+void dfree(T*& p) {
+  if (p) cudaFree(p);
+  p = nullptr;
+}
+
+// Compensated (Neumaier) summation for host reductions over the grid.
+struct NSum {
+  double s = 0.0, c = 0.0;
+  void add(double x) {
+    const double t = s + x;
+    if (std::fabs(s) >= std::fabs(x))
+      c += (s - t) + x;
+    else
+      c += (x - t) + s;
+    s = t;
+  }
+  double value() const { return s + c; }
+};
+
+// n-th derivative of f^p (ln f)^lg at f as coefficients: f^(p-n) (a ln f + b).
+double basis_derivative(double p, int lg, int n, double f) {
+  if (!lg) {
+    double fall = 1.0;
+    for (int i = 0; i < n; ++i) fall *= (p - i);
+    return fall * std::pow(f, p - n);
+  }
+  double a = 1.0, b = 0.0;
+  for (int i = 0; i < n; ++i) {
+    const double na = (p - i) * a, nb = (p - i) * b + a;
+    a = na;
+    b = nb;
+  }
+  return std::pow(f, p - n) * (a * std::log(f) + b);
+}
+
+// |n-th derivative| bound on [f0, f1] (monotone power times log factor).
+double basis_derivative_bound(double p, int lg, int n, double f0, double f1) {
+  if (!lg) {
+    double fall = 1.0;
+    for (int i = 0; i < n; ++i) fall *= (p - i);
+    return std::fabs(fall) * std::max(std::pow(f0, p - n), std::pow(f1, p - n));
+  }
+  double a = 1.0, b = 0.0;
+  for (int i = 0; i < n; ++i) {
+    const double na = (p - i) * a, nb = (p - i) * b + a;
+    a = na;
+    b = nb;
+  }
+  const double lmax = std::max(std::fabs(std::log(f0)), std::fabs(std::log(f1)));
+  return std::max(std::pow(f0, p - n), std::pow(f1, p - n)) * (std::fabs(a) * lmax + std::fabs(b));
+}
+
+const double kBasisPow[NBASIS] = {-5.0 / 3.0, -1.0, -2.0 / 3.0, -1.0 / 3.0, 0.0, 1.0 / 3.0,
+                                  1.0 / 3.0,  2.0 / 3.0, 5.0 / 3.0, 7.0 / 3.0, 0.0};
+const int kBasisLog[NBASIS] = {0, 0, 0, 0, 1, 0, 1, 0, 0, 0, 0};
+
+void split_df(double x, float* hi, float* lo) {
+  const float h = (float)x;
+  *hi = h;
+  *lo = (float)(x - (double)h);
+}
+
+// Largest |c_j| over the corners of the intrinsic prior box (x1.25 margin).
+void coefficient_bounds(const swig_ctx* c, double* cmax) {
+  double lo[6], hi[6];
+  const double dlo[6] = {0.87, 0.125, -0.1, -0.1, 0.0, 0.0}, dhi[6] = {3.0, 1.0, 0.1, 0.1, 5000.0, 5000.0};
+  for (int i = 0; i < 6; ++i) {
+    lo[i] = dlo[i];
+    hi[i] = dhi[i];
+    if (c->prior_set) {
+      const swig_param& p = c->params[i];
+      if (p.mode == SWIG_MODE_FIXED) {
+        lo[i] = hi[i] = p.value;
+      } else if (p.mode == SWIG_MODE_SAMPLE) {
+        lo[i] = p.lo;
+        hi[i] = p.hi;
+      }
+    }
+  }
+  for (int j = 0; j < NBASIS; ++j) cmax[j] = 0.0;
+  for (int m = 0; m < 64; ++m) {
+    double v[6];
+    for (int i = 0; i < 6; ++i) v[i] = (m >> i & 1) ? hi[i] : lo[i];
+    double cc[NBASIS];
+    taylorf2_basis_coeffs(v[0], v[1], v[2], v[3], v[4], v[5], cc);
+    for (int j = 0; j < NBASIS; ++j) cmax[j] = std::max(cmax[j], std::fabs(cc[j]));
+  }
+  for (int j = 0; j < NBASIS; ++j) cmax[j] *= 1.25;
+}
+
+// Tiles of 2^m bins (1 .. kMaxTileBins) whose degree-kTaylorDeg Taylor
+// remainder of the phase (in cycles) stays below `eps` over the prior box.
+// Tiles up to 32 bins start at a multiple of their size (so they never cross a
+// 32-bin chunk); larger tiles start on a chunk boundary.
+void plan_tiles(const swig_ctx* c, std::vector<TileInfo>& tiles, std::vector<TileBasis>& basis) {
+  double cmax[NBASIS];
+  coefficient_bounds(c, cmax);
+  const double eps = 1e-8;
+  const int n = (int)c->n_bins;
+  const int order = kTaylorDeg + 1;
+  double fact = 1.0;
+  for (int i = 2; i <= order; ++i) fact *= i;
+  tiles.clear();
+  basis.clear();
+  int k = 0;
+  while (k < n) {
+    int T = 1;
+    while (T * 2 <= kMaxTileBins) {
+      const int T2 = T * 2;
+      if (T2 <= kChunk && k % T2 != 0) break;
+      if (T2 > kChunk && k % kChunk != 0) break;
+      const double fa = (double)(c->k_min + k) * c->df, fb = fa + T2 * c->df;
+      double R = 0.0;
+      for (int j = 0; j < NBASIS - 1; ++j)
+        R += cmax[j] * basis_derivative_bound(kBasisPow[j], kBasisLog[j], order, fa, fb);
+      R *= std::pow(T2 * c->df, order) / fact;
+      if (R > eps) break;
+      T = T2;
+    }
+    TileInfo ti;
+    ti.k0 = k;
+    ti.nbins = std::min(T, n - k);
+    const double fa = (double)(c->k_min + k) * c->df;
+    split_df(fa, &ti.fa_hi, &ti.fa_lo);
+    int span = 1, bits = 0;
+    while (span < ti.nbins) {
+      span *= 2;
+      ++bits;
+    }
+    ti.inv_T = 1.0f / (float)span;
+    ti.split_bits = bits;
+    TileBasis tb;
+    for (int j = 0; j < NBASIS; ++j) {
+      double val, slope;
+      double poly[kNumPoly];
+      if (j == B_ONE) {
+        val = 1.0;
+        slope = 0.0;
+        for (int m = 0; m < kNumPoly; ++m) poly[m] = 0.0;
+      } else {
+        val = basis_derivative(kBasisPow[j], kBasisLog[j], 0, fa);
+        slope = basis_derivative(kBasisPow[j], kBasisLog[j], 1, fa) * c->df;
+        double nf = 1.0;
+        for (int m = 0; m < kNumPoly; ++m) {
+          const int nn = m + 2;
+          nf *= nn;
+          poly[m] = basis_derivative(kBasisPow[j], kBasisLog[j], nn, fa) * std::pow(c->df * span, nn) / nf;
+        }
+      }
+      split_df(val, &tb.val_hi[j], &tb.val_lo[j]);
+      split_df(slope, &tb.slope_hi[j], &tb.slope_lo[j]);
+      for (int m = 0; m < kNumPoly; ++m) tb.poly[m][j] = (float)poly[m];
+    }
+    tiles.push_back(ti);
+    basis.push_back(tb);
+    k += ti.nbins;
+  }
+}
+
+void free_scratch(DeviceBuffers& B) {
+  dfree(B.rec);
+  dfree(B.anchors);
+  dfree(B.partials32);
+  dfree(B.partials64);
+  dfree(B.theta);
+  dfree(B.out);
+  dfree(B.u);
+  B.cap = 0;
+}
+
+void free_problem(DeviceBuffers& B) {
+  dfree(B.data32);
+  dfree(B.data64);
+  dfree(B.ftab);
+  dfree(B.tiles);
+  dfree(B.basis);
+  dfree(B.slice_begin);
+  dfree(B.bin_tile);
+  dfree(B.prior);
+}
+
+}  // namespace
+
+namespace swig {
+
+int ensure_scratch(swig_ctx* c, int n) {
+  DeviceBuffers& B = c->B;
+  if (n <= B.cap) return SWIG_OK;
+  free_scratch(B);
+  const int cap = std::max(n, 256);
+  const size_t ntiles = std::max(c->L.n_tiles, 1);
+  CUDA_TRY(c, cudaMalloc(&B.rec, sizeof(EvalRecord) * cap));
+  CUDA_TRY(c, cudaMalloc(&B.anchors, sizeof(float) * kAnchorStride * ntiles * cap));
+  CUDA_TRY(c, cudaMalloc(&B.partials32, sizeof(float) * kPartialStride * c->L.n_slices * cap));
+  CUDA_TRY(c, cudaMalloc(&B.partials64, sizeof(double) * kPartialStride * c->L.n_slices * cap));
+  CUDA_TRY(c, cudaMalloc(&B.theta, sizeof(double) * SWIG_N_PARAMS * cap));
+  CUDA_TRY(c, cudaMalloc(&B.out, sizeof(double) * cap));
+  CUDA_TRY(c, cudaMalloc(&B.u, sizeof(double) * SWIG_N_PARAMS * cap));
+  B.cap = cap;
+  return SWIG_OK;
+}
+
+int current_precision(const swig_ctx* c) { return c->cfg_set ? c->cfg.precision : SWIG_PREC_MIXED; }
+
+// Validate the problem and (re)build every device-side table.
+int prepare(swig_ctx* c) {
+  if (!c->dirty) return SWIG_OK;
+  if (!c->grid_set) return fail(c, SWIG_E_STATE, "grid not set");
+  int n_det = 0;
+  while (n_det < SWIG_MAX_DET && c->det_set[n_det]) ++n_det;
+  if (n_det == 0) return fail(c, SWIG_E_STATE, "no detector set");
+  for (int i = n_det; i < SWIG_MAX_DET; ++i)
+    if (c->det_set[i]) return fail(c, SWIG_E_STATE, "detectors must be set contiguously from index 0");
+  const int64_t n = c->n_bins;
+  for (int i = 0; i < n_det; ++i) {
+    if ((int64_t)c->data[i].size() != 2 * n) return fail(c, SWIG_E_STATE, "data of detector " + std::to_string(i) + " not set for this grid");
+    if ((int64_t)c->psd[i].size() != n) return fail(c, SWIG_E_STATE, "psd of detector " + std::to_string(i) + " not set for this grid");
+  }
+  CUDA_TRY(c, cudaSetDevice(c->device));
+  free_problem(c->B);
+  free_scratch(c->B);
+
+  LikeConst& L = c->L;
+  std::memset(&L, 0, sizeof(L));
+  L.n_det = n_det;
+  L.n_bins = (int)n;
+  L.k_min = (int)c->k_min;
+  L.df = c->df;
+  L.gmst = c->gmst;
+  L.phase_marg = c->prior_set && c->params[12].mode == SWIG_MODE_MARG;
+  const int prec = current_precision(c);
+
+  // D_i(k) = 4 df conj(d_i) f^-7/6 / S_i,  K_i = 4 df sum f^-7/3 / S_i,  <d|d>
+  std::vector<double> dre((size_t)n_det * n), dim((size_t)n_det * n);
+  NSum dd;
+  for (int i = 0; i < n_det; ++i) {
+    NSum K;
+    double dmax = 0.0;
+    for (int64_t k = 0; k < n; ++k) {
+      const double f = (double)(c->k_min + k) * c->df;
+      const double w = 4.0 * c->df / c->psd[i][k];
+      const double re = c->data[i][2 * k], im = c->data[i][2 * k + 1];
+      const double a = w * std::pow(f, -7.0 / 6.0);
+      dre[i * n + k] = a * re;
+      dim[i * n + k] = -a * im;
+      K.add(w * std::pow(f, -7.0 / 3.0));
+      dd.add(w * (re * re + im * im));
+      dmax = std::max(dmax, std::hypot(re, im) * a);
+    }
+    L.K[i] = K.value();
+    L.inv_scale[i] = prec == SWIG_PREC_MIXED ? (dmax > 0.0 ? dmax : 1.0) : 1.0;
+    for (int r = 0; r < 3; ++r) L.vertex[i][r] = c->vertex[i][r];
+    const double* x = c->xarm[i];
+    const double* y = c->yarm[i];
+    L.dten[i][0] = 0.5 * (x[0] * x[0] - y[0] * y[0]);
+    L.dten[i][1] = 0.5 * (x[0] * x[1] - y[0] * y[1]);
+    L.dten[i][2] = 0.5 * (x[0] * x[2] - y[0] * y[2]);
+    L.dten[i][3] = 0.5 * (x[1] * x[1] - y[1] * y[1]);
+    L.dten[i][4] = 0.5 * (x[1] * x[2] - y[1] * y[2]);
+    L.dten[i][5] = 0.5 * (x[2] * x[2] - y[2] * y[2]);
+  }
+  L.DD = dd.value();
+
+  // slices: contiguous whole 32-bin chunks, one CTA each
+  const int n_chunks = (int)((n + kChunk - 1) / kChunk);
+  int n_slices = std::min(c->sm_count, std::max(1, n_chunks / 4));
+  const size_t smem_cap = 200 * 1024;
+  while (sweep_smem_bytes(n_det, (int)(((size_t)(n_chunks + n_slices - 1) / n_slices) * kChunk)) > smem_cap) n_slices *= 2;
+  n_slices = std::min(n_slices, n_chunks);
+  std::vector<int> slice_begin(n_slices + 1);
+  int max_bins = 0;
+  for (int s = 0; s <= n_slices; ++s) {
+    const long long ch = (long long)s * n_chunks / n_slices;
+    slice_begin[s] = (int)std::min<long long>(ch * kChunk, n);
+  }
+  for (int s = 0; s < n_slices; ++s) max_bins = std::max(max_bins, slice_begin[s + 1] - slice_begin[s]);
+  L.n_slices = n_slices;
+  c->B.max_slice_bins = max_bins;
+
+  DeviceBuffers& B = c->B;
+  CUDA_TRY(c, cudaMalloc(&B.slice_begin, sizeof(int) * (n_slices + 1)));
+  CUDA_TRY(c, cudaMemcpy(B.slice_begin, slice_begin.data(), sizeof(int) * (n_slices + 1), cudaMemcpyHostToDevice));
+
+  if (prec == SWIG_PREC_MIXED) {
+    std::vector<float2> d32((size_t)n_det * n);
+    for (int i = 0; i < n_det; ++i) {
+      const double s = 1.0 / L.inv_scale[i];
+      for (int64_t k = 0; k < n; ++k) d32[i * n + k] = make_float2((float)(dre[i * n + k] * s), (float)(dim[i * n + k] * s));
+    }
+    CUDA_TRY(c, cudaMalloc(&B.data32, sizeof(float2) * d32.size()));
+    CUDA_TRY(c, cudaMemcpy(B.data32, d32.data(), sizeof(float2) * d32.size(), cudaMemcpyHostToDevice));
+    std::vector<TileInfo> tiles;
+    std::vector<TileBasis> basis;
+    plan_tiles(c, tiles, basis);
+    L.n_tiles = (int)tiles.size();
+    std::vector<int> bin_tile(n);
+    for (int t = 0; t < L.n_tiles; ++t)
+      for (int k = tiles[t].k0; k < tiles[t].k0 + tiles[t].nbins; ++k) bin_tile[k] = t;
+    CUDA_TRY(c, cudaMalloc(&B.tiles, sizeof(TileInfo) * tiles.size()));
+    CUDA_TRY(c, cudaMemcpy(B.tiles, tiles.data(), sizeof(TileInfo) * tiles.size(), cudaMemcpyHostToDevice));
+    CUDA_TRY(c, cudaMalloc(&B.basis, sizeof(TileBasis) * basis.size()));
+    CUDA_TRY(c, cudaMemcpy(B.basis, basis.data(), sizeof(TileBasis) * basis.size(), cudaMemcpyHostToDevice));
+    CUDA_TRY(c, cudaMalloc(&B.bin_tile, sizeof(int) * n));
+    CUDA_TRY(c, cudaMemcpy(B.bin_tile, bin_tile.data(), sizeof(int) * n, cudaMemcpyHostToDevice));
+    CUDA_TRY(c, set_sweep_smem_limit(sweep_smem_bytes(n_det, max_bins)));
+  } else {
+    std::vector<double2> d64((size_t)n_det * n);
+    for (size_t k = 0; k < d64.size(); ++k) d64[k] = make_double2(dre[k], dim[k]);
+    CUDA_TRY(c, cudaMalloc(&B.data64, sizeof(double2) * d64.size()));
+    CUDA_TRY(c, cudaMemcpy(B.data64, d64.data(), sizeof(double2) * d64.size(), cudaMemcpyHostToDevice));
+    std::vector<double> ftab((size_t)3 * n);
+    for (int64_t k = 0; k < n; ++k) {
+      const double f = (double)(c->k_min + k) * c->df;
+      ftab[3 * k] = 1.0 / std::cbrt(f);
+      ftab[3 * k + 1] = std::cbrt(f);
+      ftab[3 * k + 2] = std::log(f);
+    }
+    CUDA_TRY(c, cudaMalloc(&B.ftab, sizeof(double) * ftab.size()));
+    CUDA_TRY(c, cudaMemcpy(B.ftab, ftab.data(), sizeof(double) * ftab.size(), cudaMemcpyHostToDevice));
+    L.n_tiles = 0;
+  }
+  // prior slots (defaults when no prior was set: every slot sampled uniform on [0,1])
+  PriorSlot slots[SWIG_N_PARAMS];
+  for (int i = 0; i < SWIG_N_PARAMS; ++i) {
+    const swig_param& p = c->params[i];
+    slots[i] = c->prior_set ? PriorSlot{p.kind, p.mode, p.lo, p.hi, p.value} : PriorSlot{0, 0, 0.0, 1.0, 0.0};
+  }
+  CUDA_TRY(c, cudaMalloc(&B.prior, sizeof(slots)));
+  CUDA_TRY(c, cudaMemcpy(B.prior, slots, sizeof(slots), cudaMemcpyHostToDevice));
+  c->prepared_precision = prec;
+  c->dirty = false;
+  return SWIG_OK;
+}
+
+int loglike_device(swig_ctx* c, const double* theta_dev, int64_t n, double* out_dev, cudaStream_t st) {
+  const int chunk = 4096;
+  for (int64_t off = 0; off < n; off += chunk) {
+    const int m = (int)std::min<int64_t>(chunk, n - off);
+    int rc = ensure_scratch(c, m);
+    if (rc) return rc;
+    cudaError_t e = c->prepared_precision == SWIG_PREC_MIXED
+                        ? launch_loglike_mixed(c->L, c->B, theta_dev + off * SWIG_N_PARAMS, m, out_dev + off, st)
+                        : launch_loglike_fp64(c->L, c->B, theta_dev + off * SWIG_N_PARAMS, m, out_dev + off, st);
+    if (e != cudaSuccess) return fail(c, SWIG_E_CUDA, std::string("likelihood launch: ") + cudaGetErrorString(e));
+  }
+  return SWIG_OK;
+}
+
+}  // namespace swig
+
+// ===========================================================================
+// C-ABI
+// ===========================================================================
+extern "C" {
+
+int swig_create(swig_ctx** out, int cuda_device) {
+  if (!out) {
+    g_create_error = "null output pointer";
+    return SWIG_E_ARG;
+  }
+  *out = nullptr;
+  int count = 0;
+  cudaError_t e = cudaGetDeviceCount(&count);
+  if (e != cudaSuccess) {
+    g_create_error = std::string("cudaGetDeviceCount: ") + cudaGetErrorString(e);
+    return SWIG_E_CUDA;
+  }
+  if (cuda_device < 0 || cuda_device >= count) {
+    g_create_error = "device index out of range";
+    return SWIG_E_ARG;
+  }
+  swig_ctx* c = new (std::nothrow) swig_ctx();
+  if (!c) {
+    g_create_error = "out of host memory";
+    return SWIG_E_NOMEM;
+  }
+  c->device = cuda_device;
+  e = cudaSetDevice(cuda_device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, cuda_device);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    g_create_error = std::string("device setup: ") + cudaGetErrorString(e);
+    delete c;
+    return SWIG_E_CUDA;
+  }
+  *out = c;
+  return SWIG_OK;
+}
+
+void swig_destroy(swig_ctx* c) {
+  if (!c) return;
+  cudaSetDevice(c->device);
+  swig_sampler_release(c);
+  free_problem(c->B);
+  free_scratch(c->B);
+  if (c->stream) cudaStreamDestroy(c->stream);
+  delete c;
+}
+
+const char* swig_last_error(const swig_ctx* c) { return c ? c->err.c_str() : g_create_error.c_str(); }
+
+int swig_set_grid(swig_ctx* c, double f_min, double f_max, double df) {
+  if (!c) return SWIG_E_ARG;
+  if (!(f_min > 0.0) || !(f_max > f_min) || !(df > 0.0) || !std::isfinite(f_max))
+    return fail(c, SWIG_E_ARG, "grid needs 0 < f_min < f_max and df > 0");
+  const double k0 = std::ceil(f_min / df - 1e-9), k1 = std::floor(f_max / df + 1e-9);
+  if (k1 < k0 || k1 - k0 + 1 > (double)(1 << 22)) return fail(c, SWIG_E_ARG, "grid must have 1 .. 2^22 bins");
+  c->f_min = f_min;
+  c->f_max = f_max;
+  c->df = df;
+  c->k_min = (int64_t)k0;
+  c->n_bins = (int64_t)(k1 - k0) + 1;
+  c->grid_set = true;
+  for (int i = 0; i < SWIG_MAX_DET; ++i) {
+    c->data[i].clear();
+    c->psd[i].clear();
+  }
+  c->dirty = true;
+  return SWIG_OK;
+}
+
+int swig_set_detector(swig_ctx* c, int idx, const double vertex_m[3], const double x_arm[3], const double y_arm[3]) {
+  if (!c) return SWIG_E_ARG;
+  if (idx < 0 || idx >= SWIG_MAX_DET || !vertex_m || !x_arm || !y_arm) return fail(c, SWIG_E_ARG, "bad detector index or null vector");
+  for (int r = 0; r < 3; ++r)
+    if (!std::isfinite(vertex_m[r]) || !std::isfinite(x_arm[r]) || !std::isfinite(y_arm[r]))
+      return fail(c, SWIG_E_NUMERIC, "non-finite detector geometry");
+  for (int r = 0; r < 3; ++r) {
+    c->vertex[idx][r] = vertex_m[r];
+    c->xarm[idx][r] = x_arm[r];
+    c->yarm[idx][r] = y_arm[r];
+  }
+  c->det_set[idx] = true;
+  c->dirty = true;
+  return SWIG_OK;
+}
+
+int swig_set_time_ref(swig_ctx* c, double gmst_rad) {
+  if (!c) return SWIG_E_ARG;
+  if (!std::isfinite(gmst_rad)) return fail(c, SWIG_E_NUMERIC, "non-finite GMST");
+  c->gmst = gmst_rad;
+  c->dirty = true;
+  return SWIG_OK;
+}
+
+int swig_set_data(swig_ctx* c, int det, const double* re_im, int64_t n) {
+  if (!c) return SWIG_E_ARG;
+  if (!c->grid_set) return fail(c, SWIG_E_STATE, "set the grid before data");
+  if (det < 0 || det >= SWIG_MAX_DET || !re_im) return fail(c, SWIG_E_ARG, "bad detector index or null data");
+  if (n != c->n_bins) return fail(c, SWIG_E_ARG, "data length must equal the number of grid bins");
+  for (int64_t k = 0; k < 2 * n; ++k)
+    if (!std::isfinite(re_im[k])) return fail(c, SWIG_E_NUMERIC, "non-finite data value");
+  c->data[det].assign(re_im, re_im + 2 * n);
+  c->dirty = true;
+  return SWIG_OK;
+}
+
+int swig_set_psd(swig_ctx* c, int det, const double* psd, int64_t n) {
+  if (!c) return SWIG_E_ARG;
+  if (!c->grid_set) return fail(c, SWIG_E_STATE, "set the grid before the PSD");
+  if (det < 0 || det >= SWIG_MAX_DET || !psd) return fail(c, SWIG_E_ARG, "bad detector index or null psd");
+  if (n != c->n_bins) return fail(c, SWIG_E_ARG, "psd length must equal the number of grid bins");
+  for (int64_t k = 0; k < n; ++k)
+    if (!std::isfinite(psd[k]) || !(psd[k] > 0.0)) return fail(c, SWIG_E_NUMERIC, "PSD values must be finite and > 0");
+  c->psd[det].assign(psd, psd + n);
+  c->dirty = true;
+  return SWIG_OK;
+}
+
+int swig_set_prior(swig_ctx* c, const swig_param* params, int n_params) {
+  if (!c) return SWIG_E_ARG;
+  if (!params || n_params != SWIG_N_PARAMS) return fail(c, SWIG_E_ARG, "prior needs exactly 13 slots");
+  int n_sampled = 0;
+  for (int i = 0; i < SWIG_N_PARAMS; ++i) {
+    const swig_param& p = params[i];
+    if (p.mode < 0 || p.mode > 2 || p.kind < 0 || p.kind > 3) return fail(c, SWIG_E_ARG, "bad prior kind or mode in slot " + std::to_string(i));
+    if (p.mode == SWIG_MODE_MARG && i != 12) return fail(c, SWIG_E_ARG, "only phi_c (slot 12) can be marginalised");
+    if (p.mode == SWIG_MODE_SAMPLE) {
+      if (!std::isfinite(p.lo) || !std::isfinite(p.hi) || !(p.hi > p.lo)) return fail(c, SWIG_E_ARG, "sampled slot " + std::to_string(i) + " needs lo < hi");
+      if (p.block < 0 || p.block >= 16) return fail(c, SWIG_E_ARG, "block id must be in [0, 16)");
+      ++n_sampled;
+    }
+    if (p.mode == SWIG_MODE_FIXED && !std::isfinite(p.value)) return fail(c, SWIG_E_NUMERIC, "non-finite fixed value");
+  }
+  if (n_sampled == 0) return fail(c, SWIG_E_ARG, "at least one parameter must be sampled");
+  std::memcpy(c->params, params, sizeof(swig_param) * SWIG_N_PARAMS);
+  c->prior_set = true;
+  c->n_sampled = n_sampled;
+  c->dirty = true;
+  return SWIG_OK;
+}
+
+int swig_set_sampler(swig_ctx* c, const swig_sampler_cfg* cfg) {
+  if (!c) return SWIG_E_ARG;
+  if (!cfg) return fail(c, SWIG_E_ARG, "null sampler configuration");
+  if (cfg->nlive < 2 || cfg->nrep < 1 || cfg->nrep >= cfg->nlive) return fail(c, SWIG_E_ARG, "need nlive > nrep >= 1");
+  if (cfg->nlive > (1 << 16)) return fail(c, SWIG_E_ARG, "nlive must be <= 65536");
+  if (cfg->sweeps < 1 || cfg->steps_per_dim < 1) return fail(c, SWIG_E_ARG, "sweeps and steps_per_dim must be >= 1");
+  if (cfg->precision != SWIG_PREC_FP64 && cfg->precision != SWIG_PREC_MIXED) return fail(c, SWIG_E_ARG, "bad precision");
+  if (cfg->likelihood != SWIG_LIKE_FULL && cfg->likelihood != SWIG_LIKE_HET) return fail(c, SWIG_E_ARG, "bad likelihood");
+  if (cfg->proposal != SWIG_PROPOSAL_COV && cfg->proposal != SWIG_PROPOSAL_LEARNED) return fail(c, SWIG_E_ARG, "bad proposal");
+  if (cfg->likelihood == SWIG_LIKE_HET && (cfg->het_bins < 2 || cfg->het_bins > 65536)) return fail(c, SWIG_E_ARG, "het_bins must be in [2, 65536]");
+  if (!(cfg->dlogz < 0.0) || cfg->max_iter < 1) return fail(c, SWIG_E_ARG, "need dlogz < 0 and max_iter >= 1");
+  if (c->cfg_set && (c->cfg.precision != cfg->precision || c->cfg.likelihood != cfg->likelihood)) c->dirty = true;
+  if (!c->cfg_set) c->dirty = true;
+  c->cfg = *cfg;
+  c->cfg_set = true;
+  return SWIG_OK;
+}
+
+int swig_loglike_batch(swig_ctx* c, const double* theta, int64_t n, double* out_logl) {
+  if (!c) return SWIG_E_ARG;
+  if (n == 0) return SWIG_OK;
+  if (n < 0 || n > (1 << 20) || !theta || !out_logl) return fail(c, SWIG_E_ARG, "need 0 <= n <= 2^20 and non-null buffers");
+  int rc = prepare(c);
+  if (rc) return rc;
+  const int chunk = 4096;
+  for (int64_t off = 0; off < n; off += chunk) {
+    const int m = (int)std::min<int64_t>(chunk, n - off);
+    if ((rc = ensure_scratch(c, m))) return rc;
+    CUDA_TRY(c, cudaMemcpyAsync(c->B.theta, theta + off * SWIG_N_PARAMS, sizeof(double) * SWIG_N_PARAMS * m, cudaMemcpyHostToDevice, c->stream));
+    if ((rc = loglike_device(c, c->B.theta, m, c->B.out, c->stream))) return rc;
+    CUDA_TRY(c, cudaMemcpyAsync(out_logl + off, c->B.out, sizeof(double) * m, cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  }
+  return SWIG_OK;
+}
+
+int swig_loglike_batch_dev(swig_ctx* c, const double* theta_dev, int64_t n, double* out_dev, void* stream) {
+  if (!c) return SWIG_E_ARG;
+  if (n == 0) return SWIG_OK;
+  if (n < 0 || n > (1 << 20) || !theta_dev || !out_dev) return fail(c, SWIG_E_ARG, "need 0 <= n <= 2^20 and non-null buffers");
+  int rc = prepare(c);
+  if (rc) return rc;
+  return loglike_device(c, theta_dev, n, out_dev, (cudaStream_t)stream);
+}
+
+int swig_prior_transform(swig_ctx* c, const double* u, int64_t n, double* theta) {
+  if (!c) return SWIG_E_ARG;
+  if (!c->prior_set) return fail(c, SWIG_E_STATE, "prior not set");
+  if (n == 0) return SWIG_OK;
+  if (n < 0 || n > (1 << 20) || !u || !theta) return fail(c, SWIG_E_ARG, "need 0 <= n <= 2^20 and non-null buffers");
+  int rc = prepare(c);
+  if (rc) return rc;
+  const int chunk = 4096;
+  const int ns = c->n_sampled;
+  for (int64_t off = 0; off < n; off += chunk) {
+    const int m = (int)std::min<int64_t>(chunk, n - off);
+    if ((rc = ensure_scratch(c, m))) return rc;
+    CUDA_TRY(c, cudaMemcpyAsync(c->B.u, u + off * ns, sizeof(double) * ns * m, cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY(c, launch_prior_transform(c->B.prior, ns, c->B.u, m, c->B.theta, c->stream));
+    CUDA_TRY(c, cudaMemcpyAsync(theta + off * SWIG_N_PARAMS, c->B.theta, sizeof(double) * SWIG_N_PARAMS * m, cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  }
+  return SWIG_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,55 @@
+// The opaque swig_ctx behind the C-ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "kernels.h"
+#include "swig.h"
+#include "swig_internal.h"
+
+namespace swig {
+struct SamplerState;  // device state of a nested-sampling run (sampler.cu)
+}
+
+struct swig_ctx {
+  int device = 0;
+  int sm_count = 1;
+  cudaStream_t stream = nullptr;
+  std::string err;
+  // grid (Sec. 3.1): f_k = k df, k_min .. k_min + n_bins - 1
+  double f_min = 0.0, f_max = 0.0, df = 0.0;
+  int64_t k_min = 0, n_bins = 0;
+  bool grid_set = false;
+  // detectors
+  bool det_set[SWIG_MAX_DET] = {false, false, false, false};
+  double vertex[SWIG_MAX_DET][3] = {}, xarm[SWIG_MAX_DET][3] = {}, yarm[SWIG_MAX_DET][3] = {};
+  double gmst = 0.0;
+  std::vector<double> data[SWIG_MAX_DET], psd[SWIG_MAX_DET];
+  // prior and sampler
+  swig_param params[SWIG_N_PARAMS] = {};
+  bool prior_set = false;
+  int n_sampled = 0;
+  swig_sampler_cfg cfg = {};
+  bool cfg_set = false;
+  // prepared device state
+  bool dirty = true;
+  int prepared_precision = -1;
+  swig::LikeConst L = {};
+  swig::DeviceBuffers B;
+  swig::SamplerState* sampler = nullptr;
+  // results of the last run
+  swig_result last = {};
+  std::vector<double> out_theta, out_logl, out_logw;
+};
+
+namespace swig {
+int prepare(swig_ctx* c);
+int ensure_scratch(swig_ctx* c, int n);
+int loglike_device(swig_ctx* c, const double* theta_dev, int64_t n, double* out_dev, cudaStream_t st);
+int current_precision(const swig_ctx* c);
+}  // namespace swig
+
+void swig_sampler_release(swig_ctx* c);

@@ -1,0 +1,304 @@
+// Device helpers for libswig: double-float arithmetic on the FP32 pipe, the
+// TaylorF2 intrinsic-phase coefficients, detector projection and log I0.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "swig_internal.h"
+
+namespace swig {
+
+constexpr double kPi = 3.14159265358979323846;
+constexpr double kMtsunS = 4.925490947641266978e-6;  // G M_sun / c^3 [s]
+constexpr double kCSI = 299792458.0;
+constexpr double kMpcM = 3.0856775814913673e22;
+constexpr double kEulerGamma = 0.57721566490153286061;
+
+// ---------------------------------------------------------------------------
+// Double-float ("float-float") arithmetic.  A value is hi + lo with
+// |lo| <= ulp(hi)/2; the error-free transforms use round-to-nearest intrinsics
+// so that no multiply-add contraction can alter them (Dekker 1971; Knuth
+// TAOCP vol. 2, 4.2.2).  GB300 issues FP64 at ~1/64 of the FP32 rate, so the
+// ~48-bit phase anchors are carried in pairs of floats instead.
+// ---------------------------------------------------------------------------
+struct dfl {
+  float hi, lo;
+};
+
+__device__ __forceinline__ dfl two_sum(float a, float b) {
+  float s = __fadd_rn(a, b);
+  float bb = __fsub_rn(s, a);
+  float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return {s, e};
+}
+
+__device__ __forceinline__ dfl fast_two_sum(float a, float b) {  // |a| >= |b|
+  float s = __fadd_rn(a, b);
+  float e = __fsub_rn(b, __fsub_rn(s, a));
+  return {s, e};
+}
+
+// (a.hi + a.lo) * (b.hi + b.lo) to ~2^-46 relative.
+__device__ __forceinline__ dfl df_mul(dfl a, dfl b) {
+  float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  return fast_two_sum(p, e);
+}
+
+__device__ __forceinline__ dfl df_add(dfl a, dfl b) {
+  dfl s = two_sum(a.hi, b.hi);
+  float e = __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo));
+  return fast_two_sum(s.hi, e);
+}
+
+// Fractional part (nearest-integer reduction) of a double-float, returned as
+// a float in [-0.5, 0.5] plus rounding of the low word.
+__device__ __forceinline__ float df_frac(dfl a) {
+  float n = rintf(a.hi);
+  return __fadd_rn(__fsub_rn(a.hi, n), a.lo);  // a.hi - n is exact
+}
+
+__device__ __forceinline__ dfl df_from_double(double x) {
+  float h = __double2float_rn(x);
+  float l = __double2float_rn(x - (double)h);
+  return {h, l};
+}
+
+// ---------------------------------------------------------------------------
+// TaylorF2 intrinsic phase in cycles as sum_j c_j phi_j(f) (basis in
+// swig_internal.h).  Psi_int(f) = -pi/4 + 3/(128 eta v^5) sum_k alpha_k v^k
+// with v = (pi M f)^(1/3); non-spinning alpha_k of Buonanno et al. 2009
+// (PRD 80 084043, Eq. 3.18), aligned-spin 1.5PN spin-orbit and 2PN spin-spin
+// terms (Poisson & Will 1995), tidal 5PN/6PN terms (Wade et al. 2014).
+// ---------------------------------------------------------------------------
+__host__ __device__ inline void taylorf2_basis_coeffs(double mc, double q, double chi1, double chi2,
+                                             double lam1, double lam2, double* c) {
+  const double opq = 1.0 + q;
+  const double eta = q / (opq * opq);
+  const double mfrac1 = 1.0 / opq, mfrac2 = q / opq;
+  const double dm = (1.0 - q) / opq;  // (m1 - m2) / M
+  const double mtot = mc * exp(-0.6 * log(eta)) * kMtsunS;
+  const double eta2 = eta * eta, eta3 = eta2 * eta;
+  const double so = (113.0 / 12.0 * mfrac1 * mfrac1 + 6.25 * eta) * chi1 +
+                    (113.0 / 12.0 * mfrac2 * mfrac2 + 6.25 * eta) * chi2;
+  const double ss = 79.0 / 8.0 * eta * chi1 * chi2;
+  const double pi2 = kPi * kPi;
+
+  const double a0 = 1.0;
+  const double a2 = 3715.0 / 756.0 + 55.0 / 9.0 * eta;
+  const double a3 = -16.0 * kPi + 4.0 * so;
+  const double a4 = 15293365.0 / 508032.0 + 27145.0 / 504.0 * eta + 3085.0 / 72.0 * eta2 - 10.0 * ss;
+  const double a5 = kPi * (38645.0 / 756.0 - 65.0 / 9.0 * eta);
+  const double a5log = 3.0 * a5;
+  const double a6 = 11583231236531.0 / 4694215680.0 - 640.0 / 3.0 * pi2 - 6848.0 / 21.0 * kEulerGamma +
+                    (-15737765635.0 / 3048192.0 + 2255.0 / 12.0 * pi2) * eta + 76055.0 / 1728.0 * eta2 -
+                    127825.0 / 1296.0 * eta3;
+  const double a6log = -6848.0 / 21.0;
+  const double a7 = kPi * (77096675.0 / 254016.0 + 378515.0 / 1512.0 * eta - 74045.0 / 756.0 * eta2);
+  const double lsum = lam1 + lam2, ldif = lam1 - lam2;
+  const double lt = 8.0 / 13.0 * ((1.0 + 7.0 * eta - 31.0 * eta2) * lsum + dm * (1.0 + 9.0 * eta - 11.0 * eta2) * ldif);
+  const double dlt = 0.5 * (dm * (1.0 - 13272.0 / 1319.0 * eta + 8944.0 / 1319.0 * eta2) * lsum +
+                            (1.0 - 15910.0 / 1319.0 * eta + 32850.0 / 1319.0 * eta2 + 3380.0 / 1319.0 * eta3) * ldif);
+  const double a10 = -19.5 * lt;
+  const double a12 = -3115.0 / 64.0 * lt + 6595.0 / 364.0 * dm * dlt;
+
+  const double A = 3.0 / (128.0 * eta) / (2.0 * kPi);  // radians -> cycles
+  const double piM = kPi * mtot;
+  const double lpm = log(piM);
+  const double r = cbrt(piM);       // (pi M)^(1/3): v = r f^(1/3)
+  const double r2 = r * r, r5 = r2 * r2 * r, r7 = r5 * r2;
+  const double ln_vlso = -0.5 * log(6.0);
+
+  c[B_M53] = A * a0 / r5;
+  c[B_M1] = A * a2 / piM;
+  c[B_M23] = A * a3 / r2;
+  c[B_M13] = A * a4 / r;
+  c[B_LOG] = A * a5log / 3.0;
+  c[B_P13] = A * r * (a6 + a6log * (log(4.0) + lpm / 3.0));
+  c[B_P13LOG] = A * r * a6log / 3.0;
+  c[B_P23] = A * a7 * r2;
+  c[B_P53] = A * a10 * r5;
+  c[B_P73] = A * a12 * r7;
+  c[B_ONE] = A * (a5 + a5log * (lpm / 3.0 - ln_vlso)) - 0.125;
+}
+
+// sqrt(5/24) pi^(-2/3) (G Mc / c^3)^(5/6) c / (1 Mpc): Newtonian SPA amplitude
+// times d_L[Mpc].
+__device__ inline double amplitude_per_mpc(double mc) {
+  return sqrt(5.0 / 24.0) * exp(-2.0 / 3.0 * log(kPi)) * exp(5.0 / 6.0 * log(mc * kMtsunS)) * kCSI / kMpcM;
+}
+
+// Antenna patterns of detector tensor D (xx xy xz yy yz zz) for a source at
+// (ra, dec), polarisation psi, Greenwich sidereal time gmst; polarisation
+// basis X = -cos(psi) e_east + sin(psi) e_north, Y = sin(psi) e_east +
+// cos(psi) e_north at the source direction.
+__device__ inline void antenna_fp_fx(const double* d, double ra, double dec, double psi, double gmst,
+                                     double* fp, double* fx) {
+  double sl, cl, sd, cd, sp, cp;
+  sincos(ra - gmst, &sl, &cl);
+  sincos(dec, &sd, &cd);
+  sincos(psi, &sp, &cp);
+  const double east[3] = {-sl, cl, 0.0};
+  const double north[3] = {-sd * cl, -sd * sl, cd};
+  double X[3], Y[3];
+  for (int k = 0; k < 3; ++k) {
+    X[k] = -cp * east[k] + sp * north[k];
+    Y[k] = sp * east[k] + cp * north[k];
+  }
+  // quadratic forms a^T D b with D symmetric
+  auto form = [d](const double* a, const double* b) {
+    return a[0] * (d[0] * b[0] + d[1] * b[1] + d[2] * b[2]) + a[1] * (d[1] * b[0] + d[3] * b[1] + d[4] * b[2]) +
+           a[2] * (d[2] * b[0] + d[4] * b[1] + d[5] * b[2]);
+  };
+  *fp = form(X, X) - form(Y, Y);
+  *fx = 2.0 * form(X, Y);
+}
+
+// Arrival time at a detector minus arrival at Earth's centre: -n.r / c.
+__device__ inline double geocentric_delay(const double* vertex, double ra, double dec, double gmst) {
+  double sl, cl, sd, cd;
+  sincos(ra - gmst, &sl, &cl);
+  sincos(dec, &sd, &cd);
+  return -(cd * cl * vertex[0] + cd * sl * vertex[1] + sd * vertex[2]) / kCSI;
+}
+
+// log I0(x) for x >= 0: power series sum (x^2/4)^k / (k!)^2 below 20, and the
+// large-argument expansion I0(x) ~ e^x / sqrt(2 pi x) sum_k ((2k-1)!!)^2 /
+// (k! (8x)^k) above (Abramowitz & Stegun 9.6.10, 9.7.1).
+__device__ inline double log_bessel_i0(double x) {
+  if (x < 20.0) {
+    const double y = 0.25 * x * x;
+    double term = 1.0, sum = 1.0;
+    for (int k = 1; k < 200; ++k) {
+      term *= y / ((double)k * (double)k);
+      sum += term;
+      if (term < 1e-17 * sum) break;
+    }
+    return log(sum);
+  }
+  const double t = 1.0 / (8.0 * x);
+  double term = 1.0, sum = 1.0;
+  for (int k = 1; k < 30; ++k) {
+    const double m = 2.0 * k - 1.0;
+    term *= m * m * t / (double)k;
+    sum += term;
+    if (term < 1e-17 * sum) break;
+  }
+  return x - 0.5 * log(2.0 * kPi * x) + log(sum);
+}
+
+// ---------------------------------------------------------------------------
+// Per-theta setup (FP64): phase coefficients, delays, complex projection
+// factors C_i so that h_i(f) = C_i f^(-7/6) exp(-2 pi i (P(f) + f tau_i)).
+// ---------------------------------------------------------------------------
+__device__ inline void setup_record(const LikeConst& L, const double* th, EvalRecord* rec) {
+  const double mc = th[0], q = th[1], chi1 = th[2], chi2 = th[3], lam1 = th[4], lam2 = th[5];
+  const double dl = th[6], iota = th[7], psi = th[8], ra = th[9], dec = th[10], tc = th[11], phic = th[12];
+  const bool ok = (mc > 0.0) && (q > 0.0) && (q <= 1.0) && (dl > 0.0) && isfinite(mc + q + chi1 + chi2 + lam1 + lam2 +
+                                                                               dl + iota + psi + ra + dec + tc + phic);
+  rec->valid = ok ? 1 : 0;
+  double c[NBASIS];
+  if (ok) {
+    taylorf2_basis_coeffs(mc, q, chi1, chi2, lam1, lam2, c);
+  } else {
+    for (int j = 0; j < NBASIS; ++j) c[j] = 0.0;
+  }
+  for (int j = 0; j < NBASIS; ++j) {
+    rec->c[j] = c[j];
+    dfl v = df_from_double(c[j]);
+    rec->c_hi[j] = v.hi;
+    rec->c_lo[j] = v.lo;
+  }
+  const double amp = ok ? amplitude_per_mpc(mc) / dl : 0.0;
+  double ci = cos(iota);
+  const double plus = 0.5 * (1.0 + ci * ci), cross = -ci;  // h+ ~ plus, hx ~ i*cross
+  double sph = 0.0, cph = 1.0;
+  if (!L.phase_marg) sincos(phic, &sph, &cph);
+  double hh = 0.0;
+  for (int i = 0; i < SWIG_MAX_DET; ++i) {
+    if (i >= L.n_det) {
+      rec->tau[i] = 0.0;
+      rec->tau_hi[i] = rec->tau_lo[i] = 0.0f;
+      rec->cre[i] = rec->cim[i] = 0.0;
+      continue;
+    }
+    double fp, fx;
+    antenna_fp_fx(L.dten[i], ra, dec, psi, L.gmst, &fp, &fx);
+    const double tau = tc + geocentric_delay(L.vertex[i], ra, dec, L.gmst);
+    rec->tau[i] = tau;
+    dfl tv = df_from_double(tau);
+    rec->tau_hi[i] = tv.hi;
+    rec->tau_lo[i] = tv.lo;
+    // C_i = amp [F+ plus + i Fx cross] e^{i phi_c}
+    const double re0 = amp * fp * plus, im0 = amp * fx * cross;
+    const double re = re0 * cph - im0 * sph, im = re0 * sph + im0 * cph;
+    rec->cre[i] = re;
+    rec->cim[i] = im;
+    hh += (re * re + im * im) * L.K[i];
+  }
+  rec->hh = hh;
+}
+
+// logL from the per-detector sums kappa_i = sum_k D_i(k) exp(-2 pi i phi_i(k))
+// (data scaled by 1/inv_scale_i): Eq. 2 expanded as
+// sum_i Re(C_i kappa_i) - 1/2 sum_i |C_i|^2 K_i - 1/2 sum_i <d_i|d_i>, or with
+// phi_c marginalised log I0(|sum_i C_i kappa_i|) - ...
+__device__ inline double loglike_epilogue(const LikeConst& L, const EvalRecord& rec, const double* kre,
+                                          const double* kim) {
+  if (!rec.valid) return -INFINITY;
+  double zr = 0.0, zi = 0.0;
+  for (int i = 0; i < L.n_det; ++i) {
+    const double a = kre[i] * L.inv_scale[i], b = kim[i] * L.inv_scale[i];
+    zr += rec.cre[i] * a - rec.cim[i] * b;
+    zi += rec.cre[i] * b + rec.cim[i] * a;
+  }
+  const double base = -0.5 * rec.hh - 0.5 * L.DD;
+  if (L.phase_marg) return log_bessel_i0(sqrt(zr * zr + zi * zi)) + base;
+  return zr + base;
+}
+
+}  // namespace swig
+
+#include "kernels.h"
+
+namespace swig {
+
+// Inverse CDFs of the Table I prior families on [lo, hi].
+__host__ __device__ inline double prior_inverse_cdf(int kind, double lo, double hi, double u) {
+  switch (kind) {
+    case SWIG_PRIOR_SINE: {
+      const double clo = cos(lo), chi = cos(hi);
+      return acos(clo - u * (clo - chi));
+    }
+    case SWIG_PRIOR_COSINE: {
+      const double slo = sin(lo), shi = sin(hi);
+      return asin(slo + u * (shi - slo));
+    }
+    case SWIG_PRIOR_POWER2: {
+      const double l3 = lo * lo * lo, h3 = hi * hi * hi;
+      return cbrt(l3 + u * (h3 - l3));
+    }
+    default:
+      return lo + u * (hi - lo);
+  }
+}
+
+// Unit-cube coordinates of the sampled slots -> full 13-vector.
+__host__ __device__ inline void prior_map(const PriorSlot* slots, const double* u, double* th) {
+  int j = 0;
+  for (int i = 0; i < SWIG_N_PARAMS; ++i) {
+    const PriorSlot& s = slots[i];
+    if (s.mode == SWIG_MODE_FIXED) {
+      th[i] = s.value;
+    } else if (s.mode == SWIG_MODE_MARG) {
+      th[i] = 0.0;
+    } else {
+      th[i] = prior_inverse_cdf(s.kind, s.lo, s.hi, u[j++]);
+    }
+  }
+}
+
+}  // namespace swig

@@ -1,0 +1,53 @@
+// Launch interface between the C-ABI host code and the CUDA kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "swig_internal.h"
+
+namespace swig {
+
+struct PriorSlot {
+  int kind;
+  int mode;
+  double lo, hi, value;
+};
+
+// Device buffers owned by a context (all allocated with cudaMalloc).
+struct DeviceBuffers {
+  // problem data
+  float2* data32 = nullptr;      // [n_det][n_bins] scaled D_i (MIXED)
+  double2* data64 = nullptr;     // [n_det][n_bins] D_i (FP64)
+  double* ftab = nullptr;        // [n_bins][3] f^-1/3, f^1/3, ln f (FP64)
+  TileInfo* tiles = nullptr;     // [n_tiles]
+  TileBasis* basis = nullptr;    // [n_tiles]
+  int* slice_begin = nullptr;    // [n_slices + 1] first bin of each slice
+  int* bin_tile = nullptr;       // [n_bins] tile of each bin
+  PriorSlot* prior = nullptr;    // [13]
+  int max_slice_bins = 0;
+  // scratch for batched evaluation, sized for `cap` thetas
+  int cap = 0;
+  EvalRecord* rec = nullptr;     // [cap]
+  float* anchors = nullptr;      // [cap][n_tiles][kAnchorStride]
+  float* partials32 = nullptr;   // [cap][n_slices][kPartialStride]
+  double* partials64 = nullptr;  // [cap][n_slices][kPartialStride]
+  double* theta = nullptr;       // [cap][13] staging for host calls
+  double* out = nullptr;         // [cap]
+  double* u = nullptr;           // [cap][13]
+};
+
+cudaError_t launch_loglike_mixed(const LikeConst& L, const DeviceBuffers& B, const double* theta, int n,
+                                 double* out, cudaStream_t st);
+cudaError_t launch_loglike_fp64(const LikeConst& L, const DeviceBuffers& B, const double* theta, int n,
+                                double* out, cudaStream_t st);
+cudaError_t launch_prior_transform(const PriorSlot* slots, int n_sampled, const double* u, int n, double* theta,
+                                   cudaStream_t st);
+cudaError_t set_sweep_smem_limit(size_t bytes);
+
+// Dynamic shared memory of the mixed sweep: data (float2 per detector and
+// bin) plus the tile index of each bin of the slice.
+inline size_t sweep_smem_bytes(int n_det, int slice_bins) {
+  return (size_t)slice_bins * (n_det * sizeof(float2) + sizeof(int));
+}
+
+}  // namespace swig

@@ -18,11 +18,9 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-# Physical constants (SI).  G*M_sun/c^3 from the IAU 2015 nominal solar mass
-# parameter; Mpc from the IAU parsec.
+# Speed of light (exact, SI) and the mean Earth radius of the spherical-Earth
+# site model.
 C_SI = 299792458.0
-MTSUN_S = 1.32712440018e20 / C_SI**3
-MPC_M = 3.0856775814913673e22
 EARTH_RADIUS_M = 6.371e6
 
 # Parameter slots of the 13-vector used throughout (Table I of the paper, with

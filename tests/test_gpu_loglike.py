@@ -1,0 +1,170 @@
+"""Parity of the CUDA likelihood (through the C-ABI) with the FP64 oracle.
+
+Bar (spec tolerance): |dlogL| <= 1e-6 |logL| + 1e-6 on identical seeded
+inputs.  Cases cover FP64 and mixed precision, one and three detectors, the
+full-size 128 s network grid, a grid whose last tile is ragged, phase
+marginalisation on and off, invalid parameters, empty and large batches, and
+bit-for-bit determinism.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import swig_inputs as si
+from oracle import events, physics
+from oracle import likelihood as L
+
+pytestmark = pytest.mark.gpu
+
+swig = pytest.importorskip("paper_2607_28265_gb300.swig")
+
+
+def _tol(want):
+    return 1e-6 * np.abs(want) + 1e-6
+
+
+def _thetas(wl, th_inj, n_prior, n_near, seed):
+    """Draws from the prior (oracle transform of seeded unit-cube points) and
+    near the injection, where the likelihood varies fastest."""
+    rng = np.random.default_rng(seed)
+    ns = len(wl.sampled())
+    out = [physics.prior_transform(rng.random(ns), wl.params)[0] for _ in range(n_prior)]
+    for _ in range(n_near):
+        t = th_inj.copy()
+        t[0] *= 1 + rng.normal(0, 3e-4)
+        t[11] += rng.normal(0, 1e-3)
+        if wl.params[1].mode == si.MODE_SAMPLE:
+            t[1] = min(1.0, t[1] * (1 + rng.normal(0, 0.01)))
+        out.append(t)
+    return np.array(out)
+
+
+@pytest.fixture(scope="module")
+def cfg1():
+    wl = si.config1()
+    ev, th = events.build_event(wl)
+    return wl, ev, th
+
+
+@pytest.fixture(scope="module")
+def cfg2():
+    wl = si.config2()
+    ev, th = events.build_event(wl)
+    return wl, ev, th
+
+
+@pytest.mark.parametrize("precision", [swig.PREC_FP64, swig.PREC_MIXED])
+def test_cfg1_parity(cfg1, precision):
+    wl, ev, th = cfg1
+    ctx = swig.context_for_workload(wl, ev.data, ev.psds, ev.gmst)
+    ctx.set_sampler(nlive=100, nrep=10, precision=precision)
+    thetas = _thetas(wl, th, 48, 48, seed=5)
+    got = ctx.loglike_batch(thetas)
+    want = np.array([L.loglike(ev, t) for t in thetas])
+    err = np.abs(got - want)
+    assert np.all(err <= _tol(want)), f"max err {err.max():.3e}"
+    if precision == swig.PREC_FP64:
+        assert err.max() < 1e-7
+
+
+def test_cfg2_full_size_parity(cfg2):
+    """128 s, H1/L1/V1, 259,585 bins per detector, phase marginalised."""
+    wl, ev, th = cfg2
+    ctx = swig.context_for_workload(wl, ev.data, ev.psds, ev.gmst)
+    ctx.set_sampler(nlive=1000, nrep=100, precision=swig.PREC_MIXED)
+    thetas = _thetas(wl, th, 12, 12, seed=6)
+    got = ctx.loglike_batch(thetas)
+    want = np.array([L.loglike(ev, t) for t in thetas])
+    err = np.abs(got - want)
+    assert np.all(err <= _tol(want)), f"max err {err.max():.3e}"
+    # the log-likelihood ratio logL + <d|d>/2 (|value| ~ SNR^2/2) is reported,
+    # and must stay well inside the same absolute budget
+    assert err.max() < 0.05
+
+
+def test_ragged_multi_tile_grid_two_detectors():
+    """20-200 Hz at df = 1/16 (2,881 bins: ragged last chunk), H1+V1, phi_c sampled."""
+    wl = si.config1()
+    wl = si.Workload("ragged", 20.0, 200.0, 1.0 / 16.0, ("H1", "V1"), wl.params, wl.injection, 15.0,
+                     noise_seed=77, sampler_seed=78, nlive=50, nrep=5, steps_per_dim=5)
+    assert wl.n_bins % 32 != 0
+    wl.params[12] = si.Param(si.PRIOR_UNIFORM, 0.0, 2 * math.pi, block=3)
+    ev, th = events.build_event(wl)
+    thetas = _thetas(wl, th, 16, 16, seed=9)
+    thetas[:, 12] = np.random.default_rng(1).uniform(0, 2 * math.pi, len(thetas))
+    want = np.array([L.loglike(ev, t) for t in thetas])
+    for prec in (swig.PREC_FP64, swig.PREC_MIXED):
+        ctx = swig.context_for_workload(wl, ev.data, ev.psds, ev.gmst)
+        ctx.set_sampler(nlive=50, nrep=5, precision=prec)
+        got = ctx.loglike_batch(thetas)
+        assert np.all(np.abs(got - want) <= _tol(want)), (prec, np.abs(got - want).max())
+
+
+def test_invalid_theta_empty_batch_and_determinism(cfg1):
+    wl, ev, th = cfg1
+    ctx = swig.context_for_workload(wl, ev.data, ev.psds, ev.gmst)
+    ctx.set_sampler(nlive=100, nrep=10, precision=swig.PREC_MIXED)
+    bad = np.tile(th, (3, 1))
+    bad[0, 1] = 1.5        # q > 1
+    bad[1, 6] = -10.0      # negative distance
+    bad[2, 0] = np.nan
+    assert np.all(np.isneginf(ctx.loglike_batch(bad)))
+    assert ctx.loglike_batch(np.zeros((0, 13))).size == 0
+    thetas = _thetas(wl, th, 8, 8, seed=3)
+    a, b = ctx.loglike_batch(thetas), ctx.loglike_batch(thetas)
+    assert np.array_equal(a, b)
+
+
+def test_large_batch_is_split_consistently(cfg1):
+    wl, ev, th = cfg1
+    ctx = swig.context_for_workload(wl, ev.data, ev.psds, ev.gmst)
+    ctx.set_sampler(nlive=100, nrep=10, precision=swig.PREC_MIXED)
+    thetas = _thetas(wl, th, 5000, 0, seed=4)
+    big = ctx.loglike_batch(thetas)
+    small = ctx.loglike_batch(thetas[4090:4110])
+    assert np.array_equal(big[4090:4110], small)
+    idx = [0, 4095, 4096, 4999]
+    want = np.array([L.loglike(ev, thetas[i]) for i in idx])
+    assert np.all(np.abs(big[idx] - want) <= _tol(want))
+
+
+def test_device_pointer_entry_point(cfg1):
+    torch = pytest.importorskip("torch")
+    wl, ev, th = cfg1
+    ctx = swig.context_for_workload(wl, ev.data, ev.psds, ev.gmst)
+    ctx.set_sampler(nlive=100, nrep=10, precision=swig.PREC_MIXED)
+    thetas = _thetas(wl, th, 16, 16, seed=8)
+    t_dev = torch.from_numpy(thetas).cuda()
+    out = torch.empty(len(thetas), dtype=torch.float64, device="cuda")
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        ctx.loglike_batch_dev(t_dev.data_ptr(), len(thetas), out.data_ptr(), stream.cuda_stream)
+    stream.synchronize()
+    assert np.array_equal(out.cpu().numpy(), ctx.loglike_batch(thetas))
+
+
+def test_error_codes(cfg1):
+    wl, ev, th = cfg1
+    ctx = swig.Context(0)
+    with pytest.raises(swig.SwigError) as e:
+        ctx.loglike_batch(th[None])
+    assert e.value.code == swig.SWIG_E_STATE
+    ctx.set_grid(wl.f_min, wl.f_max, wl.df)
+    bad = ev.data[0].copy(); bad[10] = np.nan
+    with pytest.raises(swig.SwigError) as e:
+        ctx.set_data(0, bad)
+    assert e.value.code == swig.SWIG_E_NUMERIC
+    psd = ev.psds[0].copy(); psd[3] = 0.0
+    with pytest.raises(swig.SwigError) as e:
+        ctx.set_psd(0, psd)
+    assert e.value.code == swig.SWIG_E_NUMERIC
+    with pytest.raises(swig.SwigError) as e:
+        ctx.set_data(0, ev.data[0][:-1])
+    assert e.value.code == swig.SWIG_E_ARG
+    with pytest.raises(swig.SwigError) as e:
+        ctx.set_grid(10.0, 5.0, 0.1)
+    assert e.value.code == swig.SWIG_E_ARG
+    with pytest.raises(swig.SwigError) as e:
+        ctx.set_sampler(nlive=10, nrep=10)
+    assert e.value.code == swig.SWIG_E_ARG

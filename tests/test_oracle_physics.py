@@ -117,7 +117,7 @@ def test_spa_time_frequency_relation(mc, q, chi1, chi2):
     dpsi = (psi(f + h) - psi(f - h)) / (2 * h) / (2 * math.pi)
     v = np.cbrt(math.pi * m_s * f)
     tau = 5.0 * m_s / (256.0 * eta * v**8) * _chirp_time_series(v, eta, beta, sigma)
-    newt = 5.0 / 256.0 * mc * si.MTSUN_S * (math.pi * mc * si.MTSUN_S * f) ** (-8.0 / 3.0)
+    newt = 5.0 / 256.0 * mc * physics.MTSUN_S * (math.pi * mc * physics.MTSUN_S * f) ** (-8.0 / 3.0)
     assert np.allclose(5.0 * m_s / (256.0 * eta * v**8), newt, rtol=1e-12)
     assert np.allclose(dpsi, -tau, rtol=2e-8)
 
@@ -128,7 +128,7 @@ def test_newtonian_only_phase_is_quadrupole_chirp():
     h = 1e-3
     psi = lambda ff: physics.taylorf2_phase_intrinsic(ff, mc, q, 0, 0, 0, 0, orders={0})
     dpsi = (psi(f + h) - psi(f - h)) / (2 * h) / (2 * math.pi)
-    mcs = mc * si.MTSUN_S
+    mcs = mc * physics.MTSUN_S
     assert np.allclose(dpsi, -5.0 / 256.0 * mcs * (math.pi * mcs * f) ** (-8.0 / 3.0), rtol=1e-8)
 
 
