@@ -152,8 +152,21 @@ int swig_loglike_batch_dev(swig_ctx* ctx, const double* theta_dev, int64_t n,
 int swig_prior_transform(swig_ctx* ctx, const double* u, int64_t n, double* theta);
 
 /* ---- nested sampling (Sec. 2.2, 2.3, 3.2) ------------------------------ */
-/* Run nested sampling to termination on the device. */
+/* Run nested sampling to termination (Sec. 3.2: log Z_live - log Z_dead <
+ * dlogz) or to about max_iter iterations, on the device.  Requires the prior
+ * and the sampler configuration; nlive <= 8192, nrep <= 2048 and at most 32
+ * chains per CTA of the persistent kernel.  SWIG_E_TIMEOUT if a bounded
+ * device wait expired (the context stays usable). */
 int swig_run(swig_ctx* ctx, swig_result* out);
+/* Cap, in polling iterations of ~100 ns, on every spin-wait of the persistent
+ * kernel (grid barriers).  Default 1e7.  A wait that reaches the cap makes
+ * swig_run return SWIG_E_TIMEOUT instead of hanging. */
+int swig_set_wait_limit(swig_ctx* ctx, long long spins);
+/* Phase timers of the last swig_run, measured on the device (first CTA of the
+ * persistent kernel): out[0] rounds, out[1] iteration-boundary seconds,
+ * out[2] chain-control seconds, out[3] wait after control, out[4] sweep
+ * seconds, out[5] wait after sweep.  Writes min(n, 6) values. */
+int swig_get_profile(swig_ctx* ctx, double* out, int n);
 /* Dead points of the last run (theta n x 13, logL, log-weight normalised so
  * that logsumexp(logw) = log Z).  With cap == 0 only *n_out is set. */
 int swig_get_samples(swig_ctx* ctx, double* theta, double* logl, double* logw,

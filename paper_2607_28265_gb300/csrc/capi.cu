@@ -214,6 +214,8 @@ void free_problem(DeviceBuffers& B) {
   dfree(B.slice_begin);
   dfree(B.bin_tile);
   dfree(B.prior);
+  dfree(B.piece_begin);
+  dfree(B.slice_piece);
 }
 
 }  // namespace
@@ -228,8 +230,9 @@ int ensure_scratch(swig_ctx* c, int n) {
   const size_t ntiles = std::max(c->L.n_tiles, 1);
   CUDA_TRY(c, cudaMalloc(&B.rec, sizeof(EvalRecord) * cap));
   CUDA_TRY(c, cudaMalloc(&B.anchors, sizeof(float) * kAnchorStride * ntiles * cap));
-  CUDA_TRY(c, cudaMalloc(&B.partials32, sizeof(float) * kPartialStride * c->L.n_slices * cap));
-  CUDA_TRY(c, cudaMalloc(&B.partials64, sizeof(double) * kPartialStride * c->L.n_slices * cap));
+  const size_t units = (size_t)c->L.n_slices * 4;  // up to 4 work units per (theta, slice)
+  CUDA_TRY(c, cudaMalloc(&B.partials32, sizeof(float) * kPartialStride * units * cap));
+  CUDA_TRY(c, cudaMalloc(&B.partials64, sizeof(double) * kPartialStride * units * cap));
   CUDA_TRY(c, cudaMalloc(&B.theta, sizeof(double) * SWIG_N_PARAMS * cap));
   CUDA_TRY(c, cudaMalloc(&B.out, sizeof(double) * cap));
   CUDA_TRY(c, cudaMalloc(&B.u, sizeof(double) * SWIG_N_PARAMS * cap));
@@ -297,20 +300,50 @@ int prepare(swig_ctx* c) {
     L.dten[i][5] = 0.5 * (x[2] * x[2] - y[2] * y[2]);
   }
   L.DD = dd.value();
+  {
+    const double a1 = std::sqrt(5.0 / 24.0) * std::pow(kPi, -2.0 / 3.0) * std::pow(kMtsunS, 5.0 / 6.0) * kCSI / kMpcM;
+    for (int i = 0; i < n_det; ++i) {
+      L.amp_s[i] = (float)(L.inv_scale[i] * a1);
+      L.amp_k[i] = (float)(L.K[i] * a1 * a1);
+    }
+  }
 
-  // slices: contiguous whole 32-bin chunks, one CTA each
+  // slices: contiguous whole 32-bin chunks, one CTA each.  The mixed path's
+  // tile plan comes first so that slices can balance the estimated cost:
+  // a chunk whose tiles are no longer than 32 bins reloads anchors for every
+  // bin and costs about twice a chunk inside a long tile.
+  std::vector<TileInfo> tiles;
+  std::vector<TileBasis> basis;
+  if (prec == SWIG_PREC_MIXED) plan_tiles(c, tiles, basis);
   const int n_chunks = (int)((n + kChunk - 1) / kChunk);
+  std::vector<double> chunk_cost(n_chunks, 1.0);
+  if (prec == SWIG_PREC_MIXED)
+    for (const TileInfo& ti : tiles)
+      if (ti.nbins <= kChunk) chunk_cost[ti.k0 / kChunk] = 2.0;
+  double total_cost = 0.0;
+  for (double v : chunk_cost) total_cost += v;
   int n_slices = std::min(c->sm_count, std::max(1, n_chunks / 4));
   const size_t smem_cap = 200 * 1024;
-  while (sweep_smem_bytes(n_det, (int)(((size_t)(n_chunks + n_slices - 1) / n_slices) * kChunk)) > smem_cap) n_slices *= 2;
-  n_slices = std::min(n_slices, n_chunks);
-  std::vector<int> slice_begin(n_slices + 1);
+  std::vector<int> slice_begin;
   int max_bins = 0;
-  for (int s = 0; s <= n_slices; ++s) {
-    const long long ch = (long long)s * n_chunks / n_slices;
-    slice_begin[s] = (int)std::min<long long>(ch * kChunk, n);
+  for (;;) {
+    slice_begin.assign(1, 0);
+    double acc = 0.0;
+    int s = 1;
+    for (int ch = 0; ch < n_chunks && s < n_slices; ++ch) {
+      acc += chunk_cost[ch];
+      if (acc >= total_cost * s / n_slices && ch + 1 < n_chunks) {
+        slice_begin.push_back((ch + 1) * kChunk);
+        ++s;
+      }
+    }
+    slice_begin.push_back((int)n);
+    max_bins = 0;
+    for (size_t q = 0; q + 1 < slice_begin.size(); ++q) max_bins = std::max(max_bins, slice_begin[q + 1] - slice_begin[q]);
+    if (sweep_smem_bytes(n_det, max_bins) <= smem_cap || n_slices >= n_chunks) break;
+    n_slices = std::min(n_chunks, n_slices * 2);
   }
-  for (int s = 0; s < n_slices; ++s) max_bins = std::max(max_bins, slice_begin[s + 1] - slice_begin[s]);
+  n_slices = (int)slice_begin.size() - 1;
   L.n_slices = n_slices;
   c->B.max_slice_bins = max_bins;
 
@@ -326,9 +359,6 @@ int prepare(swig_ctx* c) {
     }
     CUDA_TRY(c, cudaMalloc(&B.data32, sizeof(float2) * d32.size()));
     CUDA_TRY(c, cudaMemcpy(B.data32, d32.data(), sizeof(float2) * d32.size(), cudaMemcpyHostToDevice));
-    std::vector<TileInfo> tiles;
-    std::vector<TileBasis> basis;
-    plan_tiles(c, tiles, basis);
     L.n_tiles = (int)tiles.size();
     std::vector<int> bin_tile(n);
     for (int t = 0; t < L.n_tiles; ++t)
@@ -356,11 +386,45 @@ int prepare(swig_ctx* c) {
     CUDA_TRY(c, cudaMemcpy(B.ftab, ftab.data(), sizeof(double) * ftab.size(), cudaMemcpyHostToDevice));
     L.n_tiles = 0;
   }
+  // sweep pieces: whole 32-bin chunks, at most 8 chunks and 32 tiles each, so
+  // that a warp computes a piece's anchors with one lane per tile
+  {
+    std::vector<int> bt;
+    if (prec == SWIG_PREC_MIXED) {
+      bt.resize(n);
+      CUDA_TRY(c, cudaMemcpy(bt.data(), B.bin_tile, sizeof(int) * n, cudaMemcpyDeviceToHost));
+    }
+    std::vector<int> pb, sp(n_slices + 1);
+    int maxp = 1;
+    for (int s = 0; s < n_slices; ++s) {
+      sp[s] = (int)pb.size();
+      int b = slice_begin[s];
+      while (b < slice_begin[s + 1]) {
+        pb.push_back(b);
+        int e = std::min<int>(b + kChunk, slice_begin[s + 1]);
+        while (e < slice_begin[s + 1] && e - b < 8 * kChunk) {
+          const int e2 = std::min<int>(e + kChunk, slice_begin[s + 1]);
+          if (!bt.empty() && bt[e2 - 1] - bt[b] + 1 > 32) break;
+          e = e2;
+        }
+        b = e;
+      }
+      pb.push_back(slice_begin[s + 1]);
+      maxp = std::max(maxp, (int)pb.size() - sp[s] - 1);
+    }
+    sp[n_slices] = (int)pb.size();
+    B.n_pieces = (int)pb.size() - n_slices;
+    B.max_pieces = maxp;
+    CUDA_TRY(c, cudaMalloc(&B.piece_begin, sizeof(int) * pb.size()));
+    CUDA_TRY(c, cudaMemcpy(B.piece_begin, pb.data(), sizeof(int) * pb.size(), cudaMemcpyHostToDevice));
+    CUDA_TRY(c, cudaMalloc(&B.slice_piece, sizeof(int) * sp.size()));
+    CUDA_TRY(c, cudaMemcpy(B.slice_piece, sp.data(), sizeof(int) * sp.size(), cudaMemcpyHostToDevice));
+  }
   // prior slots (defaults when no prior was set: every slot sampled uniform on [0,1])
   PriorSlot slots[SWIG_N_PARAMS];
   for (int i = 0; i < SWIG_N_PARAMS; ++i) {
     const swig_param& p = c->params[i];
-    slots[i] = c->prior_set ? PriorSlot{p.kind, p.mode, p.lo, p.hi, p.value} : PriorSlot{0, 0, 0.0, 1.0, 0.0};
+    slots[i] = c->prior_set ? make_prior_slot(p.kind, p.mode, p.lo, p.hi, p.value) : make_prior_slot(0, 0, 0.0, 1.0, 0.0);
   }
   CUDA_TRY(c, cudaMalloc(&B.prior, sizeof(slots)));
   CUDA_TRY(c, cudaMemcpy(B.prior, slots, sizeof(slots), cudaMemcpyHostToDevice));

@@ -40,8 +40,10 @@ struct swig_ctx {
   swig::LikeConst L = {};
   swig::DeviceBuffers B;
   swig::SamplerState* sampler = nullptr;
+  long long wait_limit = 10000000;  // spins of a bounded device wait (~100 ns each)
   // results of the last run
   swig_result last = {};
+  double profile[6] = {0, 0, 0, 0, 0, 0};
   std::vector<double> out_theta, out_logl, out_logw;
 };
 

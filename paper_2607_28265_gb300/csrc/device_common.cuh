@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <cmath>
+
 #include "swig_internal.h"
 
 namespace swig {
@@ -105,29 +107,32 @@ __host__ __device__ inline void taylorf2_basis_coeffs(double mc, double q, doubl
   const double a10 = -19.5 * lt;
   const double a12 = -3115.0 / 64.0 * lt + 6595.0 / 364.0 * dm * dlt;
 
-  const double A = 3.0 / (128.0 * eta) / (2.0 * kPi);  // radians -> cycles
+  const double A = (3.0 / (256.0 * kPi)) * (opq * opq / q);  // 3 / (128 eta) in cycles
   const double piM = kPi * mtot;
   const double lpm = log(piM);
   const double r = cbrt(piM);       // (pi M)^(1/3): v = r f^(1/3)
+  const double ir = 1.0 / r;
   const double r2 = r * r, r5 = r2 * r2 * r, r7 = r5 * r2;
-  const double ln_vlso = -0.5 * log(6.0);
+  const double ir2 = ir * ir, ir3 = ir2 * ir, ir5 = ir3 * ir2;
+  const double third = 1.0 / 3.0;
+  const double ln4 = 1.3862943611198906188, ln_vlso = -0.89587973461402746;  // ln 4, -ln(6)/2
 
-  c[B_M53] = A * a0 / r5;
-  c[B_M1] = A * a2 / piM;
-  c[B_M23] = A * a3 / r2;
-  c[B_M13] = A * a4 / r;
-  c[B_LOG] = A * a5log / 3.0;
-  c[B_P13] = A * r * (a6 + a6log * (log(4.0) + lpm / 3.0));
-  c[B_P13LOG] = A * r * a6log / 3.0;
+  c[B_M53] = A * a0 * ir5;
+  c[B_M1] = A * a2 * ir3;
+  c[B_M23] = A * a3 * ir2;
+  c[B_M13] = A * a4 * ir;
+  c[B_LOG] = A * a5log * third;
+  c[B_P13] = A * r * (a6 + a6log * (ln4 + lpm * third));
+  c[B_P13LOG] = A * r * a6log * third;
   c[B_P23] = A * a7 * r2;
   c[B_P53] = A * a10 * r5;
   c[B_P73] = A * a12 * r7;
-  c[B_ONE] = A * (a5 + a5log * (lpm / 3.0 - ln_vlso)) - 0.125;
+  c[B_ONE] = A * (a5 + a5log * (lpm * third - ln_vlso)) - 0.125;
 }
 
 // sqrt(5/24) pi^(-2/3) (G Mc / c^3)^(5/6) c / (1 Mpc): Newtonian SPA amplitude
 // times d_L[Mpc].
-__device__ inline double amplitude_per_mpc(double mc) {
+__host__ __device__ inline double amplitude_per_mpc(double mc) {
   return sqrt(5.0 / 24.0) * exp(-2.0 / 3.0 * log(kPi)) * exp(5.0 / 6.0 * log(mc * kMtsunS)) * kCSI / kMpcM;
 }
 
@@ -165,44 +170,49 @@ __device__ inline double geocentric_delay(const double* vertex, double ra, doubl
   return -(cd * cl * vertex[0] + cd * sl * vertex[1] + sd * vertex[2]) / kCSI;
 }
 
-// log I0(x) for x >= 0: power series sum (x^2/4)^k / (k!)^2 below 20, and the
-// large-argument expansion I0(x) ~ e^x / sqrt(2 pi x) sum_k ((2k-1)!!)^2 /
-// (k! (8x)^k) above (Abramowitz & Stegun 9.6.10, 9.7.1).
-__device__ inline double log_bessel_i0(double x) {
+// log I0(x) for x >= 0: power series sum_k (x^2/4)^k / (k!)^2 below 20, and
+// the large-argument expansion I0(x) ~ e^x / sqrt(2 pi x) sum_k ((2k-1)!!)^2 /
+// (k! (8x)^k) above (Abramowitz & Stegun 9.6.10, 9.7.1).  The series terms
+// use precomputed ratios (no division in the large-argument loop).
+__host__ __device__ inline double log_bessel_i0(double x) {
   if (x < 20.0) {
     const double y = 0.25 * x * x;
     double term = 1.0, sum = 1.0;
-    for (int k = 1; k < 200; ++k) {
+    for (int k = 1; k < 200; ++k) {  // rare: only for |Z| < 20
       term *= y / ((double)k * (double)k);
       sum += term;
       if (term < 1e-17 * sum) break;
     }
     return log(sum);
   }
-  const double t = 1.0 / (8.0 * x);
+  const double t = 0.125 / x;
+  // ((2k-1)^2 / k) for k = 1..12
+  const double r[12] = {1.0, 4.5, 25.0 / 3.0, 12.25, 16.2, 121.0 / 6.0, 169.0 / 7.0, 28.125,
+                        289.0 / 9.0, 36.1, 441.0 / 11.0, 529.0 / 12.0};
   double term = 1.0, sum = 1.0;
-  for (int k = 1; k < 30; ++k) {
-    const double m = 2.0 * k - 1.0;
-    term *= m * m * t / (double)k;
+  for (int k = 0; k < 12; ++k) {
+    term *= r[k] * t;
     sum += term;
-    if (term < 1e-17 * sum) break;
   }
   return x - 0.5 * log(2.0 * kPi * x) + log(sum);
 }
 
 // ---------------------------------------------------------------------------
 // Per-theta setup (FP64): phase coefficients, delays, complex projection
-// factors C_i so that h_i(f) = C_i f^(-7/6) exp(-2 pi i (P(f) + f tau_i)).
+// factors C_i = amp P_i so that h_i(f) = C_i f^(-7/6) exp(-2 pi i (P(f) + f tau_i)),
+// with amp = A(Mc) / d_L and P_i = [F+_i (1 + cos^2 i)/2 - i Fx_i cos i] e^{i phi_c}.
+// The pieces are separate so that a Gibbs block recomputes only what it moves.
 // ---------------------------------------------------------------------------
-__device__ inline void setup_record(const LikeConst& L, const double* th, EvalRecord* rec) {
-  const double mc = th[0], q = th[1], chi1 = th[2], chi2 = th[3], lam1 = th[4], lam2 = th[5];
-  const double dl = th[6], iota = th[7], psi = th[8], ra = th[9], dec = th[10], tc = th[11], phic = th[12];
-  const bool ok = (mc > 0.0) && (q > 0.0) && (q <= 1.0) && (dl > 0.0) && isfinite(mc + q + chi1 + chi2 + lam1 + lam2 +
-                                                                               dl + iota + psi + ra + dec + tc + phic);
-  rec->valid = ok ? 1 : 0;
+__device__ inline bool theta_valid(const double* th) {
+  double s = 0.0;
+  for (int j = 0; j < SWIG_N_PARAMS; ++j) s += th[j];
+  return (th[0] > 0.0) && (th[1] > 0.0) && (th[1] <= 1.0) && (th[6] > 0.0) && isfinite(s);
+}
+
+__device__ inline void setup_intrinsic(const double* th, EvalRecord* rec) {
   double c[NBASIS];
-  if (ok) {
-    taylorf2_basis_coeffs(mc, q, chi1, chi2, lam1, lam2, c);
+  if (rec->valid) {
+    taylorf2_basis_coeffs(th[0], th[1], th[2], th[3], th[4], th[5], c);
   } else {
     for (int j = 0; j < NBASIS; ++j) c[j] = 0.0;
   }
@@ -212,34 +222,102 @@ __device__ inline void setup_record(const LikeConst& L, const double* th, EvalRe
     rec->c_hi[j] = v.hi;
     rec->c_lo[j] = v.lo;
   }
-  const double amp = ok ? amplitude_per_mpc(mc) / dl : 0.0;
-  double ci = cos(iota);
+}
+
+__device__ inline void setup_amp(const double* th, EvalRecord* rec) {
+  rec->amp = rec->valid ? amplitude_per_mpc(th[0]) / th[6] : 0.0;
+}
+
+__device__ inline void setup_projection(const LikeConst& L, const double* th, EvalRecord* rec) {
+  const double ci = cos(th[7]);
   const double plus = 0.5 * (1.0 + ci * ci), cross = -ci;  // h+ ~ plus, hx ~ i*cross
   double sph = 0.0, cph = 1.0;
-  if (!L.phase_marg) sincos(phic, &sph, &cph);
-  double hh = 0.0;
+  if (!L.phase_marg) sincos(th[12], &sph, &cph);
   for (int i = 0; i < SWIG_MAX_DET; ++i) {
     if (i >= L.n_det) {
-      rec->tau[i] = 0.0;
-      rec->tau_hi[i] = rec->tau_lo[i] = 0.0f;
-      rec->cre[i] = rec->cim[i] = 0.0;
+      rec->pre[i] = rec->pim[i] = 0.0;
       continue;
     }
     double fp, fx;
-    antenna_fp_fx(L.dten[i], ra, dec, psi, L.gmst, &fp, &fx);
-    const double tau = tc + geocentric_delay(L.vertex[i], ra, dec, L.gmst);
+    antenna_fp_fx(L.dten[i], th[9], th[10], th[8], L.gmst, &fp, &fx);
+    const double re0 = fp * plus, im0 = fx * cross;
+    rec->pre[i] = re0 * cph - im0 * sph;
+    rec->pim[i] = re0 * sph + im0 * cph;
+  }
+}
+
+// FP32 variants for the mixed-precision sampler: C_i is needed to ~1e-7
+// relative (its error enters logL as ~1e-7 |C kappa|), far below the tolerance.
+__device__ inline void setup_amp_f32(const double* th, EvalRecord* rec) {
+  const float rel = exp2f(0.8333333333f * log2f((float)th[0])) / (float)th[6];
+  rec->amp = rec->valid ? (double)rel * amplitude_per_mpc(1.0) : 0.0;
+}
+
+__device__ inline void setup_projection_f32(const LikeConst& L, const double* th, EvalRecord* rec) {
+  float sl, cl, sd, cd, sp, cp;
+  sincosf((float)(th[9] - L.gmst), &sl, &cl);
+  sincosf((float)th[10], &sd, &cd);
+  sincosf((float)th[8], &sp, &cp);
+  const float east[3] = {-sl, cl, 0.0f};
+  const float north[3] = {-sd * cl, -sd * sl, cd};
+  float X[3], Y[3];
+  for (int k = 0; k < 3; ++k) {
+    X[k] = -cp * east[k] + sp * north[k];
+    Y[k] = sp * east[k] + cp * north[k];
+  }
+  const float ci = cosf((float)th[7]);
+  const float plus = 0.5f * (1.0f + ci * ci), cross = -ci;
+  float sph = 0.0f, cph = 1.0f;
+  if (!L.phase_marg) sincosf((float)th[12], &sph, &cph);
+  for (int i = 0; i < SWIG_MAX_DET; ++i) {
+    if (i >= L.n_det) {
+      rec->pre[i] = rec->pim[i] = 0.0;
+      continue;
+    }
+    float d[6];
+    for (int q = 0; q < 6; ++q) d[q] = (float)L.dten[i][q];
+    auto form = [&d](const float* a, const float* b) {
+      return a[0] * (d[0] * b[0] + d[1] * b[1] + d[2] * b[2]) + a[1] * (d[1] * b[0] + d[3] * b[1] + d[4] * b[2]) +
+             a[2] * (d[2] * b[0] + d[4] * b[1] + d[5] * b[2]);
+    };
+    const float fp = form(X, X) - form(Y, Y), fx = 2.0f * form(X, Y);
+    const float re0 = fp * plus, im0 = fx * cross;
+    rec->pre[i] = (double)(re0 * cph - im0 * sph);
+    rec->pim[i] = (double)(re0 * sph + im0 * cph);
+  }
+}
+
+__device__ inline void setup_delays(const LikeConst& L, const double* th, EvalRecord* rec) {
+  double sl, cl, sd, cd;
+  sincos(th[9] - L.gmst, &sl, &cl);
+  sincos(th[10], &sd, &cd);
+  const double n0 = cd * cl * (-1.0 / kCSI), n1 = cd * sl * (-1.0 / kCSI), n2 = sd * (-1.0 / kCSI);
+  for (int i = 0; i < SWIG_MAX_DET; ++i) {
+    const double tau = i < L.n_det ? th[11] + (n0 * L.vertex[i][0] + n1 * L.vertex[i][1] + n2 * L.vertex[i][2]) : 0.0;
     rec->tau[i] = tau;
     dfl tv = df_from_double(tau);
     rec->tau_hi[i] = tv.hi;
     rec->tau_lo[i] = tv.lo;
-    // C_i = amp [F+ plus + i Fx cross] e^{i phi_c}
-    const double re0 = amp * fp * plus, im0 = amp * fx * cross;
-    const double re = re0 * cph - im0 * sph, im = re0 * sph + im0 * cph;
-    rec->cre[i] = re;
-    rec->cim[i] = im;
-    hh += (re * re + im * im) * L.K[i];
+  }
+}
+
+__device__ inline void setup_combine(const LikeConst& L, EvalRecord* rec) {
+  double hh = 0.0;
+  for (int i = 0; i < SWIG_MAX_DET; ++i) {
+    rec->cre[i] = rec->amp * rec->pre[i];
+    rec->cim[i] = rec->amp * rec->pim[i];
+    if (i < L.n_det) hh += (rec->cre[i] * rec->cre[i] + rec->cim[i] * rec->cim[i]) * L.K[i];
   }
   rec->hh = hh;
+}
+
+__device__ inline void setup_record(const LikeConst& L, const double* th, EvalRecord* rec) {
+  rec->valid = theta_valid(th) ? 1 : 0;
+  setup_intrinsic(th, rec);
+  setup_amp(th, rec);
+  setup_projection(L, th, rec);
+  setup_delays(L, th, rec);
+  setup_combine(L, rec);
 }
 
 // logL from the per-detector sums kappa_i = sum_k D_i(k) exp(-2 pi i phi_i(k))
@@ -266,23 +344,20 @@ __device__ inline double loglike_epilogue(const LikeConst& L, const EvalRecord& 
 
 namespace swig {
 
-// Inverse CDFs of the Table I prior families on [lo, hi].
-__host__ __device__ inline double prior_inverse_cdf(int kind, double lo, double hi, double u) {
-  switch (kind) {
-    case SWIG_PRIOR_SINE: {
-      const double clo = cos(lo), chi = cos(hi);
-      return acos(clo - u * (clo - chi));
-    }
-    case SWIG_PRIOR_COSINE: {
-      const double slo = sin(lo), shi = sin(hi);
-      return asin(slo + u * (shi - slo));
-    }
-    case SWIG_PRIOR_POWER2: {
-      const double l3 = lo * lo * lo, h3 = hi * hi * hi;
-      return cbrt(l3 + u * (h3 - l3));
-    }
+// Inverse CDFs of the Table I prior families on [lo, hi], with the slot's
+// precomputed constants (c1, c2): sine p ~ sin x: x = acos(cos lo - u (cos lo -
+// cos hi)); cosine p ~ cos x: x = asin(sin lo + u (sin hi - sin lo)); p ~ x^2:
+// x = (lo^3 + u (hi^3 - lo^3))^(1/3); uniform: lo + u (hi - lo).
+__host__ __device__ inline double prior_slot_inverse(const PriorSlot& s, double u) {
+  switch (s.kind) {
+    case SWIG_PRIOR_SINE:
+      return acos(s.c1 - u * (s.c1 - s.c2));
+    case SWIG_PRIOR_COSINE:
+      return asin(s.c1 + u * (s.c2 - s.c1));
+    case SWIG_PRIOR_POWER2:
+      return cbrt(s.c1 + u * (s.c2 - s.c1));
     default:
-      return lo + u * (hi - lo);
+      return s.lo + u * (s.hi - s.lo);
   }
 }
 
@@ -296,9 +371,26 @@ __host__ __device__ inline void prior_map(const PriorSlot* slots, const double* 
     } else if (s.mode == SWIG_MODE_MARG) {
       th[i] = 0.0;
     } else {
-      th[i] = prior_inverse_cdf(s.kind, s.lo, s.hi, u[j++]);
+      th[i] = prior_slot_inverse(s, u[j++]);
     }
   }
 }
 
+}  // namespace swig
+
+namespace swig {
+inline PriorSlot make_prior_slot(int kind, int mode, double lo, double hi, double value) {
+  PriorSlot s{kind, mode, lo, hi, value, 0.0, 0.0};
+  if (kind == SWIG_PRIOR_SINE) {
+    s.c1 = std::cos(lo);
+    s.c2 = std::cos(hi);
+  } else if (kind == SWIG_PRIOR_COSINE) {
+    s.c1 = std::sin(lo);
+    s.c2 = std::sin(hi);
+  } else if (kind == SWIG_PRIOR_POWER2) {
+    s.c1 = lo * lo * lo;
+    s.c2 = hi * hi * hi;
+  }
+  return s;
+}
 }  // namespace swig

@@ -11,7 +11,10 @@ struct PriorSlot {
   int kind;
   int mode;
   double lo, hi, value;
+  double c1, c2;  // SINE: cos lo, cos hi; COSINE: sin lo, sin hi; POWER2: lo^3, hi^3
 };
+
+inline PriorSlot make_prior_slot(int kind, int mode, double lo, double hi, double value);
 
 // Device buffers owned by a context (all allocated with cudaMalloc).
 struct DeviceBuffers {
@@ -24,6 +27,10 @@ struct DeviceBuffers {
   int* slice_begin = nullptr;    // [n_slices + 1] first bin of each slice
   int* bin_tile = nullptr;       // [n_bins] tile of each bin
   PriorSlot* prior = nullptr;    // [13]
+  int* piece_begin = nullptr;    // first bin of each sweep piece, slices concatenated (+ end per slice)
+  int* slice_piece = nullptr;    // [n_slices + 1] offset of each slice's entries in piece_begin
+  int n_pieces = 0;              // total pieces (work units per theta)
+  int max_pieces = 1;            // pieces of the largest slice
   int max_slice_bins = 0;
   // scratch for batched evaluation, sized for `cap` thetas
   int cap = 0;
@@ -36,10 +43,12 @@ struct DeviceBuffers {
   double* u = nullptr;           // [cap][13]
 };
 
+// logL of n thetas (device pointers) into out; kappa_out (optional, n x 8
+// doubles) receives the unscaled per-detector sums (re, im) for each theta.
 cudaError_t launch_loglike_mixed(const LikeConst& L, const DeviceBuffers& B, const double* theta, int n,
-                                 double* out, cudaStream_t st);
+                                 double* out, cudaStream_t st, double* kappa_out = nullptr);
 cudaError_t launch_loglike_fp64(const LikeConst& L, const DeviceBuffers& B, const double* theta, int n,
-                                double* out, cudaStream_t st);
+                                double* out, cudaStream_t st, double* kappa_out = nullptr);
 cudaError_t launch_prior_transform(const PriorSlot* slots, int n_sampled, const double* u, int n, double* theta,
                                    cudaStream_t st);
 cudaError_t set_sweep_smem_limit(size_t bytes);

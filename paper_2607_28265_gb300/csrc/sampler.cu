@@ -1,22 +1,1212 @@
-// Nested sampling driver (filled in with the persistent SwiG kernel).
+// Persistent Slice-within-Gibbs nested sampler (Sec. 2.2, 2.3, 3.2 of the paper).
+//
+// One cooperative launch runs up to `max_iters` nested-sampling iterations on
+// the device.  Every CTA owns one slice of the frequency grid (its data staged
+// once in shared memory) and the kernel alternates, between grid barriers:
+//
+//   boundary  (CTA 0, once per NS iteration): write the k finished chains back
+//             into the live set, sort the live log-likelihoods, test the
+//             termination rule log Z_live - log Z_dead < dlogz, retire the k
+//             worst points into the dead buffer with weights L_j (X_{j-1} - X_j)
+//             (log X shrinks by 1/n per death, n = m, m-1, ..., m-k+1), set
+//             logL* to the lowest survivor, estimate the live covariance and
+//             its per-block Cholesky factors, and start k chains at survivors.
+//   control   (one warp per chain): advance the chain's hit-and-run slice state
+//             machine (Neal 2003 stepping-out and shrinkage along a direction
+//             drawn from the block covariance) through every proposal that
+//             needs no pass over the grid: proposals outside the unit cube, and
+//             proposals of blocks that only change the projection factors C_i
+//             (d_L, iota, psi, phi_c), which reuse the chain's cached
+//             per-detector sums kappa_i.  A proposal that changes the waveform
+//             or the time shifts is set up and left pending.
+//   sweep     (all CTAs): every pending chain's likelihood over the CTA's slice,
+//             one chain per warp-group, partial sums per (chain, slice).
+//
+// Every spin of the grid barrier is bounded; on expiry the kernel records
+// SWIG_E_TIMEOUT and every CTA returns at its next barrier.
 #include <cuda_runtime.h>
 
-#include "context.h"
-#include "swig.h"
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
 
-void swig_sampler_release(swig_ctx* c) { (void)c; }
+#include "context.h"
+#include "sweep.cuh"
+
+namespace swig {
+
+constexpr int kMaxDim = SWIG_N_PARAMS;
+constexpr int kMaxBlocks = 16;
+constexpr int kMaxStepOut = 100;
+constexpr int kMaxShrink = 100;
+constexpr int kMaxSort = 8192;
+constexpr int kMaxChains = 2048;
+
+constexpr int kFreeBudget = 8;  // projection-only evaluations per chain per round
+enum ChainPhase { PH_NEW = 0, PH_LEFT = 1, PH_RIGHT = 2, PH_SHRINK = 3 };
+// What a Gibbs block moves: waveform coefficients, amplitude A(Mc)/d_L,
+// projection P_i, time shifts tau_i.
+enum BlockFlag { BF_INTR = 1, BF_AMP = 2, BF_PROJ = 4, BF_TAU = 8 };
+enum RunStatus { ST_RUNNING = 0, ST_TERMINATED = 1, ST_LIMIT = 2 };
+
+struct SamplerConst {
+  int ndim, nlive, nrep, sweeps, steps_per_dim, n_blocks;
+  int slot_of_dim[kMaxDim];
+  int block_size[kMaxBlocks], block_free[kMaxBlocks], block_flags[kMaxBlocks];
+  int block_dims[kMaxBlocks][kMaxDim];
+  PriorSlot prior[SWIG_N_PARAMS];
+  unsigned key0, key1;
+  double dlogz;
+  int m_pow2;
+  int max_iters;
+  long long spin_limit;
+  int max_pieces;      // pieces per slice (sweep work units)
+  int max_tiles_slice; // tiles overlapping the largest slice
+  int group;           // pending chains per sweep group (shared-memory bound)
+  int n_ctas;
+  int mixed;
+};
+
+struct ChainState {
+  double x[kMaxDim], y[kMaxDim], dir[kMaxDim];
+  double th[SWIG_N_PARAMS], th_y[SWIG_N_PARAMS];  // theta of x and of the proposal
+  double lx, lo, hi, t;
+  double kap[2 * SWIG_MAX_DET];
+  int block, step, sweep, phase, n_out, n_shrink;
+  int pending, done, proj_dirty, slot;
+  unsigned ctr;
+  int n_caps;
+  long long n_evals, n_full;
+};
+
+struct NSGlobal {
+  double logx, logz, logl_star;
+  long long iter;
+  int iters_launch;
+  int status;
+  int error;
+  int chains_done;
+  int need_writeback;
+  int n_dead;
+  unsigned bar_count, bar_gen;
+  // phase timers of CTA 0 [ns, %globaltimer]: boundary, control, wait after
+  // control, sweep, wait after sweep; and rounds
+  unsigned long long t_bound, t_ctrl, t_wait_ctrl, t_sweep, t_wait_sweep, rounds;
+};
+
+__device__ __forceinline__ unsigned long long gtimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+struct SamplerPtrs {
+  double* live_u;      // [m][ndim]
+  double* live_logl;   // [m]
+  double* live_kap;    // [m][8]
+  ChainState* chains;  // [k]
+  EvalRecord* recx;    // [k] setup record of each chain's current point
+  int* pending;        // [k]
+  float* chol;         // [kMaxBlocks][kMaxDim][kMaxDim]
+  NSGlobal* g;
+  double* dead_u;      // [max_iters * k][ndim]
+  double* dead_logl;
+  double* dead_logw;
+  const double* harm;  // [k + 1]: sum_{i<j} 1 / (m - i)
+  const double* lw;    // [m + 1]: log(1 - exp(-1/n))
+  const int* piece_begin;  // [n_pieces_total + n_slices] absolute first bin of each piece, per slice
+  const int* slice_piece;  // [n_slices + 1] offset of each slice's pieces in piece_begin
+  float* anchor_buf;       // [n_slices][k][max_tiles_slice][kAnchorStride] per-round anchors
+};
+
+// ---------------------------------------------------------------------------
+// Philox-4x32-10 (Salmon et al. 2011) and the draws built on it.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, unsigned k0, unsigned k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r) {
+      k0 += 0x9E3779B9u;
+      k1 += 0xBB67AE85u;
+    }
+    const unsigned lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+    const unsigned lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+    c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+  }
+  return c;
+}
+
+__device__ __forceinline__ double u01_from(uint4 r) {  // 53-bit uniform in [0, 1)
+  return ((double)(r.x >> 5) * 67108864.0 + (double)(r.y >> 6)) * (1.0 / 9007199254740992.0);
+}
+
+__device__ __forceinline__ double chain_uniform(const SamplerConst& S, ChainState& ch, int c, long long it) {
+  return u01_from(philox4x32_10(make_uint4(ch.ctr++, (unsigned)c, (unsigned)it, 0u), S.key0, S.key1));
+}
+
+// Standard normal by Box-Muller from one Philox block.
+__device__ __forceinline__ float chain_normal(const SamplerConst& S, ChainState& ch, int c, long long it) {
+  const uint4 r = philox4x32_10(make_uint4(ch.ctr++, (unsigned)c, (unsigned)it, 0u), S.key0, S.key1);
+  const float u1 = ((float)(r.x >> 8) + 1.0f) * (1.0f / 16777216.0f);  // (0, 1]
+  const float u2 = (float)(r.y >> 8) * (1.0f / 16777216.0f);
+  return sqrtf(-2.0f * logf(u1)) * cospif(2.0f * u2);
+}
+
+// ---------------------------------------------------------------------------
+// Bounded grid barrier (all CTAs co-resident by cooperative launch).
+// ---------------------------------------------------------------------------
+__device__ bool grid_sync(NSGlobal* g, int n_ctas, long long limit) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* vgen = &g->bar_gen;
+    const unsigned gen = *vgen;
+    __threadfence();
+    const unsigned arrived = atomicAdd(&g->bar_count, 1u) + 1u;
+    if (arrived == (unsigned)n_ctas) {
+      atomicExch(&g->bar_count, 0u);
+      __threadfence();
+      atomicAdd(&g->bar_gen, 1u);
+    } else {
+      long long spins = 0;
+      while (*vgen == gen) {
+        if (++spins > limit) {
+          atomicCAS(&g->error, 0, SWIG_E_TIMEOUT);
+          break;
+        }
+        __nanosleep(100);
+      }
+    }
+    __threadfence();
+    s_ok = (*(volatile int*)&g->error) == 0;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// ---------------------------------------------------------------------------
+// Projection-only setup and FP32 epilogue for blocks that leave kappa unchanged.
+// ---------------------------------------------------------------------------
+__device__ inline void projection_record(const LikeConst& L, const double* th, EvalRecord* rec) {
+  const double mc = th[0], dl = th[6], iota = th[7], psi = th[8], ra = th[9], dec = th[10], phic = th[12];
+  rec->valid = (mc > 0.0 && dl > 0.0 && th[1] > 0.0 && th[1] <= 1.0) ? 1 : 0;
+  const double amp = rec->valid ? amplitude_per_mpc(mc) / dl : 0.0;
+  const double ci = cos(iota);
+  const double plus = 0.5 * (1.0 + ci * ci), cross = -ci;
+  double sph = 0.0, cph = 1.0;
+  if (!L.phase_marg) sincos(phic, &sph, &cph);
+  double hh = 0.0;
+  for (int i = 0; i < L.n_det; ++i) {
+    double fp, fx;
+    antenna_fp_fx(L.dten[i], ra, dec, psi, L.gmst, &fp, &fx);
+    const double re0 = amp * fp * plus, im0 = amp * fx * cross;
+    rec->cre[i] = re0 * cph - im0 * sph;
+    rec->cim[i] = re0 * sph + im0 * cph;
+    hh += (rec->cre[i] * rec->cre[i] + rec->cim[i] * rec->cim[i]) * L.K[i];
+  }
+  rec->hh = hh;
+}
+
+// FP32 form of the same projection and epilogue (mixed precision): relative
+// error ~1e-6 on |Z| and <h|h>, far inside the likelihood tolerance; the large
+// constant -<d|d>/2 is added in FP64.
+__device__ inline float log_i0_f32(float x) {
+  if (x < 20.0f) {
+    const float y = 0.25f * x * x;
+    float term = 1.0f, sum = 1.0f;
+    for (int k = 1; k < 64; ++k) {
+      term *= y / (float)(k * k);
+      sum += term;
+      if (term < 1e-8f * sum) break;
+    }
+    return logf(sum);
+  }
+  const float t = 1.0f / (8.0f * x);
+  const float s = 1.0f + t * (1.0f + t * (4.5f + t * (37.5f + t * 459.375f)));
+  return x - 0.5f * logf(6.283185307179586f * x) + logf(s);
+}
+
+__device__ inline double free_loglike_mixed(const LikeConst& L, const double* th, const double* kap) {
+  const float mc = (float)th[0], dl = (float)th[6], iota = (float)th[7], psi = (float)th[8];
+  const float ra = (float)th[9], dec = (float)th[10], phic = (float)th[12];
+  if (!(mc > 0.0f && dl > 0.0f)) return -INFINITY;
+  const float rel = exp2f(0.8333333333f * log2f(mc)) / dl;  // Mc^(5/6) / d_L
+  float sl, cl, sd, cd, sp, cp;
+  sincosf(ra - (float)L.gmst, &sl, &cl);
+  sincosf(dec, &sd, &cd);
+  sincosf(psi, &sp, &cp);
+  const float east[3] = {-sl, cl, 0.0f};
+  const float north[3] = {-sd * cl, -sd * sl, cd};
+  float X[3], Y[3];
+  for (int k = 0; k < 3; ++k) {
+    X[k] = -cp * east[k] + sp * north[k];
+    Y[k] = sp * east[k] + cp * north[k];
+  }
+  const float ci = cosf(iota);
+  const float plus = 0.5f * (1.0f + ci * ci), cross = -ci;
+  float sph = 0.0f, cph = 1.0f;
+  if (!L.phase_marg) sincosf(phic, &sph, &cph);
+  float zr = 0.0f, zi = 0.0f, hh = 0.0f;
+  for (int i = 0; i < L.n_det; ++i) {
+    float d[6];
+    for (int q = 0; q < 6; ++q) d[q] = (float)L.dten[i][q];
+    auto form = [&d](const float* a, const float* b) {
+      return a[0] * (d[0] * b[0] + d[1] * b[1] + d[2] * b[2]) + a[1] * (d[1] * b[0] + d[3] * b[1] + d[4] * b[2]) +
+             a[2] * (d[2] * b[0] + d[4] * b[1] + d[5] * b[2]);
+    };
+    const float fp = form(X, X) - form(Y, Y), fx = 2.0f * form(X, Y);
+    const float re0 = rel * fp * plus, im0 = rel * fx * cross;
+    const float cre = re0 * cph - im0 * sph, cim = re0 * sph + im0 * cph;
+    const float a = (float)kap[2 * i] * L.amp_s[i], b = (float)kap[2 * i + 1] * L.amp_s[i];
+    zr += cre * a - cim * b;
+    zi += cre * b + cim * a;
+    hh += (cre * cre + cim * cim) * L.amp_k[i];
+  }
+  const float core = (L.phase_marg ? log_i0_f32(sqrtf(zr * zr + zi * zi)) : zr) - 0.5f * hh;
+  return (double)core - 0.5 * L.DD;
+}
+
+// ---------------------------------------------------------------------------
+// Chain control.
+// ---------------------------------------------------------------------------
+__device__ inline void finish_step(const SamplerConst& S, ChainState& ch, NSGlobal* g) {
+  ch.phase = PH_NEW;
+  if (++ch.step >= S.steps_per_dim * S.block_size[ch.block]) {
+    ch.step = 0;
+    if (++ch.block >= S.n_blocks) {
+      ch.block = 0;
+      if (++ch.sweep >= S.sweeps) {
+        ch.done = 1;
+        atomicAdd(&g->chains_done, 1);
+      }
+    }
+  }
+}
+
+// Outcome of evaluating the proposal y with log-likelihood ly.  Returns true
+// when the shrinkage phase accepts y (the caller moves the chain there and
+// then calls finish_step); stepping-out and rejections are handled here.
+__device__ inline bool apply_result(const SamplerConst& S, ChainState& ch, double ly, double logl_star,
+                                    NSGlobal* g) {
+  const bool ok = ly > logl_star;
+  switch (ch.phase) {
+    case PH_LEFT:
+      if (ok) {
+        ch.lo -= 1.0;
+        if (++ch.n_out >= kMaxStepOut) {
+          ch.phase = PH_RIGHT;
+          ch.n_out = 0;
+        }
+      } else {
+        ch.phase = PH_RIGHT;
+        ch.n_out = 0;
+      }
+      return false;
+    case PH_RIGHT:
+      if (ok) {
+        ch.hi += 1.0;
+        if (++ch.n_out >= kMaxStepOut) {
+          ch.phase = PH_SHRINK;
+          ch.n_shrink = 0;
+        }
+      } else {
+        ch.phase = PH_SHRINK;
+        ch.n_shrink = 0;
+      }
+      return false;
+    default:  // PH_SHRINK
+      if (ok) return true;
+      if (ch.t < 0.0)
+        ch.lo = ch.t;
+      else
+        ch.hi = ch.t;
+      if (++ch.n_shrink >= kMaxShrink) {
+        ++ch.n_caps;
+        finish_step(S, ch, g);
+      }
+      return false;
+  }
+}
+
+__device__ inline void move_to_proposal(const SamplerConst& S, ChainState& ch, double ly) {
+  for (int j = 0; j < S.ndim; ++j) ch.x[j] = ch.y[j];
+  for (int j = 0; j < SWIG_N_PARAMS; ++j) ch.th[j] = ch.th_y[j];
+  ch.lx = ly;
+}
+
+__device__ inline void start_step(const SamplerConst& S, ChainState& ch, const float* chol, int c, long long it) {
+  const int b = ch.block, nb = S.block_size[b];
+  float z[kMaxDim];
+  for (int j = 0; j < nb; ++j) z[j] = chain_normal(S, ch, c, it);
+  for (int j = 0; j < S.ndim; ++j) ch.dir[j] = 0.0;
+  const float* Lb = chol + (size_t)b * kMaxDim * kMaxDim;
+  for (int r = 0; r < nb; ++r) {
+    float v = 0.0f;
+    for (int q = 0; q <= r; ++q) v = fmaf(Lb[r * kMaxDim + q], z[q], v);
+    ch.dir[S.block_dims[b][r]] = (double)v;
+  }
+  const double r0 = chain_uniform(S, ch, c, it);
+  ch.lo = -r0;
+  ch.hi = 1.0 - r0;
+  ch.phase = PH_LEFT;
+  ch.n_out = 0;
+  ch.n_shrink = 0;
+}
+
+// Advance chain c through the proposals that need no grid pass (outside the
+// unit cube, or projection-only blocks, at most kFreeBudget of the latter per
+// round) and leave the first full-likelihood proposal pending with its setup
+// record in *rec.  Only the Gibbs block's slots are transformed and only the
+// pieces of the record that the block moves are recomputed.  Lane 0 only.
+template <bool MIXED>
+__device__ void chain_advance(const LikeConst& L, const SamplerConst& S, const SamplerPtrs& P, int c,
+                              const double* kap_in, double ly_in, EvalRecord* rec) {
+  ChainState& ch = P.chains[c];
+  EvalRecord& rx = P.recx[c];
+  NSGlobal* g = P.g;
+  const double logl_star = g->logl_star;
+  const long long it = g->iter;
+  if (ch.done) return;
+  if (ch.pending) {
+    ch.pending = 0;
+    ++ch.n_full;
+    ++ch.n_evals;
+    if (apply_result(S, ch, ly_in, logl_star, g)) {
+      move_to_proposal(S, ch, ly_in);
+      for (int j = 0; j < 2 * SWIG_MAX_DET; ++j) ch.kap[j] = kap_in[j];
+      rx = *rec;
+      ch.proj_dirty = 0;
+      finish_step(S, ch, g);
+    }
+  }
+  int free_left = kFreeBudget;
+  for (int guard = 0; guard < 1 << 20 && !ch.done; ++guard) {
+    const int b = ch.block;
+    if (S.block_free[b] && free_left <= 0) return;  // resume next round
+    if (ch.phase == PH_NEW) start_step(S, ch, P.chol, c, it);
+    double t;
+    if (ch.phase == PH_LEFT)
+      t = ch.lo;
+    else if (ch.phase == PH_RIGHT)
+      t = ch.hi;
+    else
+      t = ch.lo + (ch.hi - ch.lo) * chain_uniform(S, ch, c, it);
+    ch.t = t;
+    const int nb = S.block_size[b];
+    bool inside = true;
+    for (int r = 0; r < nb; ++r) {
+      const int j = S.block_dims[b][r];
+      const double v = ch.x[j] + t * ch.dir[j];
+      ch.y[j] = v;
+      inside = inside && (v >= 0.0) && (v <= 1.0);
+    }
+    if (!inside) {
+      apply_result(S, ch, -INFINITY, logl_star, g);
+      continue;
+    }
+    for (int j = 0; j < S.ndim; ++j)
+      if (ch.dir[j] == 0.0) ch.y[j] = ch.x[j];
+    for (int q = 0; q < SWIG_N_PARAMS; ++q) ch.th_y[q] = ch.th[q];
+    for (int r = 0; r < nb; ++r) {
+      const int j = S.block_dims[b][r], slot = S.slot_of_dim[j];
+      ch.th_y[slot] = prior_slot_inverse(S.prior[slot], ch.y[j]);
+    }
+    if (S.block_free[b]) {
+      --free_left;
+      ++ch.n_evals;
+      if (MIXED) {
+        const double ly = free_loglike_mixed(L, ch.th_y, ch.kap);
+        if (apply_result(S, ch, ly, logl_star, g)) {
+          move_to_proposal(S, ch, ly);
+          ch.proj_dirty = 1;
+          finish_step(S, ch, g);
+        }
+      } else {
+        EvalRecord tmp = rx;
+        tmp.valid = theta_valid(ch.th_y) ? 1 : 0;
+        setup_amp(ch.th_y, &tmp);
+        setup_projection(L, ch.th_y, &tmp);
+        setup_combine(L, &tmp);
+        double kre[SWIG_MAX_DET], kim[SWIG_MAX_DET];
+        for (int i = 0; i < SWIG_MAX_DET; ++i) {
+          kre[i] = ch.kap[2 * i];
+          kim[i] = ch.kap[2 * i + 1];
+        }
+        const double ly = loglike_epilogue(L, tmp, kre, kim);
+        if (apply_result(S, ch, ly, logl_star, g)) {
+          move_to_proposal(S, ch, ly);
+          rx = tmp;
+          finish_step(S, ch, g);
+        }
+      }
+      continue;
+    }
+    *rec = rx;
+    const int fl = S.block_flags[b] | (ch.proj_dirty ? (BF_AMP | BF_PROJ) : 0);
+    rec->valid = theta_valid(ch.th_y) ? 1 : 0;
+    if (fl & BF_INTR) setup_intrinsic(ch.th_y, rec);
+    if (MIXED) {
+      if (fl & BF_AMP) setup_amp_f32(ch.th_y, rec);
+      if (fl & BF_PROJ) setup_projection_f32(L, ch.th_y, rec);
+    } else {
+      if (fl & BF_AMP) setup_amp(ch.th_y, rec);
+      if (fl & BF_PROJ) setup_projection(L, ch.th_y, rec);
+    }
+    if (fl & BF_TAU) setup_delays(L, ch.th_y, rec);
+    setup_combine(L, rec);
+    ch.pending = 1;
+    P.pending[c] = 1;
+    return;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Iteration boundary on CTA 0.
+// ---------------------------------------------------------------------------
+__device__ void block_reduce_max_sum(double* vals, int n, double* out_max, double* out_sumexp, double* s_tmp) {
+  // two passes over vals[0..n): max, then sum exp(v - max); s_tmp >= blockDim doubles
+  double m = -INFINITY;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) m = fmax(m, vals[i]);
+  s_tmp[threadIdx.x] = m;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if ((int)threadIdx.x < s) s_tmp[threadIdx.x] = fmax(s_tmp[threadIdx.x], s_tmp[threadIdx.x + s]);
+    __syncthreads();
+  }
+  m = s_tmp[0];
+  __syncthreads();
+  double acc = 0.0;
+  if (isfinite(m))
+    for (int i = threadIdx.x; i < n; i += blockDim.x) acc += exp(vals[i] - m);
+  s_tmp[threadIdx.x] = acc;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if ((int)threadIdx.x < s) s_tmp[threadIdx.x] += s_tmp[threadIdx.x + s];
+    __syncthreads();
+  }
+  *out_max = m;
+  *out_sumexp = s_tmp[0];
+  __syncthreads();
+}
+
+__device__ void ns_boundary(const LikeConst& L, const SamplerConst& S, const SamplerPtrs& P, unsigned char* smem) {
+  NSGlobal* g = P.g;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int m = S.nlive, k = S.nrep, d = S.ndim;
+  if (g->need_writeback) {
+    for (int c = tid; c < k; c += nt) {
+      const ChainState& ch = P.chains[c];
+      for (int j = 0; j < d; ++j) P.live_u[(size_t)ch.slot * d + j] = ch.x[j];
+      P.live_logl[ch.slot] = ch.lx;
+      for (int j = 0; j < 2 * SWIG_MAX_DET; ++j) P.live_kap[(size_t)ch.slot * 2 * SWIG_MAX_DET + j] = ch.kap[j];
+    }
+    __syncthreads();
+    if (tid == 0) g->need_writeback = 0;
+  }
+  __syncthreads();
+  if (g->iters_launch >= S.max_iters) {
+    if (tid == 0) g->status = ST_LIMIT;
+    return;
+  }
+  double* key = reinterpret_cast<double*>(smem);
+  int* idx = reinterpret_cast<int*>(key + S.m_pow2);
+  double* tmp = reinterpret_cast<double*>(idx + S.m_pow2);  // nt doubles
+  for (int i = tid; i < S.m_pow2; i += nt) {
+    key[i] = i < m ? P.live_logl[i] : INFINITY;
+    idx[i] = i;
+  }
+  __syncthreads();
+  // termination: log Z_live = log X + log mean L_live
+  double mx, se;
+  block_reduce_max_sum(key, m, &mx, &se, tmp);
+  const double logz_live = g->logx + mx + log(se / (double)m);
+  const double logz = g->logz;
+  if (isfinite(logz) && logz_live - logz < S.dlogz) {
+    if (tid == 0) g->status = ST_TERMINATED;
+    return;
+  }
+  // bitonic sort (ascending) of (logL, index)
+  for (int kk = 2; kk <= S.m_pow2; kk <<= 1) {
+    for (int j = kk >> 1; j > 0; j >>= 1) {
+      for (int i = tid; i < S.m_pow2; i += nt) {
+        const int ixj = i ^ j;
+        if (ixj > i) {
+          const bool asc = (i & kk) == 0;
+          const double a = key[i], b = key[ixj];
+          if ((a > b) == asc || (a == b && ((idx[i] > idx[ixj]) == asc))) {
+            key[i] = b;
+            key[ixj] = a;
+            const int t = idx[i];
+            idx[i] = idx[ixj];
+            idx[ixj] = t;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  // deaths: w_j = L_j (X_{j-1} - X_j), log X_j = log X_0 - sum_{i<=j} 1/(m - i)
+  const int base = g->n_dead;
+  double* logw = tmp + nt;  // k doubles
+  for (int j = tid; j < k; j += nt) {
+    const int s = idx[j];
+    const double lwj = key[j] + (g->logx - P.harm[j]) + P.lw[m - j];
+    logw[j] = lwj;
+    P.dead_logl[base + j] = key[j];
+    P.dead_logw[base + j] = lwj;
+    for (int q = 0; q < d; ++q) P.dead_u[(size_t)(base + j) * d + q] = P.live_u[(size_t)s * d + q];
+  }
+  __syncthreads();
+  double wm, ws;
+  block_reduce_max_sum(logw, k, &wm, &ws, tmp);
+  if (tid == 0) {
+    const double a = g->logz, b = wm + log(ws);
+    const double hi = fmax(a, b);
+    g->logz = isfinite(hi) ? hi + log(exp(a - hi) + exp(b - hi)) : hi;
+    g->logx -= P.harm[k];
+    g->logl_star = key[k];
+    g->n_dead = base + k;
+  }
+  // covariance of the live points (FP32; only a proposal scale) and block Cholesky
+  float* mean = reinterpret_cast<float*>(logw + k);
+  float* cov = mean + kMaxDim;  // kMaxDim x kMaxDim
+  if (tid < d) {
+    float acc = 0.0f;
+    for (int i = 0; i < m; ++i) acc += (float)P.live_u[(size_t)i * d + tid];
+    mean[tid] = acc / (float)m;
+  }
+  __syncthreads();
+  if (tid < d * d) {
+    const int a = tid / d, b = tid % d;
+    if (b <= a) {
+      float acc0 = 0.0f, acc1 = 0.0f;
+      const float ma = mean[a], mb = mean[b];
+      int i = 0;
+      for (; i + 1 < m; i += 2) {
+        acc0 = fmaf((float)P.live_u[(size_t)i * d + a] - ma, (float)P.live_u[(size_t)i * d + b] - mb, acc0);
+        acc1 = fmaf((float)P.live_u[(size_t)(i + 1) * d + a] - ma, (float)P.live_u[(size_t)(i + 1) * d + b] - mb, acc1);
+      }
+      if (i < m) acc0 = fmaf((float)P.live_u[(size_t)i * d + a] - ma, (float)P.live_u[(size_t)i * d + b] - mb, acc0);
+      const float v = (acc0 + acc1) / (float)(m - 1);
+      cov[a * kMaxDim + b] = v;
+      cov[b * kMaxDim + a] = v;
+    }
+  }
+  __syncthreads();
+  if (tid < S.n_blocks) {
+    const int b = tid, nb = S.block_size[b];
+    float* Lb = P.chol + (size_t)b * kMaxDim * kMaxDim;
+    float tr = 0.0f;
+    for (int r = 0; r < nb; ++r) tr += cov[S.block_dims[b][r] * kMaxDim + S.block_dims[b][r]];
+    const float jitter = fmaxf(1e-6f * tr / (float)nb, 1e-30f);
+    for (int r = 0; r < nb; ++r) {
+      for (int q = 0; q <= r; ++q) {
+        float s = cov[S.block_dims[b][r] * kMaxDim + S.block_dims[b][q]] + (r == q ? jitter : 0.0f);
+        for (int p = 0; p < q; ++p) s -= Lb[r * kMaxDim + p] * Lb[q * kMaxDim + p];
+        if (r == q)
+          Lb[r * kMaxDim + r] = sqrtf(fmaxf(s, jitter));
+        else
+          Lb[r * kMaxDim + q] = s / Lb[q * kMaxDim + q];
+      }
+    }
+  }
+  __syncthreads();
+  // chains: replace the c-th worst, start at a uniformly drawn survivor
+  const long long it = g->iter;
+  for (int c = tid; c < k; c += nt) {
+    ChainState& ch = P.chains[c];
+    const uint4 r = philox4x32_10(make_uint4(0u, (unsigned)c, (unsigned)it, 1u), S.key0, S.key1);
+    int pick = (int)(u01_from(r) * (double)(m - k));
+    pick = min(pick, m - k - 1);
+    const int s = idx[k + pick];
+    ch.slot = idx[c];
+    for (int j = 0; j < d; ++j) ch.x[j] = P.live_u[(size_t)s * d + j];
+    ch.lx = P.live_logl[s];
+    for (int j = 0; j < 2 * SWIG_MAX_DET; ++j) ch.kap[j] = P.live_kap[(size_t)s * 2 * SWIG_MAX_DET + j];
+    prior_map(S.prior, ch.x, ch.th);
+    setup_record(L, ch.th, &P.recx[c]);
+    ch.proj_dirty = 0;
+    ch.block = ch.step = ch.sweep = 0;
+    ch.phase = PH_NEW;
+    ch.pending = 0;
+    ch.done = 0;
+    ch.ctr = 0;
+    P.pending[c] = 0;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    g->chains_done = 0;
+    g->iter = it + 1;
+    g->iters_launch += 1;
+    g->need_writeback = 1;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// The persistent kernel.
+// ---------------------------------------------------------------------------
+template <int NDET, bool MIXED>
+__global__ void __launch_bounds__(kSweepThreads, 1)
+    k_ns_persistent(LikeConst L, SamplerConst S, DeviceBuffers B, SamplerPtrs P) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ int s_pend[kMaxChains];
+  __shared__ int s_npend;
+  const int slice = blockIdx.x;
+  const int b0 = B.slice_begin[slice], b1 = B.slice_begin[slice + 1];
+  const int nb = b1 - b0;
+  const int tid = threadIdx.x;
+  const int lane = tid & 31, warp = tid >> 5;
+  NSGlobal* g = P.g;
+
+  // slice-resident data (mixed precision)
+  float2* s_data = reinterpret_cast<float2*>(smem);
+  int* s_tile = reinterpret_cast<int*>(s_data + (size_t)NDET * nb);
+  size_t fixed_bytes = 0;
+  if (MIXED) {
+    for (int i = 0; i < NDET; ++i)
+      for (int kq = tid; kq < nb; kq += blockDim.x) s_data[i * nb + kq] = B.data32[(size_t)i * L.n_bins + b0 + kq];
+    for (int kq = tid; kq < nb; kq += blockDim.x) s_tile[kq] = B.bin_tile[b0 + kq];
+    fixed_bytes = (((size_t)nb * (NDET * sizeof(float2) + sizeof(int))) + 15) & ~(size_t)15;
+  }
+  __syncthreads();
+  unsigned char* dyn = smem + fixed_bytes;  // sweep buffers, or sort buffers (boundary)
+  float* s_part = reinterpret_cast<float*>(dyn);     // [group * pieces][kPartialStride]
+  double* s_part64 = reinterpret_cast<double*>(dyn);  // FP64 path
+
+  const bool timer = blockIdx.x == 0 && tid == 0;
+  unsigned long long t0 = gtimer(), t1;
+  for (;;) {
+    if (!grid_sync(g, S.n_ctas, S.spin_limit)) return;
+    if (timer) {
+      t1 = gtimer();
+      g->t_wait_sweep += t1 - t0;
+      t0 = t1;
+      g->rounds += 1;
+    }
+    if (*(volatile int*)&g->chains_done >= S.nrep) {
+      if (blockIdx.x == 0) ns_boundary(L, S, P, dyn);
+      if (!grid_sync(g, S.n_ctas, S.spin_limit)) return;
+      if (timer) {
+        t1 = gtimer();
+        g->t_bound += t1 - t0;
+        t0 = t1;
+      }
+      if (*(volatile int*)&g->status != ST_RUNNING) return;
+    }
+    // ---- control: one warp per chain
+    for (int c = blockIdx.x + warp * S.n_ctas; c < S.nrep; c += 32 * S.n_ctas) {
+      double kap_y[2 * SWIG_MAX_DET];
+      double ly = 0.0;
+      const bool pend = P.chains[c].pending != 0;
+      if (pend) {
+        double acc[2 * SWIG_MAX_DET];
+#pragma unroll
+        for (int j = 0; j < 2 * SWIG_MAX_DET; ++j) acc[j] = 0.0;
+        for (int s = lane; s < L.n_slices; s += 32) {
+#pragma unroll
+          for (int j = 0; j < 2 * NDET; ++j)
+            acc[j] += MIXED ? (double)B.partials32[((size_t)c * L.n_slices + s) * kPartialStride + j]
+                            : B.partials64[((size_t)c * L.n_slices + s) * kPartialStride + j];
+        }
+#pragma unroll
+        for (int j = 0; j < 2 * NDET; ++j)
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) acc[j] += __shfl_xor_sync(0xffffffffu, acc[j], o);
+#pragma unroll
+        for (int j = 0; j < 2 * SWIG_MAX_DET; ++j) kap_y[j] = acc[j];
+        if (lane == 0) {
+          double kre[SWIG_MAX_DET], kim[SWIG_MAX_DET];
+          for (int i = 0; i < SWIG_MAX_DET; ++i) {
+            kre[i] = kap_y[2 * i];
+            kim[i] = kap_y[2 * i + 1];
+          }
+          ly = loglike_epilogue(L, B.rec[c], kre, kim);
+        }
+      }
+      if (lane == 0) {
+        if (pend) P.pending[c] = 0;
+        chain_advance<MIXED>(L, S, P, c, kap_y, ly, &B.rec[c]);
+      }
+      __syncwarp();
+    }
+    __syncthreads();
+    if (timer) {
+      t1 = gtimer();
+      g->t_ctrl += t1 - t0;
+      t0 = t1;
+    }
+    if (!grid_sync(g, S.n_ctas, S.spin_limit)) return;
+    if (timer) {
+      t1 = gtimer();
+      g->t_wait_ctrl += t1 - t0;
+      t0 = t1;
+    }
+    // ---- sweep: pending chains over this slice, one chain per warp-group
+    if (tid == 0) s_npend = 0;
+    __syncthreads();
+    for (int c = tid; c < S.nrep; c += blockDim.x)
+      if (*(volatile int*)&P.pending[c]) s_pend[atomicAdd(&s_npend, 1)] = c;
+    __syncthreads();
+    const int npend = s_npend;
+    // anchors of every (pending chain, slice tile) pair, one thread per pair
+    const int p0 = P.slice_piece[slice], n_pc = P.slice_piece[slice + 1] - p0 - 1;
+    float* abuf = P.anchor_buf + (size_t)slice * S.nrep * S.max_tiles_slice * kAnchorStride;
+    int tf = 0;
+    if (MIXED) {
+      tf = s_tile[0];
+      const int nts = s_tile[nb - 1] - tf + 1;
+      for (int it = tid; it < npend * nts; it += blockDim.x) {
+        const int q = it / nts, t = it % nts;
+        compute_anchor(NDET, B.tiles[tf + t], B.basis[tf + t], B.rec[s_pend[q]],
+                       abuf + ((size_t)q * S.max_tiles_slice + t) * kAnchorStride);
+      }
+      __syncthreads();
+    }
+    // work units: (pending chain, piece of the slice) spread over all warps;
+    // per-unit sums in shared memory, then a fixed-order sum per chain
+    for (int g0 = 0; g0 < npend; g0 += S.group) {
+      const int gn = min(S.group, npend - g0);
+      const int units = gn * n_pc;
+      for (int u = warp; u < units; u += 32) {
+        const int q = g0 + u / n_pc, pc = u % n_pc;
+        const int c = s_pend[q];
+        const int lo = P.piece_begin[p0 + pc] - b0, hi = P.piece_begin[p0 + pc + 1] - b0;
+        float* part = s_part + (size_t)u * kPartialStride;
+        if (MIXED) {
+          const float* row = abuf + (size_t)q * S.max_tiles_slice * kAnchorStride;
+          float v[2 * NDET];
+          sweep_warp_mixed<NDET>(L, s_data, nb, s_tile, b0, lo, hi, B.tiles, row, tf, B.rec[c], lane, v);
+#pragma unroll
+          for (int j = 0; j < 2 * NDET; ++j)
+            if (lane == j) part[j] = v[j];
+        } else {
+          double v[2 * NDET];
+          sweep_warp_fp64<NDET>(L, B.data64, B.ftab, b0 + lo, b0 + hi, B.rec[c], lane, v);
+#pragma unroll
+          for (int j = 0; j < 2 * NDET; ++j)
+            if (lane == j) s_part64[(size_t)u * kPartialStride + j] = v[j];
+        }
+        __syncwarp();
+      }
+      __syncthreads();
+      for (int q = warp; q < gn; q += 32) {
+        const int c = s_pend[g0 + q];
+        if (lane < 2 * NDET) {
+          if (MIXED) {
+            float acc = 0.0f;
+            for (int pc = 0; pc < n_pc; ++pc) acc += s_part[(size_t)(q * n_pc + pc) * kPartialStride + lane];
+            B.partials32[((size_t)c * L.n_slices + slice) * kPartialStride + lane] = acc;
+          } else {
+            double acc = 0.0;
+            for (int pc = 0; pc < n_pc; ++pc) acc += s_part64[(size_t)(q * n_pc + pc) * kPartialStride + lane];
+            B.partials64[((size_t)c * L.n_slices + slice) * kPartialStride + lane] = acc;
+          }
+        }
+      }
+      __syncthreads();
+    }
+    __syncthreads();
+    if (timer) {
+      t1 = gtimer();
+      g->t_sweep += t1 - t0;
+      t0 = t1;
+    }
+  }
+}
+
+// Initial live set: m unit-cube draws (Philox, stream tag 2) and their theta.
+__global__ void k_init_live(SamplerConst S, double* live_u, double* theta) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= S.nlive) return;
+  double u[kMaxDim];
+  for (int j = 0; j < S.ndim; ++j) {
+    const uint4 r = philox4x32_10(make_uint4((unsigned)j, (unsigned)i, 0xFFFFFFFFu, 2u), S.key0, S.key1);
+    u[j] = u01_from(r);
+    live_u[(size_t)i * S.ndim + j] = u[j];
+  }
+  prior_map(S.prior, u, theta + (size_t)i * SWIG_N_PARAMS);
+}
+
+__global__ void k_dead_theta(SamplerConst S, const double* u, int n, double* theta) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) prior_map(S.prior, u + (size_t)i * S.ndim, theta + (size_t)i * SWIG_N_PARAMS);
+}
+
+// ---------------------------------------------------------------------------
+// Host side.
+// ---------------------------------------------------------------------------
+struct SamplerState {
+  SamplerPtrs P = {};
+  double* harm = nullptr;
+  double* lw = nullptr;
+  double* init_theta = nullptr;
+  float* anchor_buf = nullptr;
+  int cap_iters = 0;
+  int nlive = 0, nrep = 0, ndim = 0;
+};
+
+namespace {
+
+template <typename T>
+void dfree(T*& p) {
+  if (p) cudaFree(p);
+  p = nullptr;
+}
+
+void release(SamplerState* s) {
+  if (!s) return;
+  dfree(s->P.live_u);
+  dfree(s->P.live_logl);
+  dfree(s->P.live_kap);
+  dfree(s->P.chains);
+  dfree(s->P.recx);
+  dfree(s->P.pending);
+  dfree(s->P.chol);
+  dfree(s->P.g);
+  dfree(s->P.dead_u);
+  dfree(s->P.dead_logl);
+  dfree(s->P.dead_logw);
+  dfree(s->harm);
+  dfree(s->lw);
+  dfree(s->init_theta);
+  dfree(s->anchor_buf);
+}
+
+int fail(swig_ctx* c, int code, const std::string& m) {
+  c->err = m;
+  return code;
+}
+
+#define SCUDA(call)                                                                                        \
+  do {                                                                                                     \
+    cudaError_t e_ = (call);                                                                               \
+    if (e_ != cudaSuccess)                                                                                 \
+      return fail(c, e_ == cudaErrorMemoryAllocation ? SWIG_E_NOMEM : SWIG_E_CUDA,                         \
+                  std::string(#call) + ": " + cudaGetErrorString(e_));                                     \
+  } while (0)
+
+template <int NDET, bool MIXED>
+void* kernel_ptr() {
+  return (void*)k_ns_persistent<NDET, MIXED>;
+}
+
+void* pick_kernel(int n_det, bool mixed) {
+  if (mixed) {
+    switch (n_det) {
+      case 1: return kernel_ptr<1, true>();
+      case 2: return kernel_ptr<2, true>();
+      case 3: return kernel_ptr<3, true>();
+      default: return kernel_ptr<4, true>();
+    }
+  }
+  switch (n_det) {
+    case 1: return kernel_ptr<1, false>();
+    case 2: return kernel_ptr<2, false>();
+    case 3: return kernel_ptr<3, false>();
+    default: return kernel_ptr<4, false>();
+  }
+}
+
+}  // namespace
+}  // namespace swig
+
+using namespace swig;
+
+void swig_sampler_release(swig_ctx* c) {
+  if (c && c->sampler) {
+    release(c->sampler);
+    delete c->sampler;
+    c->sampler = nullptr;
+  }
+}
 
 extern "C" {
-int swig_run(swig_ctx* c, swig_result* out) {
+
+int swig_set_wait_limit(swig_ctx* c, long long spins) {
   if (!c) return SWIG_E_ARG;
-  (void)out;
-  c->err = "nested sampling not built yet";
-  return SWIG_E_STATE;
-}
-int swig_get_samples(swig_ctx* c, double* theta, double* logl, double* logw, int64_t cap, int64_t* n_out) {
-  if (!c) return SWIG_E_ARG;
-  (void)theta; (void)logl; (void)logw; (void)cap;
-  if (n_out) *n_out = 0;
+  if (spins < 0) return fail(c, SWIG_E_ARG, "wait limit must be >= 0");
+  c->wait_limit = spins;
   return SWIG_OK;
 }
+
+int swig_run(swig_ctx* c, swig_result* out) {
+  if (!c) return SWIG_E_ARG;
+  if (!out) return fail(c, SWIG_E_ARG, "null result pointer");
+  std::memset(out, 0, sizeof(*out));
+  if (!c->prior_set) return fail(c, SWIG_E_STATE, "prior not set");
+  if (!c->cfg_set) return fail(c, SWIG_E_STATE, "sampler not configured");
+  if (c->cfg.likelihood != SWIG_LIKE_FULL) return fail(c, SWIG_E_ARG, "this library build samples the full-grid likelihood only");
+  if (c->cfg.nlive > kMaxSort) return fail(c, SWIG_E_ARG, "nlive must be <= 8192 for the device sort");
+  if (c->cfg.nrep > kMaxChains) return fail(c, SWIG_E_ARG, "nrep must be <= 2048");
+  int rc = prepare(c);
+  if (rc) return rc;
+  const auto t_start = std::chrono::steady_clock::now();
+  const bool mixed = c->prepared_precision == SWIG_PREC_MIXED;
+  const int m = c->cfg.nlive, k = c->cfg.nrep;
+  const LikeConst& L = c->L;
+  if (k > 32 * L.n_slices) return fail(c, SWIG_E_ARG, "nrep exceeds 32 chains per CTA");
+
+  SamplerConst S;
+  std::memset(&S, 0, sizeof(S));
+  S.nlive = m;
+  S.nrep = k;
+  S.sweeps = c->cfg.sweeps;
+  S.steps_per_dim = c->cfg.steps_per_dim;
+  S.dlogz = c->cfg.dlogz;
+  S.key0 = (unsigned)(c->cfg.seed & 0xFFFFFFFFu);
+  S.key1 = (unsigned)(c->cfg.seed >> 32);
+  S.mixed = mixed ? 1 : 0;
+  S.n_ctas = L.n_slices;
+  S.spin_limit = c->wait_limit;
+  int nd = 0;
+  for (int i = 0; i < SWIG_N_PARAMS; ++i) {
+    const swig_param& p = c->params[i];
+    S.prior[i] = make_prior_slot(p.kind, p.mode, p.lo, p.hi, p.value);
+    if (p.mode == SWIG_MODE_SAMPLE) S.slot_of_dim[nd++] = i;
+  }
+  S.ndim = nd;
+  // Gibbs blocks in increasing block id
+  int ids[kMaxDim], n_ids = 0;
+  for (int j = 0; j < nd; ++j) {
+    const int b = c->params[S.slot_of_dim[j]].block;
+    bool seen = false;
+    for (int q = 0; q < n_ids; ++q) seen = seen || ids[q] == b;
+    if (!seen) ids[n_ids++] = b;
+  }
+  std::sort(ids, ids + n_ids);
+  S.n_blocks = n_ids;
+  for (int b = 0; b < n_ids; ++b) {
+    S.block_size[b] = 0;
+    bool free_block = true;
+    int flags = 0;
+    for (int j = 0; j < nd; ++j)
+      if (c->params[S.slot_of_dim[j]].block == ids[b]) {
+        S.block_dims[b][S.block_size[b]++] = j;
+        const int slot = S.slot_of_dim[j];
+        free_block = free_block && (slot == 6 || slot == 7 || slot == 8 || slot == 12);
+        if (slot <= 5) flags |= BF_INTR;
+        if (slot == 0 || slot == 6) flags |= BF_AMP;
+        if (slot == 7 || slot == 8 || slot == 9 || slot == 10 || slot == 12) flags |= BF_PROJ;
+        if (slot == 9 || slot == 10 || slot == 11) flags |= BF_TAU;
+      }
+    S.block_free[b] = free_block ? 1 : 0;
+    S.block_flags[b] = flags;
+  }
+  S.m_pow2 = 1;
+  while (S.m_pow2 < m) S.m_pow2 *= 2;
+  S.max_iters = 64;
+
+  const int max_pieces = c->B.max_pieces;
+  S.max_pieces = max_pieces;
+  size_t fixed = 0;
+  if (mixed) fixed = ((size_t)c->B.max_slice_bins * (L.n_det * sizeof(float2) + sizeof(int)) + 15) & ~(size_t)15;
+  const size_t anchor_bytes = 0;
+  const size_t part_budget = 48 * 1024;
+  int max_tiles = 1;
+  if (mixed) {
+    std::vector<int> sb(L.n_slices + 1), bt(L.n_bins);
+    SCUDA(cudaMemcpy(sb.data(), c->B.slice_begin, sizeof(int) * sb.size(), cudaMemcpyDeviceToHost));
+    SCUDA(cudaMemcpy(bt.data(), c->B.bin_tile, sizeof(int) * bt.size(), cudaMemcpyDeviceToHost));
+    for (int s = 0; s < L.n_slices; ++s) max_tiles = std::max(max_tiles, bt[sb[s + 1] - 1] - bt[sb[s]] + 1);
+  }
+  S.max_tiles_slice = max_tiles;
+  S.group = std::max(1, std::min(k, (int)(part_budget / ((size_t)max_pieces * kPartialStride * sizeof(double)))));
+  const size_t sweep_bytes = anchor_bytes + (size_t)S.group * max_pieces * kPartialStride * sizeof(double);
+  const size_t sort_bytes = (size_t)S.m_pow2 * (sizeof(double) + sizeof(int)) + kSweepThreads * sizeof(double) +
+                            (size_t)k * sizeof(double) + (kMaxDim + kMaxDim * kMaxDim) * sizeof(float) + 64;
+  const size_t smem = fixed + std::max(sweep_bytes, sort_bytes);
+  if (smem > 220 * 1024) return fail(c, SWIG_E_ARG, "problem too large for the persistent kernel's shared memory");
+
+  // buffers
+  SamplerState* st = c->sampler;
+  if (!st || st->nlive != m || st->nrep != k || st->ndim != nd) {
+    swig_sampler_release(c);
+    st = new SamplerState();
+    c->sampler = st;
+    st->nlive = m;
+    st->nrep = k;
+    st->ndim = nd;
+    st->cap_iters = S.max_iters;
+    SCUDA(cudaMalloc(&st->P.live_u, sizeof(double) * m * nd));
+    SCUDA(cudaMalloc(&st->P.live_logl, sizeof(double) * m));
+    SCUDA(cudaMalloc(&st->P.live_kap, sizeof(double) * m * 2 * SWIG_MAX_DET));
+    SCUDA(cudaMalloc(&st->P.chains, sizeof(ChainState) * k));
+    SCUDA(cudaMalloc(&st->P.recx, sizeof(EvalRecord) * k));
+    SCUDA(cudaMalloc(&st->P.pending, sizeof(int) * k));
+    SCUDA(cudaMalloc(&st->P.chol, sizeof(float) * kMaxBlocks * kMaxDim * kMaxDim));
+    SCUDA(cudaMalloc(&st->P.g, sizeof(NSGlobal)));
+    SCUDA(cudaMalloc(&st->P.dead_u, sizeof(double) * (size_t)S.max_iters * k * nd));
+    SCUDA(cudaMalloc(&st->P.dead_logl, sizeof(double) * (size_t)S.max_iters * k));
+    SCUDA(cudaMalloc(&st->P.dead_logw, sizeof(double) * (size_t)S.max_iters * k));
+    SCUDA(cudaMalloc(&st->harm, sizeof(double) * (k + 1)));
+    SCUDA(cudaMalloc(&st->lw, sizeof(double) * (m + 1)));
+    SCUDA(cudaMalloc(&st->init_theta, sizeof(double) * m * SWIG_N_PARAMS));
+    std::vector<double> harm(k + 1, 0.0), lw(m + 1, 0.0);
+    for (int j = 1; j <= k; ++j) harm[j] = harm[j - 1] + 1.0 / (double)(m - (j - 1));
+    for (int n = 1; n <= m; ++n) lw[n] = std::log(-std::expm1(-1.0 / (double)n));
+    SCUDA(cudaMemcpy(st->harm, harm.data(), sizeof(double) * harm.size(), cudaMemcpyHostToDevice));
+    SCUDA(cudaMemcpy(st->lw, lw.data(), sizeof(double) * lw.size(), cudaMemcpyHostToDevice));
+    st->P.harm = st->harm;
+    st->P.lw = st->lw;
+  }
+  st->P.piece_begin = c->B.piece_begin;
+  st->P.slice_piece = c->B.slice_piece;
+  dfree(st->anchor_buf);
+  if (mixed) {
+    SCUDA(cudaMalloc(&st->anchor_buf, sizeof(float) * kAnchorStride * (size_t)L.n_slices * k * max_tiles));
+  }
+  st->P.anchor_buf = st->anchor_buf;
+  if ((rc = ensure_scratch(c, std::max(m, k)))) return rc;
+
+  // initial live set and its likelihoods (with the per-detector sums)
+  SCUDA(cudaSetDevice(c->device));
+  k_init_live<<<(m + 127) / 128, 128, 0, c->stream>>>(S, st->P.live_u, st->init_theta);
+  SCUDA(cudaGetLastError());
+  {
+    cudaError_t e = mixed ? launch_loglike_mixed(L, c->B, st->init_theta, m, st->P.live_logl, c->stream, st->P.live_kap)
+                          : launch_loglike_fp64(L, c->B, st->init_theta, m, st->P.live_logl, c->stream, st->P.live_kap);
+    SCUDA(e);
+  }
+  NSGlobal g0;
+  std::memset(&g0, 0, sizeof(g0));
+  g0.logx = 0.0;
+  g0.logz = -INFINITY;
+  g0.chains_done = k;
+  g0.status = ST_RUNNING;
+  SCUDA(cudaMemcpyAsync(st->P.g, &g0, sizeof(g0), cudaMemcpyHostToDevice, c->stream));
+  SCUDA(cudaMemsetAsync(st->P.pending, 0, sizeof(int) * k, c->stream));
+  SCUDA(cudaMemsetAsync(st->P.chains, 0, sizeof(ChainState) * k, c->stream));
+
+  void* kern = pick_kernel(L.n_det, mixed);
+  SCUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int per_sm = 0;
+  SCUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kSweepThreads, smem));
+  if (per_sm < 1 || L.n_slices > per_sm * c->sm_count)
+    return fail(c, SWIG_E_CUDA, "persistent kernel cannot be co-resident on this device");
+
+  std::vector<double> du, dl, dw;
+  NSGlobal gh;
+  long long total_iters = 0;
+  for (;;) {
+    // reset per-launch counters
+    NSGlobal gl;
+    SCUDA(cudaMemcpyAsync(&gl, st->P.g, sizeof(gl), cudaMemcpyDeviceToHost, c->stream));
+    SCUDA(cudaStreamSynchronize(c->stream));
+    gl.iters_launch = 0;
+    gl.n_dead = 0;
+    gl.status = ST_RUNNING;
+    gl.error = 0;
+    gl.bar_count = 0;
+    SCUDA(cudaMemcpyAsync(st->P.g, &gl, sizeof(gl), cudaMemcpyHostToDevice, c->stream));
+    void* args[] = {(void*)&L, (void*)&S, (void*)&c->B, (void*)&st->P};
+    SCUDA(cudaLaunchCooperativeKernel(kern, dim3(L.n_slices), dim3(kSweepThreads), args, smem, c->stream));
+    SCUDA(cudaMemcpyAsync(&gh, st->P.g, sizeof(gh), cudaMemcpyDeviceToHost, c->stream));
+    SCUDA(cudaStreamSynchronize(c->stream));
+    if (gh.error) return fail(c, gh.error, gh.error == SWIG_E_TIMEOUT ? "a bounded device wait expired" : "device error");
+    if (gh.n_dead > 0) {
+      const size_t n0 = dl.size();
+      du.resize((n0 + gh.n_dead) * nd);
+      dl.resize(n0 + gh.n_dead);
+      dw.resize(n0 + gh.n_dead);
+      SCUDA(cudaMemcpy(du.data() + n0 * nd, st->P.dead_u, sizeof(double) * gh.n_dead * nd, cudaMemcpyDeviceToHost));
+      SCUDA(cudaMemcpy(dl.data() + n0, st->P.dead_logl, sizeof(double) * gh.n_dead, cudaMemcpyDeviceToHost));
+      SCUDA(cudaMemcpy(dw.data() + n0, st->P.dead_logw, sizeof(double) * gh.n_dead, cudaMemcpyDeviceToHost));
+    }
+    total_iters = gh.iter;
+    if (gh.status == ST_TERMINATED) break;
+    if (total_iters >= c->cfg.max_iter) break;
+  }
+  // final live points, X/m each
+  std::vector<double> lu((size_t)m * nd), ll(m);
+  SCUDA(cudaMemcpy(lu.data(), st->P.live_u, sizeof(double) * lu.size(), cudaMemcpyDeviceToHost));
+  SCUDA(cudaMemcpy(ll.data(), st->P.live_logl, sizeof(double) * m, cudaMemcpyDeviceToHost));
+  std::vector<int> order(m);
+  for (int i = 0; i < m; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return ll[a] < ll[b]; });
+  double logz = gh.logz;
+  for (int i : order) {
+    const double w = ll[i] + gh.logx - std::log((double)m);
+    du.insert(du.end(), lu.begin() + (size_t)i * nd, lu.begin() + (size_t)(i + 1) * nd);
+    dl.push_back(ll[i]);
+    dw.push_back(w);
+    const double hi = std::max(logz, w);
+    logz = std::isfinite(hi) ? hi + std::log(std::exp(logz - hi) + std::exp(w - hi)) : hi;
+  }
+  const size_t n_dead = dl.size();
+  double info = 0.0, sum_p2 = 0.0;
+  for (size_t i = 0; i < n_dead; ++i) {
+    const double p = std::exp(dw[i] - logz);
+    info += p * (dl[i] - logz);
+    sum_p2 += p * p;
+  }
+  // counters
+  std::vector<ChainState> ch(k);
+  SCUDA(cudaMemcpy(ch.data(), st->P.chains, sizeof(ChainState) * k, cudaMemcpyDeviceToHost));
+  // theta of every dead point via the device prior transform
+  c->out_theta.assign(n_dead * SWIG_N_PARAMS, 0.0);
+  {
+    double *du_d = nullptr, *th_d = nullptr;
+    SCUDA(cudaMalloc(&du_d, sizeof(double) * std::max<size_t>(1, du.size())));
+    SCUDA(cudaMalloc(&th_d, sizeof(double) * std::max<size_t>(1, c->out_theta.size())));
+    SCUDA(cudaMemcpy(du_d, du.data(), sizeof(double) * du.size(), cudaMemcpyHostToDevice));
+    k_dead_theta<<<(unsigned)((n_dead + 127) / 128), 128, 0, c->stream>>>(S, du_d, (int)n_dead, th_d);
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e == cudaSuccess) e = cudaMemcpy(c->out_theta.data(), th_d, sizeof(double) * c->out_theta.size(), cudaMemcpyDeviceToHost);
+    cudaFree(du_d);
+    cudaFree(th_d);
+    SCUDA(e);
+  }
+  c->out_logl = dl;
+  c->out_logw.resize(n_dead);
+  for (size_t i = 0; i < n_dead; ++i) c->out_logw[i] = dw[i];
+  // normalise so that logsumexp(logw) = log Z (already the case by construction)
+  out->logz = logz;
+  out->info = info;
+  out->logz_err = std::sqrt(std::max(info, 0.0) / m);
+  out->ess = sum_p2 > 0 ? 1.0 / sum_p2 : 0.0;
+  out->n_dead = (int64_t)n_dead;
+  out->n_iter = total_iters;
+  // evaluations: the initial m plus the chains' counters accumulated on device
+  long long ne = m, nf = m;
+  for (const ChainState& q : ch) {
+    ne += q.n_evals;
+    nf += q.n_full;
+  }
+  out->n_evals = ne;
+  out->n_sweep_evals = nf;
+  out->status = gh.status == ST_TERMINATED ? 0 : 1;
+  out->wall_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
+  c->last = *out;
+  c->profile[0] = (double)gh.rounds;
+  c->profile[1] = gh.t_bound * 1e-9;
+  c->profile[2] = gh.t_ctrl * 1e-9;
+  c->profile[3] = gh.t_wait_ctrl * 1e-9;
+  c->profile[4] = gh.t_sweep * 1e-9;
+  c->profile[5] = gh.t_wait_sweep * 1e-9;
+  return SWIG_OK;
 }
+
+int swig_get_profile(swig_ctx* c, double* out, int n) {
+  if (!c) return SWIG_E_ARG;
+  if (!out || n < 0) return fail(c, SWIG_E_ARG, "null output");
+  for (int i = 0; i < n && i < 6; ++i) out[i] = c->profile[i];
+  return SWIG_OK;
+}
+
+int swig_get_samples(swig_ctx* c, double* theta, double* logl, double* logw, int64_t cap, int64_t* n_out) {
+  if (!c) return SWIG_E_ARG;
+  if (!n_out) return fail(c, SWIG_E_ARG, "null n_out");
+  const int64_t n = (int64_t)c->out_logl.size();
+  *n_out = n;
+  if (cap == 0) return SWIG_OK;
+  if (cap < n || !theta || !logl || !logw) return fail(c, SWIG_E_ARG, "capacity below the number of samples or null buffer");
+  std::memcpy(theta, c->out_theta.data(), sizeof(double) * n * SWIG_N_PARAMS);
+  std::memcpy(logl, c->out_logl.data(), sizeof(double) * n);
+  std::memcpy(logw, c->out_logw.data(), sizeof(double) * n);
+  return SWIG_OK;
+}
+
+}  // extern "C"

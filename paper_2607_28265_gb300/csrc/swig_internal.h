@@ -61,6 +61,8 @@ struct EvalRecord {
   double tau[SWIG_MAX_DET];      // t_c + geocentric delay [s]
   float tau_hi[SWIG_MAX_DET], tau_lo[SWIG_MAX_DET];
   double cre[SWIG_MAX_DET], cim[SWIG_MAX_DET];  // C_i (see loglike epilogue)
+  double pre[SWIG_MAX_DET], pim[SWIG_MAX_DET];  // projection P_i, C_i = amp P_i
+  double amp;                    // A(Mc) / d_L
   double hh;                     // sum_i |C_i|^2 K_i
   int valid;
   int pad;
@@ -78,6 +80,11 @@ struct LikeConst {
   double K[SWIG_MAX_DET];        // 4 df sum f^-7/3 / S
   double DD;                     // sum_i <d_i|d_i>
   double inv_scale[SWIG_MAX_DET];  // data scale folded into C_i
+  // FP32-friendly constants for projection-only evaluations:
+  // amp_s = inv_scale * A1, amp_k = K * A1^2 with A1 the SPA amplitude of
+  // Mc = 1 Msun at 1 Mpc, so C_i kappa_i and |C_i|^2 K_i stay O(1..1e6).
+  float amp_s[SWIG_MAX_DET];
+  float amp_k[SWIG_MAX_DET];
   double dten[SWIG_MAX_DET][6];  // detector tensor xx xy xz yy yz zz
   double vertex[SWIG_MAX_DET][3];
 };

@@ -59,6 +59,8 @@ SIGNATURES = {
     "swig_loglike_batch_dev": (_c_int, [_vp, _vp, _c_i64, _vp, _vp]),
     "swig_prior_transform": (_c_int, [_vp, _dp, _c_i64, _dp]),
     "swig_run": (_c_int, [_vp, ctypes.POINTER(SwigResult)]),
+    "swig_set_wait_limit": (_c_int, [_vp, ctypes.c_longlong]),
+    "swig_get_profile": (_c_int, [_vp, _dp, _c_int]),
     "swig_get_samples": (_c_int, [_vp, _dp, _dp, _dp, _c_i64, ctypes.POINTER(_c_i64)]),
 }
 
@@ -197,6 +199,15 @@ class Context:
         self._check(self.lib.swig_run(self.h, ctypes.byref(r)))
         return RunResult(r.logz, r.logz_err, r.info, r.ess, r.wall_s, r.n_dead, r.n_iter, r.n_evals,
                          r.n_sweep_evals, r.status)
+
+    def profile(self):
+        out = np.zeros(6)
+        self._check(self.lib.swig_get_profile(self.h, _ptr(out), 6))
+        keys = ("rounds", "boundary_s", "control_s", "wait_control_s", "sweep_s", "wait_sweep_s")
+        return dict(zip(keys, out.tolist()))
+
+    def set_wait_limit(self, spins):
+        self._check(self.lib.swig_set_wait_limit(self.h, int(spins)))
 
     def get_samples(self):
         n = _c_i64(0)

@@ -117,13 +117,16 @@ def test_invalid_theta_empty_batch_and_determinism(cfg1):
 
 
 def test_large_batch_is_split_consistently(cfg1):
+    """Batches above 4096 are split; the work partition (and so the FP32
+    summation grouping) depends on the batch size, so results agree to a few
+    FP32 roundings of the per-detector sums rather than bit for bit."""
     wl, ev, th = cfg1
     ctx = swig.context_for_workload(wl, ev.data, ev.psds, ev.gmst)
     ctx.set_sampler(nlive=100, nrep=10, precision=swig.PREC_MIXED)
     thetas = _thetas(wl, th, 5000, 0, seed=4)
     big = ctx.loglike_batch(thetas)
     small = ctx.loglike_batch(thetas[4090:4110])
-    assert np.array_equal(big[4090:4110], small)
+    assert np.allclose(big[4090:4110], small, rtol=1e-8, atol=1e-4)
     idx = [0, 4095, 4096, 4999]
     want = np.array([L.loglike(ev, thetas[i]) for i in idx])
     assert np.all(np.abs(big[idx] - want) <= _tol(want))
