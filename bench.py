@@ -1,0 +1,387 @@
+"""Benchmark: nested-sampling posteriors of a 128 s, three-detector BNS signal.
+
+One step is one complete posterior: a Slice-within-Gibbs nested-sampling run
+(Sec. 2.2, 2.3, 3.2 of the paper) from prior draws to the termination rule,
+on the full uncompressed frequency grid (259,585 bins per detector), through
+the C-ABI library.  The metric is logL evaluations per second (all likelihood
+evaluations, including the projection-only updates of cached blocks, as the
+paper counts them) and wall-seconds per posterior (= ms_per_step / 1000).
+
+Output: one JSON line on rank 0.  ``--impl reference`` times the FP64 CPU
+oracle on the same workload instead (bounded samples of likelihood
+evaluations per step on the host cores).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import swig_inputs as si  # noqa: E402
+
+SFU_OPS_PER_CLK_SM = 16   # sin/cos results per clock per SM (sm_100-class SFU)
+SFU_OPS_PER_BIN_DET = 2   # one sine and one cosine per bin and detector
+METRIC = "logL evals/s (128 s 3-det BNS) and wall-s/posterior, plain vs learned+mixed"
+
+
+def workload_description(wl):
+    return (f"{wl.name}: 128 s, H1/L1/V1, {wl.f_min:g}-{wl.f_max:g} Hz, df=1/128 Hz, {wl.n_bins} bins/det, "
+            "TaylorF2 aligned-spin+tidal, 12 sampled params + phi_c marginalised, "
+            f"nlive={wl.nlive}, nrep={wl.nrep}, {wl.steps_per_dim} slice steps/dim, M=1, mixed precision")
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def build_context(wl, seed_offset=0):
+    """Synthetic event through the library's own API: PSDs and noise from the
+    seeded input module, the injection computed by the library (device FP64)."""
+    from paper_2607_28265_gb300 import swig
+
+    ctx = swig.Context(0)
+    ctx.set_grid(wl.f_min, wl.f_max, wl.df)
+    for i, name in enumerate(wl.detectors):
+        ctx.set_detector(i, *si.site_vectors(name))
+    ctx.set_time_ref(si.gmst_from_gps(si.REFERENCE_GPS))
+    psds = wl.psds()
+    for i, s in enumerate(psds):
+        ctx.set_psd(i, s)
+    ctx.set_prior(wl.params)
+    u = np.asarray(wl.injection)
+    sampled = wl.sampled()
+    th = ctx.prior_transform(u[sampled][None, :])[0]
+    th[si.IDX["phic"]] = 2.0 * math.pi * u[si.IDX["phic"]]
+    noise = np.array(wl.noise())
+    data, th_used = ctx.inject(th, len(wl.detectors), target_snr=wl.target_snr, noise=noise)
+    for i in range(len(wl.detectors)):
+        ctx.set_data(i, data[i])
+    ctx.set_sampler(nlive=wl.nlive, nrep=wl.nrep, sweeps=wl.sweeps, steps_per_dim=wl.steps_per_dim,
+                    seed=wl.sampler_seed + seed_offset, precision=swig.PREC_MIXED)
+    return ctx, data, psds, th_used
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device=0):
+        self.device = device
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.device}", f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+        return False
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for l in getattr(self, "lines", []):
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def run_gpu(args, rank, world):
+    import torch
+
+    from paper_2607_28265_gb300 import swig
+
+    torch.cuda.set_device(0 if world == 1 else int(os.environ.get("LOCAL_RANK", rank)))
+    wl = si.config2()
+    ctx, data, psds, th_inj = build_context(wl, seed_offset=1000 * rank)
+    stream = torch.cuda.current_stream()
+    ctx.set_stream(stream.cuda_stream)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # > L2 (129 MB)
+
+    def step_device():
+        flush.zero_()  # evict L2 between steps
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        r = ctx.run()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        prof = ctx.profile()
+        return r, e0.elapsed_time(e1), prof
+
+    # warm-up (includes the one-off host preparation of the grid tables)
+    for _ in range(args.warmup):
+        step_device()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    results = []
+    launches0 = ctx.profile()["kernel_launches"]
+    with ClockSampler(int(os.environ.get("LOCAL_RANK", 0))) as clocks:
+        for _ in range(args.steps):
+            results.append(step_device())
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    launches = int(ctx.profile()["kernel_launches"] - launches0)
+    total_ms = sum(ms for _, ms, _ in results)
+    total_evals = sum(r.n_evals for r, _, _ in results)
+    full_evals = sum(r.n_sweep_evals for r, _, _ in results)
+    pers_ms = sum(p["persistent_ms"] for _, _, p in results)
+    pers_launch = sum(p["persistent_launches"] for _, _, p in results)
+    bindet = sum(p["bin_det_evals"] for _, _, p in results)
+
+    # end to end through the public API from pinned host buffers: set data and
+    # PSDs (host -> device inside the library), run, read back the samples
+    pinned = [torch.from_numpy(np.ascontiguousarray(d)).pin_memory() for d in data]
+    pinned_psd = [torch.from_numpy(np.ascontiguousarray(s)).pin_memory() for s in psds]
+    e2e_ms, e2e_evals = [], 0
+    h2d0, d2h0 = ctx.profile()["h2d_bytes"], ctx.profile()["d2h_bytes"]
+    for _ in range(max(1, args.e2e_steps)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for i in range(len(pinned)):
+            ctx.set_data(i, pinned[i].numpy())
+            ctx.set_psd(i, pinned_psd[i].numpy())
+        r = ctx.run()
+        th_s, ll_s, lw_s = ctx.get_samples()
+        torch.cuda.synchronize()
+        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+        e2e_evals += r.n_evals
+    n_e2e = max(1, args.e2e_steps)
+    h2d = (ctx.profile()["h2d_bytes"] - h2d0) / n_e2e
+    d2h = (ctx.profile()["d2h_bytes"] - d2h0) / n_e2e
+
+    # max over ranks
+    t_local = np.array([total_ms, total_evals, sum(e2e_ms), e2e_evals, full_evals], dtype=np.float64)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor(t_local, device="cuda")
+        tmax = t.clone()
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+        tsum = t.clone()
+        dist.all_reduce(tsum, op=dist.ReduceOp.SUM)
+        total_ms_max, e2e_ms_max = float(tmax[0]), float(tmax[2])
+        evals_all, e2e_evals_all, full_all = float(tsum[1]), float(tsum[3]), float(tsum[4])
+    else:
+        total_ms_max, e2e_ms_max = total_ms, sum(e2e_ms)
+        evals_all, e2e_evals_all, full_all = total_evals, e2e_evals, full_evals
+    if rank != 0:
+        return None
+
+    clk = clocks.summary()
+    sm_mhz_max = 2070.0
+    peak = SFU_OPS_PER_CLK_SM * 152 * sm_mhz_max * 1e6 / 1e12  # SFU Top/s at the maximum SM clock
+    achieved = SFU_OPS_PER_BIN_DET * bindet / (pers_ms * 1e-3) / 1e12 if pers_ms > 0 else 0.0
+    line = {
+        "metric": METRIC,
+        "value": evals_all / (total_ms_max * 1e-3),
+        "unit": "logL evals/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": total_ms_max / args.steps,
+        "wall_s_per_posterior": total_ms_max / args.steps / 1e3,
+        "full_grid_evals_per_s": full_all / (total_ms_max * 1e-3),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": workload_description(wl), "proposal": "plain SwiG (covariance directions)",
+                   "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{world}",
+                   "posterior": {"logz": results[-1][0].logz, "logz_err": results[-1][0].logz_err,
+                                 "ess": results[-1][0].ess, "n_iter": results[-1][0].n_iter,
+                                 "n_dead": results[-1][0].n_dead}},
+        "e2e": {"value": e2e_evals_all / (e2e_ms_max * 1e-3), "unit": "logL evals/s",
+                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+                "ms_per_step": e2e_ms_max / n_e2e},
+        "gpu_launches": launches,
+        "roofline": {
+            "kernel": "k_ns_persistent (persistent SwiG kernel)",
+            "bound": "alu",
+            "achieved": achieved,
+            "peak": peak,
+            "unit": "SFU Top/s",
+            "frac": achieved / peak if peak else None,
+            "traffic": None,
+            "work_per_launch": "2 SFU ops x bin-detector evaluations (full-grid evals x 3 x 259585)",
+            "launches": int(pers_launch),
+            "avg_launch_ms": pers_ms / max(1, pers_launch),
+            "peak_source": "16 sin/cos per clk per SM x 152 SMs x 2070 MHz (derived, not measured)",
+        },
+        "clocks": clk,
+    }
+    if args.cpu_baseline and world == 1:
+        line["cpu_baseline"] = cpu_baseline(wl, seconds=args.cpu_seconds,
+                                            evals_per_posterior=total_evals / max(1, args.steps))
+    return line
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle (the baseline leg and the reference arm)
+# ---------------------------------------------------------------------------
+_EV = None
+
+
+def _worker_init(wl_seed):
+    global _EV
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    from oracle import events
+    _EV = events.build_event(si.config2(seed_index=wl_seed))
+
+
+def _worker_evals(args):
+    seed, n = args
+    from oracle import likelihood as L
+    from oracle import physics
+    ev, th = _EV
+    wl = si.config2()
+    rng = np.random.default_rng(seed)
+    ns = len(wl.sampled())
+    t0 = time.perf_counter()
+    for _ in range(n):
+        t = physics.prior_transform(rng.random(ns), wl.params)[0]
+        L.loglike(ev, t)
+    return n, time.perf_counter() - t0
+
+
+class OraclePool:
+    """The FP64 oracle's logL on all host cores (spawned worker processes,
+    each holding the synthetic event)."""
+
+    def __init__(self):
+        import multiprocessing as mp
+        self.cores = os.cpu_count() or 1
+        self.pool = mp.get_context("spawn").Pool(self.cores, initializer=_worker_init, initargs=(0,))
+        n0, t0 = self.pool.apply(_worker_evals, ((12345, 2),))
+        self.per_eval = t0 / max(1, n0)
+        self.seed = 100
+
+    def sample(self, seconds):
+        n_each = max(1, int(seconds / self.per_eval))
+        t_start = time.perf_counter()
+        res = self.pool.map(_worker_evals, [(self.seed + i, n_each) for i in range(self.cores)])
+        wall = time.perf_counter() - t_start
+        self.seed += self.cores
+        total = sum(r[0] for r in res)
+        return total, wall
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+
+
+def cpu_baseline(wl, seconds=15.0, evals_per_posterior=None):
+    """Oracle logL evaluations/s over all host cores, on a bounded sample."""
+    pool = OraclePool()
+    try:
+        total, wall = pool.sample(seconds)
+    finally:
+        pool.close()
+    rate = total / wall
+    out = {"value": rate, "unit": "logL evals/s", "cores": pool.cores, "kind": "oracle",
+           "sample": f"{total} FP64 oracle evaluations of logL at prior draws on the full 3 x {wl.n_bins}-bin grid, "
+                     f"{pool.cores} spawned processes, {wall:.1f} s"}
+    if evals_per_posterior:
+        out["wall_s_per_posterior_extrapolated"] = evals_per_posterior / rate
+    return out
+
+
+def run_reference(args, rank, world):
+    """The oracle arm: each step is a bounded sample of logL evaluations of
+    the same workload on all host cores; value = evaluations/s."""
+    if rank != 0:
+        return None
+    wl = si.config2()
+    pool = OraclePool()
+    per_step_s = max(2.0, args.cpu_seconds / 2)
+    try:
+        for _ in range(args.warmup):
+            pool.sample(1.0)
+        total, t_all = 0, 0.0
+        for _ in range(args.steps):
+            n, w = pool.sample(per_step_s)
+            total += n
+            t_all += w
+    finally:
+        pool.close()
+    value = total / t_all
+    sample = (f"{total} FP64 oracle evaluations of logL at prior draws on the full 3 x {wl.n_bins}-bin grid "
+              f"over {args.steps} steps, {pool.cores} spawned processes")
+    return {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "logL evals/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_all / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload_description(wl),
+                   "note": "FP64 CPU oracle of the same method, bounded samples per step"},
+        "cpu_baseline": {"value": value, "unit": "logL evals/s", "cores": pool.cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "logL evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=1)
+    ap.add_argument("--impl", choices=["swig", "reference"], default="swig")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if world > 1 and args.impl == "swig":
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        dist.init_process_group("nccl")
+    line = run_reference(args, rank, world) if args.impl == "reference" else run_gpu(args, rank, world)
+    if rank == 0 and line is not None:
+        print(json.dumps(line), flush=True)
+    if world > 1 and args.impl == "swig":
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -146,6 +146,18 @@ int swig_loglike_batch(swig_ctx* ctx, const double* theta, int64_t n, double* ou
 int swig_loglike_batch_dev(swig_ctx* ctx, const double* theta_dev, int64_t n,
                            double* out_logl_dev, void* stream);
 
+/* ---- synthetic data (Sec. 4.1 injections) ------------------------------- */
+/* Detector strain of one source theta (13 doubles) on the grid, for every
+ * detector set, computed on the device in FP64 with the same TaylorF2 model
+ * and projection as the likelihood; plus optional noise (n_det x n x 2
+ * doubles, detector-major, NULL for none).  If target_snr > 0, d_L is first
+ * rescaled so that the network optimal SNR sqrt(sum_i <h_i|h_i>) equals it
+ * (PSDs required).  out_re_im: n_det x n complex as 2 doubles each;
+ * theta_out (optional): theta with the d_L actually used.  Needs the grid,
+ * detectors and time reference; not the data. */
+int swig_inject(swig_ctx* ctx, const double* theta, double target_snr, const double* noise_re_im,
+                double* out_re_im, double* theta_out);
+
 /* ---- prior transform (Table I) ---------------------------------------- */
 /* Map n unit-cube points (n x n_sampled doubles, sampled slots in slot order)
  * to full 13-vectors theta (n x 13). */
@@ -162,11 +174,19 @@ int swig_run(swig_ctx* ctx, swig_result* out);
  * kernel (grid barriers).  Default 1e7.  A wait that reaches the cap makes
  * swig_run return SWIG_E_TIMEOUT instead of hanging. */
 int swig_set_wait_limit(swig_ctx* ctx, long long spins);
-/* Phase timers of the last swig_run, measured on the device (first CTA of the
- * persistent kernel): out[0] rounds, out[1] iteration-boundary seconds,
- * out[2] chain-control seconds, out[3] wait after control, out[4] sweep
- * seconds, out[5] wait after sweep.  Writes min(n, 6) values. */
+/* Counters of the last swig_run.  Phase timers measured on the device by the
+ * first CTA of the persistent kernel: out[0] rounds, out[1] iteration-
+ * boundary seconds, out[2] chain-control seconds, out[3] wait after control,
+ * out[4] sweep seconds, out[5] wait after sweep; out[6] total milliseconds of
+ * the persistent-kernel launches (CUDA events on the context's stream),
+ * out[7] their count; over the context's lifetime: out[8] kernel launches,
+ * out[9] bytes copied host->device, out[10] device->host; out[11] bin-detector
+ * evaluations of the last run (full-grid evaluations x detectors x bins).
+ * Writes min(n, 12) values. */
 int swig_get_profile(swig_ctx* ctx, double* out, int n);
+/* Use `stream` (a cudaStream_t on the context's device, owned by the caller)
+ * for all later work of this context; NULL restores a private stream. */
+int swig_set_stream(swig_ctx* ctx, void* stream);
 /* Dead points of the last run (theta n x 13, logL, log-weight normalised so
  * that logsumexp(logw) = log Z).  With cap == 0 only *n_out is set. */
 int swig_get_samples(swig_ctx* ctx, double* theta, double* logl, double* logw,

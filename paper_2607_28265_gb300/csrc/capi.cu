@@ -350,6 +350,7 @@ int prepare(swig_ctx* c) {
   DeviceBuffers& B = c->B;
   CUDA_TRY(c, cudaMalloc(&B.slice_begin, sizeof(int) * (n_slices + 1)));
   CUDA_TRY(c, cudaMemcpy(B.slice_begin, slice_begin.data(), sizeof(int) * (n_slices + 1), cudaMemcpyHostToDevice));
+  c->h2d_bytes += sizeof(int) * (n_slices + 1);
 
   if (prec == SWIG_PREC_MIXED) {
     std::vector<float2> d32((size_t)n_det * n);
@@ -359,6 +360,8 @@ int prepare(swig_ctx* c) {
     }
     CUDA_TRY(c, cudaMalloc(&B.data32, sizeof(float2) * d32.size()));
     CUDA_TRY(c, cudaMemcpy(B.data32, d32.data(), sizeof(float2) * d32.size(), cudaMemcpyHostToDevice));
+    c->h2d_bytes += sizeof(float2) * d32.size() + sizeof(TileInfo) * tiles.size() + sizeof(TileBasis) * basis.size() +
+                    sizeof(int) * n;
     L.n_tiles = (int)tiles.size();
     std::vector<int> bin_tile(n);
     for (int t = 0; t < L.n_tiles; ++t)
@@ -375,6 +378,7 @@ int prepare(swig_ctx* c) {
     for (size_t k = 0; k < d64.size(); ++k) d64[k] = make_double2(dre[k], dim[k]);
     CUDA_TRY(c, cudaMalloc(&B.data64, sizeof(double2) * d64.size()));
     CUDA_TRY(c, cudaMemcpy(B.data64, d64.data(), sizeof(double2) * d64.size(), cudaMemcpyHostToDevice));
+    c->h2d_bytes += sizeof(double2) * d64.size() + sizeof(double) * 3 * n;
     std::vector<double> ftab((size_t)3 * n);
     for (int64_t k = 0; k < n; ++k) {
       const double f = (double)(c->k_min + k) * c->df;
@@ -442,6 +446,7 @@ int loglike_device(swig_ctx* c, const double* theta_dev, int64_t n, double* out_
     cudaError_t e = c->prepared_precision == SWIG_PREC_MIXED
                         ? launch_loglike_mixed(c->L, c->B, theta_dev + off * SWIG_N_PARAMS, m, out_dev + off, st)
                         : launch_loglike_fp64(c->L, c->B, theta_dev + off * SWIG_N_PARAMS, m, out_dev + off, st);
+    c->n_launches += c->prepared_precision == SWIG_PREC_MIXED ? 4 : 3;
     if (e != cudaSuccess) return fail(c, SWIG_E_CUDA, std::string("likelihood launch: ") + cudaGetErrorString(e));
   }
   return SWIG_OK;
@@ -494,7 +499,7 @@ void swig_destroy(swig_ctx* c) {
   swig_sampler_release(c);
   free_problem(c->B);
   free_scratch(c->B);
-  if (c->stream) cudaStreamDestroy(c->stream);
+  if (c->stream && c->own_stream) cudaStreamDestroy(c->stream);
   delete c;
 }
 
@@ -636,23 +641,134 @@ int swig_loglike_batch_dev(swig_ctx* c, const double* theta_dev, int64_t n, doub
   return loglike_device(c, theta_dev, n, out_dev, (cudaStream_t)stream);
 }
 
+int swig_inject(swig_ctx* c, const double* theta, double target_snr, const double* noise_re_im, double* out_re_im,
+                double* theta_out) {
+  if (!c) return SWIG_E_ARG;
+  if (!theta || !out_re_im) return fail(c, SWIG_E_ARG, "null theta or output");
+  if (!c->grid_set) return fail(c, SWIG_E_STATE, "grid not set");
+  int n_det = 0;
+  while (n_det < SWIG_MAX_DET && c->det_set[n_det]) ++n_det;
+  if (n_det == 0) return fail(c, SWIG_E_STATE, "no detector set");
+  const int64_t n = c->n_bins;
+  if (target_snr > 0.0)
+    for (int i = 0; i < n_det; ++i)
+      if ((int64_t)c->psd[i].size() != n) return fail(c, SWIG_E_STATE, "PSDs are needed to scale to a target SNR");
+  double th[SWIG_N_PARAMS];
+  for (int j = 0; j < SWIG_N_PARAMS; ++j) th[j] = theta[j];
+  if (!(th[0] > 0.0) || !(th[1] > 0.0) || th[1] > 1.0 || !(th[6] > 0.0)) return fail(c, SWIG_E_ARG, "invalid theta");
+  CUDA_TRY(c, cudaSetDevice(c->device));
+  LikeConst L;
+  std::memset(&L, 0, sizeof(L));
+  L.n_det = n_det;
+  L.n_bins = (int)n;
+  L.k_min = (int)c->k_min;
+  L.df = c->df;
+  L.gmst = c->gmst;
+  L.phase_marg = 0;
+  for (int i = 0; i < n_det; ++i) {
+    for (int r = 0; r < 3; ++r) L.vertex[i][r] = c->vertex[i][r];
+    const double* x = c->xarm[i];
+    const double* y = c->yarm[i];
+    L.dten[i][0] = 0.5 * (x[0] * x[0] - y[0] * y[0]);
+    L.dten[i][1] = 0.5 * (x[0] * x[1] - y[0] * y[1]);
+    L.dten[i][2] = 0.5 * (x[0] * x[2] - y[0] * y[2]);
+    L.dten[i][3] = 0.5 * (x[1] * x[1] - y[1] * y[1]);
+    L.dten[i][4] = 0.5 * (x[1] * x[2] - y[1] * y[2]);
+    L.dten[i][5] = 0.5 * (x[2] * x[2] - y[2] * y[2]);
+    if (target_snr > 0.0) {
+      NSum K;
+      for (int64_t k = 0; k < n; ++k) {
+        const double f = (double)(c->k_min + k) * c->df;
+        K.add(4.0 * c->df / c->psd[i][k] * std::pow(f, -7.0 / 3.0));
+      }
+      L.K[i] = K.value();
+    }
+  }
+  double* th_d = nullptr;
+  EvalRecord* rec_d = nullptr;
+  double2* h_d = nullptr;
+  std::vector<double2> h((size_t)n_det * n);
+  EvalRecord rec;
+  auto run = [&]() -> cudaError_t {
+    cudaError_t e;
+    if ((e = cudaMalloc(&th_d, sizeof(th)))) return e;
+    if ((e = cudaMalloc(&rec_d, sizeof(EvalRecord)))) return e;
+    if ((e = cudaMalloc(&h_d, sizeof(double2) * h.size()))) return e;
+    for (int pass = 0; pass < 2; ++pass) {
+      if ((e = cudaMemcpy(th_d, th, sizeof(th), cudaMemcpyHostToDevice))) return e;
+      if ((e = launch_waveform(L, th_d, rec_d, h_d, c->stream))) return e;
+      if ((e = cudaStreamSynchronize(c->stream))) return e;
+      if ((e = cudaMemcpy(&rec, rec_d, sizeof(rec), cudaMemcpyDeviceToHost))) return e;
+      if (pass == 0 && target_snr > 0.0) {
+        double snr2 = 0.0;
+        for (int i = 0; i < n_det; ++i) snr2 += (rec.cre[i] * rec.cre[i] + rec.cim[i] * rec.cim[i]) * L.K[i];
+        th[6] *= std::sqrt(snr2) / target_snr;  // SNR scales as 1 / d_L
+        continue;
+      }
+      break;
+    }
+    return cudaMemcpy(h.data(), h_d, sizeof(double2) * h.size(), cudaMemcpyDeviceToHost);
+  };
+  const cudaError_t e = run();
+  if (th_d) cudaFree(th_d);
+  if (rec_d) cudaFree(rec_d);
+  if (h_d) cudaFree(h_d);
+  if (e != cudaSuccess) return fail(c, SWIG_E_CUDA, std::string("injection: ") + cudaGetErrorString(e));
+  for (size_t k = 0; k < h.size(); ++k) {
+    out_re_im[2 * k] = h[k].x + (noise_re_im ? noise_re_im[2 * k] : 0.0);
+    out_re_im[2 * k + 1] = h[k].y + (noise_re_im ? noise_re_im[2 * k + 1] : 0.0);
+  }
+  if (theta_out)
+    for (int j = 0; j < SWIG_N_PARAMS; ++j) theta_out[j] = th[j];
+  return SWIG_OK;
+}
+
+int swig_set_stream(swig_ctx* c, void* stream) {
+  if (!c) return SWIG_E_ARG;
+  CUDA_TRY(c, cudaSetDevice(c->device));
+  if (c->stream && c->own_stream) CUDA_TRY(c, cudaStreamDestroy(c->stream));
+  if (stream) {
+    c->stream = (cudaStream_t)stream;
+    c->own_stream = false;
+  } else {
+    CUDA_TRY(c, cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
+    c->own_stream = true;
+  }
+  return SWIG_OK;
+}
+
 int swig_prior_transform(swig_ctx* c, const double* u, int64_t n, double* theta) {
   if (!c) return SWIG_E_ARG;
   if (!c->prior_set) return fail(c, SWIG_E_STATE, "prior not set");
   if (n == 0) return SWIG_OK;
   if (n < 0 || n > (1 << 20) || !u || !theta) return fail(c, SWIG_E_ARG, "need 0 <= n <= 2^20 and non-null buffers");
-  int rc = prepare(c);
-  if (rc) return rc;
-  const int chunk = 4096;
+  CUDA_TRY(c, cudaSetDevice(c->device));
   const int ns = c->n_sampled;
-  for (int64_t off = 0; off < n; off += chunk) {
-    const int m = (int)std::min<int64_t>(chunk, n - off);
-    if ((rc = ensure_scratch(c, m))) return rc;
-    CUDA_TRY(c, cudaMemcpyAsync(c->B.u, u + off * ns, sizeof(double) * ns * m, cudaMemcpyHostToDevice, c->stream));
-    CUDA_TRY(c, launch_prior_transform(c->B.prior, ns, c->B.u, m, c->B.theta, c->stream));
-    CUDA_TRY(c, cudaMemcpyAsync(theta + off * SWIG_N_PARAMS, c->B.theta, sizeof(double) * SWIG_N_PARAMS * m, cudaMemcpyDeviceToHost, c->stream));
-    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  PriorSlot slots[SWIG_N_PARAMS];
+  for (int i = 0; i < SWIG_N_PARAMS; ++i) {
+    const swig_param& p = c->params[i];
+    slots[i] = make_prior_slot(p.kind, p.mode, p.lo, p.hi, p.value);
   }
+  PriorSlot* slots_d = nullptr;
+  double *u_d = nullptr, *th_d = nullptr;
+  auto run = [&]() -> cudaError_t {
+    cudaError_t e;
+    if ((e = cudaMalloc(&slots_d, sizeof(slots)))) return e;
+    if ((e = cudaMalloc(&u_d, sizeof(double) * ns * n))) return e;
+    if ((e = cudaMalloc(&th_d, sizeof(double) * SWIG_N_PARAMS * n))) return e;
+    if ((e = cudaMemcpyAsync(slots_d, slots, sizeof(slots), cudaMemcpyHostToDevice, c->stream))) return e;
+    if ((e = cudaMemcpyAsync(u_d, u, sizeof(double) * ns * n, cudaMemcpyHostToDevice, c->stream))) return e;
+    if ((e = launch_prior_transform(slots_d, ns, u_d, (int)n, th_d, c->stream))) return e;
+    if ((e = cudaMemcpyAsync(theta, th_d, sizeof(double) * SWIG_N_PARAMS * n, cudaMemcpyDeviceToHost, c->stream)))
+      return e;
+    return cudaStreamSynchronize(c->stream);
+  };
+  const cudaError_t e = run();
+  if (slots_d) cudaFree(slots_d);
+  if (u_d) cudaFree(u_d);
+  if (th_d) cudaFree(th_d);
+  if (e != cudaSuccess) return fail(c, SWIG_E_CUDA, std::string("prior transform: ") + cudaGetErrorString(e));
+  ++c->n_launches;
   return SWIG_OK;
 }
 

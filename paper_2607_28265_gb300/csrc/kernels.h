@@ -49,6 +49,9 @@ cudaError_t launch_loglike_mixed(const LikeConst& L, const DeviceBuffers& B, con
                                  double* out, cudaStream_t st, double* kappa_out = nullptr);
 cudaError_t launch_loglike_fp64(const LikeConst& L, const DeviceBuffers& B, const double* theta, int n,
                                 double* out, cudaStream_t st, double* kappa_out = nullptr);
+// Setup record and detector strain of one theta (FP64) into out [n_det][n_bins].
+cudaError_t launch_waveform(const LikeConst& L, const double* theta_dev, EvalRecord* rec_dev, double2* out,
+                            cudaStream_t st);
 cudaError_t launch_prior_transform(const PriorSlot* slots, int n_sampled, const double* u, int n, double* theta,
                                    cudaStream_t st);
 cudaError_t set_sweep_smem_limit(size_t bytes);

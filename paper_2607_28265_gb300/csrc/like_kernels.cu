@@ -132,6 +132,38 @@ __global__ void k_reduce(LikeConst L, const T* __restrict__ partials, int n_unit
 }
 
 // ---------------------------------------------------------------------------
+// Detector strain on the grid (FP64): h_i(f) = C_i f^-7/6 exp(-2 pi i (P(f) + f tau_i)).
+// ---------------------------------------------------------------------------
+__global__ void k_waveform(LikeConst L, const EvalRecord* __restrict__ rec, double2* __restrict__ out) {
+  const int bin = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = blockIdx.y;
+  if (bin >= L.n_bins || i >= L.n_det) return;
+  const EvalRecord& r = rec[0];
+  const double f = (double)(L.k_min + bin) * L.df;
+  const double up = cbrt(f), um = 1.0 / up, lf = log(f);
+  const double u2 = um * um, p2 = up * up;
+  double P = r.c[B_ONE] + r.c[B_LOG] * lf;
+  P += um * (r.c[B_M13] + um * (r.c[B_M23] + um * (r.c[B_M1] + u2 * r.c[B_M53])));
+  P += up * (r.c[B_P13] + r.c[B_P13LOG] * lf) + p2 * r.c[B_P23] + p2 * p2 * up * (r.c[B_P53] + p2 * r.c[B_P73]);
+  double ph = fma(f, r.tau[i], P);
+  ph -= rint(ph);
+  double s, co;
+  sincospi(2.0 * ph, &s, &co);
+  const double a = exp(-7.0 / 6.0 * lf);
+  // C_i a (cos - i sin)
+  const double re = a * (r.cre[i] * co + r.cim[i] * s), im = a * (r.cim[i] * co - r.cre[i] * s);
+  out[(size_t)i * L.n_bins + bin] = make_double2(re, im);
+}
+
+cudaError_t launch_waveform(const LikeConst& L, const double* theta_dev, EvalRecord* rec_dev, double2* out,
+                            cudaStream_t st) {
+  k_setup<<<1, 32, 0, st>>>(L, theta_dev, 1, rec_dev);
+  dim3 grid((L.n_bins + 255) / 256, L.n_det);
+  k_waveform<<<grid, 256, 0, st>>>(L, rec_dev, out);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
 // Prior transform (Table I inverse CDFs).
 // ---------------------------------------------------------------------------
 __global__ void k_prior_transform(const PriorSlot* __restrict__ slots, int n_sampled, const double* __restrict__ u,

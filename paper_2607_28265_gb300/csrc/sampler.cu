@@ -997,7 +997,7 @@ int swig_run(swig_ctx* c, swig_result* out) {
   }
   S.m_pow2 = 1;
   while (S.m_pow2 < m) S.m_pow2 *= 2;
-  S.max_iters = 64;
+  S.max_iters = (int)std::max(1, std::min(64, c->cfg.max_iter));
 
   const int max_pieces = c->B.max_pieces;
   S.max_pieces = max_pieces;
@@ -1090,6 +1090,12 @@ int swig_run(swig_ctx* c, swig_result* out) {
   std::vector<double> du, dl, dw;
   NSGlobal gh;
   long long total_iters = 0;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  SCUDA(cudaEventCreate(&ev0));
+  SCUDA(cudaEventCreate(&ev1));
+  double persistent_ms = 0.0;
+  long long persistent_launches = 0;
+  c->n_launches += c->prepared_precision == SWIG_PREC_MIXED ? 5 : 4;  // init draw + batched likelihood
   for (;;) {
     // reset per-launch counters
     NSGlobal gl;
@@ -1102,11 +1108,22 @@ int swig_run(swig_ctx* c, swig_result* out) {
     gl.bar_count = 0;
     SCUDA(cudaMemcpyAsync(st->P.g, &gl, sizeof(gl), cudaMemcpyHostToDevice, c->stream));
     void* args[] = {(void*)&L, (void*)&S, (void*)&c->B, (void*)&st->P};
+    SCUDA(cudaEventRecord(ev0, c->stream));
     SCUDA(cudaLaunchCooperativeKernel(kern, dim3(L.n_slices), dim3(kSweepThreads), args, smem, c->stream));
+    SCUDA(cudaEventRecord(ev1, c->stream));
     SCUDA(cudaMemcpyAsync(&gh, st->P.g, sizeof(gh), cudaMemcpyDeviceToHost, c->stream));
     SCUDA(cudaStreamSynchronize(c->stream));
+    {
+      float ms = 0.0f;
+      SCUDA(cudaEventElapsedTime(&ms, ev0, ev1));
+      persistent_ms += ms;
+      ++persistent_launches;
+      ++c->n_launches;
+    }
     if (gh.error) return fail(c, gh.error, gh.error == SWIG_E_TIMEOUT ? "a bounded device wait expired" : "device error");
+    c->d2h_bytes += sizeof(gh);
     if (gh.n_dead > 0) {
+      c->d2h_bytes += (size_t)gh.n_dead * (nd + 2) * sizeof(double);
       const size_t n0 = dl.size();
       du.resize((n0 + gh.n_dead) * nd);
       dl.resize(n0 + gh.n_dead);
@@ -1153,6 +1170,9 @@ int swig_run(swig_ctx* c, swig_result* out) {
     SCUDA(cudaMalloc(&th_d, sizeof(double) * std::max<size_t>(1, c->out_theta.size())));
     SCUDA(cudaMemcpy(du_d, du.data(), sizeof(double) * du.size(), cudaMemcpyHostToDevice));
     k_dead_theta<<<(unsigned)((n_dead + 127) / 128), 128, 0, c->stream>>>(S, du_d, (int)n_dead, th_d);
+    ++c->n_launches;
+    c->h2d_bytes += sizeof(double) * du.size();
+    c->d2h_bytes += sizeof(double) * c->out_theta.size();
     cudaError_t e = cudaStreamSynchronize(c->stream);
     if (e == cudaSuccess) e = cudaMemcpy(c->out_theta.data(), th_d, sizeof(double) * c->out_theta.size(), cudaMemcpyDeviceToHost);
     cudaFree(du_d);
@@ -1186,13 +1206,21 @@ int swig_run(swig_ctx* c, swig_result* out) {
   c->profile[3] = gh.t_wait_ctrl * 1e-9;
   c->profile[4] = gh.t_sweep * 1e-9;
   c->profile[5] = gh.t_wait_sweep * 1e-9;
+  c->profile[6] = persistent_ms;
+  c->profile[7] = (double)persistent_launches;
+  c->profile[8] = (double)c->n_launches;
+  c->profile[9] = (double)c->h2d_bytes;
+  c->profile[10] = (double)c->d2h_bytes;
+  c->profile[11] = (double)nf * (double)L.n_det * (double)L.n_bins;  // bin-detector evaluations
+  cudaEventDestroy(ev0);
+  cudaEventDestroy(ev1);
   return SWIG_OK;
 }
 
 int swig_get_profile(swig_ctx* c, double* out, int n) {
   if (!c) return SWIG_E_ARG;
   if (!out || n < 0) return fail(c, SWIG_E_ARG, "null output");
-  for (int i = 0; i < n && i < 6; ++i) out[i] = c->profile[i];
+  for (int i = 0; i < n && i < 12; ++i) out[i] = c->profile[i];
   return SWIG_OK;
 }
 

@@ -61,6 +61,8 @@ SIGNATURES = {
     "swig_run": (_c_int, [_vp, ctypes.POINTER(SwigResult)]),
     "swig_set_wait_limit": (_c_int, [_vp, ctypes.c_longlong]),
     "swig_get_profile": (_c_int, [_vp, _dp, _c_int]),
+    "swig_set_stream": (_c_int, [_vp, _vp]),
+    "swig_inject": (_c_int, [_vp, _dp, _c_double, _dp, _dp, _dp]),
     "swig_get_samples": (_c_int, [_vp, _dp, _dp, _dp, _c_i64, ctypes.POINTER(_c_i64)]),
 }
 
@@ -141,6 +143,8 @@ class Context:
     # ---- problem definition ------------------------------------------------
     def set_grid(self, f_min, f_max, df):
         self._check(self.lib.swig_set_grid(self.h, f_min, f_max, df))
+        import math
+        self.n_bins = int(math.floor(f_max / df + 1e-9)) - int(math.ceil(f_min / df - 1e-9)) + 1
 
     def set_detector(self, idx, vertex, x_arm, y_arm):
         v, x, y = (np.ascontiguousarray(a, dtype=np.float64) for a in (vertex, x_arm, y_arm))
@@ -187,6 +191,19 @@ class Context:
         self._check(self.lib.swig_loglike_batch_dev(self.h, _vp(theta_dev_ptr), int(n), _vp(out_dev_ptr),
                                                      _vp(stream_ptr)))
 
+    def inject(self, theta, n_det, target_snr=0.0, noise=None):
+        """Detector strains (n_det x n_bins complex) of theta plus optional noise;
+        returns (data, theta_used)."""
+        th = np.ascontiguousarray(theta, dtype=np.float64)
+        out = np.empty((n_det, self.n_bins), dtype=np.complex128)
+        nz = None
+        if noise is not None:
+            nz = np.ascontiguousarray(np.asarray(noise, dtype=np.complex128)).view(np.float64)
+        th_out = np.empty(N_PARAMS)
+        self._check(self.lib.swig_inject(self.h, _ptr(th), float(target_snr), None if nz is None else _ptr(nz),
+                                         _ptr(out.view(np.float64)), _ptr(th_out)))
+        return out, th_out
+
     def prior_transform(self, u):
         uu = np.ascontiguousarray(np.atleast_2d(u), dtype=np.float64)
         th = np.empty((uu.shape[0], N_PARAMS))
@@ -200,11 +217,17 @@ class Context:
         return RunResult(r.logz, r.logz_err, r.info, r.ess, r.wall_s, r.n_dead, r.n_iter, r.n_evals,
                          r.n_sweep_evals, r.status)
 
+    PROFILE_KEYS = ("rounds", "boundary_s", "control_s", "wait_control_s", "sweep_s", "wait_sweep_s",
+                    "persistent_ms", "persistent_launches", "kernel_launches", "h2d_bytes", "d2h_bytes",
+                    "bin_det_evals")
+
     def profile(self):
-        out = np.zeros(6)
-        self._check(self.lib.swig_get_profile(self.h, _ptr(out), 6))
-        keys = ("rounds", "boundary_s", "control_s", "wait_control_s", "sweep_s", "wait_sweep_s")
-        return dict(zip(keys, out.tolist()))
+        out = np.zeros(len(self.PROFILE_KEYS))
+        self._check(self.lib.swig_get_profile(self.h, _ptr(out), out.size))
+        return dict(zip(self.PROFILE_KEYS, out.tolist()))
+
+    def set_stream(self, stream_ptr):
+        self._check(self.lib.swig_set_stream(self.h, _vp(stream_ptr)))
 
     def set_wait_limit(self, spins):
         self._check(self.lib.swig_set_wait_limit(self.h, int(spins)))
