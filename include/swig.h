@@ -146,6 +146,32 @@ int swig_loglike_batch(swig_ctx* ctx, const double* theta, int64_t n, double* ou
 int swig_loglike_batch_dev(swig_ctx* ctx, const double* theta_dev, int64_t n,
                            double* out_logl_dev, void* stream);
 
+/* ---- likelihood without allocation ------------------------------------ */
+/* The same batched likelihood as swig_loglike_batch_dev (mixed precision),
+ * for callers that cannot allocate device memory once they are running: a
+ * latency-critical loop with all memory reserved up front, a host runtime that
+ * forbids cudaMalloc/cudaFree after start-up, or a process whose device memory
+ * belongs to another framework's pool.  (The paper has no counterpart; this is
+ * a deployment interface of this library.)
+ *   - Allocates nothing.  Its scratch is one fixed 8 MiB array in the library's
+ *     device image, held on every device that loads the library until the
+ *     process exits.  Batches that do not fit return SWIG_E_ARG with the
+ *     capacity in the message (about 250 parameter vectors on the 128 s,
+ *     three-detector grid); split larger batches.
+ *   - The context must already be prepared, for SWIG_PREC_MIXED, by an
+ *     earlier swig_loglike_batch / swig_loglike_batch_dev / swig_run call with
+ *     the current data (preparation allocates); otherwise SWIG_E_STATE.
+ *   - The first call on a device looks up the array's device address (no
+ *     allocation); make that first call before any stream capture.
+ *   - Every call shares the one scratch array, which keeps the previous
+ *     call's contents; nothing in it needs to start at zero.  Calls that
+ *     overlap on the GPU (other streams, other threads, other contexts in the
+ *     same process on the same device) race on it: serialise them.
+ * theta_dev: n x 13 doubles; out_logl_dev: n doubles; both device pointers on
+ * the context's device.  stream: cudaStream_t (NULL = legacy default stream). */
+int swig_loglike_batch_noalloc(swig_ctx* ctx, const double* theta_dev, int64_t n, double* out_logl_dev,
+                               void* stream);
+
 /* ---- synthetic data (Sec. 4.1 injections) ------------------------------- */
 /* Detector strain of one source theta (13 doubles) on the grid, for every
  * detector set, computed on the device in FP64 with the same TaylorF2 model

@@ -63,6 +63,7 @@ SIGNATURES = {
     "swig_get_profile": (_c_int, [_vp, _dp, _c_int]),
     "swig_set_stream": (_c_int, [_vp, _vp]),
     "swig_inject": (_c_int, [_vp, _dp, _c_double, _dp, _dp, _dp]),
+    "swig_loglike_batch_noalloc": (_c_int, [_vp, _vp, _c_i64, _vp, _vp]),
     "swig_get_samples": (_c_int, [_vp, _dp, _dp, _dp, _c_i64, ctypes.POINTER(_c_i64)]),
 }
 
@@ -203,6 +204,13 @@ class Context:
         self._check(self.lib.swig_inject(self.h, _ptr(th), float(target_snr), None if nz is None else _ptr(nz),
                                          _ptr(out.view(np.float64)), _ptr(th_out)))
         return out, th_out
+
+    def loglike_batch_noalloc(self, theta_dev_ptr, n, out_dev_ptr, stream_ptr=0):
+        """Batched likelihood with the library's fixed scratch (no device
+        allocation); the context must have been prepared by an earlier
+        likelihood call."""
+        self._check(self.lib.swig_loglike_batch_noalloc(self.h, _vp(theta_dev_ptr), int(n), _vp(out_dev_ptr),
+                                                         _vp(stream_ptr)))
 
     def prior_transform(self, u):
         uu = np.ascontiguousarray(np.atleast_2d(u), dtype=np.float64)
