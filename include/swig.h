@@ -207,8 +207,10 @@ int swig_set_wait_limit(swig_ctx* ctx, long long spins);
  * the persistent-kernel launches (CUDA events on the context's stream),
  * out[7] their count; over the context's lifetime: out[8] kernel launches,
  * out[9] bytes copied host->device, out[10] device->host; out[11] bin-detector
- * evaluations of the last run (full-grid evaluations x detectors x bins).
- * Writes min(n, 12) values. */
+ * evaluations of the last run (full-grid evaluations x detectors x bins);
+ * out[12..16] clock cycles the first chain's control spent on pending results,
+ * new slice steps, proposals, projection-only evaluations and full-evaluation
+ * set-up, out[17..19] the counts of the last three.  Writes min(n, 20) values. */
 int swig_get_profile(swig_ctx* ctx, double* out, int n);
 /* Use `stream` (a cudaStream_t on the context's device, owned by the caller)
  * for all later work of this context; NULL restores a private stream. */

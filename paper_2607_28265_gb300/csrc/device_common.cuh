@@ -76,23 +76,61 @@ __device__ __forceinline__ dfl df_from_double(double x) {
 // (PRD 80 084043, Eq. 3.18), aligned-spin 1.5PN spin-orbit and 2PN spin-spin
 // terms (Poisson & Will 1995), tidal 5PN/6PN terms (Wade et al. 2014).
 // ---------------------------------------------------------------------------
-__host__ __device__ inline void taylorf2_basis_coeffs(double mc, double q, double chi1, double chi2,
-                                             double lam1, double lam2, double* c) {
-  const double opq = 1.0 + q;
-  const double eta = q / (opq * opq);
-  const double mfrac1 = 1.0 / opq, mfrac2 = q / opq;
-  const double dm = (1.0 - q) / opq;  // (m1 - m2) / M
-  const double mtot = mc * exp(-0.6 * log(eta)) * kMtsunS;
-  const double eta2 = eta * eta, eta3 = eta2 * eta;
-  const double so = (113.0 / 12.0 * mfrac1 * mfrac1 + 6.25 * eta) * chi1 +
-                    (113.0 / 12.0 * mfrac2 * mfrac2 + 6.25 * eta) * chi2;
-  const double ss = 79.0 / 8.0 * eta * chi1 * chi2;
-  const double pi2 = kPi * kPi;
+// Shared mass-dependent factors of the basis coefficients, computed once per
+// (Mc, q): two reciprocals and three transcendentals on the critical path.
+struct MassTerms {
+  double eta, dm, m1, m2, A, r, ir, lpm;
+};
 
-  const double a0 = 1.0;
-  const double a2 = 3715.0 / 756.0 + 55.0 / 9.0 * eta;
+__host__ __device__ inline MassTerms taylorf2_mass_terms(double mc, double q) {
+  MassTerms t;
+  const double opq = 1.0 + q;
+  const double inv_opq = 1.0 / opq, inv_q = 1.0 / q;
+  t.m1 = inv_opq;
+  t.m2 = q * inv_opq;
+  t.dm = (1.0 - q) * inv_opq;                 // (m1 - m2) / M
+  t.eta = t.m1 * t.m2;                        // q / (1 + q)^2
+  const double inv_eta = opq * opq * inv_q;   // 1 / eta
+  t.A = (3.0 / (256.0 * kPi)) * inv_eta;      // 3 / (128 eta) in cycles
+  // ln(pi M) = ln(pi T_sun Mc) - (3/5) ln eta;  r = (pi M)^(1/3)
+  t.lpm = log(kPi * kMtsunS * mc) + 0.6 * log(inv_eta);
+  t.r = exp(t.lpm * (1.0 / 3.0));
+  t.ir = 1.0 / t.r;
+  return t;
+}
+
+// Spin terms: 1.5PN spin-orbit beta and 2PN spin-spin sigma enter alpha_3, alpha_4.
+__host__ __device__ inline void taylorf2_spin_coeffs(const MassTerms& t, double chi1, double chi2, double* c) {
+  const double eta = t.eta, eta2 = eta * eta;
+  const double so = (113.0 / 12.0 * t.m1 * t.m1 + 6.25 * eta) * chi1 + (113.0 / 12.0 * t.m2 * t.m2 + 6.25 * eta) * chi2;
+  const double ss = 79.0 / 8.0 * eta * chi1 * chi2;
   const double a3 = -16.0 * kPi + 4.0 * so;
   const double a4 = 15293365.0 / 508032.0 + 27145.0 / 504.0 * eta + 3085.0 / 72.0 * eta2 - 10.0 * ss;
+  const double ir2 = t.ir * t.ir;
+  c[B_M23] = t.A * a3 * ir2;
+  c[B_M13] = t.A * a4 * t.ir;
+}
+
+// Tidal terms (Wade et al. 2014): 5PN and 6PN, alpha_10 and alpha_12.
+__host__ __device__ inline void taylorf2_tidal_coeffs(const MassTerms& t, double lam1, double lam2, double* c) {
+  const double eta = t.eta, eta2 = eta * eta, eta3 = eta2 * eta, dm = t.dm;
+  const double lsum = lam1 + lam2, ldif = lam1 - lam2;
+  const double lt = 8.0 / 13.0 * ((1.0 + 7.0 * eta - 31.0 * eta2) * lsum + dm * (1.0 + 9.0 * eta - 11.0 * eta2) * ldif);
+  const double dlt = 0.5 * (dm * (1.0 - 13272.0 / 1319.0 * eta + 8944.0 / 1319.0 * eta2) * lsum +
+                            (1.0 - 15910.0 / 1319.0 * eta + 32850.0 / 1319.0 * eta2 + 3380.0 / 1319.0 * eta3) * ldif);
+  const double a10 = -19.5 * lt;
+  const double a12 = -3115.0 / 64.0 * lt + 6595.0 / 364.0 * dm * dlt;
+  const double r2 = t.r * t.r, r5 = r2 * r2 * t.r, r7 = r5 * r2;
+  c[B_P53] = t.A * a10 * r5;
+  c[B_P73] = t.A * a12 * r7;
+}
+
+__host__ __device__ inline void taylorf2_basis_coeffs_from(const MassTerms& t, double chi1, double chi2,
+                                                           double lam1, double lam2, double* c) {
+  const double eta = t.eta, eta2 = eta * eta, eta3 = eta2 * eta;
+  const double pi2 = kPi * kPi;
+  const double a0 = 1.0;
+  const double a2 = 3715.0 / 756.0 + 55.0 / 9.0 * eta;
   const double a5 = kPi * (38645.0 / 756.0 - 65.0 / 9.0 * eta);
   const double a5log = 3.0 * a5;
   const double a6 = 11583231236531.0 / 4694215680.0 - 640.0 / 3.0 * pi2 - 6848.0 / 21.0 * kEulerGamma +
@@ -100,34 +138,24 @@ __host__ __device__ inline void taylorf2_basis_coeffs(double mc, double q, doubl
                     127825.0 / 1296.0 * eta3;
   const double a6log = -6848.0 / 21.0;
   const double a7 = kPi * (77096675.0 / 254016.0 + 378515.0 / 1512.0 * eta - 74045.0 / 756.0 * eta2);
-  const double lsum = lam1 + lam2, ldif = lam1 - lam2;
-  const double lt = 8.0 / 13.0 * ((1.0 + 7.0 * eta - 31.0 * eta2) * lsum + dm * (1.0 + 9.0 * eta - 11.0 * eta2) * ldif);
-  const double dlt = 0.5 * (dm * (1.0 - 13272.0 / 1319.0 * eta + 8944.0 / 1319.0 * eta2) * lsum +
-                            (1.0 - 15910.0 / 1319.0 * eta + 32850.0 / 1319.0 * eta2 + 3380.0 / 1319.0 * eta3) * ldif);
-  const double a10 = -19.5 * lt;
-  const double a12 = -3115.0 / 64.0 * lt + 6595.0 / 364.0 * dm * dlt;
-
-  const double A = (3.0 / (256.0 * kPi)) * (opq * opq / q);  // 3 / (128 eta) in cycles
-  const double piM = kPi * mtot;
-  const double lpm = log(piM);
-  const double r = cbrt(piM);       // (pi M)^(1/3): v = r f^(1/3)
-  const double ir = 1.0 / r;
-  const double r2 = r * r, r5 = r2 * r2 * r, r7 = r5 * r2;
-  const double ir2 = ir * ir, ir3 = ir2 * ir, ir5 = ir3 * ir2;
+  const double ir2 = t.ir * t.ir, ir3 = ir2 * t.ir, ir5 = ir3 * ir2;
+  const double r2 = t.r * t.r;
   const double third = 1.0 / 3.0;
   const double ln4 = 1.3862943611198906188, ln_vlso = -0.89587973461402746;  // ln 4, -ln(6)/2
+  c[B_M53] = t.A * a0 * ir5;
+  c[B_M1] = t.A * a2 * ir3;
+  c[B_LOG] = t.A * a5log * third;
+  c[B_P13] = t.A * t.r * (a6 + a6log * (ln4 + t.lpm * third));
+  c[B_P13LOG] = t.A * t.r * a6log * third;
+  c[B_P23] = t.A * a7 * r2;
+  c[B_ONE] = t.A * (a5 + a5log * (t.lpm * third - ln_vlso)) - 0.125;
+  taylorf2_spin_coeffs(t, chi1, chi2, c);
+  taylorf2_tidal_coeffs(t, lam1, lam2, c);
+}
 
-  c[B_M53] = A * a0 * ir5;
-  c[B_M1] = A * a2 * ir3;
-  c[B_M23] = A * a3 * ir2;
-  c[B_M13] = A * a4 * ir;
-  c[B_LOG] = A * a5log * third;
-  c[B_P13] = A * r * (a6 + a6log * (ln4 + lpm * third));
-  c[B_P13LOG] = A * r * a6log * third;
-  c[B_P23] = A * a7 * r2;
-  c[B_P53] = A * a10 * r5;
-  c[B_P73] = A * a12 * r7;
-  c[B_ONE] = A * (a5 + a5log * (lpm * third - ln_vlso)) - 0.125;
+__host__ __device__ inline void taylorf2_basis_coeffs(double mc, double q, double chi1, double chi2,
+                                                      double lam1, double lam2, double* c) {
+  taylorf2_basis_coeffs_from(taylorf2_mass_terms(mc, q), chi1, chi2, lam1, lam2, c);
 }
 
 // sqrt(5/24) pi^(-2/3) (G Mc / c^3)^(5/6) c / (1 Mpc): Newtonian SPA amplitude
@@ -212,11 +240,46 @@ __device__ inline bool theta_valid(const double* th) {
 __device__ inline void setup_intrinsic(const double* th, EvalRecord* rec) {
   double c[NBASIS];
   if (rec->valid) {
-    taylorf2_basis_coeffs(th[0], th[1], th[2], th[3], th[4], th[5], c);
+    const MassTerms t = taylorf2_mass_terms(th[0], th[1]);
+    taylorf2_basis_coeffs_from(t, th[2], th[3], th[4], th[5], c);
+    rec->mterm[0] = t.eta;
+    rec->mterm[1] = t.dm;
+    rec->mterm[2] = t.m1;
+    rec->mterm[3] = t.m2;
+    rec->mterm[4] = t.A;
+    rec->mterm[5] = t.r;
+    rec->mterm[6] = t.ir;
+    rec->mterm[7] = t.lpm;
   } else {
     for (int j = 0; j < NBASIS; ++j) c[j] = 0.0;
   }
   for (int j = 0; j < NBASIS; ++j) {
+    rec->c[j] = c[j];
+    dfl v = df_from_double(c[j]);
+    rec->c_hi[j] = v.hi;
+    rec->c_lo[j] = v.lo;
+  }
+}
+
+// Only the spin (slots 2, 3) or only the tidal (slots 4, 5) coefficients.
+__device__ inline void setup_intrinsic_partial(const double* th, EvalRecord* rec, bool spin, bool tide) {
+  if (!rec->valid) return;
+  MassTerms t;  // Mc and q are unchanged: reuse the cached mass factors
+  t.eta = rec->mterm[0];
+  t.dm = rec->mterm[1];
+  t.m1 = rec->mterm[2];
+  t.m2 = rec->mterm[3];
+  t.A = rec->mterm[4];
+  t.r = rec->mterm[5];
+  t.ir = rec->mterm[6];
+  t.lpm = rec->mterm[7];
+  double c[NBASIS];
+  for (int j = 0; j < NBASIS; ++j) c[j] = rec->c[j];
+  if (spin) taylorf2_spin_coeffs(t, th[2], th[3], c);
+  if (tide) taylorf2_tidal_coeffs(t, th[4], th[5], c);
+  const int js[4] = {B_M23, B_M13, B_P53, B_P73};
+  for (int q = 0; q < 4; ++q) {
+    const int j = js[q];
     rec->c[j] = c[j];
     dfl v = df_from_double(c[j]);
     rec->c_hi[j] = v.hi;
@@ -356,6 +419,22 @@ __host__ __device__ inline double prior_slot_inverse(const PriorSlot& s, double 
       return asin(s.c1 + u * (s.c2 - s.c1));
     case SWIG_PRIOR_POWER2:
       return cbrt(s.c1 + u * (s.c2 - s.c1));
+    default:
+      return s.lo + u * (s.hi - s.lo);
+  }
+}
+
+// Same families with FP32 transcendentals (relative error ~1e-7 on theta):
+// used by the mixed-precision sampler, where the likelihood is evaluated at
+// exactly the returned theta, so only the prior measure moves by ~1e-7.
+__device__ inline double prior_slot_inverse_f32(const PriorSlot& s, double u) {
+  switch (s.kind) {
+    case SWIG_PRIOR_SINE:
+      return (double)acosf((float)(s.c1 - u * (s.c1 - s.c2)));
+    case SWIG_PRIOR_COSINE:
+      return (double)asinf((float)(s.c1 + u * (s.c2 - s.c1)));
+    case SWIG_PRIOR_POWER2:
+      return (double)cbrtf((float)(s.c1 + u * (s.c2 - s.c1)));
     default:
       return s.lo + u * (s.hi - s.lo);
   }

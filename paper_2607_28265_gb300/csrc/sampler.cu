@@ -49,7 +49,7 @@ constexpr int kFreeBudget = 8;  // projection-only evaluations per chain per rou
 enum ChainPhase { PH_NEW = 0, PH_LEFT = 1, PH_RIGHT = 2, PH_SHRINK = 3 };
 // What a Gibbs block moves: waveform coefficients, amplitude A(Mc)/d_L,
 // projection P_i, time shifts tau_i.
-enum BlockFlag { BF_INTR = 1, BF_AMP = 2, BF_PROJ = 4, BF_TAU = 8 };
+enum BlockFlag { BF_INTR = 1, BF_AMP = 2, BF_PROJ = 4, BF_TAU = 8, BF_SPIN = 16, BF_TIDE = 32 };
 enum RunStatus { ST_RUNNING = 0, ST_TERMINATED = 1, ST_LIMIT = 2 };
 
 struct SamplerConst {
@@ -95,6 +95,9 @@ struct NSGlobal {
   // phase timers of CTA 0 [ns, %globaltimer]: boundary, control, wait after
   // control, sweep, wait after sweep; and rounds
   unsigned long long t_bound, t_ctrl, t_wait_ctrl, t_sweep, t_wait_sweep, rounds;
+  // chain 0's control breakdown [clock64 cycles]: pending result, new step,
+  // proposal + transform, projection-only evaluations, full setup; counts
+  unsigned long long c_result, c_step, c_prop, c_free, c_setup, n_free, n_setup, n_step;
 };
 
 __device__ __forceinline__ unsigned long long gtimer() {
@@ -362,14 +365,33 @@ __device__ inline void start_step(const SamplerConst& S, ChainState& ch, const f
 // record in *rec.  Only the Gibbs block's slots are transformed and only the
 // pieces of the record that the block moves are recomputed.  Lane 0 only.
 template <bool MIXED>
-__device__ void chain_advance(const LikeConst& L, const SamplerConst& S, const SamplerPtrs& P, int c,
-                              const double* kap_in, double ly_in, EvalRecord* rec) {
-  ChainState& ch = P.chains[c];
-  EvalRecord& rx = P.recx[c];
+__device__ __noinline__ void chain_advance_local(const LikeConst& L, const SamplerConst& S, const SamplerPtrs& P, int c,
+                                    const double* kap_in, double ly_in, ChainState& ch, EvalRecord& rx,
+                                    bool& rx_dirty, EvalRecord& rec, bool& rec_set) {
   NSGlobal* g = P.g;
   const double logl_star = g->logl_star;
   const long long it = g->iter;
   if (ch.done) return;
+  const bool prof = (c == 0);
+  long long tk = clock64();
+  unsigned long long acc_res = 0, acc_step = 0, acc_prop = 0, acc_free = 0, acc_setup = 0, cnt_free = 0, cnt_setup = 0,
+                     cnt_step = 0;
+  struct Flush {
+    NSGlobal* g;
+    bool on;
+    unsigned long long *a0, *a1, *a2, *a3, *a4, *n0, *n1, *n2;
+    __device__ ~Flush() {
+      if (!on) return;
+      g->c_result += *a0;
+      g->c_step += *a1;
+      g->c_prop += *a2;
+      g->c_free += *a3;
+      g->c_setup += *a4;
+      g->n_free += *n0;
+      g->n_setup += *n1;
+      g->n_step += *n2;
+    }
+  } flush{g, prof, &acc_res, &acc_step, &acc_prop, &acc_free, &acc_setup, &cnt_free, &cnt_setup, &cnt_step};
   if (ch.pending) {
     ch.pending = 0;
     ++ch.n_full;
@@ -377,16 +399,30 @@ __device__ void chain_advance(const LikeConst& L, const SamplerConst& S, const S
     if (apply_result(S, ch, ly_in, logl_star, g)) {
       move_to_proposal(S, ch, ly_in);
       for (int j = 0; j < 2 * SWIG_MAX_DET; ++j) ch.kap[j] = kap_in[j];
-      rx = *rec;
+      rx = rec;
+      rx_dirty = true;
       ch.proj_dirty = 0;
       finish_step(S, ch, g);
     }
+  }
+  if (prof) {
+    const long long t2 = clock64();
+    acc_res += t2 - tk;
+    tk = t2;
   }
   int free_left = kFreeBudget;
   for (int guard = 0; guard < 1 << 20 && !ch.done; ++guard) {
     const int b = ch.block;
     if (S.block_free[b] && free_left <= 0) return;  // resume next round
-    if (ch.phase == PH_NEW) start_step(S, ch, P.chol, c, it);
+    if (ch.phase == PH_NEW) {
+      start_step(S, ch, P.chol, c, it);
+      if (prof) {
+        const long long t2 = clock64();
+        acc_step += t2 - tk;
+        cnt_step += 1;
+        tk = t2;
+      }
+    }
     double t;
     if (ch.phase == PH_LEFT)
       t = ch.lo;
@@ -412,7 +448,12 @@ __device__ void chain_advance(const LikeConst& L, const SamplerConst& S, const S
     for (int q = 0; q < SWIG_N_PARAMS; ++q) ch.th_y[q] = ch.th[q];
     for (int r = 0; r < nb; ++r) {
       const int j = S.block_dims[b][r], slot = S.slot_of_dim[j];
-      ch.th_y[slot] = prior_slot_inverse(S.prior[slot], ch.y[j]);
+      ch.th_y[slot] = MIXED ? prior_slot_inverse_f32(S.prior[slot], ch.y[j]) : prior_slot_inverse(S.prior[slot], ch.y[j]);
+    }
+    if (prof) {
+      const long long t2 = clock64();
+      acc_prop += t2 - tk;
+      tk = t2;
     }
     if (S.block_free[b]) {
       --free_left;
@@ -423,6 +464,12 @@ __device__ void chain_advance(const LikeConst& L, const SamplerConst& S, const S
           move_to_proposal(S, ch, ly);
           ch.proj_dirty = 1;
           finish_step(S, ch, g);
+        }
+        if (prof) {
+          const long long t2 = clock64();
+          acc_free += t2 - tk;
+          cnt_free += 1;
+          tk = t2;
         }
       } else {
         EvalRecord tmp = rx;
@@ -439,28 +486,54 @@ __device__ void chain_advance(const LikeConst& L, const SamplerConst& S, const S
         if (apply_result(S, ch, ly, logl_star, g)) {
           move_to_proposal(S, ch, ly);
           rx = tmp;
+          rx_dirty = true;
           finish_step(S, ch, g);
         }
       }
       continue;
     }
-    *rec = rx;
+    rec = rx;
     const int fl = S.block_flags[b] | (ch.proj_dirty ? (BF_AMP | BF_PROJ) : 0);
-    rec->valid = theta_valid(ch.th_y) ? 1 : 0;
-    if (fl & BF_INTR) setup_intrinsic(ch.th_y, rec);
+    rec.valid = theta_valid(ch.th_y) ? 1 : 0;
+    if (fl & BF_INTR)
+      setup_intrinsic(ch.th_y, &rec);
+    else if (fl & (BF_SPIN | BF_TIDE))
+      setup_intrinsic_partial(ch.th_y, &rec, (fl & BF_SPIN) != 0, (fl & BF_TIDE) != 0);
     if (MIXED) {
-      if (fl & BF_AMP) setup_amp_f32(ch.th_y, rec);
-      if (fl & BF_PROJ) setup_projection_f32(L, ch.th_y, rec);
+      if (fl & BF_AMP) setup_amp_f32(ch.th_y, &rec);
+      if (fl & BF_PROJ) setup_projection_f32(L, ch.th_y, &rec);
     } else {
-      if (fl & BF_AMP) setup_amp(ch.th_y, rec);
-      if (fl & BF_PROJ) setup_projection(L, ch.th_y, rec);
+      if (fl & BF_AMP) setup_amp(ch.th_y, &rec);
+      if (fl & BF_PROJ) setup_projection(L, ch.th_y, &rec);
     }
-    if (fl & BF_TAU) setup_delays(L, ch.th_y, rec);
-    setup_combine(L, rec);
+    if (fl & BF_TAU) setup_delays(L, ch.th_y, &rec);
+    setup_combine(L, &rec);
+    rec_set = true;
     ch.pending = 1;
     P.pending[c] = 1;
+    if (prof) {
+      acc_setup += clock64() - tk;
+      cnt_setup += 1;
+    }
     return;
   }
+}
+
+// Chain control on local copies of the chain state and records (local
+// memory is cached in L1; the global copies are read and written once).
+template <bool MIXED>
+__device__ __noinline__ void chain_advance(const LikeConst& L, const SamplerConst& S, const SamplerPtrs& P, int c,
+                              const double* kap_in, double ly_in, EvalRecord* rec_out) {
+  if (P.chains[c].done) return;
+  ChainState ch = P.chains[c];
+  EvalRecord rx = P.recx[c];
+  EvalRecord rec;
+  if (ch.pending) rec = *rec_out;
+  bool rx_dirty = false, rec_set = false;
+  chain_advance_local<MIXED>(L, S, P, c, kap_in, ly_in, ch, rx, rx_dirty, rec, rec_set);
+  P.chains[c] = ch;
+  if (rx_dirty) P.recx[c] = rx;
+  if (rec_set) *rec_out = rec;
 }
 
 // ---------------------------------------------------------------------------
@@ -492,7 +565,7 @@ __device__ void block_reduce_max_sum(double* vals, int n, double* out_max, doubl
   __syncthreads();
 }
 
-__device__ void ns_boundary(const LikeConst& L, const SamplerConst& S, const SamplerPtrs& P, unsigned char* smem) {
+__device__ __noinline__ void ns_boundary(const LikeConst& L, const SamplerConst& S, const SamplerPtrs& P, unsigned char* smem) {
   NSGlobal* g = P.g;
   const int tid = threadIdx.x, nt = blockDim.x;
   const int m = S.nlive, k = S.nrep, d = S.ndim;
@@ -987,7 +1060,9 @@ int swig_run(swig_ctx* c, swig_result* out) {
         S.block_dims[b][S.block_size[b]++] = j;
         const int slot = S.slot_of_dim[j];
         free_block = free_block && (slot == 6 || slot == 7 || slot == 8 || slot == 12);
-        if (slot <= 5) flags |= BF_INTR;
+        if (slot <= 1) flags |= BF_INTR;
+        if (slot == 2 || slot == 3) flags |= BF_SPIN;
+        if (slot == 4 || slot == 5) flags |= BF_TIDE;
         if (slot == 0 || slot == 6) flags |= BF_AMP;
         if (slot == 7 || slot == 8 || slot == 9 || slot == 10 || slot == 12) flags |= BF_PROJ;
         if (slot == 9 || slot == 10 || slot == 11) flags |= BF_TAU;
@@ -1212,6 +1287,14 @@ int swig_run(swig_ctx* c, swig_result* out) {
   c->profile[9] = (double)c->h2d_bytes;
   c->profile[10] = (double)c->d2h_bytes;
   c->profile[11] = (double)nf * (double)L.n_det * (double)L.n_bins;  // bin-detector evaluations
+  c->profile[12] = (double)gh.c_result;
+  c->profile[13] = (double)gh.c_step;
+  c->profile[14] = (double)gh.c_prop;
+  c->profile[15] = (double)gh.c_free;
+  c->profile[16] = (double)gh.c_setup;
+  c->profile[17] = (double)gh.n_free;
+  c->profile[18] = (double)gh.n_setup;
+  c->profile[19] = (double)gh.n_step;
   cudaEventDestroy(ev0);
   cudaEventDestroy(ev1);
   return SWIG_OK;
@@ -1220,7 +1303,7 @@ int swig_run(swig_ctx* c, swig_result* out) {
 int swig_get_profile(swig_ctx* c, double* out, int n) {
   if (!c) return SWIG_E_ARG;
   if (!out || n < 0) return fail(c, SWIG_E_ARG, "null output");
-  for (int i = 0; i < n && i < 12; ++i) out[i] = c->profile[i];
+  for (int i = 0; i < n && i < 20; ++i) out[i] = c->profile[i];
   return SWIG_OK;
 }
 

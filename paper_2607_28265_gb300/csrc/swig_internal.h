@@ -63,6 +63,7 @@ struct EvalRecord {
   double cre[SWIG_MAX_DET], cim[SWIG_MAX_DET];  // C_i (see loglike epilogue)
   double pre[SWIG_MAX_DET], pim[SWIG_MAX_DET];  // projection P_i, C_i = amp P_i
   double amp;                    // A(Mc) / d_L
+  double mterm[8];               // cached mass factors (eta, dm, m1, m2, A, r, ir, ln pi M)
   double hh;                     // sum_i |C_i|^2 K_i
   int valid;
   int pad;

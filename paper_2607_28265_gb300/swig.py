@@ -227,7 +227,8 @@ class Context:
 
     PROFILE_KEYS = ("rounds", "boundary_s", "control_s", "wait_control_s", "sweep_s", "wait_sweep_s",
                     "persistent_ms", "persistent_launches", "kernel_launches", "h2d_bytes", "d2h_bytes",
-                    "bin_det_evals")
+                    "bin_det_evals", "cyc_result", "cyc_step", "cyc_prop", "cyc_free", "cyc_setup", "n_free",
+                    "n_setup", "n_step")
 
     def profile(self):
         out = np.zeros(len(self.PROFILE_KEYS))
