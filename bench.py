@@ -44,33 +44,6 @@ def workload_description(wl):
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
-def build_context(wl, seed_offset=0):
-    """Synthetic event through the library's own API: PSDs and noise from the
-    seeded input module, the injection computed by the library (device FP64)."""
-    from paper_2607_28265_gb300 import swig
-
-    ctx = swig.Context(0)
-    ctx.set_grid(wl.f_min, wl.f_max, wl.df)
-    for i, name in enumerate(wl.detectors):
-        ctx.set_detector(i, *si.site_vectors(name))
-    ctx.set_time_ref(si.gmst_from_gps(si.REFERENCE_GPS))
-    psds = wl.psds()
-    for i, s in enumerate(psds):
-        ctx.set_psd(i, s)
-    ctx.set_prior(wl.params)
-    u = np.asarray(wl.injection)
-    sampled = wl.sampled()
-    th = ctx.prior_transform(u[sampled][None, :])[0]
-    th[si.IDX["phic"]] = 2.0 * math.pi * u[si.IDX["phic"]]
-    noise = np.array(wl.noise())
-    data, th_used = ctx.inject(th, len(wl.detectors), target_snr=wl.target_snr, noise=noise)
-    for i in range(len(wl.detectors)):
-        ctx.set_data(i, data[i])
-    ctx.set_sampler(nlive=wl.nlive, nrep=wl.nrep, sweeps=wl.sweeps, steps_per_dim=wl.steps_per_dim,
-                    seed=wl.sampler_seed + seed_offset, precision=swig.PREC_MIXED)
-    return ctx, data, psds, th_used
-
-
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled during the timed region."""
 
@@ -127,7 +100,7 @@ class ClockSampler:
 def run_gpu(args, rank, world):
     import torch
 
-    from paper_2607_28265_gb300 import swig
+    from paper_2607_28265_gb300.workloads import build_context
 
     torch.cuda.set_device(0 if world == 1 else int(os.environ.get("LOCAL_RANK", rank)))
     wl = si.config2()

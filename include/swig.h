@@ -138,7 +138,16 @@ int swig_set_sampler(swig_ctx* ctx, const swig_sampler_cfg* cfg);
  * marginalised form log I0(|Z|) - 1/2 sum <h|h> - 1/2 sum <d|d> (Sec. 3.1).
  * theta: n x 13 doubles (row-major, host).  out_logl: n doubles (host).
  * Precision and likelihood type follow the sampler configuration (FULL and
- * MIXED if none was set).  n == 0 is a no-op; n > 2^20 -> SWIG_E_ARG. */
+ * MIXED if none was set).  n == 0 is a no-op; n > 2^20 -> SWIG_E_ARG.
+ * With SWIG_LIKE_HET the heterodyned (relative-binning) approximation of
+ * Sec. 3.4 is evaluated instead: the grid is cut into het_bins bins of equal
+ * maximum phase change (het_spacing 0; 1 = geometric), edges snapped to grid
+ * frequencies; summary data A0, A1, B0, B1 of the fiducial waveform
+ * het_fiducial are formed once in FP64 (phi_c set to 0 when marginalised);
+ * h/h0 is taken linear in each bin (value at the centre, slope), so
+ *   <d|h> ~ Re sum_b (A0 r0 + A1 r1),  <h|h> ~ sum_b (B0 |r0|^2 + 2 B1 Re(r0 r1*)).
+ * The per-bin contraction is FP32 with double-float phase differences; the
+ * precision setting does not apply.  An invalid fiducial -> SWIG_E_ARG. */
 int swig_loglike_batch(swig_ctx* ctx, const double* theta, int64_t n, double* out_logl);
 /* Same with device pointers on the context's device, enqueued on `stream`
  * (cudaStream_t).  Uses the context's scratch buffers, so calls on one
@@ -158,7 +167,8 @@ int swig_loglike_batch_dev(swig_ctx* ctx, const double* theta_dev, int64_t n,
  *     process exits.  Batches that do not fit return SWIG_E_ARG with the
  *     capacity in the message (about 250 parameter vectors on the 128 s,
  *     three-detector grid); split larger batches.
- *   - The context must already be prepared, for SWIG_PREC_MIXED, by an
+ *   - Full-grid likelihood only.  The context must already be prepared, for
+ *     SWIG_LIKE_FULL and SWIG_PREC_MIXED, by an
  *     earlier swig_loglike_batch / swig_loglike_batch_dev / swig_run call with
  *     the current data (preparation allocates); otherwise SWIG_E_STATE.
  *   - The first call on a device looks up the array's device address (no

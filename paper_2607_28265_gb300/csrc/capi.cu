@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <iterator>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -216,11 +217,148 @@ void free_problem(DeviceBuffers& B) {
   dfree(B.prior);
   dfree(B.piece_begin);
   dfree(B.slice_piece);
+  dfree(B.het_edge_basis);
+  dfree(B.het_edge_f);
+  dfree(B.het_inv_width);
+  dfree(B.het_coef);
+  dfree(B.het_coefB);
+  dfree(B.het_fid);
+  B.het_nb = 0;
+}
+
+// Bin edges (grid indices) of the heterodyned likelihood.  spacing 0: equal
+// increments of the maximum dephasing g(f) = sum_gamma sign(gamma) (f/f*)^gamma,
+// gamma in {-5/3, -2/3, 1, 5/3, 7/3}, f* = f_lo for gamma < 0 and f_hi
+// otherwise (Zackay, Dai & Venumadhav 2018); spacing 1: geometric.  Targets are
+// snapped to the first grid frequency at or above them; duplicates dropped.
+std::vector<int> het_edge_indices(const std::vector<double>& f, int nb, int spacing) {
+  const int n = (int)f.size();
+  std::vector<double> g(n);
+  const double f_lo = f.front(), f_hi = f.back();
+  if (spacing == 0) {
+    const double gam[5] = {-5.0 / 3.0, -2.0 / 3.0, 1.0, 5.0 / 3.0, 7.0 / 3.0};
+    for (int k = 0; k < n; ++k) {
+      double v = 0.0;
+      for (double gm : gam) {
+        const double fs = gm < 0 ? f_lo : f_hi;
+        v += (gm < 0 ? -1.0 : 1.0) * std::pow(f[k] / fs, gm);
+      }
+      g[k] = v;
+    }
+  } else {
+    g = f;
+  }
+  std::vector<int> idx;
+  const double ga = g.front(), gb = g.back();
+  for (int i = 0; i <= nb; ++i) {
+    double t;
+    if (spacing == 0) {
+      t = (i == nb) ? gb : ga + i * ((gb - ga) / nb);
+    } else {
+      const double l0 = std::log10(f_lo), l1 = std::log10(f_hi);
+      t = (i == 0) ? f_lo : (i == nb) ? f_hi : std::pow(10.0, l0 + i * ((l1 - l0) / nb));
+    }
+    int k = (int)(std::lower_bound(g.begin(), g.end(), t) - g.begin());
+    if (i == 0) k = 0;
+    if (i == nb) k = n - 1;
+    k = std::min(k, n - 1);
+    if (idx.empty() || k > idx.back()) idx.push_back(k);
+  }
+  if (idx.back() != n - 1) idx.push_back(n - 1);
+  return idx;
 }
 
 }  // namespace
 
 namespace swig {
+
+// Summary data of the heterodyned likelihood (host FP64 from the device FP64
+// fiducial waveform) and the per-edge basis tables.
+int prepare_het(swig_ctx* c) {
+  LikeConst& L = c->L;
+  DeviceBuffers& B = c->B;
+  const int n = L.n_bins, n_det = L.n_det;
+  std::vector<double> f(n);
+  for (int k = 0; k < n; ++k) f[k] = (double)(c->k_min + k) * c->df;
+  const std::vector<int> idx = het_edge_indices(f, c->cfg.het_bins, c->cfg.het_spacing);
+  const int nb = (int)idx.size() - 1;
+  if (nb < 1) return fail(c, SWIG_E_ARG, "heterodyne needs at least one bin");
+  double th[SWIG_N_PARAMS];
+  for (int j = 0; j < SWIG_N_PARAMS; ++j) th[j] = c->cfg.het_fiducial[j];
+  if (L.phase_marg) th[12] = 0.0;
+  if (!(th[0] > 0.0) || !(th[1] > 0.0) || th[1] > 1.0 || !(th[6] > 0.0)) return fail(c, SWIG_E_ARG, "invalid fiducial theta");
+  double* th_d = nullptr;
+  double2* h_d = nullptr;
+  std::vector<double2> h0((size_t)n_det * n);
+  CUDA_TRY(c, cudaMalloc(&B.het_fid, sizeof(EvalRecord)));
+  CUDA_TRY(c, cudaMalloc(&th_d, sizeof(th)));
+  cudaError_t e = cudaMalloc(&h_d, sizeof(double2) * h0.size());
+  if (e == cudaSuccess) e = cudaMemcpy(th_d, th, sizeof(th), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = launch_waveform(L, th_d, B.het_fid, h_d, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e == cudaSuccess) e = cudaMemcpy(h0.data(), h_d, sizeof(double2) * h0.size(), cudaMemcpyDeviceToHost);
+  EvalRecord fid{};
+  if (e == cudaSuccess) e = cudaMemcpy(&fid, B.het_fid, sizeof(EvalRecord), cudaMemcpyDeviceToHost);
+  cudaFree(th_d);
+  if (h_d) cudaFree(h_d);
+  if (e != cudaSuccess) return fail(c, SWIG_E_CUDA, std::string("heterodyne fiducial: ") + cudaGetErrorString(e));
+  c->n_launches += 2;
+  c->d2h_bytes += sizeof(double2) * h0.size() + sizeof(EvalRecord);
+  if (!fid.valid) return fail(c, SWIG_E_ARG, "invalid fiducial theta");
+  for (int i = 0; i < n_det; ++i)
+    if (!(fid.cre[i] * fid.cre[i] + fid.cim[i] * fid.cim[i] > 0.0))
+      return fail(c, SWIG_E_ARG, "fiducial waveform vanishes in detector " + std::to_string(i));
+  // summary data per detector and bin
+  std::vector<float4> coef((size_t)n_det * nb);
+  std::vector<float2> coefB((size_t)n_det * nb);
+  std::vector<float> inv_w(nb);
+  for (int b = 0; b < nb; ++b) inv_w[b] = (float)(1.0 / (f[idx[b + 1]] - f[idx[b]]));
+  for (int i = 0; i < n_det; ++i) {
+    for (int b = 0; b < nb; ++b) {
+      const int k_end = (b == nb - 1) ? n : idx[b + 1];
+      const double fc = 0.5 * (f[idx[b]] + f[idx[b + 1]]);
+      NSum a0r, a0i, a1r, a1i, b0, b1;
+      for (int k = idx[b]; k < k_end; ++k) {
+        const double w = 4.0 * c->df / c->psd[i][k];
+        const double dr = c->data[i][2 * k], di = c->data[i][2 * k + 1];
+        const double hr = h0[(size_t)i * n + k].x, hi = h0[(size_t)i * n + k].y;
+        const double pr = (dr * hr + di * hi) * w, pi = (dr * hi - di * hr) * w;  // conj(d) h0 w
+        const double hh = (hr * hr + hi * hi) * w, off = f[k] - fc;
+        a0r.add(pr);
+        a0i.add(pi);
+        a1r.add(pr * off);
+        a1i.add(pi * off);
+        b0.add(hh);
+        b1.add(hh * off);
+      }
+      coef[(size_t)i * nb + b] = make_float4((float)a0r.value(), (float)a0i.value(), (float)a1r.value(), (float)a1i.value());
+      coefB[(size_t)i * nb + b] = make_float2((float)b0.value(), (float)b1.value());
+    }
+  }
+  std::vector<float> eb((size_t)(nb + 1) * 2 * NBASIS), ef((size_t)(nb + 1) * 2);
+  for (int q = 0; q <= nb; ++q) {
+    const double fe = f[idx[q]];
+    for (int j = 0; j < NBASIS; ++j) {
+      const double v = (j == B_ONE) ? 1.0 : basis_derivative(kBasisPow[j], kBasisLog[j], 0, fe);
+      split_df(v, &eb[(size_t)q * 2 * NBASIS + 2 * j], &eb[(size_t)q * 2 * NBASIS + 2 * j + 1]);
+    }
+    split_df(fe, &ef[2 * q], &ef[2 * q + 1]);
+  }
+  CUDA_TRY(c, cudaMalloc(&B.het_edge_basis, sizeof(float) * eb.size()));
+  CUDA_TRY(c, cudaMalloc(&B.het_edge_f, sizeof(float) * ef.size()));
+  CUDA_TRY(c, cudaMalloc(&B.het_inv_width, sizeof(float) * inv_w.size()));
+  CUDA_TRY(c, cudaMalloc(&B.het_coef, sizeof(float4) * coef.size()));
+  CUDA_TRY(c, cudaMalloc(&B.het_coefB, sizeof(float2) * coefB.size()));
+  CUDA_TRY(c, cudaMemcpy(B.het_edge_basis, eb.data(), sizeof(float) * eb.size(), cudaMemcpyHostToDevice));
+  CUDA_TRY(c, cudaMemcpy(B.het_edge_f, ef.data(), sizeof(float) * ef.size(), cudaMemcpyHostToDevice));
+  CUDA_TRY(c, cudaMemcpy(B.het_inv_width, inv_w.data(), sizeof(float) * inv_w.size(), cudaMemcpyHostToDevice));
+  CUDA_TRY(c, cudaMemcpy(B.het_coef, coef.data(), sizeof(float4) * coef.size(), cudaMemcpyHostToDevice));
+  CUDA_TRY(c, cudaMemcpy(B.het_coefB, coefB.data(), sizeof(float2) * coefB.size(), cudaMemcpyHostToDevice));
+  c->h2d_bytes += sizeof(float) * (eb.size() + ef.size() + inv_w.size()) + sizeof(float4) * coef.size() +
+                  sizeof(float2) * coefB.size();
+  B.het_nb = nb;
+  return SWIG_OK;
+}
 
 int ensure_scratch(swig_ctx* c, int n) {
   DeviceBuffers& B = c->B;
@@ -433,6 +571,11 @@ int prepare(swig_ctx* c) {
   CUDA_TRY(c, cudaMalloc(&B.prior, sizeof(slots)));
   CUDA_TRY(c, cudaMemcpy(B.prior, slots, sizeof(slots), cudaMemcpyHostToDevice));
   c->prepared_precision = prec;
+  c->prepared_like = c->cfg_set ? c->cfg.likelihood : SWIG_LIKE_FULL;
+  if (c->prepared_like == SWIG_LIKE_HET) {
+    const int rc = prepare_het(c);
+    if (rc) return rc;
+  }
   c->dirty = false;
   return SWIG_OK;
 }
@@ -443,10 +586,16 @@ int loglike_device(swig_ctx* c, const double* theta_dev, int64_t n, double* out_
     const int m = (int)std::min<int64_t>(chunk, n - off);
     int rc = ensure_scratch(c, m);
     if (rc) return rc;
-    cudaError_t e = c->prepared_precision == SWIG_PREC_MIXED
-                        ? launch_loglike_mixed(c->L, c->B, theta_dev + off * SWIG_N_PARAMS, m, out_dev + off, st)
-                        : launch_loglike_fp64(c->L, c->B, theta_dev + off * SWIG_N_PARAMS, m, out_dev + off, st);
-    c->n_launches += c->prepared_precision == SWIG_PREC_MIXED ? 4 : 3;
+    cudaError_t e;
+    if (c->prepared_like == SWIG_LIKE_HET) {
+      e = launch_loglike_het(c->L, c->B, theta_dev + off * SWIG_N_PARAMS, m, out_dev + off, st);
+      c->n_launches += 2;
+    } else {
+      e = c->prepared_precision == SWIG_PREC_MIXED
+              ? launch_loglike_mixed(c->L, c->B, theta_dev + off * SWIG_N_PARAMS, m, out_dev + off, st)
+              : launch_loglike_fp64(c->L, c->B, theta_dev + off * SWIG_N_PARAMS, m, out_dev + off, st);
+      c->n_launches += c->prepared_precision == SWIG_PREC_MIXED ? 4 : 3;
+    }
     if (e != cudaSuccess) return fail(c, SWIG_E_CUDA, std::string("likelihood launch: ") + cudaGetErrorString(e));
   }
   return SWIG_OK;
@@ -606,8 +755,12 @@ int swig_set_sampler(swig_ctx* c, const swig_sampler_cfg* cfg) {
   if (cfg->likelihood != SWIG_LIKE_FULL && cfg->likelihood != SWIG_LIKE_HET) return fail(c, SWIG_E_ARG, "bad likelihood");
   if (cfg->proposal != SWIG_PROPOSAL_COV && cfg->proposal != SWIG_PROPOSAL_LEARNED) return fail(c, SWIG_E_ARG, "bad proposal");
   if (cfg->likelihood == SWIG_LIKE_HET && (cfg->het_bins < 2 || cfg->het_bins > 65536)) return fail(c, SWIG_E_ARG, "het_bins must be in [2, 65536]");
+  if (cfg->het_spacing != 0 && cfg->het_spacing != 1) return fail(c, SWIG_E_ARG, "het_spacing must be 0 or 1");
   if (!(cfg->dlogz < 0.0) || cfg->max_iter < 1) return fail(c, SWIG_E_ARG, "need dlogz < 0 and max_iter >= 1");
-  if (c->cfg_set && (c->cfg.precision != cfg->precision || c->cfg.likelihood != cfg->likelihood)) c->dirty = true;
+  if (c->cfg_set && (c->cfg.precision != cfg->precision || c->cfg.likelihood != cfg->likelihood ||
+                     c->cfg.het_bins != cfg->het_bins || c->cfg.het_spacing != cfg->het_spacing ||
+                     std::memcmp(c->cfg.het_fiducial, cfg->het_fiducial, sizeof(cfg->het_fiducial)) != 0))
+    c->dirty = true;
   if (!c->cfg_set) c->dirty = true;
   c->cfg = *cfg;
   c->cfg_set = true;

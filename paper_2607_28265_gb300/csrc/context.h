@@ -37,6 +37,7 @@ struct swig_ctx {
   // prepared device state
   bool dirty = true;
   int prepared_precision = -1;
+  int prepared_like = SWIG_LIKE_FULL;
   swig::LikeConst L = {};
   swig::DeviceBuffers B;
   swig::SamplerState* sampler = nullptr;

@@ -32,6 +32,14 @@ struct DeviceBuffers {
   int n_pieces = 0;              // total pieces (work units per theta)
   int max_pieces = 1;            // pieces of the largest slice
   int max_slice_bins = 0;
+  // heterodyned likelihood tables (SWIG_LIKE_HET)
+  int het_nb = 0;
+  float* het_edge_basis = nullptr;  // [N_b + 1][2 * NBASIS]
+  float* het_edge_f = nullptr;      // [N_b + 1][2]
+  float* het_inv_width = nullptr;   // [N_b]
+  float4* het_coef = nullptr;       // [n_det][N_b]
+  float2* het_coefB = nullptr;      // [n_det][N_b]
+  EvalRecord* het_fid = nullptr;    // fiducial record
   // scratch for batched evaluation, sized for `cap` thetas
   int cap = 0;
   EvalRecord* rec = nullptr;     // [cap]
@@ -52,6 +60,9 @@ cudaError_t launch_loglike_fp64(const LikeConst& L, const DeviceBuffers& B, cons
 // Setup record and detector strain of one theta (FP64) into out [n_det][n_bins].
 cudaError_t launch_waveform(const LikeConst& L, const double* theta_dev, EvalRecord* rec_dev, double2* out,
                             cudaStream_t st);
+// Heterodyned logL of n thetas (device pointers), one warp per theta.
+cudaError_t launch_loglike_het(const LikeConst& L, const DeviceBuffers& B, const double* theta, int n, double* out,
+                               cudaStream_t st);
 cudaError_t launch_prior_transform(const PriorSlot* slots, int n_sampled, const double* u, int n, double* theta,
                                    cudaStream_t st);
 cudaError_t set_sweep_smem_limit(size_t bytes);

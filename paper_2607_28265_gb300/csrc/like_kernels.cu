@@ -21,6 +21,7 @@
 #include <cuda_runtime.h>
 
 #include "kernels.h"
+#include "het.cuh"
 #include "sweep.cuh"
 
 namespace swig {
@@ -129,6 +130,45 @@ __global__ void k_reduce(LikeConst L, const T* __restrict__ partials, int n_unit
     if (kappa_out)
       for (int j = 0; j < 2 * SWIG_MAX_DET; ++j) kappa_out[(size_t)th * 2 * SWIG_MAX_DET + j] = acc[j];
   }
+}
+
+// ---------------------------------------------------------------------------
+// Heterodyned likelihood, one warp per theta.
+// ---------------------------------------------------------------------------
+inline HetTables het_tables(const DeviceBuffers& B) {
+  HetTables H;
+  H.n_bins = B.het_nb;
+  H.edge_basis = B.het_edge_basis;
+  H.edge_f = B.het_edge_f;
+  H.inv_width = B.het_inv_width;
+  H.coef = B.het_coef;
+  H.coefB = B.het_coefB;
+  H.fid = B.het_fid;
+  return H;
+}
+
+template <int NDET>
+__global__ void k_het(LikeConst L, HetTables H, const EvalRecord* __restrict__ rec, int n, double* __restrict__ out) {
+  const int th = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (th >= n) return;
+  const double v = het_loglike_warp<NDET>(L, H, rec[th], lane);
+  if (lane == 0) out[th] = v;
+}
+
+cudaError_t launch_loglike_het(const LikeConst& L, const DeviceBuffers& B, const double* theta, int n, double* out,
+                               cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  k_setup<<<(n + 127) / 128, 128, 0, st>>>(L, theta, n, B.rec);
+  const HetTables H = het_tables(B);
+  const unsigned grid = (unsigned)((n + 3) / 4);
+  switch (L.n_det) {
+    case 1: k_het<1><<<grid, 128, 0, st>>>(L, H, B.rec, n, out); break;
+    case 2: k_het<2><<<grid, 128, 0, st>>>(L, H, B.rec, n, out); break;
+    case 3: k_het<3><<<grid, 128, 0, st>>>(L, H, B.rec, n, out); break;
+    default: k_het<4><<<grid, 128, 0, st>>>(L, H, B.rec, n, out); break;
+  }
+  return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------

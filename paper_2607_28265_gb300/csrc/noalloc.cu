@@ -63,8 +63,8 @@ extern "C" int swig_loglike_batch_noalloc(swig_ctx* c, const double* theta_dev, 
     c->err = "need n >= 0 and non-null device buffers";
     return SWIG_E_ARG;
   }
-  if (c->dirty || c->prepared_precision != SWIG_PREC_MIXED) {
-    c->err = "the context must be prepared for mixed precision by an earlier swig_loglike_batch(_dev) or "
+  if (c->dirty || c->prepared_precision != SWIG_PREC_MIXED || c->prepared_like != SWIG_LIKE_FULL) {
+    c->err = "the context must be prepared for the mixed-precision full-grid likelihood by an earlier swig_loglike_batch(_dev) or "
              "swig_run call with the current problem (preparation allocates; this entry point does not)";
     return SWIG_E_STATE;
   }
