@@ -32,6 +32,11 @@ import swig_inputs as si  # noqa: E402
 
 SFU_OPS_PER_CLK_SM = 16   # sin/cos results per clock per SM (sm_100-class SFU)
 SFU_OPS_PER_BIN_DET = 2   # one sine and one cosine per bin and detector
+# DRAM bytes (read + write) per logL evaluation inside k_ns_persistent, from one
+# ncu capture of a 2-iteration launch on this workload (14.27 MB / 106,944
+# evaluations; profiles/k_ns_persistent_cfg2_hlv_128s_2iter.md), scaled to a
+# full launch by its evaluations.
+TRAFFIC_B_PER_EVAL = 14.27328e6 / 106944
 METRIC = "logL evals/s (128 s 3-det BNS) and wall-s/posterior, plain vs learned+mixed"
 
 
@@ -214,7 +219,8 @@ def run_gpu(args, rank, world):
             "peak": peak,
             "unit": "SFU Top/s",
             "frac": achieved / peak if peak else None,
-            "traffic": None,
+            "traffic": TRAFFIC_B_PER_EVAL * total_evals / max(1, pers_launch),
+            "traffic_unit": "bytes per launch (ncu, 2-iteration capture scaled by evaluations)",
             "work_per_launch": "2 SFU ops x bin-detector evaluations (full-grid evals x 3 x 259585)",
             "launches": int(pers_launch),
             "avg_launch_ms": pers_ms / max(1, pers_launch),
