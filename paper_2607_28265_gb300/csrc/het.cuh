@@ -27,6 +27,18 @@ struct HetTables {
   const EvalRecord* fid;      // fiducial record
 };
 
+__host__ __device__ inline HetTables het_tables(const DeviceBuffers& B) {
+  HetTables H;
+  H.n_bins = B.het_nb;
+  H.edge_basis = B.het_edge_basis;
+  H.edge_f = B.het_edge_f;
+  H.inv_width = B.het_inv_width;
+  H.coef = B.het_coef;
+  H.coefB = B.het_coefB;
+  H.fid = B.het_fid;
+  return H;
+}
+
 // One warp evaluates the heterodyned logL of record r (all lanes return it).
 // z_out/hh_out (optional, lane-uniform): per-detector Z_i (re, im) and HH_i.
 template <int NDET>

@@ -135,18 +135,6 @@ __global__ void k_reduce(LikeConst L, const T* __restrict__ partials, int n_unit
 // ---------------------------------------------------------------------------
 // Heterodyned likelihood, one warp per theta.
 // ---------------------------------------------------------------------------
-inline HetTables het_tables(const DeviceBuffers& B) {
-  HetTables H;
-  H.n_bins = B.het_nb;
-  H.edge_basis = B.het_edge_basis;
-  H.edge_f = B.het_edge_f;
-  H.inv_width = B.het_inv_width;
-  H.coef = B.het_coef;
-  H.coefB = B.het_coefB;
-  H.fid = B.het_fid;
-  return H;
-}
-
 template <int NDET>
 __global__ void k_het(LikeConst L, HetTables H, const EvalRecord* __restrict__ rec, int n, double* __restrict__ out) {
   const int th = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);

@@ -34,6 +34,7 @@
 #include <vector>
 
 #include "context.h"
+#include "het.cuh"
 #include "sweep.cuh"
 
 namespace swig {
@@ -45,6 +46,7 @@ constexpr int kMaxShrink = 100;
 constexpr int kMaxSort = 8192;
 constexpr int kMaxChains = 2048;
 
+constexpr int kHetThreads = 256;  // heterodyned sampler: 8 chains per CTA
 constexpr int kFreeBudget = 8;  // projection-only evaluations per chain per round
 enum ChainPhase { PH_NEW = 0, PH_LEFT = 1, PH_RIGHT = 2, PH_SHRINK = 3 };
 // What a Gibbs block moves: waveform coefficients, amplitude A(Mc)/d_L,
@@ -890,6 +892,60 @@ __global__ void __launch_bounds__(kSweepThreads, 1)
   }
 }
 
+// Persistent sampler for the heterodyned likelihood (Sec. 3.4).  A
+// heterodyned evaluation is a few hundred to a few thousand bins, so the
+// chain's own warp evaluates every proposal right after its control step: the
+// chains of one NS iteration run to completion independently, and the grid
+// meets only at the iteration boundary.  Every proposal is evaluated in full
+// (no projection-only shortcut) and the set-up is FP64.
+template <int NDET>
+__global__ void __launch_bounds__(kHetThreads, 1)
+    k_ns_het(LikeConst L, SamplerConst S, DeviceBuffers B, SamplerPtrs P) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int lane = threadIdx.x & 31;
+  const int gw = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int n_warps = gridDim.x * (blockDim.x >> 5);
+  NSGlobal* g = P.g;
+  const HetTables H = het_tables(B);
+  const bool timer = blockIdx.x == 0 && threadIdx.x == 0;
+  unsigned long long t0 = gtimer(), t1;
+  for (;;) {
+    if (!grid_sync(g, S.n_ctas, S.spin_limit)) return;
+    if (timer) {
+      t1 = gtimer();
+      g->t_wait_sweep += t1 - t0;
+      t0 = t1;
+      g->rounds += 1;
+    }
+    if (blockIdx.x == 0) ns_boundary(L, S, P, smem);
+    if (!grid_sync(g, S.n_ctas, S.spin_limit)) return;
+    if (timer) {
+      t1 = gtimer();
+      g->t_bound += t1 - t0;
+      t0 = t1;
+    }
+    if (*(volatile int*)&g->status != ST_RUNNING) return;
+    for (int c = gw; c < S.nrep; c += n_warps) {
+      double kap0[2 * SWIG_MAX_DET];
+#pragma unroll
+      for (int j = 0; j < 2 * SWIG_MAX_DET; ++j) kap0[j] = 0.0;
+      double ly = 0.0;
+      for (long long guard = 0; guard < (1ll << 24); ++guard) {
+        if (lane == 0) chain_advance<false>(L, S, P, c, kap0, ly, &B.rec[c]);
+        __syncwarp();
+        if (*(volatile int*)&P.chains[c].done) break;
+        ly = het_loglike_warp<NDET>(L, H, B.rec[c], lane);
+        __syncwarp();
+      }
+    }
+    if (timer) {
+      t1 = gtimer();
+      g->t_ctrl += t1 - t0;
+      t0 = t1;
+    }
+  }
+}
+
 // Initial live set: m unit-cube draws (Philox, stream tag 2) and their theta.
 __global__ void k_init_live(SamplerConst S, double* live_u, double* theta) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -983,6 +1039,15 @@ void* pick_kernel(int n_det, bool mixed) {
   }
 }
 
+void* pick_het_kernel(int n_det) {
+  switch (n_det) {
+    case 1: return (void*)k_ns_het<1>;
+    case 2: return (void*)k_ns_het<2>;
+    case 3: return (void*)k_ns_het<3>;
+    default: return (void*)k_ns_het<4>;
+  }
+}
+
 }  // namespace
 }  // namespace swig
 
@@ -1011,16 +1076,17 @@ int swig_run(swig_ctx* c, swig_result* out) {
   std::memset(out, 0, sizeof(*out));
   if (!c->prior_set) return fail(c, SWIG_E_STATE, "prior not set");
   if (!c->cfg_set) return fail(c, SWIG_E_STATE, "sampler not configured");
-  if (c->cfg.likelihood != SWIG_LIKE_FULL) return fail(c, SWIG_E_ARG, "this library build samples the full-grid likelihood only");
   if (c->cfg.nlive > kMaxSort) return fail(c, SWIG_E_ARG, "nlive must be <= 8192 for the device sort");
   if (c->cfg.nrep > kMaxChains) return fail(c, SWIG_E_ARG, "nrep must be <= 2048");
   int rc = prepare(c);
   if (rc) return rc;
   const auto t_start = std::chrono::steady_clock::now();
-  const bool mixed = c->prepared_precision == SWIG_PREC_MIXED;
+  const bool het = c->prepared_like == SWIG_LIKE_HET;
+  const bool mixed = !het && c->prepared_precision == SWIG_PREC_MIXED;
   const int m = c->cfg.nlive, k = c->cfg.nrep;
   const LikeConst& L = c->L;
-  if (k > 32 * L.n_slices) return fail(c, SWIG_E_ARG, "nrep exceeds 32 chains per CTA");
+  if (!het && k > 32 * L.n_slices) return fail(c, SWIG_E_ARG, "nrep exceeds 32 chains per CTA");
+  const int het_ctas = std::max(1, std::min(c->sm_count, (k + kHetThreads / 32 - 1) / (kHetThreads / 32)));
 
   SamplerConst S;
   std::memset(&S, 0, sizeof(S));
@@ -1032,7 +1098,7 @@ int swig_run(swig_ctx* c, swig_result* out) {
   S.key0 = (unsigned)(c->cfg.seed & 0xFFFFFFFFu);
   S.key1 = (unsigned)(c->cfg.seed >> 32);
   S.mixed = mixed ? 1 : 0;
-  S.n_ctas = L.n_slices;
+  S.n_ctas = het ? het_ctas : L.n_slices;
   S.spin_limit = c->wait_limit;
   int nd = 0;
   for (int i = 0; i < SWIG_N_PARAMS; ++i) {
@@ -1067,7 +1133,7 @@ int swig_run(swig_ctx* c, swig_result* out) {
         if (slot == 7 || slot == 8 || slot == 9 || slot == 10 || slot == 12) flags |= BF_PROJ;
         if (slot == 9 || slot == 10 || slot == 11) flags |= BF_TAU;
       }
-    S.block_free[b] = free_block ? 1 : 0;
+    S.block_free[b] = (free_block && !het) ? 1 : 0;
     S.block_flags[b] = flags;
   }
   S.m_pow2 = 1;
@@ -1092,7 +1158,7 @@ int swig_run(swig_ctx* c, swig_result* out) {
   const size_t sweep_bytes = anchor_bytes + (size_t)S.group * max_pieces * kPartialStride * sizeof(double);
   const size_t sort_bytes = (size_t)S.m_pow2 * (sizeof(double) + sizeof(int)) + kSweepThreads * sizeof(double) +
                             (size_t)k * sizeof(double) + (kMaxDim + kMaxDim * kMaxDim) * sizeof(float) + 64;
-  const size_t smem = fixed + std::max(sweep_bytes, sort_bytes);
+  const size_t smem = het ? sort_bytes : fixed + std::max(sweep_bytes, sort_bytes);
   if (smem > 220 * 1024) return fail(c, SWIG_E_ARG, "problem too large for the persistent kernel's shared memory");
 
   // buffers
@@ -1141,8 +1207,14 @@ int swig_run(swig_ctx* c, swig_result* out) {
   k_init_live<<<(m + 127) / 128, 128, 0, c->stream>>>(S, st->P.live_u, st->init_theta);
   SCUDA(cudaGetLastError());
   {
-    cudaError_t e = mixed ? launch_loglike_mixed(L, c->B, st->init_theta, m, st->P.live_logl, c->stream, st->P.live_kap)
-                          : launch_loglike_fp64(L, c->B, st->init_theta, m, st->P.live_logl, c->stream, st->P.live_kap);
+    cudaError_t e;
+    if (het) {
+      e = cudaMemsetAsync(st->P.live_kap, 0, sizeof(double) * m * 2 * SWIG_MAX_DET, c->stream);
+      if (e == cudaSuccess) e = launch_loglike_het(L, c->B, st->init_theta, m, st->P.live_logl, c->stream);
+    } else {
+      e = mixed ? launch_loglike_mixed(L, c->B, st->init_theta, m, st->P.live_logl, c->stream, st->P.live_kap)
+                : launch_loglike_fp64(L, c->B, st->init_theta, m, st->P.live_logl, c->stream, st->P.live_kap);
+    }
     SCUDA(e);
   }
   NSGlobal g0;
@@ -1155,11 +1227,12 @@ int swig_run(swig_ctx* c, swig_result* out) {
   SCUDA(cudaMemsetAsync(st->P.pending, 0, sizeof(int) * k, c->stream));
   SCUDA(cudaMemsetAsync(st->P.chains, 0, sizeof(ChainState) * k, c->stream));
 
-  void* kern = pick_kernel(L.n_det, mixed);
+  void* kern = het ? pick_het_kernel(L.n_det) : pick_kernel(L.n_det, mixed);
+  const int threads = het ? kHetThreads : kSweepThreads;
   SCUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;
-  SCUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kSweepThreads, smem));
-  if (per_sm < 1 || L.n_slices > per_sm * c->sm_count)
+  SCUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem));
+  if (per_sm < 1 || S.n_ctas > per_sm * c->sm_count)
     return fail(c, SWIG_E_CUDA, "persistent kernel cannot be co-resident on this device");
 
   std::vector<double> du, dl, dw;
@@ -1170,7 +1243,7 @@ int swig_run(swig_ctx* c, swig_result* out) {
   SCUDA(cudaEventCreate(&ev1));
   double persistent_ms = 0.0;
   long long persistent_launches = 0;
-  c->n_launches += c->prepared_precision == SWIG_PREC_MIXED ? 5 : 4;  // init draw + batched likelihood
+  c->n_launches += het ? 3 : (mixed ? 5 : 4);  // init draw + batched likelihood
   for (;;) {
     // reset per-launch counters
     NSGlobal gl;
@@ -1184,7 +1257,7 @@ int swig_run(swig_ctx* c, swig_result* out) {
     SCUDA(cudaMemcpyAsync(st->P.g, &gl, sizeof(gl), cudaMemcpyHostToDevice, c->stream));
     void* args[] = {(void*)&L, (void*)&S, (void*)&c->B, (void*)&st->P};
     SCUDA(cudaEventRecord(ev0, c->stream));
-    SCUDA(cudaLaunchCooperativeKernel(kern, dim3(L.n_slices), dim3(kSweepThreads), args, smem, c->stream));
+    SCUDA(cudaLaunchCooperativeKernel(kern, dim3(S.n_ctas), dim3(threads), args, smem, c->stream));
     SCUDA(cudaEventRecord(ev1, c->stream));
     SCUDA(cudaMemcpyAsync(&gh, st->P.g, sizeof(gh), cudaMemcpyDeviceToHost, c->stream));
     SCUDA(cudaStreamSynchronize(c->stream));
@@ -1286,7 +1359,8 @@ int swig_run(swig_ctx* c, swig_result* out) {
   c->profile[8] = (double)c->n_launches;
   c->profile[9] = (double)c->h2d_bytes;
   c->profile[10] = (double)c->d2h_bytes;
-  c->profile[11] = (double)nf * (double)L.n_det * (double)L.n_bins;  // bin-detector evaluations
+  // bin-detector evaluations (heterodyned: bins of the coarse grid)
+  c->profile[11] = (double)nf * (double)L.n_det * (double)(het ? c->B.het_nb : L.n_bins);
   c->profile[12] = (double)gh.c_result;
   c->profile[13] = (double)gh.c_step;
   c->profile[14] = (double)gh.c_prop;
