@@ -87,6 +87,11 @@ typedef struct swig_sampler_cfg {
   double dlogz;         /* termination threshold, e.g. -3                */
   int max_iter;         /* safety cap on outer iterations                */
   double het_fiducial[SWIG_N_PARAMS]; /* theta of the reference waveform  */
+  /* SWIG_PROPOSAL_LEARNED (0 selects the default in brackets):            */
+  double learn_mix;     /* probability of a learned direction [0.5]      */
+  double learn_lr;      /* Adam learning rate [1e-3]                     */
+  int learn_steps;      /* Adam steps per retraining [50; 4x at start]   */
+  int learn_interval;   /* NS iterations between retrainings [8]         */
 } swig_sampler_cfg;
 
 typedef struct swig_result {
@@ -220,7 +225,9 @@ int swig_set_wait_limit(swig_ctx* ctx, long long spins);
  * evaluations of the last run (full-grid evaluations x detectors x bins);
  * out[12..16] clock cycles the first chain's control spent on pending results,
  * new slice steps, proposals, projection-only evaluations and full-evaluation
- * set-up, out[17..19] the counts of the last three.  Writes min(n, 20) values. */
+ * set-up, out[17..19] the counts of the last three; out[20] milliseconds of
+ * learned-proposal training (targets, Adam steps, output rows; CUDA events)
+ * and out[21] the number of retrainings.  Writes min(n, 22) values. */
 int swig_get_profile(swig_ctx* ctx, double* out, int n);
 /* Use `stream` (a cudaStream_t on the context's device, owned by the caller)
  * for all later work of this context; NULL restores a private stream. */
@@ -229,6 +236,45 @@ int swig_set_stream(swig_ctx* ctx, void* stream);
  * that logsumexp(logw) = log Z).  With cap == 0 only *n_out is set. */
 int swig_get_samples(swig_ctx* ctx, double* theta, double* logl, double* logw,
                      int64_t cap, int64_t* n_out);
+
+/* ---- learned slice proposal (SWIG_PROPOSAL_LEARNED) --------------------- */
+/* The paper draws slice directions from the live covariance (Sec. 2.3, Eq. 3)
+ * and learns nothing; this network is the library's optional alternative and
+ * these calls expose its pieces for verification.  Model: 13 -> 256 -> 256 ->
+ * 26 with SiLU; input a live point standardised by the live set's mean and
+ * standard deviation (zero beyond the d sampled dimensions); output a
+ * direction u (13) and log-widths s (13).  Training targets per live point:
+ * the leading eigenvector e1 of the correlation matrix of its 2d nearest live
+ * neighbours (standardised Euclidean distance, ties by index) and their log
+ * standard deviations t; loss = mean(1 - (u_hat . e1)^2 + |s - t|^2) over the
+ * sampled dimensions.  Matrix products take bfloat16 operands (round to
+ * nearest even) and accumulate in FP32; master weights and Adam are FP32.
+ * A sampler run retrains every learn_interval iterations on the current live
+ * set and draws, with probability learn_mix, the direction
+ * exp(s_b) * u_b / |u_b| of the Gibbs block from the output row of a live
+ * point picked uniformly from that snapshot.
+ * Parameter vector (SWIG_MLP_PARAMS floats, host): W1 [13][256], b1 [256],
+ * W2 [256][256], b2 [256], W3 [256][26], b3 [26], row = input unit.
+ * All buffers below are host arrays; n <= 8192, 1 <= d <= 13. */
+#define SWIG_MLP_PARAMS 76058
+/* Initial parameters: W ~ N(0, 1/fan_in) by Philox-4x32-10 (counter
+ * (column, row, layer, 9), key = seed) and Box-Muller; biases 0. */
+int swig_mlp_init(swig_ctx* ctx, uint64_t seed, float* params_out);
+/* Outputs (n x 26) of n standardised inputs x_std (n x 13). */
+int swig_mlp_forward(swig_ctx* ctx, const float* params, const float* x_std, int64_t n, float* out);
+/* Loss and its gradient (SWIG_MLP_PARAMS floats) for inputs x_std (n x 13)
+ * and targets tdir, tls (n x 13, zero beyond d). */
+int swig_mlp_loss_grad(swig_ctx* ctx, const float* params, const float* x_std, const float* tdir,
+                       const float* tls, int64_t n, int d, double* loss_out, float* grad_out);
+/* Training targets of n live points (live_u: n x d doubles in the unit cube):
+ * tdir, tls (n x 13 floats); nbr (optional, n x 26 ints): the 2d neighbour
+ * indices in distance order.  Requires 2d < n. */
+int swig_mlp_targets(swig_ctx* ctx, const double* live_u, int64_t n, int d, float* tdir, float* tls, int* nbr);
+/* `steps` Adam steps (fresh Adam state, learning rate lr) from params_inout on
+ * the targets of live_u; params_inout receives the trained parameters and
+ * out_rows (optional, n x 26) the trained network's outputs on live_u. */
+int swig_mlp_train(swig_ctx* ctx, const double* live_u, int64_t n, int d, int steps, double lr,
+                   float* params_inout, float* out_rows);
 
 #ifdef __cplusplus
 }

@@ -168,14 +168,19 @@ def adam_update(params, grad, m, v, t, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
     return params - lr * mh / (np.sqrt(vh) + eps), m, v
 
 
-def local_pca_targets(live_u, k=None):
-    """Per live point: (e1 padded to 13, log sigma padded to 13)."""
+def local_pca_targets(live_u, k=None, details=False):
+    """Per live point: (e1 padded to 13, log sigma padded to 13); with
+    details also the neighbour indices (n x k, distance order) and the
+    relative eigen-gap (lambda1 - lambda2) / lambda1 of each correlation
+    matrix (e1 is well defined only where it is not small)."""
     live_u = np.asarray(live_u, dtype=np.float64)
     n, d = live_u.shape
     k = 2 * d if k is None else k
     xs = standardise(live_u, d)[:, :d]
     tdir = np.zeros((n, D_IN))
     tls = np.zeros((n, D_IN))
+    nbrs = np.zeros((n, k), dtype=np.int64)
+    gaps = np.zeros(n)
     for i in range(n):
         d2 = np.sum((xs - xs[i]) ** 2, axis=1)
         d2[i] = np.inf
@@ -190,6 +195,10 @@ def local_pca_targets(live_u, k=None):
             e1 = -e1
         tdir[i, :d] = e1
         tls[i, :d] = np.log(sig)
+        nbrs[i] = nb
+        gaps[i] = (w[-1] - w[-2]) / w[-1] if d > 1 else 1.0
+    if details:
+        return tdir, tls, nbrs, gaps
     return tdir, tls
 
 

@@ -18,7 +18,7 @@ INCLUDE = os.path.join(ROOT, "include")
 LIBDIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(LIBDIR, "libswig.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["capi.cu", "like_kernels.cu", "sampler.cu", "noalloc.cu"]
+SOURCES = ["capi.cu", "like_kernels.cu", "sampler.cu", "noalloc.cu", "mlp.cu"]
 
 
 def nvcc() -> str:

@@ -646,6 +646,7 @@ void swig_destroy(swig_ctx* c) {
   if (!c) return;
   cudaSetDevice(c->device);
   swig_sampler_release(c);
+  swig_mlp_release(c);
   free_problem(c->B);
   free_scratch(c->B);
   if (c->stream && c->own_stream) cudaStreamDestroy(c->stream);

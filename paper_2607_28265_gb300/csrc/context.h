@@ -12,6 +12,7 @@
 
 namespace swig {
 struct SamplerState;  // device state of a nested-sampling run (sampler.cu)
+struct Mlp;           // learned-proposal network (mlp.cu)
 }
 
 struct swig_ctx {
@@ -41,10 +42,11 @@ struct swig_ctx {
   swig::LikeConst L = {};
   swig::DeviceBuffers B;
   swig::SamplerState* sampler = nullptr;
+  swig::Mlp* mlp = nullptr;
   long long wait_limit = 10000000;  // spins of a bounded device wait (~100 ns each)
   // results of the last run
   swig_result last = {};
-  double profile[20] = {};
+  double profile[22] = {};
   // counters over the context's lifetime: kernel launches, bytes copied host
   // to device and device to host by the library
   long long n_launches = 0, h2d_bytes = 0, d2h_bytes = 0;
@@ -60,3 +62,4 @@ int current_precision(const swig_ctx* c);
 }  // namespace swig
 
 void swig_sampler_release(swig_ctx* c);
+void swig_mlp_release(swig_ctx* c);

@@ -28,6 +28,22 @@ struct dfl {
   float hi, lo;
 };
 
+// Philox-4x32-10 (Salmon, Moraes, Dror & Shaw 2011): 10 rounds of two 32x32
+// multiplications with the key bumped by the Weyl constants between rounds.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, unsigned k0, unsigned k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r) {
+      k0 += 0x9E3779B9u;
+      k1 += 0xBB67AE85u;
+    }
+    const unsigned lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+    const unsigned lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+    c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+  }
+  return c;
+}
+
 __device__ __forceinline__ dfl two_sum(float a, float b) {
   float s = __fadd_rn(a, b);
   float bb = __fsub_rn(s, a);

@@ -35,6 +35,7 @@
 
 #include "context.h"
 #include "het.cuh"
+#include "mlp.h"
 #include "sweep.cuh"
 
 namespace swig {
@@ -70,6 +71,8 @@ struct SamplerConst {
   int group;           // pending chains per sweep group (shared-memory bound)
   int n_ctas;
   int mixed;
+  int learn_on;     // learned directions available (SWIG_PROPOSAL_LEARNED)
+  float learn_mix;  // probability of a learned direction per slice step
 };
 
 struct ChainState {
@@ -125,25 +128,12 @@ struct SamplerPtrs {
   const int* piece_begin;  // [n_pieces_total + n_slices] absolute first bin of each piece, per slice
   const int* slice_piece;  // [n_slices + 1] offset of each slice's pieces in piece_begin
   float* anchor_buf;       // [n_slices][k][max_tiles_slice][kAnchorStride] per-round anchors
+  const float* learn_out;  // [m][32] network outputs (u, s) of a frozen live snapshot, or null
 };
 
 // ---------------------------------------------------------------------------
-// Philox-4x32-10 (Salmon et al. 2011) and the draws built on it.
+// Draws built on Philox-4x32-10 (device_common.cuh).
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ uint4 philox4x32_10(uint4 c, unsigned k0, unsigned k1) {
-#pragma unroll
-  for (int r = 0; r < 10; ++r) {
-    if (r) {
-      k0 += 0x9E3779B9u;
-      k1 += 0xBB67AE85u;
-    }
-    const unsigned lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
-    const unsigned lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
-    c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
-  }
-  return c;
-}
-
 __device__ __forceinline__ double u01_from(uint4 r) {  // 53-bit uniform in [0, 1)
   return ((double)(r.x >> 5) * 67108864.0 + (double)(r.y >> 6)) * (1.0 / 9007199254740992.0);
 }
@@ -342,16 +332,40 @@ __device__ inline void move_to_proposal(const SamplerConst& S, ChainState& ch, d
   ch.lx = ly;
 }
 
-__device__ inline void start_step(const SamplerConst& S, ChainState& ch, const float* chol, int c, long long it) {
+// New slice step: direction from the live covariance (n = L_b z, Sec. 2.3),
+// or, with probability learn_mix, the learned direction exp(s_b) u_b / |u_b|
+// of a live point drawn uniformly from the frozen snapshot; then a bracket
+// [-r, 1 - r] of unit width at a uniform offset.
+__device__ inline void start_step(const SamplerConst& S, ChainState& ch, const float* chol, const float* learn_out,
+                                  int c, long long it) {
   const int b = ch.block, nb = S.block_size[b];
-  float z[kMaxDim];
-  for (int j = 0; j < nb; ++j) z[j] = chain_normal(S, ch, c, it);
   for (int j = 0; j < S.ndim; ++j) ch.dir[j] = 0.0;
-  const float* Lb = chol + (size_t)b * kMaxDim * kMaxDim;
-  for (int r = 0; r < nb; ++r) {
-    float v = 0.0f;
-    for (int q = 0; q <= r; ++q) v = fmaf(Lb[r * kMaxDim + q], z[q], v);
-    ch.dir[S.block_dims[b][r]] = (double)v;
+  bool learned = false;
+  if (S.learn_on && learn_out && chain_uniform(S, ch, c, it) < (double)S.learn_mix) {
+    const int row = min((int)(chain_uniform(S, ch, c, it) * (double)S.nlive), S.nlive - 1);
+    const float* o = learn_out + (size_t)row * 32;
+    float nrm2 = 0.0f;
+    for (int r = 0; r < nb; ++r) {
+      const float u = o[S.block_dims[b][r]];
+      nrm2 = fmaf(u, u, nrm2);
+    }
+    const float inv = rsqrtf(nrm2 + 1e-12f);
+    for (int r = 0; r < nb; ++r) {
+      const int j = S.block_dims[b][r];
+      const float s = fminf(fmaxf(o[13 + j], -30.0f), 5.0f);
+      ch.dir[j] = (double)(expf(s) * o[j] * inv);
+    }
+    learned = true;
+  }
+  if (!learned) {
+    float z[kMaxDim];
+    for (int j = 0; j < nb; ++j) z[j] = chain_normal(S, ch, c, it);
+    const float* Lb = chol + (size_t)b * kMaxDim * kMaxDim;
+    for (int r = 0; r < nb; ++r) {
+      float v = 0.0f;
+      for (int q = 0; q <= r; ++q) v = fmaf(Lb[r * kMaxDim + q], z[q], v);
+      ch.dir[S.block_dims[b][r]] = (double)v;
+    }
   }
   const double r0 = chain_uniform(S, ch, c, it);
   ch.lo = -r0;
@@ -417,7 +431,7 @@ __device__ __noinline__ void chain_advance_local(const LikeConst& L, const Sampl
     const int b = ch.block;
     if (S.block_free[b] && free_left <= 0) return;  // resume next round
     if (ch.phase == PH_NEW) {
-      start_step(S, ch, P.chol, c, it);
+      start_step(S, ch, P.chol, P.learn_out, c, it);
       if (prof) {
         const long long t2 = clock64();
         acc_step += t2 - tk;
@@ -1139,6 +1153,18 @@ int swig_run(swig_ctx* c, swig_result* out) {
   S.m_pow2 = 1;
   while (S.m_pow2 < m) S.m_pow2 *= 2;
   S.max_iters = (int)std::max(1, std::min(64, c->cfg.max_iter));
+  // learned proposal: retrain every learn_interval iterations (one launch each)
+  const bool learned = c->cfg.proposal == SWIG_PROPOSAL_LEARNED;
+  const double learn_mix = c->cfg.learn_mix > 0.0 ? std::min(1.0, c->cfg.learn_mix) : 0.5;
+  const float learn_lr = c->cfg.learn_lr > 0.0 ? (float)c->cfg.learn_lr : 1e-3f;
+  const int learn_steps = c->cfg.learn_steps > 0 ? c->cfg.learn_steps : 50;
+  const int learn_interval = c->cfg.learn_interval > 0 ? c->cfg.learn_interval : 8;
+  if (learned) {
+    if (2 * nd >= m) return fail(c, SWIG_E_ARG, "the learned proposal needs nlive > 2 x sampled dimensions");
+    S.max_iters = std::min(S.max_iters, learn_interval);
+    S.learn_on = 1;
+    S.learn_mix = (float)learn_mix;
+  }
 
   const int max_pieces = c->B.max_pieces;
   S.max_pieces = max_pieces;
@@ -1163,7 +1189,7 @@ int swig_run(swig_ctx* c, swig_result* out) {
 
   // buffers
   SamplerState* st = c->sampler;
-  if (!st || st->nlive != m || st->nrep != k || st->ndim != nd) {
+  if (!st || st->nlive != m || st->nrep != k || st->ndim != nd || st->cap_iters < S.max_iters) {
     swig_sampler_release(c);
     st = new SamplerState();
     c->sampler = st;
@@ -1200,6 +1226,11 @@ int swig_run(swig_ctx* c, swig_result* out) {
     SCUDA(cudaMalloc(&st->anchor_buf, sizeof(float) * kAnchorStride * (size_t)L.n_slices * k * max_tiles));
   }
   st->P.anchor_buf = st->anchor_buf;
+  st->P.learn_out = nullptr;
+  if (learned) {
+    if (!c->mlp) c->mlp = new Mlp();
+    if (c->mlp->cap < m) SCUDA(mlp_alloc(*c->mlp, std::max(m, 1024)));
+  }
   if ((rc = ensure_scratch(c, std::max(m, k)))) return rc;
 
   // initial live set and its likelihoods (with the per-detector sums)
@@ -1241,8 +1272,9 @@ int swig_run(swig_ctx* c, swig_result* out) {
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   SCUDA(cudaEventCreate(&ev0));
   SCUDA(cudaEventCreate(&ev1));
-  double persistent_ms = 0.0;
-  long long persistent_launches = 0;
+  double persistent_ms = 0.0, learn_ms = 0.0;
+  long long persistent_launches = 0, learn_rounds = 0;
+  if (learned) SCUDA(mlp_init(*c->mlp, c->cfg.seed ^ 0x4D4C5050ull, c->stream, &c->n_launches));
   c->n_launches += het ? 3 : (mixed ? 5 : 4);  // init draw + batched likelihood
   for (;;) {
     // reset per-launch counters
@@ -1255,6 +1287,23 @@ int swig_run(swig_ctx* c, swig_result* out) {
     gl.error = 0;
     gl.bar_count = 0;
     SCUDA(cudaMemcpyAsync(st->P.g, &gl, sizeof(gl), cudaMemcpyHostToDevice, c->stream));
+    if (learned) {
+      // retrain on the current live set, then freeze the output rows of
+      // this snapshot for the launch's iterations
+      Mlp& N = *c->mlp;
+      SCUDA(cudaEventRecord(ev0, c->stream));
+      SCUDA(mlp_targets(N, st->P.live_u, m, nd, 2 * nd, c->stream, &c->n_launches));
+      SCUDA(mlp_train(N, m, nd, learn_rounds == 0 ? 4 * learn_steps : learn_steps, learn_lr, c->stream,
+                      &c->n_launches));
+      SCUDA(mlp_forward(N, m, c->stream, &c->n_launches));
+      SCUDA(cudaEventRecord(ev1, c->stream));
+      SCUDA(cudaEventSynchronize(ev1));
+      float ms = 0.0f;
+      SCUDA(cudaEventElapsedTime(&ms, ev0, ev1));
+      learn_ms += ms;
+      ++learn_rounds;
+      st->P.learn_out = N.out;
+    }
     void* args[] = {(void*)&L, (void*)&S, (void*)&c->B, (void*)&st->P};
     SCUDA(cudaEventRecord(ev0, c->stream));
     SCUDA(cudaLaunchCooperativeKernel(kern, dim3(S.n_ctas), dim3(threads), args, smem, c->stream));
@@ -1369,6 +1418,8 @@ int swig_run(swig_ctx* c, swig_result* out) {
   c->profile[17] = (double)gh.n_free;
   c->profile[18] = (double)gh.n_setup;
   c->profile[19] = (double)gh.n_step;
+  c->profile[20] = learn_ms;
+  c->profile[21] = (double)learn_rounds;
   cudaEventDestroy(ev0);
   cudaEventDestroy(ev1);
   return SWIG_OK;
@@ -1377,7 +1428,7 @@ int swig_run(swig_ctx* c, swig_result* out) {
 int swig_get_profile(swig_ctx* c, double* out, int n) {
   if (!c) return SWIG_E_ARG;
   if (!out || n < 0) return fail(c, SWIG_E_ARG, "null output");
-  for (int i = 0; i < n && i < 20; ++i) out[i] = c->profile[i];
+  for (int i = 0; i < n && i < 22; ++i) out[i] = c->profile[i];
   return SWIG_OK;
 }
 

@@ -24,6 +24,9 @@ PROPOSAL_COV, PROPOSAL_LEARNED = 0, 1
 # Every entry point declared in include/swig.h, with ctypes signatures.
 _c_int, _c_double, _c_i64, _c_u64, _vp = ctypes.c_int, ctypes.c_double, ctypes.c_int64, ctypes.c_uint64, ctypes.c_void_p
 _dp = ctypes.POINTER(ctypes.c_double)
+_fp = ctypes.POINTER(ctypes.c_float)
+_ip = ctypes.POINTER(ctypes.c_int)
+MLP_PARAMS = 76058
 
 
 class SwigParam(ctypes.Structure):
@@ -35,7 +38,8 @@ class SwigSamplerCfg(ctypes.Structure):
     _fields_ = [("nlive", _c_int), ("nrep", _c_int), ("sweeps", _c_int), ("steps_per_dim", _c_int),
                 ("seed", _c_u64), ("likelihood", _c_int), ("precision", _c_int), ("proposal", _c_int),
                 ("het_bins", _c_int), ("het_spacing", _c_int), ("dlogz", _c_double), ("max_iter", _c_int),
-                ("het_fiducial", _c_double * N_PARAMS)]
+                ("het_fiducial", _c_double * N_PARAMS), ("learn_mix", _c_double), ("learn_lr", _c_double),
+                ("learn_steps", _c_int), ("learn_interval", _c_int)]
 
 
 class SwigResult(ctypes.Structure):
@@ -65,6 +69,11 @@ SIGNATURES = {
     "swig_inject": (_c_int, [_vp, _dp, _c_double, _dp, _dp, _dp]),
     "swig_loglike_batch_noalloc": (_c_int, [_vp, _vp, _c_i64, _vp, _vp]),
     "swig_get_samples": (_c_int, [_vp, _dp, _dp, _dp, _c_i64, ctypes.POINTER(_c_i64)]),
+    "swig_mlp_init": (_c_int, [_vp, _c_u64, _fp]),
+    "swig_mlp_forward": (_c_int, [_vp, _fp, _fp, _c_i64, _fp]),
+    "swig_mlp_loss_grad": (_c_int, [_vp, _fp, _fp, _fp, _fp, _c_i64, _c_int, _dp, _fp]),
+    "swig_mlp_targets": (_c_int, [_vp, _dp, _c_i64, _c_int, _fp, _fp, _ip]),
+    "swig_mlp_train": (_c_int, [_vp, _dp, _c_i64, _c_int, _c_int, _c_double, _fp, _fp]),
 }
 
 _lib = None
@@ -94,6 +103,14 @@ def load_library(path: str = LIB_PATH):
 
 def _ptr(a):
     return a.ctypes.data_as(_dp)
+
+
+def _f32(a):
+    return np.ascontiguousarray(a, dtype=np.float32)
+
+
+def _fptr(a):
+    return a.ctypes.data_as(_fp)
 
 
 @dataclass
@@ -170,7 +187,8 @@ class Context:
 
     def set_sampler(self, nlive, nrep, sweeps=1, steps_per_dim=5, seed=0, likelihood=LIKE_FULL,
                     precision=PREC_MIXED, proposal=PROPOSAL_COV, het_bins=0, het_spacing=0, dlogz=-3.0,
-                    max_iter=100000, het_fiducial=None):
+                    max_iter=100000, het_fiducial=None, learn_mix=0.0, learn_lr=0.0, learn_steps=0,
+                    learn_interval=0):
         cfg = SwigSamplerCfg()
         cfg.nlive, cfg.nrep, cfg.sweeps, cfg.steps_per_dim = nlive, nrep, sweeps, steps_per_dim
         cfg.seed, cfg.likelihood, cfg.precision, cfg.proposal = seed, likelihood, precision, proposal
@@ -178,6 +196,8 @@ class Context:
         if het_fiducial is not None:
             for i, v in enumerate(het_fiducial):
                 cfg.het_fiducial[i] = float(v)
+        cfg.learn_mix, cfg.learn_lr = float(learn_mix), float(learn_lr)
+        cfg.learn_steps, cfg.learn_interval = int(learn_steps), int(learn_interval)
         self._check(self.lib.swig_set_sampler(self.h, ctypes.byref(cfg)))
 
     # ---- likelihood --------------------------------------------------------
@@ -228,7 +248,7 @@ class Context:
     PROFILE_KEYS = ("rounds", "boundary_s", "control_s", "wait_control_s", "sweep_s", "wait_sweep_s",
                     "persistent_ms", "persistent_launches", "kernel_launches", "h2d_bytes", "d2h_bytes",
                     "bin_det_evals", "cyc_result", "cyc_step", "cyc_prop", "cyc_free", "cyc_setup", "n_free",
-                    "n_setup", "n_step")
+                    "n_setup", "n_step", "learn_ms", "learn_rounds")
 
     def profile(self):
         out = np.zeros(len(self.PROFILE_KEYS))
@@ -249,6 +269,44 @@ class Context:
         lw = np.empty(n.value)
         self._check(self.lib.swig_get_samples(self.h, _ptr(th), _ptr(ll), _ptr(lw), n.value, ctypes.byref(n)))
         return th, ll, lw
+
+    # ---- learned slice proposal -------------------------------------------
+    def mlp_init(self, seed):
+        p = np.empty(MLP_PARAMS, dtype=np.float32)
+        self._check(self.lib.swig_mlp_init(self.h, int(seed), _fptr(p)))
+        return p
+
+    def mlp_forward(self, params, x_std):
+        p, x = _f32(params), _f32(np.atleast_2d(x_std))
+        out = np.empty((x.shape[0], 26), dtype=np.float32)
+        self._check(self.lib.swig_mlp_forward(self.h, _fptr(p), _fptr(x), x.shape[0], _fptr(out)))
+        return out
+
+    def mlp_loss_grad(self, params, x_std, tdir, tls, d):
+        p, x, t, l = _f32(params), _f32(x_std), _f32(tdir), _f32(tls)
+        g = np.empty(MLP_PARAMS, dtype=np.float32)
+        loss = ctypes.c_double(0.0)
+        self._check(self.lib.swig_mlp_loss_grad(self.h, _fptr(p), _fptr(x), _fptr(t), _fptr(l), x.shape[0], int(d),
+                                                ctypes.byref(loss), _fptr(g)))
+        return loss.value, g
+
+    def mlp_targets(self, live_u):
+        u = np.ascontiguousarray(live_u, dtype=np.float64)
+        n, d = u.shape
+        tdir = np.empty((n, 13), dtype=np.float32)
+        tls = np.empty((n, 13), dtype=np.float32)
+        nbr = np.empty((n, 26), dtype=np.int32)
+        self._check(self.lib.swig_mlp_targets(self.h, _ptr(u), n, d, _fptr(tdir), _fptr(tls),
+                                              nbr.ctypes.data_as(_ip)))
+        return tdir, tls, nbr[:, :2 * d]
+
+    def mlp_train(self, live_u, params, steps, lr=1e-3):
+        u = np.ascontiguousarray(live_u, dtype=np.float64)
+        n, d = u.shape
+        p = _f32(params).copy()
+        out = np.empty((n, 26), dtype=np.float32)
+        self._check(self.lib.swig_mlp_train(self.h, _ptr(u), n, d, int(steps), float(lr), _fptr(p), _fptr(out)))
+        return p, out
 
 
 def context_for_workload(wl, data, psds, gmst, device=0, precision=PREC_MIXED, detectors=None):
