@@ -1,11 +1,18 @@
-"""Benchmark: nested-sampling posteriors of a 128 s, three-detector BNS signal.
+"""Benchmark: nested-sampling posteriors through the C-ABI library.
 
 One step is one complete posterior: a Slice-within-Gibbs nested-sampling run
-(Sec. 2.2, 2.3, 3.2 of the paper) from prior draws to the termination rule,
-on the full uncompressed frequency grid (259,585 bins per detector), through
-the C-ABI library.  The metric is logL evaluations per second (all likelihood
-evaluations, including the projection-only updates of cached blocks, as the
-paper counts them) and wall-seconds per posterior (= ms_per_step / 1000).
+(Sec. 2.2, 2.3, 3.2 of the paper) from prior draws to the termination rule.
+The metric is logL evaluations per second (all likelihood evaluations,
+including the projection-only updates of cached blocks, as the paper counts
+them) and wall-seconds per posterior (= ms_per_step / 1000).
+
+``--workload`` picks the configuration (default ``cfg2``, the headline):
+
+  cfg2      128 s H1/L1/V1 BNS, 259,585 bins/det, full grid, plain SwiG, mixed
+  cfg5      cfg2 with the learned slice proposal (learned + mixed)
+  cfg2-het  cfg2 with the heterodyned likelihood, 5,000 bins (Sec. 3.4)
+  cfg1      4 s single detector, 4,017 bins, FP64, nlive 100
+  cfg3      cfg1 data, heterodyned likelihood, 450 geometric bins, nlive 1000
 
 Output: one JSON line on rank 0.  ``--impl reference`` times the FP64 CPU
 oracle on the same workload instead (bounded samples of likelihood
@@ -39,11 +46,33 @@ SFU_OPS_PER_BIN_DET = 2   # one sine and one cosine per bin and detector
 TRAFFIC_B_PER_EVAL = 14.27328e6 / 106944
 METRIC = "logL evals/s (128 s 3-det BNS) and wall-s/posterior, plain vs learned+mixed"
 
+# workload name -> (event, sampler options, description)
+WORKLOADS = {
+    "cfg2": dict(event="cfg2", precision="mixed", likelihood="full", proposal="cov",
+                 text="plain SwiG (covariance directions), full grid, mixed precision"),
+    "cfg5": dict(event="cfg2", precision="mixed", likelihood="full", proposal="learned",
+                 text="learned slice proposal (MLP 13-256-256-26, BF16/FP32) + covariance, full grid, mixed"),
+    "cfg2-het": dict(event="cfg2", precision="mixed", likelihood="het", proposal="cov", het_bins=5000,
+                     het_spacing=0, text="plain SwiG, heterodyned likelihood, 5000 bins of equal phase change"),
+    "cfg1": dict(event="cfg1", precision="fp64", likelihood="full", proposal="cov", nlive=100,
+                 text="plain SwiG, full grid, FP64"),
+    "cfg3": dict(event="cfg1", precision="mixed", likelihood="het", proposal="cov", nlive=1000, het_bins=450,
+                 het_spacing=1, text="plain SwiG, heterodyned likelihood, 450 geometric bins"),
+}
 
-def workload_description(wl):
-    return (f"{wl.name}: 128 s, H1/L1/V1, {wl.f_min:g}-{wl.f_max:g} Hz, df=1/128 Hz, {wl.n_bins} bins/det, "
-            "TaylorF2 aligned-spin+tidal, 12 sampled params + phi_c marginalised, "
-            f"nlive={wl.nlive}, nrep={wl.nrep}, {wl.steps_per_dim} slice steps/dim, M=1, mixed precision")
+
+def make_workload(name):
+    spec = WORKLOADS[name]
+    if spec["event"] == "cfg2":
+        return si.config2(), spec
+    return si.config1(nlive=spec.get("nlive", 100)), spec
+
+
+def workload_description(wl, spec):
+    dets = "/".join(wl.detectors)
+    return (f"{wl.name}: {1.0 / wl.df:g} s, {dets}, {wl.f_min:g}-{wl.f_max:g} Hz, {wl.n_bins} bins/det, "
+            f"{len(wl.sampled())} sampled params, nlive={wl.nlive}, nrep={wl.nrep}, "
+            f"{wl.steps_per_dim} slice steps/dim, M=1; {spec['text']}")
 
 
 # ---------------------------------------------------------------------------
@@ -105,11 +134,20 @@ class ClockSampler:
 def run_gpu(args, rank, world):
     import torch
 
+    from paper_2607_28265_gb300 import swig
     from paper_2607_28265_gb300.workloads import build_context
 
     torch.cuda.set_device(0 if world == 1 else int(os.environ.get("LOCAL_RANK", rank)))
-    wl = si.config2()
-    ctx, data, psds, th_inj = build_context(wl, seed_offset=1000 * rank)
+    wl, spec = make_workload(args.workload)
+    prec = swig.PREC_FP64 if spec["precision"] == "fp64" else swig.PREC_MIXED
+    ctx, data, psds, th_inj = build_context(wl, seed_offset=1000 * rank, precision=prec)
+    het = spec["likelihood"] == "het"
+    ctx.set_sampler(nlive=wl.nlive, nrep=wl.nrep, sweeps=wl.sweeps, steps_per_dim=wl.steps_per_dim,
+                    seed=wl.sampler_seed + 1000 * rank, precision=prec,
+                    likelihood=swig.LIKE_HET if het else swig.LIKE_FULL,
+                    proposal=swig.PROPOSAL_LEARNED if spec["proposal"] == "learned" else swig.PROPOSAL_COV,
+                    het_bins=spec.get("het_bins", 0), het_spacing=spec.get("het_spacing", 0),
+                    het_fiducial=th_inj if het else None)
     stream = torch.cuda.current_stream()
     ctx.set_stream(stream.cuda_stream)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # > L2 (129 MB)
@@ -188,6 +226,9 @@ def run_gpu(args, rank, world):
     sm_mhz_max = 2070.0
     peak = SFU_OPS_PER_CLK_SM * 152 * sm_mhz_max * 1e6 / 1e12  # SFU Top/s at the maximum SM clock
     achieved = SFU_OPS_PER_BIN_DET * bindet / (pers_ms * 1e-3) / 1e12 if pers_ms > 0 else 0.0
+    n_bins_eval = spec.get("het_bins", 0) + 1 if het else wl.n_bins
+    kernel = "k_ns_het (persistent SwiG kernel, heterodyned)" if het else "k_ns_persistent (persistent SwiG kernel)"
+    traffic = TRAFFIC_B_PER_EVAL * total_evals / max(1, pers_launch) if args.workload == "cfg2" else None
     line = {
         "metric": METRIC,
         "value": evals_all / (total_ms_max * 1e-3),
@@ -201,9 +242,9 @@ def run_gpu(args, rank, world):
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f32",
+        "dtype": "f64" if spec["precision"] == "fp64" else "f32",
         "data": "synthetic",
-        "config": {"workload": workload_description(wl), "proposal": "plain SwiG (covariance directions)",
+        "config": {"workload": workload_description(wl, spec), "name": args.workload,
                    "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{world}",
                    "posterior": {"logz": results[-1][0].logz, "logz_err": results[-1][0].logz_err,
                                  "ess": results[-1][0].ess, "n_iter": results[-1][0].n_iter,
@@ -213,15 +254,16 @@ def run_gpu(args, rank, world):
                 "ms_per_step": e2e_ms_max / n_e2e},
         "gpu_launches": launches,
         "roofline": {
-            "kernel": "k_ns_persistent (persistent SwiG kernel)",
+            "kernel": kernel,
             "bound": "alu",
             "achieved": achieved,
             "peak": peak,
             "unit": "SFU Top/s",
             "frac": achieved / peak if peak else None,
-            "traffic": TRAFFIC_B_PER_EVAL * total_evals / max(1, pers_launch),
+            "traffic": traffic,
             "traffic_unit": "bytes per launch (ncu, 2-iteration capture scaled by evaluations)",
-            "work_per_launch": "2 SFU ops x bin-detector evaluations (full-grid evals x 3 x 259585)",
+            "work_per_launch": (f"2 SFU ops x bin-detector evaluations (full evaluations x {len(wl.detectors)} x "
+                                f"{n_bins_eval} {'bin edges' if het else 'bins'})"),
             "launches": int(pers_launch),
             "avg_launch_ms": pers_ms / max(1, pers_launch),
             "peak_source": "16 sin/cos per clk per SM x 152 SMs x 2070 MHz (derived, not measured)",
@@ -229,8 +271,11 @@ def run_gpu(args, rank, world):
         "clocks": clk,
     }
     if args.cpu_baseline and world == 1:
-        line["cpu_baseline"] = cpu_baseline(wl, seconds=args.cpu_seconds,
+        line["cpu_baseline"] = cpu_baseline(args.workload, seconds=args.cpu_seconds,
                                             evals_per_posterior=total_evals / max(1, args.steps))
+    if prof_learn := sum(p.get("learn_ms", 0.0) for _, _, p in results):
+        line["learned"] = {"train_ms_per_posterior": prof_learn / args.steps,
+                           "retrainings_per_posterior": sum(p.get("learn_rounds", 0) for _, _, p in results) / args.steps}
     return line
 
 
@@ -240,25 +285,33 @@ def run_gpu(args, rank, world):
 _EV = None
 
 
-def _worker_init(wl_seed):
+def _worker_init(name):
+    """Hold the workload's synthetic event (and heterodyne tables) in the oracle."""
     global _EV
     os.environ.setdefault("OMP_NUM_THREADS", "1")
     from oracle import events
-    _EV = events.build_event(si.config2(seed_index=wl_seed))
+    from oracle import likelihood as L
+    wl, spec = make_workload(name)
+    ev, th = events.build_event(wl)
+    het = L.het_setup(ev, th, spec["het_bins"], spacing="phase" if spec.get("het_spacing", 0) == 0 else "geometric") \
+        if spec["likelihood"] == "het" else None
+    _EV = (wl, ev, het)
 
 
 def _worker_evals(args):
     seed, n = args
     from oracle import likelihood as L
     from oracle import physics
-    ev, th = _EV
-    wl = si.config2()
+    wl, ev, het = _EV
     rng = np.random.default_rng(seed)
     ns = len(wl.sampled())
     t0 = time.perf_counter()
     for _ in range(n):
         t = physics.prior_transform(rng.random(ns), wl.params)[0]
-        L.loglike(ev, t)
+        if het is None:
+            L.loglike(ev, t)
+        else:
+            L.het_loglike(ev, het, t)
     return n, time.perf_counter() - t0
 
 
@@ -266,10 +319,10 @@ class OraclePool:
     """The FP64 oracle's logL on all host cores (spawned worker processes,
     each holding the synthetic event)."""
 
-    def __init__(self):
+    def __init__(self, name):
         import multiprocessing as mp
         self.cores = os.cpu_count() or 1
-        self.pool = mp.get_context("spawn").Pool(self.cores, initializer=_worker_init, initargs=(0,))
+        self.pool = mp.get_context("spawn").Pool(self.cores, initializer=_worker_init, initargs=(name,))
         n0, t0 = self.pool.apply(_worker_evals, ((12345, 2),))
         self.per_eval = t0 / max(1, n0)
         self.seed = 100
@@ -288,17 +341,23 @@ class OraclePool:
         self.pool.join()
 
 
-def cpu_baseline(wl, seconds=15.0, evals_per_posterior=None):
+def _sample_text(name, total, cores, extra):
+    wl, spec = make_workload(name)
+    what = (f"heterodyned logL ({spec['het_bins']} bins)" if spec["likelihood"] == "het"
+            else f"logL on the full {len(wl.detectors)} x {wl.n_bins}-bin grid")
+    return f"{total} FP64 oracle evaluations of {what} at prior draws, {cores} spawned processes, {extra}"
+
+
+def cpu_baseline(name, seconds=15.0, evals_per_posterior=None):
     """Oracle logL evaluations/s over all host cores, on a bounded sample."""
-    pool = OraclePool()
+    pool = OraclePool(name)
     try:
         total, wall = pool.sample(seconds)
     finally:
         pool.close()
     rate = total / wall
     out = {"value": rate, "unit": "logL evals/s", "cores": pool.cores, "kind": "oracle",
-           "sample": f"{total} FP64 oracle evaluations of logL at prior draws on the full 3 x {wl.n_bins}-bin grid, "
-                     f"{pool.cores} spawned processes, {wall:.1f} s"}
+           "sample": _sample_text(name, total, pool.cores, f"{wall:.1f} s")}
     if evals_per_posterior:
         out["wall_s_per_posterior_extrapolated"] = evals_per_posterior / rate
     return out
@@ -309,8 +368,8 @@ def run_reference(args, rank, world):
     the same workload on all host cores; value = evaluations/s."""
     if rank != 0:
         return None
-    wl = si.config2()
-    pool = OraclePool()
+    wl, spec = make_workload(args.workload)
+    pool = OraclePool(args.workload)
     per_step_s = max(2.0, args.cpu_seconds / 2)
     try:
         for _ in range(args.warmup):
@@ -323,13 +382,12 @@ def run_reference(args, rank, world):
     finally:
         pool.close()
     value = total / t_all
-    sample = (f"{total} FP64 oracle evaluations of logL at prior draws on the full 3 x {wl.n_bins}-bin grid "
-              f"over {args.steps} steps, {pool.cores} spawned processes")
+    sample = _sample_text(args.workload, total, pool.cores, f"over {args.steps} steps")
     return {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "logL evals/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_all / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": workload_description(wl),
+        "config": {"workload": workload_description(wl, spec), "name": args.workload,
                    "note": "FP64 CPU oracle of the same method, bounded samples per step"},
         "cpu_baseline": {"value": value, "unit": "logL evals/s", "cores": pool.cores, "kind": "oracle",
                          "sample": sample},
@@ -346,6 +404,7 @@ def main():
     ap.add_argument("--impl", choices=["swig", "reference"], default="swig")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="cfg2")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

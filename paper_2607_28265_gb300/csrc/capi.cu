@@ -336,13 +336,16 @@ int prepare_het(swig_ctx* c) {
     }
   }
   std::vector<float> eb((size_t)(nb + 1) * 2 * NBASIS), ef((size_t)(nb + 1) * 2);
+  // transposed (row per basis function and hi/lo part) so that a warp reads
+  // 32 consecutive edges of a row
+  const size_t ne = (size_t)nb + 1;
   for (int q = 0; q <= nb; ++q) {
     const double fe = f[idx[q]];
     for (int j = 0; j < NBASIS; ++j) {
       const double v = (j == B_ONE) ? 1.0 : basis_derivative(kBasisPow[j], kBasisLog[j], 0, fe);
-      split_df(v, &eb[(size_t)q * 2 * NBASIS + 2 * j], &eb[(size_t)q * 2 * NBASIS + 2 * j + 1]);
+      split_df(v, &eb[2 * j * ne + q], &eb[(2 * j + 1) * ne + q]);
     }
-    split_df(fe, &ef[2 * q], &ef[2 * q + 1]);
+    split_df(fe, &ef[q], &ef[ne + q]);
   }
   CUDA_TRY(c, cudaMalloc(&B.het_edge_basis, sizeof(float) * eb.size()));
   CUDA_TRY(c, cudaMalloc(&B.het_edge_f, sizeof(float) * ef.size()));

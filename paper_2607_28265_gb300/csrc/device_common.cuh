@@ -380,6 +380,60 @@ __device__ inline void setup_delays(const LikeConst& L, const double* th, EvalRe
   }
 }
 
+// One detector's share of setup_projection(_f32) and setup_delays, so that a
+// warp can set up a record with one lane per piece (setup_record_warp).
+__device__ inline void setup_projection_det(const LikeConst& L, const double* th, int i, bool f32, EvalRecord* rec) {
+  if (f32) {
+    float sl, cl, sd, cd, sp, cp;
+    sincosf((float)(th[9] - L.gmst), &sl, &cl);
+    sincosf((float)th[10], &sd, &cd);
+    sincosf((float)th[8], &sp, &cp);
+    const float east[3] = {-sl, cl, 0.0f};
+    const float north[3] = {-sd * cl, -sd * sl, cd};
+    float X[3], Y[3];
+    for (int k = 0; k < 3; ++k) {
+      X[k] = -cp * east[k] + sp * north[k];
+      Y[k] = sp * east[k] + cp * north[k];
+    }
+    const float ci = cosf((float)th[7]);
+    const float plus = 0.5f * (1.0f + ci * ci), cross = -ci;
+    float sph = 0.0f, cph = 1.0f;
+    if (!L.phase_marg) sincosf((float)th[12], &sph, &cph);
+    float d[6];
+    for (int q = 0; q < 6; ++q) d[q] = (float)L.dten[i][q];
+    auto form = [&d](const float* a, const float* b) {
+      return a[0] * (d[0] * b[0] + d[1] * b[1] + d[2] * b[2]) + a[1] * (d[1] * b[0] + d[3] * b[1] + d[4] * b[2]) +
+             a[2] * (d[2] * b[0] + d[4] * b[1] + d[5] * b[2]);
+    };
+    const float fp = form(X, X) - form(Y, Y), fx = 2.0f * form(X, Y);
+    const float re0 = fp * plus, im0 = fx * cross;
+    rec->pre[i] = (double)(re0 * cph - im0 * sph);
+    rec->pim[i] = (double)(re0 * sph + im0 * cph);
+  } else {
+    const double ci = cos(th[7]);
+    const double plus = 0.5 * (1.0 + ci * ci), cross = -ci;
+    double sph = 0.0, cph = 1.0;
+    if (!L.phase_marg) sincos(th[12], &sph, &cph);
+    double fp, fx;
+    antenna_fp_fx(L.dten[i], th[9], th[10], th[8], L.gmst, &fp, &fx);
+    const double re0 = fp * plus, im0 = fx * cross;
+    rec->pre[i] = re0 * cph - im0 * sph;
+    rec->pim[i] = re0 * sph + im0 * cph;
+  }
+}
+
+__device__ inline void setup_delay_det(const LikeConst& L, const double* th, int i, EvalRecord* rec) {
+  double sl, cl, sd, cd;
+  sincos(th[9] - L.gmst, &sl, &cl);
+  sincos(th[10], &sd, &cd);
+  const double n0 = cd * cl * (-1.0 / kCSI), n1 = cd * sl * (-1.0 / kCSI), n2 = sd * (-1.0 / kCSI);
+  const double tau = th[11] + (n0 * L.vertex[i][0] + n1 * L.vertex[i][1] + n2 * L.vertex[i][2]);
+  rec->tau[i] = tau;
+  dfl tv = df_from_double(tau);
+  rec->tau_hi[i] = tv.hi;
+  rec->tau_lo[i] = tv.lo;
+}
+
 __device__ inline void setup_combine(const LikeConst& L, EvalRecord* rec) {
   double hh = 0.0;
   for (int i = 0; i < SWIG_MAX_DET; ++i) {

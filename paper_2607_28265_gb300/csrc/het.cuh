@@ -19,8 +19,8 @@ namespace swig {
 
 struct HetTables {
   int n_bins;                 // N_b
-  const float* edge_basis;    // [N_b + 1][2 * NBASIS] phi_j(f_e) as (hi, lo)
-  const float* edge_f;        // [N_b + 1][2] f_e as (hi, lo)
+  const float* edge_basis;    // [2 * NBASIS][N_b + 1] phi_j(f_e): row 2j hi parts, row 2j+1 lo parts
+  const float* edge_f;        // [2][N_b + 1] f_e: hi parts, lo parts
   const float* inv_width;     // [N_b] 1 / (e_{b+1} - e_b)
   const float4* coef;         // [n_det][N_b] (A0.re, A0.im, A1.re, A1.im)
   const float2* coefB;        // [n_det][N_b] (B0, B1)
@@ -39,92 +39,119 @@ __host__ __device__ inline HetTables het_tables(const DeviceBuffers& B) {
   return H;
 }
 
-// One warp evaluates the heterodyned logL of record r (all lanes return it).
-// z_out/hh_out (optional, lane-uniform): per-detector Z_i (re, im) and HH_i.
+// Per-evaluation constants: coefficient and delay differences from the
+// fiducial in double-float, and rho_i = C_i / C0_i.
 template <int NDET>
-__device__ inline double het_loglike_warp(const LikeConst& L, const HetTables& H, const EvalRecord& r, int lane,
-                                          double* z_out = nullptr, double* hh_out = nullptr) {
-  if (!r.valid) return -INFINITY;
-  const EvalRecord& f0 = *H.fid;
-  // coefficient differences in double-float (uniform)
+struct HetPrep {
   dfl dc[NBASIS];
-#pragma unroll
-  for (int j = 0; j < NBASIS; ++j) dc[j] = df_from_double(r.c[j] - f0.c[j]);
   dfl dtau[NDET];
   float rho_re[NDET], rho_im[NDET];
+};
+
+template <int NDET>
+__device__ inline void het_prepare(const HetTables& H, const EvalRecord& r, HetPrep<NDET>& p) {
+  const EvalRecord& f0 = *H.fid;
+#pragma unroll
+  for (int j = 0; j < NBASIS; ++j) p.dc[j] = df_from_double(r.c[j] - f0.c[j]);
 #pragma unroll
   for (int i = 0; i < NDET; ++i) {
-    dtau[i] = df_from_double(r.tau[i] - f0.tau[i]);
-    // rho = C_i / C0_i
+    p.dtau[i] = df_from_double(r.tau[i] - f0.tau[i]);
     const double den = f0.cre[i] * f0.cre[i] + f0.cim[i] * f0.cim[i];
-    rho_re[i] = (float)((r.cre[i] * f0.cre[i] + r.cim[i] * f0.cim[i]) / den);
-    rho_im[i] = (float)((r.cim[i] * f0.cre[i] - r.cre[i] * f0.cim[i]) / den);
+    p.rho_re[i] = (float)((r.cre[i] * f0.cre[i] + r.cim[i] * f0.cim[i]) / den);
+    p.rho_im[i] = (float)((r.cim[i] * f0.cre[i] - r.cre[i] * f0.cim[i]) / den);
   }
-  float zr[NDET], zi[NDET], hh[NDET];
-#pragma unroll
-  for (int i = 0; i < NDET; ++i) zr[i] = zi[i] = hh[i] = 0.0f;
+}
+
+// Bins [base, base + 31) of the contraction, accumulated into the lane's
+// per-detector sums: lane l holds edge base + l, bin base + l uses edges l and
+// l + 1 (the next edge by a shuffle).  All 32 lanes must call it together.
+template <int NDET>
+__device__ inline void het_chunk(const HetTables& H, const HetPrep<NDET>& p, int base, int lane, float* zr, float* zi,
+                                 float* hh) {
   const float twopi = 6.283185307179586f;
-  // chunks of 31 bins: lane l holds edge base + l; bin base + l uses edges l, l + 1
-  for (int base = 0; base < H.n_bins; base += 31) {
-    const int e = base + lane;
-    float er[NDET], ei[NDET];
-    if (e <= H.n_bins) {
-      const float* eb = H.edge_basis + (size_t)e * 2 * NBASIS;
-      dfl dp = {0.0f, 0.0f};
+  const int e = base + lane;
+  float er[NDET], ei[NDET];
+  if (e <= H.n_bins) {
+    const size_t ne = (size_t)H.n_bins + 1;  // edges; lanes read consecutive edges of each row
+    dfl dp = {0.0f, 0.0f};
 #pragma unroll
-      for (int j = 0; j < NBASIS; ++j) dp = df_add(dp, df_mul(dc[j], dfl{eb[2 * j], eb[2 * j + 1]}));
-      const dfl fe = {H.edge_f[2 * e], H.edge_f[2 * e + 1]};
-#pragma unroll
-      for (int i = 0; i < NDET; ++i) {
-        const float ph = df_frac(df_add(dp, df_mul(fe, dtau[i])));
-        float s, co;
-        __sincosf(twopi * ph, &s, &co);  // exp(-2 pi i ph) = co - i s
-        er[i] = rho_re[i] * co + rho_im[i] * s;
-        ei[i] = rho_im[i] * co - rho_re[i] * s;
-      }
-    } else {
-#pragma unroll
-      for (int i = 0; i < NDET; ++i) er[i] = ei[i] = 0.0f;
-    }
-    const int b = base + lane;
-    const bool has_bin = lane < 31 && b < H.n_bins;
-    const float iw = has_bin ? H.inv_width[b] : 0.0f;
+    for (int j = 0; j < NBASIS; ++j)
+      dp = df_add(dp, df_mul(p.dc[j], dfl{H.edge_basis[2 * j * ne + e], H.edge_basis[(2 * j + 1) * ne + e]}));
+    const dfl fe = {H.edge_f[e], H.edge_f[ne + e]};
 #pragma unroll
     for (int i = 0; i < NDET; ++i) {
-      const float nr = __shfl_down_sync(0xffffffffu, er[i], 1);
-      const float ni = __shfl_down_sync(0xffffffffu, ei[i], 1);
-      if (has_bin) {
-        const float r0r = 0.5f * (er[i] + nr), r0i = 0.5f * (ei[i] + ni);
-        const float r1r = (nr - er[i]) * iw, r1i = (ni - ei[i]) * iw;
-        const float4 a = H.coef[(size_t)i * H.n_bins + b];
-        const float2 bb = H.coefB[(size_t)i * H.n_bins + b];
-        zr[i] += a.x * r0r - a.y * r0i + a.z * r1r - a.w * r1i;
-        zi[i] += a.x * r0i + a.y * r0r + a.z * r1i + a.w * r1r;
-        hh[i] += bb.x * (r0r * r0r + r0i * r0i) + 2.0f * bb.y * (r0r * r1r + r0i * r1i);
-      }
+      const float ph = df_frac(df_add(dp, df_mul(fe, p.dtau[i])));
+      float s, co;
+      __sincosf(twopi * ph, &s, &co);  // exp(-2 pi i ph) = co - i s
+      er[i] = p.rho_re[i] * co + p.rho_im[i] * s;
+      ei[i] = p.rho_im[i] * co - p.rho_re[i] * s;
     }
+  } else {
+#pragma unroll
+    for (int i = 0; i < NDET; ++i) er[i] = ei[i] = 0.0f;
   }
-  double Z_re = 0.0, Z_im = 0.0, HH = 0.0;
+  const int b = base + lane;
+  const bool has_bin = lane < 31 && b < H.n_bins;
+  const float iw = has_bin ? H.inv_width[b] : 0.0f;
 #pragma unroll
   for (int i = 0; i < NDET; ++i) {
+    const float nr = __shfl_down_sync(0xffffffffu, er[i], 1);
+    const float ni = __shfl_down_sync(0xffffffffu, ei[i], 1);
+    if (has_bin) {
+      const float r0r = 0.5f * (er[i] + nr), r0i = 0.5f * (ei[i] + ni);
+      const float r1r = (nr - er[i]) * iw, r1i = (ni - ei[i]) * iw;
+      const float4 a = H.coef[(size_t)i * H.n_bins + b];
+      const float2 bb = H.coefB[(size_t)i * H.n_bins + b];
+      zr[i] += a.x * r0r - a.y * r0i + a.z * r1r - a.w * r1i;
+      zi[i] += a.x * r0i + a.y * r0r + a.z * r1i + a.w * r1r;
+      hh[i] += bb.x * (r0r * r0r + r0i * r0i) + 2.0f * bb.y * (r0r * r1r + r0i * r1i);
+    }
+  }
+}
+
+// Warp-sum of the lane sums (all lanes receive them).
+template <int NDET>
+__device__ inline void het_warp_reduce(float* zr, float* zi, float* hh) {
+#pragma unroll
+  for (int i = 0; i < NDET; ++i)
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       zr[i] += __shfl_xor_sync(0xffffffffu, zr[i], o);
       zi[i] += __shfl_xor_sync(0xffffffffu, zi[i], o);
       hh[i] += __shfl_xor_sync(0xffffffffu, hh[i], o);
     }
-    Z_re += (double)zr[i];
-    Z_im += (double)zi[i];
-    HH += (double)hh[i];
-    if (z_out) {
-      z_out[2 * i] = zr[i];
-      z_out[2 * i + 1] = zi[i];
-    }
-    if (hh_out) hh_out[i] = hh[i];
-  }
+}
+
+// FP64 epilogue: plain Re Z or phase-marginalised log I0(|Z|), minus
+// <h|h>/2 and <d|d>/2.
+__device__ inline double het_epilogue(const LikeConst& L, double Z_re, double Z_im, double HH) {
   const double base_ll = -0.5 * HH - 0.5 * L.DD;
   if (L.phase_marg) return log_bessel_i0(sqrt(Z_re * Z_re + Z_im * Z_im)) + base_ll;
   return Z_re + base_ll;
+}
+
+__host__ __device__ inline int het_chunks(int n_bins) { return (n_bins + 30) / 31; }
+
+// One warp evaluates the heterodyned logL of record r (all lanes return it).
+template <int NDET>
+__device__ inline double het_loglike_warp(const LikeConst& L, const HetTables& H, const EvalRecord& r, int lane) {
+  if (!r.valid) return -INFINITY;
+  HetPrep<NDET> p;
+  het_prepare<NDET>(H, r, p);
+  float zr[NDET], zi[NDET], hh[NDET];
+#pragma unroll
+  for (int i = 0; i < NDET; ++i) zr[i] = zi[i] = hh[i] = 0.0f;
+  const int nc = het_chunks(H.n_bins);
+  for (int q = 0; q < nc; ++q) het_chunk<NDET>(H, p, 31 * q, lane, zr, zi, hh);
+  het_warp_reduce<NDET>(zr, zi, hh);
+  double Z_re = 0.0, Z_im = 0.0, HH = 0.0;
+#pragma unroll
+  for (int i = 0; i < NDET; ++i) {
+    Z_re += (double)zr[i];
+    Z_im += (double)zi[i];
+    HH += (double)hh[i];
+  }
+  return het_epilogue(L, Z_re, Z_im, HH);
 }
 
 }  // namespace swig

@@ -34,8 +34,8 @@ struct DeviceBuffers {
   int max_slice_bins = 0;
   // heterodyned likelihood tables (SWIG_LIKE_HET)
   int het_nb = 0;
-  float* het_edge_basis = nullptr;  // [N_b + 1][2 * NBASIS]
-  float* het_edge_f = nullptr;      // [N_b + 1][2]
+  float* het_edge_basis = nullptr;  // [2 * NBASIS][N_b + 1] (row per basis function, hi / lo)
+  float* het_edge_f = nullptr;      // [2][N_b + 1] (hi row, lo row)
   float* het_inv_width = nullptr;   // [N_b]
   float4* het_coef = nullptr;       // [n_det][N_b]
   float2* het_coefB = nullptr;      // [n_det][N_b]

@@ -47,7 +47,7 @@ constexpr int kMaxShrink = 100;
 constexpr int kMaxSort = 8192;
 constexpr int kMaxChains = 2048;
 
-constexpr int kHetThreads = 256;  // heterodyned sampler: 8 chains per CTA
+constexpr int kHetThreads = 512;  // heterodyned sampler: one chain per CTA, 16 warps
 constexpr int kFreeBudget = 8;  // projection-only evaluations per chain per round
 enum ChainPhase { PH_NEW = 0, PH_LEFT = 1, PH_RIGHT = 2, PH_SHRINK = 3 };
 // What a Gibbs block moves: waveform coefficients, amplitude A(Mc)/d_L,
@@ -383,7 +383,7 @@ __device__ inline void start_step(const SamplerConst& S, ChainState& ch, const f
 template <bool MIXED>
 __device__ __noinline__ void chain_advance_local(const LikeConst& L, const SamplerConst& S, const SamplerPtrs& P, int c,
                                     const double* kap_in, double ly_in, ChainState& ch, EvalRecord& rx,
-                                    bool& rx_dirty, EvalRecord& rec, bool& rec_set) {
+                                    bool& rx_dirty, EvalRecord& rec, bool& rec_set, int& setup_fl) {
   NSGlobal* g = P.g;
   const double logl_star = g->logl_star;
   const long long it = g->iter;
@@ -509,21 +509,8 @@ __device__ __noinline__ void chain_advance_local(const LikeConst& L, const Sampl
       continue;
     }
     rec = rx;
-    const int fl = S.block_flags[b] | (ch.proj_dirty ? (BF_AMP | BF_PROJ) : 0);
+    setup_fl = S.block_flags[b] | (ch.proj_dirty ? (BF_AMP | BF_PROJ) : 0);
     rec.valid = theta_valid(ch.th_y) ? 1 : 0;
-    if (fl & BF_INTR)
-      setup_intrinsic(ch.th_y, &rec);
-    else if (fl & (BF_SPIN | BF_TIDE))
-      setup_intrinsic_partial(ch.th_y, &rec, (fl & BF_SPIN) != 0, (fl & BF_TIDE) != 0);
-    if (MIXED) {
-      if (fl & BF_AMP) setup_amp_f32(ch.th_y, &rec);
-      if (fl & BF_PROJ) setup_projection_f32(L, ch.th_y, &rec);
-    } else {
-      if (fl & BF_AMP) setup_amp(ch.th_y, &rec);
-      if (fl & BF_PROJ) setup_projection(L, ch.th_y, &rec);
-    }
-    if (fl & BF_TAU) setup_delays(L, ch.th_y, &rec);
-    setup_combine(L, &rec);
     rec_set = true;
     ch.pending = 1;
     P.pending[c] = 1;
@@ -537,19 +524,58 @@ __device__ __noinline__ void chain_advance_local(const LikeConst& L, const Sampl
 
 // Chain control on local copies of the chain state and records (local
 // memory is cached in L1; the global copies are read and written once).
+// Lane 0 only.  Returns the set-up flags of the new pending proposal (its
+// record in *rec_out still holds the current point's values for the pieces
+// the block moves), or -1 when nothing is pending.
 template <bool MIXED>
-__device__ __noinline__ void chain_advance(const LikeConst& L, const SamplerConst& S, const SamplerPtrs& P, int c,
-                              const double* kap_in, double ly_in, EvalRecord* rec_out) {
-  if (P.chains[c].done) return;
+__device__ __noinline__ int chain_advance(const LikeConst& L, const SamplerConst& S, const SamplerPtrs& P, int c,
+                                          const double* kap_in, double ly_in, EvalRecord* rec_out) {
+  if (P.chains[c].done) return -1;
   ChainState ch = P.chains[c];
   EvalRecord rx = P.recx[c];
   EvalRecord rec;
   if (ch.pending) rec = *rec_out;
   bool rx_dirty = false, rec_set = false;
-  chain_advance_local<MIXED>(L, S, P, c, kap_in, ly_in, ch, rx, rx_dirty, rec, rec_set);
+  int fl = -1;
+  chain_advance_local<MIXED>(L, S, P, c, kap_in, ly_in, ch, rx, rx_dirty, rec, rec_set, fl);
   P.chains[c] = ch;
   if (rx_dirty) P.recx[c] = rx;
   if (rec_set) *rec_out = rec;
+  return fl;
+}
+
+// The set-up of a pending proposal's record, one piece per lane: lane 0 the
+// waveform coefficients (all, or only spin / tidal ones), lane 1 the
+// amplitude, lanes 2.. the projection of each detector, lanes 8.. the time
+// shift of each detector; then lane 0 combines them.  All 32 lanes call it
+// with the same fl (>= 0) and th (the proposal's theta).
+__device__ __noinline__ void setup_record_warp(const LikeConst& L, const double* th, int fl, bool f32,
+                                               EvalRecord* rec, int lane) {
+  if (rec->valid) {
+    if (lane == 0) {
+      if (fl & BF_INTR)
+        setup_intrinsic(th, rec);
+      else if (fl & (BF_SPIN | BF_TIDE))
+        setup_intrinsic_partial(th, rec, (fl & BF_SPIN) != 0, (fl & BF_TIDE) != 0);
+    } else if (lane == 1) {
+      if (fl & BF_AMP) {
+        if (f32)
+          setup_amp_f32(th, rec);
+        else
+          setup_amp(th, rec);
+      }
+    } else if (lane >= 2 && lane < 2 + L.n_det) {
+      if (fl & BF_PROJ) setup_projection_det(L, th, lane - 2, f32, rec);
+    } else if (lane >= 8 && lane < 8 + L.n_det) {
+      if (fl & BF_TAU) setup_delay_det(L, th, lane - 8, rec);
+    }
+  } else if (lane == 0) {
+    // invalid proposal: the record only has to say so (logL = -inf)
+    rec->amp = 0.0;
+  }
+  __syncwarp();
+  if (lane == 0) setup_combine(L, rec);
+  __syncwarp();
 }
 
 // ---------------------------------------------------------------------------
@@ -815,11 +841,18 @@ __global__ void __launch_bounds__(kSweepThreads, 1)
           ly = loglike_epilogue(L, B.rec[c], kre, kim);
         }
       }
+      int fl = -1;
       if (lane == 0) {
         if (pend) P.pending[c] = 0;
-        chain_advance<MIXED>(L, S, P, c, kap_y, ly, &B.rec[c]);
+        fl = chain_advance<MIXED>(L, S, P, c, kap_y, ly, &B.rec[c]);
       }
+      fl = __shfl_sync(0xffffffffu, fl, 0);
       __syncwarp();
+      if (fl >= 0) {
+        const long long ts = clock64();
+        setup_record_warp(L, P.chains[c].th_y, fl, MIXED, &B.rec[c], lane);
+        if (c == 0 && lane == 0) g->c_setup += clock64() - ts;
+      }
     }
     __syncthreads();
     if (timer) {
@@ -907,20 +940,24 @@ __global__ void __launch_bounds__(kSweepThreads, 1)
 }
 
 // Persistent sampler for the heterodyned likelihood (Sec. 3.4).  A
-// heterodyned evaluation is a few hundred to a few thousand bins, so the
-// chain's own warp evaluates every proposal right after its control step: the
-// chains of one NS iteration run to completion independently, and the grid
-// meets only at the iteration boundary.  Every proposal is evaluated in full
-// (no projection-only shortcut) and the set-up is FP64.
+// heterodyned evaluation is a few hundred to a few thousand bins, so one CTA
+// owns one chain at a time: thread 0 runs the chain's control, then every
+// warp contracts a share of the bins (31-bin chunks, strided by warp) and the
+// per-warp sums are added in warp order.  The chains of one NS iteration run
+// independently to completion; the grid meets only at the iteration
+// boundary.  Every proposal is evaluated in full (no projection-only
+// shortcut) and the set-up is FP64.
 template <int NDET>
 __global__ void __launch_bounds__(kHetThreads, 1)
     k_ns_het(LikeConst L, SamplerConst S, DeviceBuffers B, SamplerPtrs P) {
   extern __shared__ __align__(16) unsigned char smem[];
-  const int lane = threadIdx.x & 31;
-  const int gw = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  const int n_warps = gridDim.x * (blockDim.x >> 5);
+  __shared__ float s_sum[kHetThreads / 32][3 * NDET];
+  __shared__ int s_done, s_fl;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int n_warps = blockDim.x >> 5;
   NSGlobal* g = P.g;
   const HetTables H = het_tables(B);
+  const int nc = het_chunks(H.n_bins);
   const bool timer = blockIdx.x == 0 && threadIdx.x == 0;
   unsigned long long t0 = gtimer(), t1;
   for (;;) {
@@ -939,18 +976,61 @@ __global__ void __launch_bounds__(kHetThreads, 1)
       t0 = t1;
     }
     if (*(volatile int*)&g->status != ST_RUNNING) return;
-    for (int c = gw; c < S.nrep; c += n_warps) {
+    for (int c = blockIdx.x; c < S.nrep; c += gridDim.x) {
       double kap0[2 * SWIG_MAX_DET];
 #pragma unroll
       for (int j = 0; j < 2 * SWIG_MAX_DET; ++j) kap0[j] = 0.0;
       double ly = 0.0;
       for (long long guard = 0; guard < (1ll << 24); ++guard) {
-        if (lane == 0) chain_advance<false>(L, S, P, c, kap0, ly, &B.rec[c]);
-        __syncwarp();
-        if (*(volatile int*)&P.chains[c].done) break;
-        ly = het_loglike_warp<NDET>(L, H, B.rec[c], lane);
-        __syncwarp();
+        if (threadIdx.x == 0) {
+          s_fl = chain_advance<false>(L, S, P, c, kap0, ly, &B.rec[c]);
+          s_done = P.chains[c].done;
+        }
+        __syncthreads();
+        if (s_done) break;
+        if (s_fl < 0) continue;  // nothing pending (cannot happen without projection-only blocks)
+        if (warp == 0) {
+          const long long ts = clock64();
+          setup_record_warp(L, P.chains[c].th_y, s_fl, false, &B.rec[c], lane);
+          if (c == 0 && lane == 0) g->c_setup += clock64() - ts;
+        }
+        __syncthreads();
+        const EvalRecord& r = B.rec[c];
+        const bool valid = r.valid != 0;
+        float zr[NDET], zi[NDET], hh[NDET];
+#pragma unroll
+        for (int i = 0; i < NDET; ++i) zr[i] = zi[i] = hh[i] = 0.0f;
+        if (valid) {
+          HetPrep<NDET> p;
+          het_prepare<NDET>(H, r, p);
+          for (int q = warp; q < nc; q += n_warps) het_chunk<NDET>(H, p, 31 * q, lane, zr, zi, hh);
+          het_warp_reduce<NDET>(zr, zi, hh);
+        }
+        if (lane == 0) {
+#pragma unroll
+          for (int i = 0; i < NDET; ++i) {
+            s_sum[warp][3 * i] = zr[i];
+            s_sum[warp][3 * i + 1] = zi[i];
+            s_sum[warp][3 * i + 2] = hh[i];
+          }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+          if (!valid) {
+            ly = -INFINITY;
+          } else {
+            double Z_re = 0.0, Z_im = 0.0, HH = 0.0;
+            for (int w = 0; w < n_warps; ++w)
+              for (int i = 0; i < NDET; ++i) {
+                Z_re += (double)s_sum[w][3 * i];
+                Z_im += (double)s_sum[w][3 * i + 1];
+                HH += (double)s_sum[w][3 * i + 2];
+              }
+            ly = het_epilogue(L, Z_re, Z_im, HH);
+          }
+        }
       }
+      __syncthreads();
     }
     if (timer) {
       t1 = gtimer();
@@ -1100,7 +1180,7 @@ int swig_run(swig_ctx* c, swig_result* out) {
   const int m = c->cfg.nlive, k = c->cfg.nrep;
   const LikeConst& L = c->L;
   if (!het && k > 32 * L.n_slices) return fail(c, SWIG_E_ARG, "nrep exceeds 32 chains per CTA");
-  const int het_ctas = std::max(1, std::min(c->sm_count, (k + kHetThreads / 32 - 1) / (kHetThreads / 32)));
+  const int het_ctas = std::max(1, std::min(c->sm_count, k));
 
   SamplerConst S;
   std::memset(&S, 0, sizeof(S));

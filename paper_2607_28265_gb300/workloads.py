@@ -10,11 +10,14 @@ Run as a module it executes one small case for a profiler capture::
     python -m paper_2607_28265_gb300.workloads sampler --max-iter 2
     python -m paper_2607_28265_gb300.workloads loglike --batch 1000
     python -m paper_2607_28265_gb300.workloads het --batch 1000 --bins 1000
+    python -m paper_2607_28265_gb300.workloads sampler-het --max-iter 2 --bins 5000
 
 ``sampler``: the persistent nested-sampling kernel on the 128 s H1/L1/V1
 workload for --max-iter outer iterations (one launch); ``loglike``: one batch
 of the full-grid mixed-precision likelihood; ``het``: one batch of the
-heterodyned likelihood.  Each case exits non-zero on any library error.
+heterodyned likelihood; ``sampler-het``: the heterodyned persistent sampler
+kernel (fiducial at the injection).  Each case exits non-zero on any library
+error.
 """
 from __future__ import annotations
 
@@ -41,10 +44,13 @@ def build_context(wl, seed_offset=0, precision=swig.PREC_MIXED):
     for i, s in enumerate(psds):
         ctx.set_psd(i, s)
     ctx.set_prior(wl.params)
-    u = np.asarray(wl.injection)
-    sampled = wl.sampled()
-    th = ctx.prior_transform(u[sampled][None, :])[0]
-    th[si.IDX["phic"]] = 2.0 * math.pi * u[si.IDX["phic"]]
+    if wl.inj_unit:
+        u = np.asarray(wl.injection)
+        sampled = wl.sampled()
+        th = ctx.prior_transform(u[sampled][None, :])[0]
+        th[si.IDX["phic"]] = 2.0 * math.pi * u[si.IDX["phic"]]
+    else:
+        th = np.asarray(wl.injection, dtype=np.float64).copy()
     noise = np.array(wl.noise())
     data, th_used = ctx.inject(th, len(wl.detectors), target_snr=wl.target_snr, noise=noise)
     for i in range(len(wl.detectors)):
@@ -61,7 +67,7 @@ def _prior_draws(ctx, wl, n, seed):
 
 def main(argv=None):
     ap = argparse.ArgumentParser(description="small profiling cases on the 128 s three-detector workload")
-    ap.add_argument("case", choices=["sampler", "loglike", "het"])
+    ap.add_argument("case", choices=["sampler", "sampler-het", "loglike", "het"])
     ap.add_argument("--max-iter", type=int, default=2)
     ap.add_argument("--batch", type=int, default=1000)
     ap.add_argument("--bins", type=int, default=1000)
@@ -75,6 +81,13 @@ def main(argv=None):
         for _ in range(a.repeat):
             r = ctx.run()
         print(f"sampler: n_iter={r.n_iter} n_evals={r.n_evals} logz={r.logz:.3f}")
+    elif a.case == "sampler-het":
+        ctx.set_sampler(nlive=wl.nlive, nrep=wl.nrep, sweeps=wl.sweeps, steps_per_dim=wl.steps_per_dim,
+                        seed=wl.sampler_seed, likelihood=swig.LIKE_HET, het_bins=a.bins, het_fiducial=th,
+                        max_iter=a.max_iter)
+        for _ in range(a.repeat):
+            r = ctx.run()
+        print(f"sampler-het: n_iter={r.n_iter} n_evals={r.n_evals} logz={r.logz:.3f}")
     else:
         if a.case == "het":
             ctx.set_sampler(nlive=wl.nlive, nrep=wl.nrep, likelihood=swig.LIKE_HET, het_bins=a.bins,
