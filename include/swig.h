@@ -227,7 +227,9 @@ int swig_set_wait_limit(swig_ctx* ctx, long long spins);
  * new slice steps, proposals, projection-only evaluations and full-evaluation
  * set-up, out[17..19] the counts of the last three; out[20] milliseconds of
  * learned-proposal training (targets, Adam steps, output rows; CUDA events)
- * and out[21] the number of retrainings.  Writes min(n, 22) values. */
+ * and out[21] the number of retrainings; out[22..24] for the first CTA's
+ * sweep warps: (chain, slice) units evaluated, clock cycles spent in them and
+ * cycles spent polling for work.  Writes min(n, 25) values. */
 int swig_get_profile(swig_ctx* ctx, double* out, int n);
 /* Use `stream` (a cudaStream_t on the context's device, owned by the caller)
  * for all later work of this context; NULL restores a private stream. */

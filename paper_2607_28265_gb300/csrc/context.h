@@ -46,7 +46,7 @@ struct swig_ctx {
   long long wait_limit = 10000000;  // spins of a bounded device wait (~100 ns each)
   // results of the last run
   swig_result last = {};
-  double profile[22] = {};
+  double profile[25] = {};
   // counters over the context's lifetime: kernel launches, bytes copied host
   // to device and device to host by the library
   long long n_launches = 0, h2d_bytes = 0, d2h_bytes = 0;

@@ -2,7 +2,8 @@
 //
 // One cooperative launch runs up to `max_iters` nested-sampling iterations on
 // the device.  Every CTA owns one slice of the frequency grid (its data staged
-// once in shared memory) and the kernel alternates, between grid barriers:
+// once in shared memory).  The grid meets at a barrier only around the
+// iteration boundary:
 //
 //   boundary  (CTA 0, once per NS iteration): write the k finished chains back
 //             into the live set, sort the live log-likelihoods, test the
@@ -11,23 +12,31 @@
 //             (log X shrinks by 1/n per death, n = m, m-1, ..., m-k+1), set
 //             logL* to the lowest survivor, estimate the live covariance and
 //             its per-block Cholesky factors, and start k chains at survivors.
-//   control   (one warp per chain): advance the chain's hit-and-run slice state
-//             machine (Neal 2003 stepping-out and shrinkage along a direction
-//             drawn from the block covariance) through every proposal that
-//             needs no pass over the grid: proposals outside the unit cube, and
-//             proposals of blocks that only change the projection factors C_i
-//             (d_L, iota, psi, phi_c), which reuse the chain's cached
-//             per-detector sums kappa_i.  A proposal that changes the waveform
-//             or the time shifts is set up and left pending.
-//   sweep     (all CTAs): every pending chain's likelihood over the CTA's slice,
-//             one chain per warp-group, partial sums per (chain, slice).
 //
-// Every spin of the grid barrier is bounded; on expiry the kernel records
-// SWIG_E_TIMEOUT and every CTA returns at its next barrier.
+// Within the iteration everything runs as a dataflow (k_ns_flow):
+//
+//   control   (warp 0 of the chain's home CTA): advance the chain's hit-and-run
+//             slice state machine (Neal 2003 stepping-out and shrinkage along a
+//             direction drawn from the block covariance, or a learned one)
+//             through every proposal that needs no pass over the grid:
+//             proposals outside the unit cube, and proposals of blocks that only
+//             change the projection factors C_i (d_L, iota, psi, phi_c), which
+//             reuse the chain's cached per-detector sums kappa_i.  A proposal
+//             that changes the waveform or the time shifts is set up (one lane
+//             per piece of the record) and published as a request.
+//   sweep     (warps 1.. of every CTA): claim published requests and evaluate
+//             the CTA's slice for them, one warp per (chain, slice), partial
+//             sums per (chain, slice); the chain's control resumes when every
+//             CTA has counted itself done.
+//
+// Every spin-wait is bounded; on expiry the kernel records SWIG_E_TIMEOUT and
+// every CTA returns at its next barrier.  The heterodyned likelihood has its
+// own persistent kernel (k_ns_het, one CTA per chain).
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <chrono>
+#include <climits>
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -68,9 +77,9 @@ struct SamplerConst {
   long long spin_limit;
   int max_pieces;      // pieces per slice (sweep work units)
   int max_tiles_slice; // tiles overlapping the largest slice
-  int group;           // pending chains per sweep group (shared-memory bound)
   int n_ctas;
   int mixed;
+  int flow_parts;   // parts per slice (dataflow kernel): fixed summation partition
   int learn_on;     // learned directions available (SWIG_PROPOSAL_LEARNED)
   float learn_mix;  // probability of a learned direction per slice step
 };
@@ -103,6 +112,9 @@ struct NSGlobal {
   // chain 0's control breakdown [clock64 cycles]: pending result, new step,
   // proposal + transform, projection-only evaluations, full setup; counts
   unsigned long long c_result, c_step, c_prop, c_free, c_setup, n_free, n_setup, n_step;
+  // CTA 0's sweep warps (dataflow kernel): units evaluated, clock64 cycles in
+  // units, cycles idle (polling for work)
+  unsigned long long f_units, f_unit_cyc, f_idle_cyc;
 };
 
 __device__ __forceinline__ unsigned long long gtimer() {
@@ -129,6 +141,8 @@ struct SamplerPtrs {
   const int* slice_piece;  // [n_slices + 1] offset of each slice's pieces in piece_begin
   float* anchor_buf;       // [n_slices][k][max_tiles_slice][kAnchorStride] per-round anchors
   const float* learn_out;  // [m][32] network outputs (u, s) of a frozen live snapshot, or null
+  int* req;                // [k] 8 * (sequence number of the chain's latest full-likelihood request) + parts per slice
+  int* done_cnt;           // [k] CTAs that finished the chain's latest request
 };
 
 // ---------------------------------------------------------------------------
@@ -614,9 +628,10 @@ __device__ __noinline__ void ns_boundary(const LikeConst& L, const SamplerConst&
   if (g->need_writeback) {
     for (int c = tid; c < k; c += nt) {
       const ChainState& ch = P.chains[c];
-      for (int j = 0; j < d; ++j) P.live_u[(size_t)ch.slot * d + j] = ch.x[j];
-      P.live_logl[ch.slot] = ch.lx;
-      for (int j = 0; j < 2 * SWIG_MAX_DET; ++j) P.live_kap[(size_t)ch.slot * 2 * SWIG_MAX_DET + j] = ch.kap[j];
+      const int slot = __ldcg(&ch.slot);
+      for (int j = 0; j < d; ++j) P.live_u[(size_t)slot * d + j] = __ldcg(&ch.x[j]);
+      P.live_logl[slot] = __ldcg(&ch.lx);
+      for (int j = 0; j < 2 * SWIG_MAX_DET; ++j) P.live_kap[(size_t)slot * 2 * SWIG_MAX_DET + j] = __ldcg(&ch.kap[j]);
     }
     __syncthreads();
     if (tid == 0) g->need_writeback = 0;
@@ -750,6 +765,8 @@ __device__ __noinline__ void ns_boundary(const LikeConst& L, const SamplerConst&
     ch.done = 0;
     ch.ctr = 0;
     P.pending[c] = 0;
+    P.req[c] = 0;
+    P.done_cnt[c] = 0;
   }
   __syncthreads();
   if (tid == 0) {
@@ -761,14 +778,104 @@ __device__ __noinline__ void ns_boundary(const LikeConst& L, const SamplerConst&
 }
 
 // ---------------------------------------------------------------------------
-// The persistent kernel.
+// The persistent kernel, dataflow form.  Within an NS iteration nothing
+// waits on a grid-wide barrier: warp 0 of each CTA runs the control of the
+// chains homed there, and publishes each full-likelihood request by bumping
+// the chain's sequence number after writing its record; warps 1.. of every
+// CTA claim (chain, request) pairs as they appear and evaluate the CTA's
+// slice of the grid for them (one warp per pair), then count themselves in
+// done_cnt.  A chain's control resumes once all CTAs have counted.  The
+// per-slice sums are written in a fixed place and added over slices in a
+// fixed order, so results do not depend on timing.  Every wait is bounded.
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ int ld_acquire(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release(int* p, int v) {
+  asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Copy a record written by another SM into shared memory (through L2).
+__device__ __forceinline__ void load_record_cg(const EvalRecord* src, EvalRecord* dst, int lane) {
+  const unsigned* s = reinterpret_cast<const unsigned*>(src);
+  unsigned* d = reinterpret_cast<unsigned*>(dst);
+  for (int w = lane; w < (int)(sizeof(EvalRecord) / 4); w += 32) d[w] = __ldcg(s + w);
+  __syncwarp();
+}
+
+// One control step of chain c by a whole warp: add the slice partials of the
+// finished request (fixed order), advance the chain's slice state machine and,
+// when it needs a full likelihood, set up its record and publish the request.
+// Returns true while the chain needs another control step right away
+// (projection-only budget used up), false once it waits for a request or is
+// done.
+template <int NDET, bool MIXED>
+__device__ bool flow_control(const LikeConst& L, const SamplerConst& S, const DeviceBuffers& B, const SamplerPtrs& P,
+                             int c, int lane) {
+  NSGlobal* g = P.g;
+  double kap_y[2 * SWIG_MAX_DET];
+#pragma unroll
+  for (int j = 0; j < 2 * SWIG_MAX_DET; ++j) kap_y[j] = 0.0;
+  double ly = 0.0;
+  const bool pend = P.chains[c].pending != 0;
+  if (pend) {
+    double acc[2 * SWIG_MAX_DET];
+#pragma unroll
+    for (int j = 0; j < 2 * SWIG_MAX_DET; ++j) acc[j] = 0.0;
+    const int n_units = L.n_slices * S.flow_parts;
+    for (int s2 = lane; s2 < n_units; s2 += 32) {
+#pragma unroll
+      for (int j = 0; j < 2 * NDET; ++j)
+        acc[j] += MIXED ? (double)__ldcg(&B.partials32[((size_t)c * n_units + s2) * kPartialStride + j])
+                        : __ldcg(&B.partials64[((size_t)c * n_units + s2) * kPartialStride + j]);
+    }
+#pragma unroll
+    for (int j = 0; j < 2 * NDET; ++j)
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) acc[j] += __shfl_xor_sync(0xffffffffu, acc[j], o);
+#pragma unroll
+    for (int j = 0; j < 2 * SWIG_MAX_DET; ++j) kap_y[j] = acc[j];
+    if (lane == 0) {
+      double kre[SWIG_MAX_DET], kim[SWIG_MAX_DET];
+      for (int i = 0; i < SWIG_MAX_DET; ++i) {
+        kre[i] = kap_y[2 * i];
+        kim[i] = kap_y[2 * i + 1];
+      }
+      ly = loglike_epilogue(L, B.rec[c], kre, kim);
+    }
+  }
+  int fl = -1, done = 0;
+  if (lane == 0) {
+    if (pend) P.pending[c] = 0;
+    fl = chain_advance<MIXED>(L, S, P, c, kap_y, ly, &B.rec[c]);
+    done = P.chains[c].done;
+  }
+  fl = __shfl_sync(0xffffffffu, fl, 0);
+  done = __shfl_sync(0xffffffffu, done, 0);
+  __syncwarp();
+  if (fl >= 0) {
+    const long long ts = clock64();
+    setup_record_warp(L, P.chains[c].th_y, fl, MIXED, &B.rec[c], lane);
+    if (lane == 0) {
+      if (c == 0) g->c_setup += clock64() - ts;
+      P.done_cnt[c] = 0;
+      __threadfence();
+      // sequence number and unit width in one word (one unit per slice)
+      st_release(&P.req[c], (((P.req[c] >> 3) + 1) << 3) | S.flow_parts);
+    }
+    __syncwarp();
+    return false;
+  }
+  return !done;
+}
+
 template <int NDET, bool MIXED>
 __global__ void __launch_bounds__(kSweepThreads, 1)
-    k_ns_persistent(LikeConst L, SamplerConst S, DeviceBuffers B, SamplerPtrs P) {
+    k_ns_flow(LikeConst L, SamplerConst S, DeviceBuffers B, SamplerPtrs P) {
   extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ int s_pend[kMaxChains];
-  __shared__ int s_npend;
+  __shared__ int s_claim[kMaxChains];
   const int slice = blockIdx.x;
   const int b0 = B.slice_begin[slice], b1 = B.slice_begin[slice + 1];
   const int nb = b1 - b0;
@@ -787,9 +894,12 @@ __global__ void __launch_bounds__(kSweepThreads, 1)
     fixed_bytes = (((size_t)nb * (NDET * sizeof(float2) + sizeof(int))) + 15) & ~(size_t)15;
   }
   __syncthreads();
-  unsigned char* dyn = smem + fixed_bytes;  // sweep buffers, or sort buffers (boundary)
-  float* s_part = reinterpret_cast<float*>(dyn);     // [group * pieces][kPartialStride]
-  double* s_part64 = reinterpret_cast<double*>(dyn);  // FP64 path
+  unsigned char* dyn = smem + fixed_bytes;  // per-warp records, or sort buffers (boundary)
+  EvalRecord* rec = reinterpret_cast<EvalRecord*>(dyn) + warp;
+  const int tf = MIXED ? s_tile[0] : 0;
+  float* abuf = P.anchor_buf + (size_t)slice * S.nrep * S.max_tiles_slice * kAnchorStride;
+  const int G = S.flow_parts;
+  const int target = S.n_ctas;  // units per request: one per slice (G parts each)
 
   const bool timer = blockIdx.x == 0 && tid == 0;
   unsigned long long t0 = gtimer(), t1;
@@ -801,139 +911,144 @@ __global__ void __launch_bounds__(kSweepThreads, 1)
       t0 = t1;
       g->rounds += 1;
     }
-    if (*(volatile int*)&g->chains_done >= S.nrep) {
-      if (blockIdx.x == 0) ns_boundary(L, S, P, dyn);
-      if (!grid_sync(g, S.n_ctas, S.spin_limit)) return;
-      if (timer) {
-        t1 = gtimer();
-        g->t_bound += t1 - t0;
-        t0 = t1;
-      }
-      if (*(volatile int*)&g->status != ST_RUNNING) return;
+    if (blockIdx.x == 0) ns_boundary(L, S, P, dyn);
+    for (int c = tid; c < S.nrep; c += blockDim.x) s_claim[c] = 0;
+    if (!grid_sync(g, S.n_ctas, S.spin_limit)) return;
+    if (timer) {
+      t1 = gtimer();
+      g->t_bound += t1 - t0;
+      t0 = t1;
     }
-    // ---- control: one warp per chain
-    for (int c = blockIdx.x + warp * S.n_ctas; c < S.nrep; c += 32 * S.n_ctas) {
-      double kap_y[2 * SWIG_MAX_DET];
-      double ly = 0.0;
-      const bool pend = P.chains[c].pending != 0;
-      if (pend) {
-        double acc[2 * SWIG_MAX_DET];
-#pragma unroll
-        for (int j = 0; j < 2 * SWIG_MAX_DET; ++j) acc[j] = 0.0;
-        for (int s = lane; s < L.n_slices; s += 32) {
-#pragma unroll
-          for (int j = 0; j < 2 * NDET; ++j)
-            acc[j] += MIXED ? (double)B.partials32[((size_t)c * L.n_slices + s) * kPartialStride + j]
-                            : B.partials64[((size_t)c * L.n_slices + s) * kPartialStride + j];
-        }
-#pragma unroll
-        for (int j = 0; j < 2 * NDET; ++j)
-#pragma unroll
-          for (int o = 16; o > 0; o >>= 1) acc[j] += __shfl_xor_sync(0xffffffffu, acc[j], o);
-#pragma unroll
-        for (int j = 0; j < 2 * SWIG_MAX_DET; ++j) kap_y[j] = acc[j];
-        if (lane == 0) {
-          double kre[SWIG_MAX_DET], kim[SWIG_MAX_DET];
-          for (int i = 0; i < SWIG_MAX_DET; ++i) {
-            kre[i] = kap_y[2 * i];
-            kim[i] = kap_y[2 * i + 1];
+    if (*(volatile int*)&g->status != ST_RUNNING) return;
+
+    long long idle = 0;
+    unsigned long long my_units = 0, my_unit_cyc = 0, my_idle_cyc = 0;
+    long long tpoll = clock64();
+    if (warp == 0) {
+      // ---- control of the chains homed on this CTA (their state stays in
+      // this SM's L1); a chain is ready when every CTA finished its request
+      for (;;) {
+        bool all_done = true, progressed = false;
+        for (int c = blockIdx.x; c < S.nrep; c += S.n_ctas) {
+          int st = 0;  // 0 done, 1 waiting, 2 ready
+          if (lane == 0) {
+            const ChainState* ch = &P.chains[c];
+            if (ch->done)
+              st = 0;
+            else if (ch->pending)
+              st = ld_acquire(&P.done_cnt[c]) >= target ? 2 : 1;
+            else
+              st = 2;
           }
-          ly = loglike_epilogue(L, B.rec[c], kre, kim);
+          st = __shfl_sync(0xffffffffu, st, 0);
+          if (st == 0) continue;
+          all_done = false;
+          if (st == 1) continue;
+          progressed = true;
+          flow_control<NDET, MIXED>(L, S, B, P, c, lane);
+        }
+        if (all_done) break;
+        if (*(volatile int*)&g->error) break;
+        if (progressed) {
+          idle = 0;
+        } else {
+          if (++idle > S.spin_limit) {
+            if (lane == 0) atomicCAS(&g->error, 0, SWIG_E_TIMEOUT);
+            break;
+          }
+          __nanosleep(64);
         }
       }
-      int fl = -1;
-      if (lane == 0) {
-        if (pend) P.pending[c] = 0;
-        fl = chain_advance<MIXED>(L, S, P, c, kap_y, ly, &B.rec[c]);
+    } else {
+      // ---- sweep: claim (chain, request) pairs, lowest chain first, and
+      // evaluate this CTA's slice for them, one warp per pair
+      for (;;) {
+        if (*(volatile int*)&g->chains_done >= S.nrep) break;
+        if (*(volatile int*)&g->error) break;
+        // s_claim[c] = request number this CTA has taken for chain c
+        int cc = -1;
+        for (int base = 0; base < S.nrep && cc < 0; base += 32) {
+          const int c = base + lane;
+          int r = 0;
+          bool cand = false;
+          if (c < S.nrep) {
+            r = (*(volatile int*)&P.req[c]) >> 3;
+            cand = r > *(volatile int*)&s_claim[c];
+          }
+          unsigned m = __ballot_sync(0xffffffffu, cand);
+          while (m) {
+            const int leader = __ffs(m) - 1;
+            int won = 0;
+            if (lane == leader) {
+              const int old = *(volatile int*)&s_claim[c];
+              won = (old < r) && atomicCAS(&s_claim[c], old, r) == old;
+            }
+            if (__shfl_sync(0xffffffffu, won, leader)) {
+              cc = base + leader;
+              break;
+            }
+            m &= ~(1u << leader);
+          }
+        }
+        if (cc < 0) {
+          if (++idle > S.spin_limit) {
+            if (lane == 0) atomicCAS(&g->error, 0, SWIG_E_TIMEOUT);
+            break;
+          }
+          __nanosleep(100);
+          continue;
+        }
+        idle = 0;
+        const long long tu0 = clock64();
+        my_idle_cyc += tu0 - tpoll;
+        __threadfence();  // acquire: the request word was read relaxed
+        load_record_cg(&B.rec[cc], rec, lane);
+        for (int part = 0; part < G; ++part) {
+          const int lo = (int)(((long long)nb * part) / G), hi = (int)(((long long)nb * (part + 1)) / G);
+          const size_t pidx = (((size_t)cc * L.n_slices + slice) * G + part) * kPartialStride;
+          if (MIXED) {
+            float* row = abuf + (size_t)cc * S.max_tiles_slice * kAnchorStride;
+            if (hi > lo) {
+              const int lo_prev = (int)(((long long)nb * (part - 1)) / G);
+              const bool cont = part > 0 && lo > lo_prev && s_tile[lo] == s_tile[lo - 1];
+              const int t_lo = s_tile[lo] - tf + (cont ? 1 : 0), t_hi = s_tile[hi - 1] - tf;
+              for (int t = t_lo + lane; t <= t_hi; t += 32)
+                compute_anchor(NDET, B.tiles[tf + t], B.basis[tf + t], *rec, row + (size_t)t * kAnchorStride);
+            }
+            __syncwarp();
+            float v[2 * NDET];
+            sweep_warp_mixed<NDET>(L, s_data, nb, s_tile, b0, lo, hi, B.tiles, row, tf, *rec, lane, v);
+#pragma unroll
+            for (int j = 0; j < 2 * NDET; ++j)
+              if (lane == j) B.partials32[pidx + j] = v[j];
+          } else {
+            double v[2 * NDET];
+            sweep_warp_fp64<NDET>(L, B.data64, B.ftab, b0 + lo, b0 + hi, *rec, lane, v);
+#pragma unroll
+            for (int j = 0; j < 2 * NDET; ++j)
+              if (lane == j) B.partials64[pidx + j] = v[j];
+          }
+        }
+        __syncwarp();
+        if (lane == 0) {
+          __threadfence();
+          atomicAdd(&P.done_cnt[cc], 1);
+        }
+        tpoll = clock64();
+        my_units += 1;
+        my_unit_cyc += tpoll - tu0;
       }
-      fl = __shfl_sync(0xffffffffu, fl, 0);
-      __syncwarp();
-      if (fl >= 0) {
-        const long long ts = clock64();
-        setup_record_warp(L, P.chains[c].th_y, fl, MIXED, &B.rec[c], lane);
-        if (c == 0 && lane == 0) g->c_setup += clock64() - ts;
-      }
+    }
+    my_idle_cyc += clock64() - tpoll;
+    if (blockIdx.x == 0 && lane == 0) {
+      atomicAdd(&g->f_units, my_units);
+      atomicAdd(&g->f_unit_cyc, my_unit_cyc);
+      atomicAdd(&g->f_idle_cyc, my_idle_cyc);
     }
     __syncthreads();
     if (timer) {
       t1 = gtimer();
       g->t_ctrl += t1 - t0;
-      t0 = t1;
-    }
-    if (!grid_sync(g, S.n_ctas, S.spin_limit)) return;
-    if (timer) {
-      t1 = gtimer();
-      g->t_wait_ctrl += t1 - t0;
-      t0 = t1;
-    }
-    // ---- sweep: pending chains over this slice, one chain per warp-group
-    if (tid == 0) s_npend = 0;
-    __syncthreads();
-    for (int c = tid; c < S.nrep; c += blockDim.x)
-      if (*(volatile int*)&P.pending[c]) s_pend[atomicAdd(&s_npend, 1)] = c;
-    __syncthreads();
-    const int npend = s_npend;
-    // anchors of every (pending chain, slice tile) pair, one thread per pair
-    const int p0 = P.slice_piece[slice], n_pc = P.slice_piece[slice + 1] - p0 - 1;
-    float* abuf = P.anchor_buf + (size_t)slice * S.nrep * S.max_tiles_slice * kAnchorStride;
-    int tf = 0;
-    if (MIXED) {
-      tf = s_tile[0];
-      const int nts = s_tile[nb - 1] - tf + 1;
-      for (int it = tid; it < npend * nts; it += blockDim.x) {
-        const int q = it / nts, t = it % nts;
-        compute_anchor(NDET, B.tiles[tf + t], B.basis[tf + t], B.rec[s_pend[q]],
-                       abuf + ((size_t)q * S.max_tiles_slice + t) * kAnchorStride);
-      }
-      __syncthreads();
-    }
-    // work units: (pending chain, piece of the slice) spread over all warps;
-    // per-unit sums in shared memory, then a fixed-order sum per chain
-    for (int g0 = 0; g0 < npend; g0 += S.group) {
-      const int gn = min(S.group, npend - g0);
-      const int units = gn * n_pc;
-      for (int u = warp; u < units; u += 32) {
-        const int q = g0 + u / n_pc, pc = u % n_pc;
-        const int c = s_pend[q];
-        const int lo = P.piece_begin[p0 + pc] - b0, hi = P.piece_begin[p0 + pc + 1] - b0;
-        float* part = s_part + (size_t)u * kPartialStride;
-        if (MIXED) {
-          const float* row = abuf + (size_t)q * S.max_tiles_slice * kAnchorStride;
-          float v[2 * NDET];
-          sweep_warp_mixed<NDET>(L, s_data, nb, s_tile, b0, lo, hi, B.tiles, row, tf, B.rec[c], lane, v);
-#pragma unroll
-          for (int j = 0; j < 2 * NDET; ++j)
-            if (lane == j) part[j] = v[j];
-        } else {
-          double v[2 * NDET];
-          sweep_warp_fp64<NDET>(L, B.data64, B.ftab, b0 + lo, b0 + hi, B.rec[c], lane, v);
-#pragma unroll
-          for (int j = 0; j < 2 * NDET; ++j)
-            if (lane == j) s_part64[(size_t)u * kPartialStride + j] = v[j];
-        }
-        __syncwarp();
-      }
-      __syncthreads();
-      for (int q = warp; q < gn; q += 32) {
-        const int c = s_pend[g0 + q];
-        if (lane < 2 * NDET) {
-          if (MIXED) {
-            float acc = 0.0f;
-            for (int pc = 0; pc < n_pc; ++pc) acc += s_part[(size_t)(q * n_pc + pc) * kPartialStride + lane];
-            B.partials32[((size_t)c * L.n_slices + slice) * kPartialStride + lane] = acc;
-          } else {
-            double acc = 0.0;
-            for (int pc = 0; pc < n_pc; ++pc) acc += s_part64[(size_t)(q * n_pc + pc) * kPartialStride + lane];
-            B.partials64[((size_t)c * L.n_slices + slice) * kPartialStride + lane] = acc;
-          }
-        }
-      }
-      __syncthreads();
-    }
-    __syncthreads();
-    if (timer) {
-      t1 = gtimer();
-      g->t_sweep += t1 - t0;
       t0 = t1;
     }
   }
@@ -1087,6 +1202,8 @@ void release(SamplerState* s) {
   dfree(s->P.chains);
   dfree(s->P.recx);
   dfree(s->P.pending);
+  dfree(s->P.req);
+  dfree(s->P.done_cnt);
   dfree(s->P.chol);
   dfree(s->P.g);
   dfree(s->P.dead_u);
@@ -1113,7 +1230,7 @@ int fail(swig_ctx* c, int code, const std::string& m) {
 
 template <int NDET, bool MIXED>
 void* kernel_ptr() {
-  return (void*)k_ns_persistent<NDET, MIXED>;
+  return (void*)k_ns_flow<NDET, MIXED>;
 }
 
 void* pick_kernel(int n_det, bool mixed) {
@@ -1233,6 +1350,7 @@ int swig_run(swig_ctx* c, swig_result* out) {
   S.m_pow2 = 1;
   while (S.m_pow2 < m) S.m_pow2 *= 2;
   S.max_iters = (int)std::max(1, std::min(64, c->cfg.max_iter));
+  S.flow_parts = 1;  // summation parts per slice, at most 4 (the partial buffers hold 4 per slice and theta)
   // learned proposal: retrain every learn_interval iterations (one launch each)
   const bool learned = c->cfg.proposal == SWIG_PROPOSAL_LEARNED;
   const double learn_mix = c->cfg.learn_mix > 0.0 ? std::min(1.0, c->cfg.learn_mix) : 0.5;
@@ -1250,8 +1368,6 @@ int swig_run(swig_ctx* c, swig_result* out) {
   S.max_pieces = max_pieces;
   size_t fixed = 0;
   if (mixed) fixed = ((size_t)c->B.max_slice_bins * (L.n_det * sizeof(float2) + sizeof(int)) + 15) & ~(size_t)15;
-  const size_t anchor_bytes = 0;
-  const size_t part_budget = 48 * 1024;
   int max_tiles = 1;
   if (mixed) {
     std::vector<int> sb(L.n_slices + 1), bt(L.n_bins);
@@ -1260,11 +1376,10 @@ int swig_run(swig_ctx* c, swig_result* out) {
     for (int s = 0; s < L.n_slices; ++s) max_tiles = std::max(max_tiles, bt[sb[s + 1] - 1] - bt[sb[s]] + 1);
   }
   S.max_tiles_slice = max_tiles;
-  S.group = std::max(1, std::min(k, (int)(part_budget / ((size_t)max_pieces * kPartialStride * sizeof(double)))));
-  const size_t sweep_bytes = anchor_bytes + (size_t)S.group * max_pieces * kPartialStride * sizeof(double);
   const size_t sort_bytes = (size_t)S.m_pow2 * (sizeof(double) + sizeof(int)) + kSweepThreads * sizeof(double) +
                             (size_t)k * sizeof(double) + (kMaxDim + kMaxDim * kMaxDim) * sizeof(float) + 64;
-  const size_t smem = het ? sort_bytes : fixed + std::max(sweep_bytes, sort_bytes);
+  const size_t rec_bytes = (size_t)(kSweepThreads / 32) * sizeof(EvalRecord);
+  const size_t smem = het ? sort_bytes : fixed + std::max(rec_bytes, sort_bytes);
   if (smem > 220 * 1024) return fail(c, SWIG_E_ARG, "problem too large for the persistent kernel's shared memory");
 
   // buffers
@@ -1283,6 +1398,8 @@ int swig_run(swig_ctx* c, swig_result* out) {
     SCUDA(cudaMalloc(&st->P.chains, sizeof(ChainState) * k));
     SCUDA(cudaMalloc(&st->P.recx, sizeof(EvalRecord) * k));
     SCUDA(cudaMalloc(&st->P.pending, sizeof(int) * k));
+    SCUDA(cudaMalloc(&st->P.req, sizeof(int) * k));
+    SCUDA(cudaMalloc(&st->P.done_cnt, sizeof(int) * k));
     SCUDA(cudaMalloc(&st->P.chol, sizeof(float) * kMaxBlocks * kMaxDim * kMaxDim));
     SCUDA(cudaMalloc(&st->P.g, sizeof(NSGlobal)));
     SCUDA(cudaMalloc(&st->P.dead_u, sizeof(double) * (size_t)S.max_iters * k * nd));
@@ -1336,6 +1453,8 @@ int swig_run(swig_ctx* c, swig_result* out) {
   g0.status = ST_RUNNING;
   SCUDA(cudaMemcpyAsync(st->P.g, &g0, sizeof(g0), cudaMemcpyHostToDevice, c->stream));
   SCUDA(cudaMemsetAsync(st->P.pending, 0, sizeof(int) * k, c->stream));
+  SCUDA(cudaMemsetAsync(st->P.req, 0, sizeof(int) * k, c->stream));
+  SCUDA(cudaMemsetAsync(st->P.done_cnt, 0, sizeof(int) * k, c->stream));
   SCUDA(cudaMemsetAsync(st->P.chains, 0, sizeof(ChainState) * k, c->stream));
 
   void* kern = het ? pick_het_kernel(L.n_det) : pick_kernel(L.n_det, mixed);
@@ -1500,6 +1619,9 @@ int swig_run(swig_ctx* c, swig_result* out) {
   c->profile[19] = (double)gh.n_step;
   c->profile[20] = learn_ms;
   c->profile[21] = (double)learn_rounds;
+  c->profile[22] = (double)gh.f_units;
+  c->profile[23] = (double)gh.f_unit_cyc;
+  c->profile[24] = (double)gh.f_idle_cyc;
   cudaEventDestroy(ev0);
   cudaEventDestroy(ev1);
   return SWIG_OK;
@@ -1508,7 +1630,7 @@ int swig_run(swig_ctx* c, swig_result* out) {
 int swig_get_profile(swig_ctx* c, double* out, int n) {
   if (!c) return SWIG_E_ARG;
   if (!out || n < 0) return fail(c, SWIG_E_ARG, "null output");
-  for (int i = 0; i < n && i < 22; ++i) out[i] = c->profile[i];
+  for (int i = 0; i < n && i < 25; ++i) out[i] = c->profile[i];
   return SWIG_OK;
 }
 

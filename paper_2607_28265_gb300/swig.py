@@ -248,7 +248,8 @@ class Context:
     PROFILE_KEYS = ("rounds", "boundary_s", "control_s", "wait_control_s", "sweep_s", "wait_sweep_s",
                     "persistent_ms", "persistent_launches", "kernel_launches", "h2d_bytes", "d2h_bytes",
                     "bin_det_evals", "cyc_result", "cyc_step", "cyc_prop", "cyc_free", "cyc_setup", "n_free",
-                    "n_setup", "n_step", "learn_ms", "learn_rounds")
+                    "n_setup", "n_step", "learn_ms", "learn_rounds", "f_units",
+                    "f_unit_cyc", "f_idle_cyc")
 
     def profile(self):
         out = np.zeros(len(self.PROFILE_KEYS))
