@@ -11,6 +11,8 @@ them) and wall-seconds per posterior (= ms_per_step / 1000).
   cfg2      128 s H1/L1/V1 BNS, 259,585 bins/det, full grid, plain SwiG, mixed
   cfg5      cfg2 with the learned slice proposal (learned + mixed)
   cfg2-het  cfg2 with the heterodyned likelihood, 5,000 bins (Sec. 3.4)
+  cfg2-nss  cfg2 without Gibbs blocks (all sampled parameters in one block)
+  cfg2-m3   cfg2 with M = 3 Gibbs sweeps per replacement (the paper's High-Res)
   cfg1      4 s single detector, 4,017 bins, FP64, nlive 100
   cfg3      cfg1 data, heterodyned likelihood, 450 geometric bins, nlive 1000
 
@@ -39,11 +41,10 @@ import swig_inputs as si  # noqa: E402
 
 SFU_OPS_PER_CLK_SM = 16   # sin/cos results per clock per SM (sm_100-class SFU)
 SFU_OPS_PER_BIN_DET = 2   # one sine and one cosine per bin and detector
-# DRAM bytes (read + write) per logL evaluation inside k_ns_persistent, from one
-# ncu capture of a 2-iteration launch on this workload (14.27 MB / 106,944
-# evaluations; profiles/k_ns_persistent_cfg2_hlv_128s_2iter.md), scaled to a
-# full launch by its evaluations.
-TRAFFIC_B_PER_EVAL = 14.27328e6 / 106944
+# DRAM bytes (read + write) per logL evaluation inside the persistent kernel,
+# from one ncu capture of a 2-iteration launch of the 128 s workload (see
+# profiles/); None until the current kernel has been captured.
+TRAFFIC_B_PER_EVAL = None
 METRIC = "logL evals/s (128 s 3-det BNS) and wall-s/posterior, plain vs learned+mixed"
 
 # workload name -> (event, sampler options, description)
@@ -54,6 +55,10 @@ WORKLOADS = {
                  text="learned slice proposal (MLP 13-256-256-26, BF16/FP32) + covariance, full grid, mixed"),
     "cfg2-het": dict(event="cfg2", precision="mixed", likelihood="het", proposal="cov", het_bins=5000,
                      het_spacing=0, text="plain SwiG, heterodyned likelihood, 5000 bins of equal phase change"),
+    "cfg2-nss": dict(event="cfg2", precision="mixed", likelihood="full", proposal="cov", single_block=True,
+                     text="unblocked nested slice sampling (one block of all sampled parameters), full grid, mixed"),
+    "cfg2-m3": dict(event="cfg2", precision="mixed", likelihood="full", proposal="cov", sweeps=3,
+                    text="plain SwiG, M = 3 Gibbs sweeps per replacement, full grid, mixed"),
     "cfg1": dict(event="cfg1", precision="fp64", likelihood="full", proposal="cov", nlive=100,
                  text="plain SwiG, full grid, FP64"),
     "cfg3": dict(event="cfg1", precision="mixed", likelihood="het", proposal="cov", nlive=1000, het_bins=450,
@@ -63,16 +68,20 @@ WORKLOADS = {
 
 def make_workload(name):
     spec = WORKLOADS[name]
-    if spec["event"] == "cfg2":
-        return si.config2(), spec
-    return si.config1(nlive=spec.get("nlive", 100)), spec
+    wl = si.config2() if spec["event"] == "cfg2" else si.config1(nlive=spec.get("nlive", 100))
+    if spec.get("single_block"):
+        for p in wl.params:
+            if p.mode == si.MODE_SAMPLE:
+                p.block = 0
+    wl.sweeps = spec.get("sweeps", 1)
+    return wl, spec
 
 
 def workload_description(wl, spec):
     dets = "/".join(wl.detectors)
     return (f"{wl.name}: {1.0 / wl.df:g} s, {dets}, {wl.f_min:g}-{wl.f_max:g} Hz, {wl.n_bins} bins/det, "
             f"{len(wl.sampled())} sampled params, nlive={wl.nlive}, nrep={wl.nrep}, "
-            f"{wl.steps_per_dim} slice steps/dim, M=1; {spec['text']}")
+            f"{wl.steps_per_dim} slice steps/dim, M={wl.sweeps}; {spec['text']}")
 
 
 # ---------------------------------------------------------------------------
@@ -227,8 +236,9 @@ def run_gpu(args, rank, world):
     peak = SFU_OPS_PER_CLK_SM * 152 * sm_mhz_max * 1e6 / 1e12  # SFU Top/s at the maximum SM clock
     achieved = SFU_OPS_PER_BIN_DET * bindet / (pers_ms * 1e-3) / 1e12 if pers_ms > 0 else 0.0
     n_bins_eval = spec.get("het_bins", 0) + 1 if het else wl.n_bins
-    kernel = "k_ns_het (persistent SwiG kernel, heterodyned)" if het else "k_ns_persistent (persistent SwiG kernel)"
-    traffic = TRAFFIC_B_PER_EVAL * total_evals / max(1, pers_launch) if args.workload == "cfg2" else None
+    kernel = "k_ns_het (persistent SwiG kernel, heterodyned)" if het else "k_ns_flow (persistent SwiG kernel, dataflow)"
+    traffic = (TRAFFIC_B_PER_EVAL * total_evals / max(1, pers_launch)
+               if TRAFFIC_B_PER_EVAL is not None and args.workload == "cfg2" else None)
     line = {
         "metric": METRIC,
         "value": evals_all / (total_ms_max * 1e-3),

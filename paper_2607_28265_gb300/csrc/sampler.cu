@@ -56,6 +56,7 @@ constexpr int kMaxShrink = 100;
 constexpr int kMaxSort = 8192;
 constexpr int kMaxChains = 2048;
 
+constexpr int kFlowThreads = 768;  // dataflow sampler: 24 warps, up to 80 registers per thread
 constexpr int kHetThreads = 512;  // heterodyned sampler: one chain per CTA, 16 warps
 constexpr int kFreeBudget = 8;  // projection-only evaluations per chain per round
 enum ChainPhase { PH_NEW = 0, PH_LEFT = 1, PH_RIGHT = 2, PH_SHRINK = 3 };
@@ -596,24 +597,31 @@ __device__ __noinline__ void setup_record_warp(const LikeConst& L, const double*
 // Iteration boundary on CTA 0.
 // ---------------------------------------------------------------------------
 __device__ void block_reduce_max_sum(double* vals, int n, double* out_max, double* out_sumexp, double* s_tmp) {
-  // two passes over vals[0..n): max, then sum exp(v - max); s_tmp >= blockDim doubles
+  // two passes over vals[0..n): max, then sum exp(v - max); s_tmp holds at
+  // least the block size rounded up to a power of two (tree over it, the
+  // padding holding the operation's identity)
+  const int nt = blockDim.x, tid = threadIdx.x;
+  int np2 = 1;
+  while (np2 < nt) np2 <<= 1;
   double m = -INFINITY;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) m = fmax(m, vals[i]);
-  s_tmp[threadIdx.x] = m;
+  for (int i = tid; i < n; i += nt) m = fmax(m, vals[i]);
+  s_tmp[tid] = m;
+  if (tid + nt < np2) s_tmp[tid + nt] = -INFINITY;
   __syncthreads();
-  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-    if ((int)threadIdx.x < s) s_tmp[threadIdx.x] = fmax(s_tmp[threadIdx.x], s_tmp[threadIdx.x + s]);
+  for (int s = np2 / 2; s > 0; s >>= 1) {
+    if (tid < s) s_tmp[tid] = fmax(s_tmp[tid], s_tmp[tid + s]);
     __syncthreads();
   }
   m = s_tmp[0];
   __syncthreads();
   double acc = 0.0;
   if (isfinite(m))
-    for (int i = threadIdx.x; i < n; i += blockDim.x) acc += exp(vals[i] - m);
-  s_tmp[threadIdx.x] = acc;
+    for (int i = tid; i < n; i += nt) acc += exp(vals[i] - m);
+  s_tmp[tid] = acc;
+  if (tid + nt < np2) s_tmp[tid + nt] = 0.0;
   __syncthreads();
-  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-    if ((int)threadIdx.x < s) s_tmp[threadIdx.x] += s_tmp[threadIdx.x + s];
+  for (int s = np2 / 2; s > 0; s >>= 1) {
+    if (tid < s) s_tmp[tid] += s_tmp[tid + s];
     __syncthreads();
   }
   *out_max = m;
@@ -643,7 +651,7 @@ __device__ __noinline__ void ns_boundary(const LikeConst& L, const SamplerConst&
   }
   double* key = reinterpret_cast<double*>(smem);
   int* idx = reinterpret_cast<int*>(key + S.m_pow2);
-  double* tmp = reinterpret_cast<double*>(idx + S.m_pow2);  // nt doubles
+  double* tmp = reinterpret_cast<double*>(idx + S.m_pow2);  // (nt rounded up to a power of two) doubles
   for (int i = tid; i < S.m_pow2; i += nt) {
     key[i] = i < m ? P.live_logl[i] : INFINITY;
     idx[i] = i;
@@ -680,7 +688,9 @@ __device__ __noinline__ void ns_boundary(const LikeConst& L, const SamplerConst&
   }
   // deaths: w_j = L_j (X_{j-1} - X_j), log X_j = log X_0 - sum_{i<=j} 1/(m - i)
   const int base = g->n_dead;
-  double* logw = tmp + nt;  // k doubles
+  int np2 = 1;  // the reduction scratch spans the block size rounded up to a power of two
+  while (np2 < nt) np2 <<= 1;
+  double* logw = tmp + np2;  // k doubles
   for (int j = tid; j < k; j += nt) {
     const int s = idx[j];
     const double lwj = key[j] + (g->logx - P.harm[j]) + P.lw[m - j];
@@ -872,7 +882,7 @@ __device__ bool flow_control(const LikeConst& L, const SamplerConst& S, const De
 }
 
 template <int NDET, bool MIXED>
-__global__ void __launch_bounds__(kSweepThreads, 1)
+__global__ void __launch_bounds__(kFlowThreads, 1)
     k_ns_flow(LikeConst L, SamplerConst S, DeviceBuffers B, SamplerPtrs P) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int s_claim[kMaxChains];
@@ -1378,7 +1388,7 @@ int swig_run(swig_ctx* c, swig_result* out) {
   S.max_tiles_slice = max_tiles;
   const size_t sort_bytes = (size_t)S.m_pow2 * (sizeof(double) + sizeof(int)) + kSweepThreads * sizeof(double) +
                             (size_t)k * sizeof(double) + (kMaxDim + kMaxDim * kMaxDim) * sizeof(float) + 64;
-  const size_t rec_bytes = (size_t)(kSweepThreads / 32) * sizeof(EvalRecord);
+  const size_t rec_bytes = (size_t)(kFlowThreads / 32) * sizeof(EvalRecord);
   const size_t smem = het ? sort_bytes : fixed + std::max(rec_bytes, sort_bytes);
   if (smem > 220 * 1024) return fail(c, SWIG_E_ARG, "problem too large for the persistent kernel's shared memory");
 
@@ -1458,7 +1468,7 @@ int swig_run(swig_ctx* c, swig_result* out) {
   SCUDA(cudaMemsetAsync(st->P.chains, 0, sizeof(ChainState) * k, c->stream));
 
   void* kern = het ? pick_het_kernel(L.n_det) : pick_kernel(L.n_det, mixed);
-  const int threads = het ? kHetThreads : kSweepThreads;
+  const int threads = het ? kHetThreads : kFlowThreads;
   SCUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;
   SCUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem));
