@@ -56,7 +56,7 @@ constexpr int kMaxShrink = 100;
 constexpr int kMaxSort = 8192;
 constexpr int kMaxChains = 2048;
 
-constexpr int kFlowThreads = 768;  // dataflow sampler: 24 warps, up to 80 registers per thread
+constexpr int kFlowThreads = 512;  // dataflow sampler: 16 warps, up to 128 registers per thread
 constexpr int kHetThreads = 512;  // heterodyned sampler: one chain per CTA, 16 warps
 constexpr int kFreeBudget = 8;  // projection-only evaluations per chain per round
 enum ChainPhase { PH_NEW = 0, PH_LEFT = 1, PH_RIGHT = 2, PH_SHRINK = 3 };
