@@ -1,5 +1,6 @@
-"""Matched-filter log-likelihood in FP64 (Sec. 3.1, Eq. 2) and its heterodyned
-approximation (Sec. 3.4).
+"""Matched-filter log-likelihood in FP64 (Sec. 3.1, Eq. 2), its phase- and
+distance-marginalised forms (Sec. 3.1) and its heterodyned approximation
+(Sec. 3.4).
 
 Event layout: an ``Event`` holds the frequency grid, per-detector data d_i(f),
 PSDs S_i(f), detector geometry, GMST and the prior description.
@@ -12,7 +13,9 @@ from dataclasses import dataclass
 import numpy as np
 from scipy.special import i0e
 
-from swig_inputs import IDX, MODE_MARG, MODE_SAMPLE
+from scipy import integrate
+
+from swig_inputs import IDX, MODE_MARG, MODE_SAMPLE, PRIOR_POWER2, PRIOR_UNIFORM
 from . import physics
 
 
@@ -29,6 +32,10 @@ class Event:
     @property
     def phase_marginalised(self) -> bool:
         return self.params[IDX["phic"]].mode == MODE_MARG
+
+    @property
+    def distance_marginalised(self) -> bool:
+        return self.params[IDX["dl"]].mode == MODE_MARG
 
 
 def inner_product(a, b, psd, df):
@@ -55,6 +62,8 @@ def loglike(ev: Event, theta):
     normalisation -1/2 sum log(2 pi S) is a constant and is omitted.
     """
     theta = np.asarray(theta, dtype=np.float64)
+    if ev.distance_marginalised:
+        return loglike_distance_marg(ev, theta)
     if ev.phase_marginalised:
         th = theta.copy()
         th[IDX["phic"]] = 0.0
@@ -87,6 +96,100 @@ def loglike_phase_grid(ev: Event, theta, n_phase=4096):
     vals = np.array(vals)
     m = vals.max()
     return m + math.log(np.mean(np.exp(vals - m)))
+
+
+# --------------------------------------------------------------------------
+# Distance marginalisation (Sec. 3.1; the paper's default injection setting)
+# --------------------------------------------------------------------------
+def distance_prior_pdf(d, p):
+    """Normalised density of the d_L prior family on [lo, hi]."""
+    d = np.asarray(d, dtype=np.float64)
+    inside = (d >= p.lo) & (d <= p.hi)
+    if p.kind == PRIOR_POWER2:
+        val = 3.0 * d * d / (p.hi ** 3 - p.lo ** 3)
+    elif p.kind == PRIOR_UNIFORM:
+        val = np.full_like(d, 1.0 / (p.hi - p.lo))
+    else:
+        raise ValueError("distance prior must be uniform or power-law 2")
+    return np.where(inside, val, 0.0)
+
+
+def overlaps_at(ev: Event, theta):
+    """(Z, H, DD) of template theta: Z = sum_i 4 df sum d_i* h_i / S_i (at
+    phi_c = 0 when it is marginalised), H = sum_i <h_i|h_i>, DD = sum_i <d_i|d_i>."""
+    th = np.asarray(theta, dtype=np.float64).copy()
+    if ev.phase_marginalised:
+        th[IDX["phic"]] = 0.0
+    hs = strains(ev, th)
+    z = sum(complex_overlap(d, h, s, ev.df) for d, h, s in zip(ev.data, hs, ev.psds))
+    hh = sum(inner_product(h, h, s, ev.df) for h, s in zip(hs, ev.psds))
+    dd = sum(inner_product(d, d, s, ev.df) for d, s in zip(ev.data, ev.psds))
+    return z, hh, dd
+
+
+def loglike_at_distance(z1, h1, dd, d, phase_marg):
+    """logL at distance d from the overlaps z1, h1 of the same template at
+    d_L = 1 Mpc: the amplitude scales as 1/d_L, so Z(d) = z1 / d and
+    <h|h>(d) = h1 / d^2 (Eq. 2 expanded; log I0 form with phi_c marginalised)."""
+    d = np.asarray(d, dtype=np.float64)
+    if phase_marg:
+        x = np.abs(z1) / d
+        core = x + np.log(i0e(x))
+    else:
+        core = np.real(z1) / d
+    return core - 0.5 * h1 / (d * d) - 0.5 * dd
+
+
+def log_distance_integral(z1, h1, dd, p, phase_marg):
+    """log int pi(d) L(d) dd over the prior [lo, hi] of slot p, by adaptive
+    quadrature around the integrand's peak (located on a dense grid)."""
+    grid = np.linspace(p.lo, p.hi, 20001)
+    lg = loglike_at_distance(z1, h1, dd, grid, phase_marg) + np.log(distance_prior_pdf(grid, p))
+    m = float(np.max(lg))
+    d_peak = float(grid[int(np.argmax(lg))])
+
+    def f(d):
+        return float(distance_prior_pdf(d, p) * np.exp(loglike_at_distance(z1, h1, dd, d, phase_marg) - m))
+
+    val, _ = integrate.quad(f, p.lo, p.hi, points=[d_peak], limit=500, epsabs=0.0, epsrel=1e-12)
+    return m + math.log(val)
+
+
+def loglike_distance_marg(ev: Event, theta):
+    """log of int pi(d_L) L(theta, d_L) d d_L over the d_L prior: the
+    likelihood marginalised over distance (the definition, written out)."""
+    th = np.asarray(theta, dtype=np.float64).copy()
+    th[IDX["dl"]] = 1.0
+    z1, h1, dd = overlaps_at(ev, th)
+    return log_distance_integral(z1, h1, dd, ev.params[IDX["dl"]], ev.phase_marginalised)
+
+
+def distance_cdf(z1, h1, dd, p, phase_marg, d):
+    """P(d_L <= d | theta, data) under the prior p (the conditional the
+    post-hoc reconstruction draws from)."""
+    lz = log_distance_integral(z1, h1, dd, p, phase_marg)
+
+    def f(x):
+        return float(distance_prior_pdf(x, p) * np.exp(loglike_at_distance(z1, h1, dd, x, phase_marg) - lz))
+
+    if d <= p.lo:
+        return 0.0
+    val, _ = integrate.quad(f, p.lo, min(d, p.hi), limit=500, epsabs=1e-14, epsrel=1e-12)
+    return min(1.0, val)
+
+
+def distance_quantile(z1, h1, dd, p, phase_marg, u):
+    """The u-quantile of p(d_L | theta, data) (root of the conditional CDF)."""
+    from scipy.optimize import brentq
+    return brentq(lambda d: distance_cdf(z1, h1, dd, p, phase_marg, d) - u, p.lo, p.hi, xtol=1e-10, rtol=1e-12)
+
+
+def draw_distance(ev: Event, theta, u):
+    """Post-hoc d_L of a sample: the u-quantile of p(d_L | theta, data)."""
+    th = np.asarray(theta, dtype=np.float64).copy()
+    th[IDX["dl"]] = 1.0
+    z1, h1, dd = overlaps_at(ev, th)
+    return distance_quantile(z1, h1, dd, ev.params[IDX["dl"]], ev.phase_marginalised, u)
 
 
 def optimal_snr_sq(ev: Event, theta):
