@@ -226,6 +226,29 @@ void free_problem(DeviceBuffers& B) {
   B.het_nb = 0;
 }
 
+// Gauss-Legendre nodes and weights on [-1, 1] (Newton iteration on the
+// three-term recurrence of the Legendre polynomials, Golub-Welsch-free).
+void gauss_legendre(int n, double* x, double* w) {
+  for (int i = 0; i < (n + 1) / 2; ++i) {
+    double z = std::cos(kPi * (i + 0.75) / (n + 0.5)), pp = 0.0;
+    for (int it = 0; it < 100; ++it) {
+      double p1 = 1.0, p2 = 0.0;
+      for (int j = 1; j <= n; ++j) {
+        const double p3 = p2;
+        p2 = p1;
+        p1 = ((2.0 * j - 1.0) * z * p2 - (j - 1.0) * p3) / j;
+      }
+      pp = n * (z * p1 - p2) / (z * z - 1.0);
+      const double dz = p1 / pp;
+      z -= dz;
+      if (std::fabs(dz) < 1e-16) break;
+    }
+    x[i] = -z;
+    x[n - 1 - i] = z;
+    w[i] = w[n - 1 - i] = 2.0 / ((1.0 - z * z) * pp * pp);
+  }
+}
+
 // Bin edges (grid indices) of the heterodyned likelihood.  spacing 0: equal
 // increments of the maximum dephasing g(f) = sum_gamma sign(gamma) (f/f*)^gamma,
 // gamma in {-5/3, -2/3, 1, 5/3, 7/3}, f* = f_lo for gamma < 0 and f_hi
@@ -409,6 +432,15 @@ int prepare(swig_ctx* c) {
   L.df = c->df;
   L.gmst = c->gmst;
   L.phase_marg = c->prior_set && c->params[12].mode == SWIG_MODE_MARG;
+  L.dist_marg = c->prior_set && c->params[6].mode == SWIG_MODE_MARG;
+  if (L.dist_marg) {
+    L.d_kind = c->params[6].kind;
+    L.d_lo = c->params[6].lo;
+    L.d_hi = c->params[6].hi;
+    gauss_legendre(kGaussLegendre, L.gl_x, L.gl_w);
+  }
+  if (L.dist_marg && c->cfg_set && c->cfg.likelihood == SWIG_LIKE_HET)
+    return fail(c, SWIG_E_ARG, "distance marginalisation is implemented for the full-grid likelihood only");
   const int prec = current_precision(c);
 
   // D_i(k) = 4 df conj(d_i) f^-7/6 / S_i,  K_i = 4 df sum f^-7/3 / S_i,  <d|d>
@@ -733,7 +765,12 @@ int swig_set_prior(swig_ctx* c, const swig_param* params, int n_params) {
   for (int i = 0; i < SWIG_N_PARAMS; ++i) {
     const swig_param& p = params[i];
     if (p.mode < 0 || p.mode > 2 || p.kind < 0 || p.kind > 3) return fail(c, SWIG_E_ARG, "bad prior kind or mode in slot " + std::to_string(i));
-    if (p.mode == SWIG_MODE_MARG && i != 12) return fail(c, SWIG_E_ARG, "only phi_c (slot 12) can be marginalised");
+    if (p.mode == SWIG_MODE_MARG && i != 12 && i != 6)
+      return fail(c, SWIG_E_ARG, "only d_L (slot 6) and phi_c (slot 12) can be marginalised");
+    if (p.mode == SWIG_MODE_MARG && i == 6 &&
+        (!(p.lo > 0.0) || !(p.hi > p.lo) || !std::isfinite(p.hi) ||
+         (p.kind != SWIG_PRIOR_UNIFORM && p.kind != SWIG_PRIOR_POWER2)))
+      return fail(c, SWIG_E_ARG, "a marginalised d_L needs a uniform or power-law-2 prior on 0 < lo < hi");
     if (p.mode == SWIG_MODE_SAMPLE) {
       if (!std::isfinite(p.lo) || !std::isfinite(p.hi) || !(p.hi > p.lo)) return fail(c, SWIG_E_ARG, "sampled slot " + std::to_string(i) + " needs lo < hi");
       if (p.block < 0 || p.block >= 16) return fail(c, SWIG_E_ARG, "block id must be in [0, 16)");
@@ -743,6 +780,9 @@ int swig_set_prior(swig_ctx* c, const swig_param* params, int n_params) {
   }
   if (n_sampled == 0) return fail(c, SWIG_E_ARG, "at least one parameter must be sampled");
   std::memcpy(c->params, params, sizeof(swig_param) * SWIG_N_PARAMS);
+  // a marginalised slot is evaluated at a fixed value: phi_c = 0, d_L = 1 Mpc
+  if (c->params[12].mode == SWIG_MODE_MARG) c->params[12].value = 0.0;
+  if (c->params[6].mode == SWIG_MODE_MARG) c->params[6].value = 1.0;
   c->prior_set = true;
   c->n_sampled = n_sampled;
   c->dirty = true;

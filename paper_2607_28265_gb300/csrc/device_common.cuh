@@ -453,6 +453,83 @@ __device__ inline void setup_record(const LikeConst& L, const double* th, EvalRe
   setup_combine(L, rec);
 }
 
+// ---------------------------------------------------------------------------
+// Distance marginalisation (Sec. 3.1).  With d_L marginalised the record is
+// set up at d_L = 1 Mpc, where the template gives Z1 = sum_i C_i kappa_i and
+// H1 = sum_i |C_i|^2 K_i; at distance d they scale as Z1/d and H1/d^2, so
+//   log L_marg = log int pi(d) exp(Re Z1 / d - H1 / (2 d^2)) dd - <d|d>/2
+// (log I0(|Z1| / d) in place of Re Z1 / d with phi_c marginalised).  The
+// integral is taken over u = 1/d by 64-node Gauss-Legendre on a window of
+// +-12 standard deviations (1 / sqrt(H1)) around the peak u* = max(X, 0) / H1
+// (X = Re Z1 or |Z1|), cut to the prior, or 12 standard deviations from the
+// nearer prior edge when the peak lies outside; the exponent is FP64, the
+// slowly varying log-prior, Jacobian and log(i0e) terms FP32.
+// ---------------------------------------------------------------------------
+__host__ __device__ inline float log_i0e_f32(float x) {  // log(I0(x) e^-x), x >= 0
+  if (x < 20.0f) {
+    const float y = 0.25f * x * x;
+    float term = 1.0f, sum = 1.0f;
+    for (int k = 1; k < 64; ++k) {
+      term *= y / (float)(k * k);
+      sum += term;
+      if (term < 1e-8f * sum) break;
+    }
+    return logf(sum) - x;
+  }
+  const float t = 1.0f / (8.0f * x);
+  const float s = 1.0f + t * (1.0f + t * (4.5f + t * (37.5f + t * 459.375f)));
+  return -0.5f * logf(6.283185307179586f * x) + logf(s);
+}
+
+// log of pi(1/u) / u^2 (prior density in d times the Jacobian |dd/du|).
+__host__ __device__ inline float distance_log_density_u(const LikeConst& L, float u) {
+  const float lu = logf(u);
+  if (L.d_kind == SWIG_PRIOR_POWER2)  // pi(d) = 3 d^2 / (hi^3 - lo^3)
+    return logf(3.0f / (float)(L.d_hi * L.d_hi * L.d_hi - L.d_lo * L.d_lo * L.d_lo)) - 4.0f * lu;
+  return -logf((float)(L.d_hi - L.d_lo)) - 2.0f * lu;  // uniform
+}
+
+// Integration window in u = 1/d.
+__host__ __device__ inline void distance_window(const LikeConst& L, double X, double H, double* lo, double* hi) {
+  const double ua = 1.0 / L.d_hi, ub = 1.0 / L.d_lo;
+  double a = ua, b = ub;
+  if (H > 0.0) {  // (no template power: the integrand is the prior, take the whole range)
+    const double us = fmax(X, 0.0) / H, su = 12.0 / sqrt(H);
+    a = fmax(ua, us - su);
+    b = fmin(ub, us + su);
+    if (a >= b) {  // peak outside the prior: the window at the nearer edge
+      if (us < ua) {
+        a = ua;
+        b = fmin(ub, ua + su);
+      } else {
+        a = fmax(ua, ub - su);
+        b = ub;
+      }
+    }
+  }
+  *lo = a;
+  *hi = b;
+}
+
+// Exponent of the integrand in u (FP64 part, without -<d|d>/2).
+__host__ __device__ inline double distance_exponent(const LikeConst& L, double zre, double X, double H, double u) {
+  const double core = L.phase_marg ? X * u + (double)log_i0e_f32((float)(X * u)) : zre * u;
+  return core - 0.5 * H * u * u + (double)distance_log_density_u(L, (float)u);
+}
+
+__host__ __device__ inline double distance_marg_logl(const LikeConst& L, double zre, double zim, double H) {
+  const double X = L.phase_marg ? sqrt(zre * zre + zim * zim) : zre;
+  double a, b;
+  distance_window(L, X, H, &a, &b);
+  const double mid = 0.5 * (a + b), half = 0.5 * (b - a);
+  double M = -INFINITY;
+  for (int k = 0; k < kGaussLegendre; ++k) M = fmax(M, distance_exponent(L, zre, X, H, mid + half * L.gl_x[k]));
+  double sum = 0.0;
+  for (int k = 0; k < kGaussLegendre; ++k)
+    sum += L.gl_w[k] * (double)expf((float)(distance_exponent(L, zre, X, H, mid + half * L.gl_x[k]) - M));
+  return M + log(half * sum) - 0.5 * L.DD;
+}
+
 // logL from the per-detector sums kappa_i = sum_k D_i(k) exp(-2 pi i phi_i(k))
 // (data scaled by 1/inv_scale_i): Eq. 2 expanded as
 // sum_i Re(C_i kappa_i) - 1/2 sum_i |C_i|^2 K_i - 1/2 sum_i <d_i|d_i>, or with
@@ -466,6 +543,7 @@ __device__ inline double loglike_epilogue(const LikeConst& L, const EvalRecord& 
     zr += rec.cre[i] * a - rec.cim[i] * b;
     zi += rec.cre[i] * b + rec.cim[i] * a;
   }
+  if (L.dist_marg) return distance_marg_logl(L, zr, zi, rec.hh);
   const double base = -0.5 * rec.hh - 0.5 * L.DD;
   if (L.phase_marg) return log_bessel_i0(sqrt(zr * zr + zi * zi)) + base;
   return zr + base;
@@ -518,7 +596,7 @@ __host__ __device__ inline void prior_map(const PriorSlot* slots, const double* 
     if (s.mode == SWIG_MODE_FIXED) {
       th[i] = s.value;
     } else if (s.mode == SWIG_MODE_MARG) {
-      th[i] = 0.0;
+      th[i] = s.value;  // phi_c: 0; d_L: the 1 Mpc reference distance
     } else {
       th[i] = prior_slot_inverse(s, u[j++]);
     }

@@ -60,6 +60,10 @@ cudaError_t launch_loglike_fp64(const LikeConst& L, const DeviceBuffers& B, cons
 // Setup record and detector strain of one theta (FP64) into out [n_det][n_bins].
 cudaError_t launch_waveform(const LikeConst& L, const double* theta_dev, EvalRecord* rec_dev, double2* out,
                             cudaStream_t st);
+// Post-hoc d_L of n samples of a distance-marginalised run (records in B.rec
+// and their kappa sums from the preceding likelihood launch); writes theta[6].
+cudaError_t launch_distance_draw(const LikeConst& L, const DeviceBuffers& B, const double* kappa, int n,
+                                 long long first, unsigned k0, unsigned k1, double* theta, cudaStream_t st);
 // Heterodyned logL of n thetas (device pointers), one warp per theta.
 cudaError_t launch_loglike_het(const LikeConst& L, const DeviceBuffers& B, const double* theta, int n, double* out,
                                cudaStream_t st);

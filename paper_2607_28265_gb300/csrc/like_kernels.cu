@@ -28,7 +28,11 @@ namespace swig {
 
 __global__ void k_setup(LikeConst L, const double* __restrict__ theta, int n, EvalRecord* __restrict__ rec) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) setup_record(L, theta + (size_t)SWIG_N_PARAMS * i, rec + i);
+  if (i >= n) return;
+  double th[SWIG_N_PARAMS];
+  for (int j = 0; j < SWIG_N_PARAMS; ++j) th[j] = theta[(size_t)SWIG_N_PARAMS * i + j];
+  if (L.dist_marg) th[6] = 1.0;  // the marginal is built from the template at 1 Mpc
+  setup_record(L, th, rec + i);
 }
 
 // Per (theta, tile) anchors, one thread each (double-float on the FP32 pipe).
@@ -130,6 +134,72 @@ __global__ void k_reduce(LikeConst L, const T* __restrict__ partials, int n_unit
     if (kappa_out)
       for (int j = 0; j < 2 * SWIG_MAX_DET; ++j) kappa_out[(size_t)th * 2 * SWIG_MAX_DET + j] = acc[j];
   }
+}
+
+// ---------------------------------------------------------------------------
+// Post-hoc distance of each sample of a distance-marginalised run: the
+// q-quantile of p(d_L | theta, data) ~ pi(d) L(d), q from Philox-4x32-10 at
+// counter (index lo, index hi, 0x64697374, 5) as a 53-bit uniform.  The
+// conditional is tabulated on 1024 trapezoid cells in u = 1/d over the
+// marginal's window; the quantile is read off the cumulative from the large-u
+// (small-d) end and interpolated linearly inside its cell.
+// ---------------------------------------------------------------------------
+__global__ void k_distance_draw(LikeConst L, const EvalRecord* __restrict__ rec, const double* __restrict__ kappa,
+                                int n, long long first, unsigned k0, unsigned k1, double* __restrict__ theta) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const EvalRecord& r = rec[i];
+  double* th = theta + (size_t)SWIG_N_PARAMS * i;
+  if (!r.valid) {
+    th[6] = NAN;
+    return;
+  }
+  double zr = 0.0, zi = 0.0;
+  for (int d = 0; d < L.n_det; ++d) {
+    const double a = kappa[(size_t)i * 2 * SWIG_MAX_DET + 2 * d] * L.inv_scale[d];
+    const double b = kappa[(size_t)i * 2 * SWIG_MAX_DET + 2 * d + 1] * L.inv_scale[d];
+    zr += r.cre[d] * a - r.cim[d] * b;
+    zi += r.cre[d] * b + r.cim[d] * a;
+  }
+  const double H = r.hh;
+  const double X = L.phase_marg ? sqrt(zr * zr + zi * zi) : zr;
+  double ua, ub;
+  distance_window(L, X, H, &ua, &ub);
+  constexpr int kCells = 1024;
+  const double h = (ub - ua) / kCells;
+  double M = -INFINITY;
+  for (int j = 0; j <= kCells; ++j) M = fmax(M, distance_exponent(L, zr, X, H, ua + h * j));
+  double total = 0.0, fprev = exp(distance_exponent(L, zr, X, H, ua) - M);
+  for (int j = 1; j <= kCells; ++j) {
+    const double f = exp(distance_exponent(L, zr, X, H, ua + h * j) - M);
+    total += 0.5 * (f + fprev);
+    fprev = f;
+  }
+  const long long gi = first + i;
+  const uint4 w = philox4x32_10(make_uint4((unsigned)(gi & 0xFFFFFFFFll), (unsigned)(gi >> 32), 0x64697374u, 5u), k0, k1);
+  const double q = ((double)(w.x >> 5) * 67108864.0 + (double)(w.y >> 6)) * (1.0 / 9007199254740992.0);
+  const double target = q * total;
+  double acc = 0.0, uq = ua;
+  fprev = exp(distance_exponent(L, zr, X, H, ub) - M);
+  for (int j = kCells - 1; j >= 0; --j) {
+    const double f = exp(distance_exponent(L, zr, X, H, ua + h * j) - M);
+    const double seg = 0.5 * (f + fprev);
+    if (acc + seg >= target || j == 0) {
+      const double frac = seg > 0.0 ? fmin(1.0, fmax(0.0, (target - acc) / seg)) : 0.5;
+      uq = ua + h * (j + 1) - frac * h;
+      break;
+    }
+    acc += seg;
+    fprev = f;
+  }
+  th[6] = 1.0 / uq;
+}
+
+cudaError_t launch_distance_draw(const LikeConst& L, const DeviceBuffers& B, const double* kappa, int n,
+                                 long long first, unsigned k0, unsigned k1, double* theta, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  k_distance_draw<<<(n + 127) / 128, 128, 0, st>>>(L, B.rec, kappa, n, first, k0, k1, theta);
+  return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------

@@ -275,6 +275,8 @@ __device__ inline double free_loglike_mixed(const LikeConst& L, const double* th
     zi += cre * b + cim * a;
     hh += (cre * cre + cim * cim) * L.amp_k[i];
   }
+  // with d_L marginalised the template is at 1 Mpc: zr, zi, hh are Z1, H1
+  if (L.dist_marg) return distance_marg_logl(L, (double)zr, (double)zi, (double)hh);
   const float core = (L.phase_marg ? log_i0_f32(sqrtf(zr * zr + zi * zi)) : zr) - 0.5f * hh;
   return (double)core - 0.5 * L.DD;
 }
@@ -1577,6 +1579,34 @@ int swig_run(swig_ctx* c, swig_result* out) {
     SCUDA(cudaMemcpy(du_d, du.data(), sizeof(double) * du.size(), cudaMemcpyHostToDevice));
     k_dead_theta<<<(unsigned)((n_dead + 127) / 128), 128, 0, c->stream>>>(S, du_d, (int)n_dead, th_d);
     ++c->n_launches;
+    if (L.dist_marg) {
+      // post-hoc distances: the kappa sums of every sample, then a draw from
+      // its conditional distance posterior
+      const int chunk = 4096;
+      double *kap_d = nullptr, *ll_d = nullptr;
+      cudaError_t e = cudaMalloc(&kap_d, sizeof(double) * 2 * SWIG_MAX_DET * chunk);
+      if (e == cudaSuccess) e = cudaMalloc(&ll_d, sizeof(double) * chunk);
+      for (size_t off = 0; e == cudaSuccess && off < n_dead; off += chunk) {
+        const int mm = (int)std::min<size_t>(chunk, n_dead - off);
+        if (ensure_scratch(c, mm)) {
+          e = cudaErrorMemoryAllocation;
+          break;
+        }
+        e = mixed ? launch_loglike_mixed(L, c->B, th_d + off * SWIG_N_PARAMS, mm, ll_d, c->stream, kap_d)
+                  : launch_loglike_fp64(L, c->B, th_d + off * SWIG_N_PARAMS, mm, ll_d, c->stream, kap_d);
+        if (e == cudaSuccess)
+          e = launch_distance_draw(L, c->B, kap_d, mm, (long long)off, S.key0, S.key1, th_d + off * SWIG_N_PARAMS,
+                                   c->stream);
+        c->n_launches += mixed ? 5 : 4;
+      }
+      if (kap_d) cudaFree(kap_d);
+      if (ll_d) cudaFree(ll_d);
+      if (e != cudaSuccess) {
+        cudaFree(du_d);
+        cudaFree(th_d);
+        SCUDA(e);
+      }
+    }
     c->h2d_bytes += sizeof(double) * du.size();
     c->d2h_bytes += sizeof(double) * c->out_theta.size();
     cudaError_t e = cudaStreamSynchronize(c->stream);

@@ -69,6 +69,8 @@ struct EvalRecord {
   int pad;
 };
 
+constexpr int kGaussLegendre = 64;  // nodes of the distance integral
+
 struct LikeConst {
   int n_det;
   int n_bins;
@@ -88,6 +90,12 @@ struct LikeConst {
   float amp_k[SWIG_MAX_DET];
   double dten[SWIG_MAX_DET][6];  // detector tensor xx xy xz yy yz zz
   double vertex[SWIG_MAX_DET][3];
+  // distance marginalisation (d_L slot marginalised): prior family and range,
+  // Gauss-Legendre nodes and weights on [-1, 1]
+  int dist_marg;
+  int d_kind;
+  double d_lo, d_hi;
+  double gl_x[kGaussLegendre], gl_w[kGaussLegendre];
 };
 
 }  // namespace swig
