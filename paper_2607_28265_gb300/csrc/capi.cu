@@ -442,6 +442,7 @@ int prepare(swig_ctx* c) {
   if (L.dist_marg && c->cfg_set && c->cfg.likelihood == SWIG_LIKE_HET)
     return fail(c, SWIG_E_ARG, "distance marginalisation is implemented for the full-grid likelihood only");
   const int prec = current_precision(c);
+  L.fast_epilogue = prec == SWIG_PREC_MIXED ? 1 : 0;
 
   // D_i(k) = 4 df conj(d_i) f^-7/6 / S_i,  K_i = 4 df sum f^-7/3 / S_i,  <d|d>
   std::vector<double> dre((size_t)n_det * n), dim((size_t)n_det * n);
@@ -484,7 +485,8 @@ int prepare(swig_ctx* c) {
   // slices: contiguous whole 32-bin chunks, one CTA each.  The mixed path's
   // tile plan comes first so that slices can balance the estimated cost:
   // a chunk whose tiles are no longer than 32 bins reloads anchors for every
-  // bin and costs about twice a chunk inside a long tile.
+  // bin and costs about twice a chunk inside a long tile, and every tile's
+  // anchor (~480 FP32 operations, one lane) costs about a quarter of a chunk.
   std::vector<TileInfo> tiles;
   std::vector<TileBasis> basis;
   if (prec == SWIG_PREC_MIXED) plan_tiles(c, tiles, basis);
@@ -493,6 +495,8 @@ int prepare(swig_ctx* c) {
   if (prec == SWIG_PREC_MIXED)
     for (const TileInfo& ti : tiles)
       if (ti.nbins <= kChunk) chunk_cost[ti.k0 / kChunk] = 2.0;
+  if (prec == SWIG_PREC_MIXED)
+    for (const TileInfo& ti : tiles) chunk_cost[ti.k0 / kChunk] += 0.25;
   double total_cost = 0.0;
   for (double v : chunk_cost) total_cost += v;
   int n_slices = std::min(c->sm_count, std::max(1, n_chunks / 4));

@@ -545,7 +545,12 @@ __device__ inline double loglike_epilogue(const LikeConst& L, const EvalRecord& 
   }
   if (L.dist_marg) return distance_marg_logl(L, zr, zi, rec.hh);
   const double base = -0.5 * rec.hh - 0.5 * L.DD;
-  if (L.phase_marg) return log_bessel_i0(sqrt(zr * zr + zi * zi)) + base;
+  if (L.phase_marg) {
+    const double x = sqrt(zr * zr + zi * zi);
+    // log I0(x) = x + log(i0e(x)); the second term is O(log x) and needs only
+    // FP32 in the mixed-precision path (absolute error ~1e-6)
+    return (L.fast_epilogue ? x + (double)log_i0e_f32((float)x) : log_bessel_i0(x)) + base;
+  }
   return zr + base;
 }
 

@@ -126,7 +126,10 @@ __device__ inline void het_warp_reduce(float* zr, float* zi, float* hh) {
 // <h|h>/2 and <d|d>/2.
 __device__ inline double het_epilogue(const LikeConst& L, double Z_re, double Z_im, double HH) {
   const double base_ll = -0.5 * HH - 0.5 * L.DD;
-  if (L.phase_marg) return log_bessel_i0(sqrt(Z_re * Z_re + Z_im * Z_im)) + base_ll;
+  if (L.phase_marg) {
+    const double x = sqrt(Z_re * Z_re + Z_im * Z_im);
+    return (L.fast_epilogue ? x + (double)log_i0e_f32((float)x) : log_bessel_i0(x)) + base_ll;
+  }
   return Z_re + base_ll;
 }
 

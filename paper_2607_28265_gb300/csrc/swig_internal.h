@@ -78,6 +78,7 @@ struct LikeConst {
   int n_tiles;
   int n_slices;
   int phase_marg;
+  int fast_epilogue;  // mixed precision: log(i0e) of the phase marginal in FP32
   double df;
   double gmst;
   double K[SWIG_MAX_DET];        // 4 df sum f^-7/3 / S
