@@ -479,6 +479,7 @@ int prepare(swig_ctx* c) {
     for (int i = 0; i < n_det; ++i) {
       L.amp_s[i] = (float)(L.inv_scale[i] * a1);
       L.amp_k[i] = (float)(L.K[i] * a1 * a1);
+      L.amp1 = a1;
     }
   }
 

@@ -135,10 +135,34 @@ __device__ inline double het_epilogue(const LikeConst& L, double Z_re, double Z_
 
 __host__ __device__ inline int het_chunks(int n_bins) { return (n_bins + 30) / 31; }
 
-// One warp evaluates the heterodyned logL of record r (all lanes return it).
+// Per-detector sums cached for projection-only evaluations: (Z_i / C_i) /
+// inv_scale_i as the chain's kappa, and <h|h>_i / |C_i|^2 times A1^2 (the
+// heterodyned Z_i is linear and <h|h>_i quadratic in C_i).
+__device__ inline void het_cache(const LikeConst& L, const EvalRecord& r, int i, double zr, double zi, double hh,
+                                 double* kap2, double* vv) {
+  const double cr = r.cre[i], ci = r.cim[i], c2 = cr * cr + ci * ci;
+  if (c2 > 0.0) {
+    kap2[0] = (zr * cr + zi * ci) / c2 / L.inv_scale[i];
+    kap2[1] = (zi * cr - zr * ci) / c2 / L.inv_scale[i];
+    *vv = hh / c2 * L.amp1 * L.amp1;
+  } else {
+    kap2[0] = kap2[1] = 0.0;
+    *vv = 0.0;
+  }
+}
+
+// One warp evaluates the heterodyned logL of record r (all lanes return it);
+// optionally the per-detector cache of het_cache (lane 0 writes it).
 template <int NDET>
-__device__ inline double het_loglike_warp(const LikeConst& L, const HetTables& H, const EvalRecord& r, int lane) {
-  if (!r.valid) return -INFINITY;
+__device__ inline double het_loglike_warp(const LikeConst& L, const HetTables& H, const EvalRecord& r, int lane,
+                                          double* kap_out = nullptr, double* vv_out = nullptr) {
+  if (!r.valid) {
+    if (lane == 0 && kap_out)
+      for (int j = 0; j < 2 * SWIG_MAX_DET; ++j) kap_out[j] = 0.0;
+    if (lane == 0 && vv_out)
+      for (int i = 0; i < SWIG_MAX_DET; ++i) vv_out[i] = 0.0;
+    return -INFINITY;
+  }
   HetPrep<NDET> p;
   het_prepare<NDET>(H, r, p);
   float zr[NDET], zi[NDET], hh[NDET];
@@ -153,6 +177,14 @@ __device__ inline double het_loglike_warp(const LikeConst& L, const HetTables& H
     Z_re += (double)zr[i];
     Z_im += (double)zi[i];
     HH += (double)hh[i];
+  }
+  if (lane == 0 && kap_out && vv_out) {
+    for (int i = 0; i < SWIG_MAX_DET; ++i) {
+      kap_out[2 * i] = kap_out[2 * i + 1] = 0.0;
+      vv_out[i] = 0.0;
+    }
+#pragma unroll
+    for (int i = 0; i < NDET; ++i) het_cache(L, r, i, zr[i], zi[i], hh[i], kap_out + 2 * i, vv_out + i);
   }
   return het_epilogue(L, Z_re, Z_im, HH);
 }

@@ -65,8 +65,10 @@ cudaError_t launch_waveform(const LikeConst& L, const double* theta_dev, EvalRec
 cudaError_t launch_distance_draw(const LikeConst& L, const DeviceBuffers& B, const double* kappa, int n,
                                  long long first, unsigned k0, unsigned k1, double* theta, cudaStream_t st);
 // Heterodyned logL of n thetas (device pointers), one warp per theta.
+// kappa_out (n x 8) / vv_out (n x 4), optional: the per-detector cache of
+// projection-only evaluations (het.cuh het_cache).
 cudaError_t launch_loglike_het(const LikeConst& L, const DeviceBuffers& B, const double* theta, int n, double* out,
-                               cudaStream_t st);
+                               cudaStream_t st, double* kappa_out = nullptr, double* vv_out = nullptr);
 cudaError_t launch_prior_transform(const PriorSlot* slots, int n_sampled, const double* u, int n, double* theta,
                                    cudaStream_t st);
 cudaError_t set_sweep_smem_limit(size_t bytes);

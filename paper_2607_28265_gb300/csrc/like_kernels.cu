@@ -206,25 +206,28 @@ cudaError_t launch_distance_draw(const LikeConst& L, const DeviceBuffers& B, con
 // Heterodyned likelihood, one warp per theta.
 // ---------------------------------------------------------------------------
 template <int NDET>
-__global__ void k_het(LikeConst L, HetTables H, const EvalRecord* __restrict__ rec, int n, double* __restrict__ out) {
+__global__ void k_het(LikeConst L, HetTables H, const EvalRecord* __restrict__ rec, int n, double* __restrict__ out,
+                      double* __restrict__ kappa_out, double* __restrict__ vv_out) {
   const int th = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (th >= n) return;
-  const double v = het_loglike_warp<NDET>(L, H, rec[th], lane);
+  const double v = het_loglike_warp<NDET>(L, H, rec[th], lane,
+                                          kappa_out ? kappa_out + (size_t)th * 2 * SWIG_MAX_DET : nullptr,
+                                          vv_out ? vv_out + (size_t)th * SWIG_MAX_DET : nullptr);
   if (lane == 0) out[th] = v;
 }
 
 cudaError_t launch_loglike_het(const LikeConst& L, const DeviceBuffers& B, const double* theta, int n, double* out,
-                               cudaStream_t st) {
+                               cudaStream_t st, double* kappa_out, double* vv_out) {
   if (n <= 0) return cudaSuccess;
   k_setup<<<(n + 127) / 128, 128, 0, st>>>(L, theta, n, B.rec);
   const HetTables H = het_tables(B);
   const unsigned grid = (unsigned)((n + 3) / 4);
   switch (L.n_det) {
-    case 1: k_het<1><<<grid, 128, 0, st>>>(L, H, B.rec, n, out); break;
-    case 2: k_het<2><<<grid, 128, 0, st>>>(L, H, B.rec, n, out); break;
-    case 3: k_het<3><<<grid, 128, 0, st>>>(L, H, B.rec, n, out); break;
-    default: k_het<4><<<grid, 128, 0, st>>>(L, H, B.rec, n, out); break;
+    case 1: k_het<1><<<grid, 128, 0, st>>>(L, H, B.rec, n, out, kappa_out, vv_out); break;
+    case 2: k_het<2><<<grid, 128, 0, st>>>(L, H, B.rec, n, out, kappa_out, vv_out); break;
+    case 3: k_het<3><<<grid, 128, 0, st>>>(L, H, B.rec, n, out, kappa_out, vv_out); break;
+    default: k_het<4><<<grid, 128, 0, st>>>(L, H, B.rec, n, out, kappa_out, vv_out); break;
   }
   return cudaGetLastError();
 }

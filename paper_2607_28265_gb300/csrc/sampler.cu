@@ -81,6 +81,7 @@ struct SamplerConst {
   int n_ctas;
   int mixed;
   int flow_parts;   // parts per slice (dataflow kernel): fixed summation partition
+  int het;          // heterodyned likelihood (projection-only evaluations use ChainState::vv)
   int learn_on;     // learned directions available (SWIG_PROPOSAL_LEARNED)
   float learn_mix;  // probability of a learned direction per slice step
 };
@@ -90,6 +91,7 @@ struct ChainState {
   double th[SWIG_N_PARAMS], th_y[SWIG_N_PARAMS];  // theta of x and of the proposal
   double lx, lo, hi, t;
   double kap[2 * SWIG_MAX_DET];
+  double vv[SWIG_MAX_DET];  // heterodyned path: <h|h>_i / |C_i|^2 of the current point, times A1^2
   int block, step, sweep, phase, n_out, n_shrink;
   int pending, done, proj_dirty, slot;
   unsigned ctr;
@@ -128,6 +130,7 @@ struct SamplerPtrs {
   double* live_u;      // [m][ndim]
   double* live_logl;   // [m]
   double* live_kap;    // [m][8]
+  double* live_vv;     // [m][4] heterodyned path: see ChainState::vv
   ChainState* chains;  // [k]
   EvalRecord* recx;    // [k] setup record of each chain's current point
   int* pending;        // [k]
@@ -239,7 +242,11 @@ __device__ inline float log_i0_f32(float x) {
   return x - 0.5f * logf(6.283185307179586f * x) + logf(s);
 }
 
-__device__ inline double free_loglike_mixed(const LikeConst& L, const double* th, const double* kap) {
+// kap: per-detector sums cached at the chain's current point (full grid:
+// kappa_i; heterodyned: (Z_i / C_i) / inv_scale_i); vv (heterodyned only):
+// <h|h>_i / |C_i|^2 times A1^2, replacing the constant K_i A1^2 of the full grid.
+__device__ inline double free_loglike_mixed(const LikeConst& L, const double* th, const double* kap,
+                                            const double* vv = nullptr) {
   const float mc = (float)th[0], dl = (float)th[6], iota = (float)th[7], psi = (float)th[8];
   const float ra = (float)th[9], dec = (float)th[10], phic = (float)th[12];
   if (!(mc > 0.0f && dl > 0.0f)) return -INFINITY;
@@ -273,7 +280,7 @@ __device__ inline double free_loglike_mixed(const LikeConst& L, const double* th
     const float a = (float)kap[2 * i] * L.amp_s[i], b = (float)kap[2 * i + 1] * L.amp_s[i];
     zr += cre * a - cim * b;
     zi += cre * b + cim * a;
-    hh += (cre * cre + cim * cim) * L.amp_k[i];
+    hh += (cre * cre + cim * cim) * (vv ? (float)vv[i] : L.amp_k[i]);
   }
   // with d_L marginalised the template is at 1 Mpc: zr, zi, hh are Z1, H1
   if (L.dist_marg) return distance_marg_logl(L, (double)zr, (double)zi, (double)hh);
@@ -399,8 +406,9 @@ __device__ inline void start_step(const SamplerConst& S, ChainState& ch, const f
 // pieces of the record that the block moves are recomputed.  Lane 0 only.
 template <bool MIXED>
 __device__ __noinline__ void chain_advance_local(const LikeConst& L, const SamplerConst& S, const SamplerPtrs& P, int c,
-                                    const double* kap_in, double ly_in, ChainState& ch, EvalRecord& rx,
-                                    bool& rx_dirty, EvalRecord& rec, bool& rec_set, int& setup_fl) {
+                                    const double* kap_in, const double* vv_in, double ly_in, ChainState& ch,
+                                    EvalRecord& rx, bool& rx_dirty, EvalRecord& rec, bool& rec_set,
+                                    int& setup_fl) {
   NSGlobal* g = P.g;
   const double logl_star = g->logl_star;
   const long long it = g->iter;
@@ -432,6 +440,8 @@ __device__ __noinline__ void chain_advance_local(const LikeConst& L, const Sampl
     if (apply_result(S, ch, ly_in, logl_star, g)) {
       move_to_proposal(S, ch, ly_in);
       for (int j = 0; j < 2 * SWIG_MAX_DET; ++j) ch.kap[j] = kap_in[j];
+      if (vv_in)
+        for (int i = 0; i < SWIG_MAX_DET; ++i) ch.vv[i] = vv_in[i];
       rx = rec;
       rx_dirty = true;
       ch.proj_dirty = 0;
@@ -492,7 +502,7 @@ __device__ __noinline__ void chain_advance_local(const LikeConst& L, const Sampl
       --free_left;
       ++ch.n_evals;
       if (MIXED) {
-        const double ly = free_loglike_mixed(L, ch.th_y, ch.kap);
+        const double ly = free_loglike_mixed(L, ch.th_y, ch.kap, S.het ? ch.vv : nullptr);
         if (apply_result(S, ch, ly, logl_star, g)) {
           move_to_proposal(S, ch, ly);
           ch.proj_dirty = 1;
@@ -546,7 +556,8 @@ __device__ __noinline__ void chain_advance_local(const LikeConst& L, const Sampl
 // the block moves), or -1 when nothing is pending.
 template <bool MIXED>
 __device__ __noinline__ int chain_advance(const LikeConst& L, const SamplerConst& S, const SamplerPtrs& P, int c,
-                                          const double* kap_in, double ly_in, EvalRecord* rec_out) {
+                                          const double* kap_in, double ly_in, EvalRecord* rec_out,
+                                          const double* vv_in = nullptr) {
   if (P.chains[c].done) return -1;
   ChainState ch = P.chains[c];
   EvalRecord rx = P.recx[c];
@@ -554,7 +565,7 @@ __device__ __noinline__ int chain_advance(const LikeConst& L, const SamplerConst
   if (ch.pending) rec = *rec_out;
   bool rx_dirty = false, rec_set = false;
   int fl = -1;
-  chain_advance_local<MIXED>(L, S, P, c, kap_in, ly_in, ch, rx, rx_dirty, rec, rec_set, fl);
+  chain_advance_local<MIXED>(L, S, P, c, kap_in, vv_in, ly_in, ch, rx, rx_dirty, rec, rec_set, fl);
   P.chains[c] = ch;
   if (rx_dirty) P.recx[c] = rx;
   if (rec_set) *rec_out = rec;
@@ -642,6 +653,7 @@ __device__ __noinline__ void ns_boundary(const LikeConst& L, const SamplerConst&
       for (int j = 0; j < d; ++j) P.live_u[(size_t)slot * d + j] = __ldcg(&ch.x[j]);
       P.live_logl[slot] = __ldcg(&ch.lx);
       for (int j = 0; j < 2 * SWIG_MAX_DET; ++j) P.live_kap[(size_t)slot * 2 * SWIG_MAX_DET + j] = __ldcg(&ch.kap[j]);
+      for (int i = 0; i < SWIG_MAX_DET; ++i) P.live_vv[(size_t)slot * SWIG_MAX_DET + i] = __ldcg(&ch.vv[i]);
     }
     __syncthreads();
     if (tid == 0) g->need_writeback = 0;
@@ -768,6 +780,7 @@ __device__ __noinline__ void ns_boundary(const LikeConst& L, const SamplerConst&
     for (int j = 0; j < d; ++j) ch.x[j] = P.live_u[(size_t)s * d + j];
     ch.lx = P.live_logl[s];
     for (int j = 0; j < 2 * SWIG_MAX_DET; ++j) ch.kap[j] = P.live_kap[(size_t)s * 2 * SWIG_MAX_DET + j];
+    for (int i = 0; i < SWIG_MAX_DET; ++i) ch.vv[i] = P.live_vv[(size_t)s * SWIG_MAX_DET + i];
     prior_map(S.prior, ch.x, ch.th);
     setup_record(L, ch.th, &P.recx[c]);
     ch.proj_dirty = 0;
@@ -1072,8 +1085,10 @@ __global__ void __launch_bounds__(kFlowThreads, 1)
 // warp contracts a share of the bins (31-bin chunks, strided by warp) and the
 // per-warp sums are added in warp order.  The chains of one NS iteration run
 // independently to completion; the grid meets only at the iteration
-// boundary.  Every proposal is evaluated in full (no projection-only
-// shortcut) and the set-up is FP64.
+// boundary.  Projection-only blocks (d_L, iota, psi, phi_c) reuse each
+// chain's per-detector cache of its last full evaluation, as on the full
+// grid; the set-up follows the mixed-precision sampler (FP64 waveform
+// coefficients and delays, FP32 prior transform, amplitude and projection).
 template <int NDET>
 __global__ void __launch_bounds__(kHetThreads, 1)
     k_ns_het(LikeConst L, SamplerConst S, DeviceBuffers B, SamplerPtrs P) {
@@ -1104,13 +1119,15 @@ __global__ void __launch_bounds__(kHetThreads, 1)
     }
     if (*(volatile int*)&g->status != ST_RUNNING) return;
     for (int c = blockIdx.x; c < S.nrep; c += gridDim.x) {
-      double kap0[2 * SWIG_MAX_DET];
+      double kap_y[2 * SWIG_MAX_DET], vv_y[SWIG_MAX_DET];  // thread 0's cache of the last evaluation
 #pragma unroll
-      for (int j = 0; j < 2 * SWIG_MAX_DET; ++j) kap0[j] = 0.0;
+      for (int j = 0; j < 2 * SWIG_MAX_DET; ++j) kap_y[j] = 0.0;
+#pragma unroll
+      for (int i = 0; i < SWIG_MAX_DET; ++i) vv_y[i] = 0.0;
       double ly = 0.0;
       for (long long guard = 0; guard < (1ll << 24); ++guard) {
         if (threadIdx.x == 0) {
-          s_fl = chain_advance<false>(L, S, P, c, kap0, ly, &B.rec[c]);
+          s_fl = chain_advance<true>(L, S, P, c, kap_y, ly, &B.rec[c], vv_y);
           s_done = P.chains[c].done;
         }
         __syncthreads();
@@ -1118,7 +1135,7 @@ __global__ void __launch_bounds__(kHetThreads, 1)
         if (s_fl < 0) continue;  // nothing pending (cannot happen without projection-only blocks)
         if (warp == 0) {
           const long long ts = clock64();
-          setup_record_warp(L, P.chains[c].th_y, s_fl, false, &B.rec[c], lane);
+          setup_record_warp(L, P.chains[c].th_y, s_fl, true, &B.rec[c], lane);
           if (c == 0 && lane == 0) g->c_setup += clock64() - ts;
         }
         __syncthreads();
@@ -1147,12 +1164,18 @@ __global__ void __launch_bounds__(kHetThreads, 1)
             ly = -INFINITY;
           } else {
             double Z_re = 0.0, Z_im = 0.0, HH = 0.0;
-            for (int w = 0; w < n_warps; ++w)
-              for (int i = 0; i < NDET; ++i) {
-                Z_re += (double)s_sum[w][3 * i];
-                Z_im += (double)s_sum[w][3 * i + 1];
-                HH += (double)s_sum[w][3 * i + 2];
+            for (int i = 0; i < NDET; ++i) {
+              double zr = 0.0, zi = 0.0, hh = 0.0;
+              for (int w = 0; w < n_warps; ++w) {
+                zr += (double)s_sum[w][3 * i];
+                zi += (double)s_sum[w][3 * i + 1];
+                hh += (double)s_sum[w][3 * i + 2];
               }
+              het_cache(L, r, i, zr, zi, hh, kap_y + 2 * i, vv_y + i);
+              Z_re += zr;
+              Z_im += zi;
+              HH += hh;
+            }
             ly = het_epilogue(L, Z_re, Z_im, HH);
           }
         }
@@ -1211,6 +1234,7 @@ void release(SamplerState* s) {
   dfree(s->P.live_u);
   dfree(s->P.live_logl);
   dfree(s->P.live_kap);
+  dfree(s->P.live_vv);
   dfree(s->P.chains);
   dfree(s->P.recx);
   dfree(s->P.pending);
@@ -1322,6 +1346,7 @@ int swig_run(swig_ctx* c, swig_result* out) {
   S.key1 = (unsigned)(c->cfg.seed >> 32);
   S.mixed = mixed ? 1 : 0;
   S.n_ctas = het ? het_ctas : L.n_slices;
+  S.het = het ? 1 : 0;
   S.spin_limit = c->wait_limit;
   int nd = 0;
   for (int i = 0; i < SWIG_N_PARAMS; ++i) {
@@ -1356,7 +1381,7 @@ int swig_run(swig_ctx* c, swig_result* out) {
         if (slot == 7 || slot == 8 || slot == 9 || slot == 10 || slot == 12) flags |= BF_PROJ;
         if (slot == 9 || slot == 10 || slot == 11) flags |= BF_TAU;
       }
-    S.block_free[b] = (free_block && !het) ? 1 : 0;
+    S.block_free[b] = free_block ? 1 : 0;
     S.block_flags[b] = flags;
   }
   S.m_pow2 = 1;
@@ -1407,6 +1432,7 @@ int swig_run(swig_ctx* c, swig_result* out) {
     SCUDA(cudaMalloc(&st->P.live_u, sizeof(double) * m * nd));
     SCUDA(cudaMalloc(&st->P.live_logl, sizeof(double) * m));
     SCUDA(cudaMalloc(&st->P.live_kap, sizeof(double) * m * 2 * SWIG_MAX_DET));
+    SCUDA(cudaMalloc(&st->P.live_vv, sizeof(double) * m * SWIG_MAX_DET));
     SCUDA(cudaMalloc(&st->P.chains, sizeof(ChainState) * k));
     SCUDA(cudaMalloc(&st->P.recx, sizeof(EvalRecord) * k));
     SCUDA(cudaMalloc(&st->P.pending, sizeof(int) * k));
@@ -1447,10 +1473,10 @@ int swig_run(swig_ctx* c, swig_result* out) {
   k_init_live<<<(m + 127) / 128, 128, 0, c->stream>>>(S, st->P.live_u, st->init_theta);
   SCUDA(cudaGetLastError());
   {
-    cudaError_t e;
-    if (het) {
-      e = cudaMemsetAsync(st->P.live_kap, 0, sizeof(double) * m * 2 * SWIG_MAX_DET, c->stream);
-      if (e == cudaSuccess) e = launch_loglike_het(L, c->B, st->init_theta, m, st->P.live_logl, c->stream);
+    cudaError_t e = cudaMemsetAsync(st->P.live_vv, 0, sizeof(double) * m * SWIG_MAX_DET, c->stream);
+    if (e != cudaSuccess) {
+    } else if (het) {
+      e = launch_loglike_het(L, c->B, st->init_theta, m, st->P.live_logl, c->stream, st->P.live_kap, st->P.live_vv);
     } else {
       e = mixed ? launch_loglike_mixed(L, c->B, st->init_theta, m, st->P.live_logl, c->stream, st->P.live_kap)
                 : launch_loglike_fp64(L, c->B, st->init_theta, m, st->P.live_logl, c->stream, st->P.live_kap);

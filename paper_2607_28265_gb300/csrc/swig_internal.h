@@ -89,6 +89,7 @@ struct LikeConst {
   // Mc = 1 Msun at 1 Mpc, so C_i kappa_i and |C_i|^2 K_i stay O(1..1e6).
   float amp_s[SWIG_MAX_DET];
   float amp_k[SWIG_MAX_DET];
+  double amp1;  // A1 itself
   double dten[SWIG_MAX_DET][6];  // detector tensor xx xy xz yy yz zz
   double vertex[SWIG_MAX_DET][3];
   // distance marginalisation (d_L slot marginalised): prior family and range,
