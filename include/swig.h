@@ -199,6 +199,18 @@ int swig_loglike_batch_noalloc(swig_ctx* ctx, const double* theta_dev, int64_t n
 int swig_inject(swig_ctx* ctx, const double* theta, double target_snr, const double* noise_re_im,
                 double* out_re_im, double* theta_out);
 
+/* ---- detector-frame sky parameterisation ------------------------------- */
+/* Sample the sky as azimuth (slot 9, uniform on [0, 2 pi]) and zenith (slot 10,
+ * sine prior on [0, pi]) about the baseline from detector det_b to detector
+ * det_a instead of (RA, Dec) (the detector-frame parameterisation the paper
+ * adopts for mixing, Sec. 3.2).  The frame's z axis is the baseline, its x axis
+ * the Earth's rotation axis made orthogonal to it; a direction maps to (RA, Dec)
+ * at the reference sidereal time.  The prior stays isotropic, so evidences and
+ * posteriors are those of the equatorial parameterisation; samples are reported
+ * as (RA, Dec).  Both slots must be sampled in one Gibbs block (checked when
+ * the prior is used: SWIG_E_ARG).  det_a = det_b = -1 restores (RA, Dec). */
+int swig_set_sky_frame(swig_ctx* ctx, int det_a, int det_b);
+
 /* ---- prior transform (Table I) ---------------------------------------- */
 /* Map n unit-cube points (n x n_sampled doubles, sampled slots in slot order)
  * to full 13-vectors theta (n x 13). */

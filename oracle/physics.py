@@ -46,11 +46,37 @@ def prior_transform_1d(u, kind, lo, hi):
     raise ValueError(f"unknown prior kind {kind}")
 
 
-def prior_transform(u_sampled, params):
+def detector_frame(vertex_a, vertex_b):
+    """Orthonormal frame of the baseline from detector b to detector a:
+    ez along the baseline, ex the Earth's rotation axis made orthogonal to ez,
+    ey = ez x ex (Earth-fixed coordinates)."""
+    ez = np.asarray(vertex_a, dtype=np.float64) - np.asarray(vertex_b, dtype=np.float64)
+    ez = ez / np.linalg.norm(ez)
+    pole = np.array([0.0, 0.0, 1.0])
+    ex = pole - ez * (pole @ ez)
+    if np.linalg.norm(ex) < 1e-12:
+        axis = np.array([1.0, 0.0, 0.0])
+        ex = axis - ez * (axis @ ez)
+    ex = ex / np.linalg.norm(ex)
+    return ex, np.cross(ez, ex), ez
+
+
+def frame_to_radec(az, zen, frame, gmst):
+    """(azimuth, zenith) about ez of `frame` -> (RA, Dec) at sidereal time gmst."""
+    ex, ey, ez = frame
+    n = math.sin(zen) * math.cos(az) * ex + math.sin(zen) * math.sin(az) * ey + math.cos(zen) * ez
+    dec = math.asin(max(-1.0, min(1.0, float(n[2]))))
+    ra = (math.atan2(float(n[1]), float(n[0])) + gmst) % (2.0 * math.pi)
+    return ra, dec
+
+
+def prior_transform(u_sampled, params, sky=None):
     """Map the sampled unit-cube coordinates to the full 13-vector theta.
 
     ``u_sampled`` has one column per parameter with mode SAMPLE, in slot order.
-    Fixed slots take their value; marginalised slots are set to 0.
+    Fixed slots take their value; marginalised slots are set to 0.  With
+    ``sky = (frame, gmst)`` slots 9 and 10 are sampled as (azimuth, zenith)
+    about the frame's ez and converted to (RA, Dec).
     """
     u_sampled = np.atleast_2d(np.asarray(u_sampled, dtype=np.float64))
     theta = np.zeros((u_sampled.shape[0], N_PARAMS))
@@ -63,6 +89,11 @@ def prior_transform(u_sampled, params):
         else:
             theta[:, i] = prior_transform_1d(u_sampled[:, j], p.kind, p.lo, p.hi)
             j += 1
+    if sky is not None:
+        frame, gmst = sky
+        for r in range(theta.shape[0]):
+            theta[r, IDX["ra"]], theta[r, IDX["dec"]] = frame_to_radec(theta[r, IDX["ra"]], theta[r, IDX["dec"]],
+                                                                       frame, gmst)
     return theta
 
 

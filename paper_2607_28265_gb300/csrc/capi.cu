@@ -386,6 +386,44 @@ int prepare_het(swig_ctx* c) {
   return SWIG_OK;
 }
 
+int make_sky_frame(swig_ctx* c, SkyFrame* F) {
+  std::memset(F, 0, sizeof(*F));
+  if (c->sky_a < 0) return SWIG_OK;
+  if (!c->det_set[c->sky_a] || !c->det_set[c->sky_b]) return fail(c, SWIG_E_STATE, "sky-frame detectors not set");
+  const swig_param& az = c->params[9];
+  const swig_param& zen = c->params[10];
+  if (az.mode != SWIG_MODE_SAMPLE || zen.mode != SWIG_MODE_SAMPLE || az.kind != SWIG_PRIOR_UNIFORM ||
+      zen.kind != SWIG_PRIOR_SINE || std::fabs(az.lo) > 1e-12 || std::fabs(az.hi - 2.0 * kPi) > 1e-9 ||
+      std::fabs(zen.lo) > 1e-12 || std::fabs(zen.hi - kPi) > 1e-9 || az.block != zen.block)
+    return fail(c, SWIG_E_ARG,
+                "the detector sky frame needs slot 9 (azimuth) uniform on [0, 2 pi] and slot 10 (zenith) sine on "
+                "[0, pi], both sampled in one block");
+  double b[3], nb = 0.0;
+  for (int k = 0; k < 3; ++k) {
+    b[k] = c->vertex[c->sky_a][k] - c->vertex[c->sky_b][k];
+    nb += b[k] * b[k];
+  }
+  nb = std::sqrt(nb);
+  if (!(nb > 0.0)) return fail(c, SWIG_E_ARG, "the sky-frame detectors share a vertex");
+  for (int k = 0; k < 3; ++k) F->ez[k] = b[k] / nb;
+  // ex: the Earth's rotation axis made orthogonal to ez (or the x axis if parallel)
+  double x[3] = {-F->ez[2] * F->ez[0], -F->ez[2] * F->ez[1], 1.0 - F->ez[2] * F->ez[2]};
+  double nx = std::sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
+  if (nx < 1e-12) {
+    x[0] = 1.0 - F->ez[0] * F->ez[0];
+    x[1] = -F->ez[0] * F->ez[1];
+    x[2] = -F->ez[0] * F->ez[2];
+    nx = std::sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
+  }
+  for (int k = 0; k < 3; ++k) F->ex[k] = x[k] / nx;
+  F->ey[0] = F->ez[1] * F->ex[2] - F->ez[2] * F->ex[1];
+  F->ey[1] = F->ez[2] * F->ex[0] - F->ez[0] * F->ex[2];
+  F->ey[2] = F->ez[0] * F->ex[1] - F->ez[1] * F->ex[0];
+  F->gmst = c->gmst;
+  F->on = 1;
+  return SWIG_OK;
+}
+
 int ensure_scratch(swig_ctx* c, int n) {
   DeviceBuffers& B = c->B;
   if (n <= B.cap) return SWIG_OK;
@@ -939,6 +977,19 @@ int swig_set_stream(swig_ctx* c, void* stream) {
   return SWIG_OK;
 }
 
+int swig_set_sky_frame(swig_ctx* c, int det_a, int det_b) {
+  if (!c) return SWIG_E_ARG;
+  if (det_a < 0 && det_b < 0) {
+    c->sky_a = c->sky_b = -1;
+    return SWIG_OK;
+  }
+  if (det_a < 0 || det_b < 0 || det_a >= SWIG_MAX_DET || det_b >= SWIG_MAX_DET || det_a == det_b)
+    return fail(c, SWIG_E_ARG, "need two different detector indices (or -1, -1 for the equatorial frame)");
+  c->sky_a = det_a;
+  c->sky_b = det_b;
+  return SWIG_OK;
+}
+
 int swig_prior_transform(swig_ctx* c, const double* u, int64_t n, double* theta) {
   if (!c) return SWIG_E_ARG;
   if (!c->prior_set) return fail(c, SWIG_E_STATE, "prior not set");
@@ -946,6 +997,9 @@ int swig_prior_transform(swig_ctx* c, const double* u, int64_t n, double* theta)
   if (n < 0 || n > (1 << 20) || !u || !theta) return fail(c, SWIG_E_ARG, "need 0 <= n <= 2^20 and non-null buffers");
   CUDA_TRY(c, cudaSetDevice(c->device));
   const int ns = c->n_sampled;
+  SkyFrame sky;
+  const int rc = make_sky_frame(c, &sky);
+  if (rc) return rc;
   PriorSlot slots[SWIG_N_PARAMS];
   for (int i = 0; i < SWIG_N_PARAMS; ++i) {
     const swig_param& p = c->params[i];
@@ -960,7 +1014,7 @@ int swig_prior_transform(swig_ctx* c, const double* u, int64_t n, double* theta)
     if ((e = cudaMalloc(&th_d, sizeof(double) * SWIG_N_PARAMS * n))) return e;
     if ((e = cudaMemcpyAsync(slots_d, slots, sizeof(slots), cudaMemcpyHostToDevice, c->stream))) return e;
     if ((e = cudaMemcpyAsync(u_d, u, sizeof(double) * ns * n, cudaMemcpyHostToDevice, c->stream))) return e;
-    if ((e = launch_prior_transform(slots_d, ns, u_d, (int)n, th_d, c->stream))) return e;
+    if ((e = launch_prior_transform(slots_d, ns, u_d, (int)n, th_d, c->stream, sky))) return e;
     if ((e = cudaMemcpyAsync(theta, th_d, sizeof(double) * SWIG_N_PARAMS * n, cudaMemcpyDeviceToHost, c->stream)))
       return e;
     return cudaStreamSynchronize(c->stream);

@@ -32,6 +32,7 @@ struct swig_ctx {
   // prior and sampler
   swig_param params[SWIG_N_PARAMS] = {};
   bool prior_set = false;
+  int sky_a = -1, sky_b = -1;  // detector-frame sky parameterisation (baseline b -> a), -1: equatorial
   int n_sampled = 0;
   swig_sampler_cfg cfg = {};
   bool cfg_set = false;
@@ -59,6 +60,9 @@ int prepare(swig_ctx* c);
 int ensure_scratch(swig_ctx* c, int n);
 int loglike_device(swig_ctx* c, const double* theta_dev, int64_t n, double* out_dev, cudaStream_t st);
 int current_precision(const swig_ctx* c);
+// The sky frame of the context (on = 0 when equatorial); SWIG_OK or a status
+// with the context's error set when the prior does not fit the frame.
+int make_sky_frame(swig_ctx* c, SkyFrame* out);
 }  // namespace swig
 
 void swig_sampler_release(swig_ctx* c);

@@ -594,7 +594,29 @@ __device__ inline double prior_slot_inverse_f32(const PriorSlot& s, double u) {
 }
 
 // Unit-cube coordinates of the sampled slots -> full 13-vector.
-__host__ __device__ inline void prior_map(const PriorSlot* slots, const double* u, double* th) {
+// (azimuth, zenith) about the frame's ez -> (RA, Dec): n = sin z cos a ex +
+// sin z sin a ey + cos z ez in the Earth-fixed frame, Dec = asin n_z,
+// RA = atan2(n_y, n_x) + GMST (mod 2 pi).
+__host__ __device__ inline void sky_frame_to_radec(const SkyFrame& F, double az, double zen, double* ra,
+                                                   double* dec) {
+  double sa, ca, sz, cz;
+  sa = sin(az);
+  ca = cos(az);
+  sz = sin(zen);
+  cz = cos(zen);
+  double n[3];
+  for (int k = 0; k < 3; ++k) n[k] = sz * ca * F.ex[k] + sz * sa * F.ey[k] + cz * F.ez[k];
+  *dec = asin(fmin(1.0, fmax(-1.0, n[2])));
+  double r = atan2(n[1], n[0]) + F.gmst;
+  r = fmod(r, 2.0 * kPi);
+  if (r < 0.0) r += 2.0 * kPi;
+  *ra = r;
+}
+
+__host__ __device__ inline void prior_map(const PriorSlot* slots, const double* u, double* th,
+                                          const SkyFrame* sky = nullptr);
+
+__host__ __device__ inline void prior_map(const PriorSlot* slots, const double* u, double* th, const SkyFrame* sky) {
   int j = 0;
   for (int i = 0; i < SWIG_N_PARAMS; ++i) {
     const PriorSlot& s = slots[i];
@@ -606,6 +628,7 @@ __host__ __device__ inline void prior_map(const PriorSlot* slots, const double* 
       th[i] = prior_slot_inverse(s, u[j++]);
     }
   }
+  if (sky && sky->on) sky_frame_to_radec(*sky, th[9], th[10], &th[9], &th[10]);
 }
 
 }  // namespace swig

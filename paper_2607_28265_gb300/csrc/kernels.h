@@ -16,6 +16,16 @@ struct PriorSlot {
 
 inline PriorSlot make_prior_slot(int kind, int mode, double lo, double hi, double value);
 
+// Detector-frame sky parameterisation: slots 9 and 10 hold the azimuth and
+// zenith of the source about the baseline between two detectors (ez, from
+// detector b to detector a; ex towards the Earth's north pole), mapped to
+// (RA, Dec) at the reference sidereal time before any use.
+struct SkyFrame {
+  int on;
+  double ex[3], ey[3], ez[3];
+  double gmst;
+};
+
 // Device buffers owned by a context (all allocated with cudaMalloc).
 struct DeviceBuffers {
   // problem data
@@ -70,7 +80,7 @@ cudaError_t launch_distance_draw(const LikeConst& L, const DeviceBuffers& B, con
 cudaError_t launch_loglike_het(const LikeConst& L, const DeviceBuffers& B, const double* theta, int n, double* out,
                                cudaStream_t st, double* kappa_out = nullptr, double* vv_out = nullptr);
 cudaError_t launch_prior_transform(const PriorSlot* slots, int n_sampled, const double* u, int n, double* theta,
-                                   cudaStream_t st);
+                                   cudaStream_t st, SkyFrame sky);
 cudaError_t set_sweep_smem_limit(size_t bytes);
 
 // Dynamic shared memory of the mixed sweep: data (float2 per detector and

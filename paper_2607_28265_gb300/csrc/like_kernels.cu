@@ -268,10 +268,10 @@ cudaError_t launch_waveform(const LikeConst& L, const double* theta_dev, EvalRec
 // Prior transform (Table I inverse CDFs).
 // ---------------------------------------------------------------------------
 __global__ void k_prior_transform(const PriorSlot* __restrict__ slots, int n_sampled, const double* __restrict__ u,
-                                  int n, double* __restrict__ theta) {
+                                  int n, double* __restrict__ theta, SkyFrame sky) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  prior_map(slots, u + (size_t)i * n_sampled, theta + (size_t)i * SWIG_N_PARAMS);
+  prior_map(slots, u + (size_t)i * n_sampled, theta + (size_t)i * SWIG_N_PARAMS, &sky);
 }
 
 // ---------------------------------------------------------------------------
@@ -318,9 +318,9 @@ cudaError_t launch_loglike_fp64(const LikeConst& L, const DeviceBuffers& B, cons
 }
 
 cudaError_t launch_prior_transform(const PriorSlot* slots, int n_sampled, const double* u, int n, double* theta,
-                                   cudaStream_t st) {
+                                   cudaStream_t st, SkyFrame sky) {
   if (n <= 0) return cudaSuccess;
-  k_prior_transform<<<(n + 127) / 128, 128, 0, st>>>(slots, n_sampled, u, n, theta);
+  k_prior_transform<<<(n + 127) / 128, 128, 0, st>>>(slots, n_sampled, u, n, theta, sky);
   return cudaGetLastError();
 }
 

@@ -82,6 +82,7 @@ struct SamplerConst {
   int mixed;
   int flow_parts;   // parts per slice (dataflow kernel): fixed summation partition
   int het;          // heterodyned likelihood (projection-only evaluations use ChainState::vv)
+  SkyFrame sky;     // detector-frame sky parameterisation (slots 9, 10), or off
   int learn_on;     // learned directions available (SWIG_PROPOSAL_LEARNED)
   float learn_mix;  // probability of a learned direction per slice step
 };
@@ -489,10 +490,16 @@ __device__ __noinline__ void chain_advance_local(const LikeConst& L, const Sampl
     for (int j = 0; j < S.ndim; ++j)
       if (ch.dir[j] == 0.0) ch.y[j] = ch.x[j];
     for (int q = 0; q < SWIG_N_PARAMS; ++q) ch.th_y[q] = ch.th[q];
+    bool sky_block = false;
     for (int r = 0; r < nb; ++r) {
       const int j = S.block_dims[b][r], slot = S.slot_of_dim[j];
-      ch.th_y[slot] = MIXED ? prior_slot_inverse_f32(S.prior[slot], ch.y[j]) : prior_slot_inverse(S.prior[slot], ch.y[j]);
+      // the sky angles go through FP64: the delays need them to ~1e-10
+      ch.th_y[slot] = (MIXED && !(S.sky.on && (slot == 9 || slot == 10)))
+                          ? prior_slot_inverse_f32(S.prior[slot], ch.y[j])
+                          : prior_slot_inverse(S.prior[slot], ch.y[j]);
+      sky_block = sky_block || slot == 9 || slot == 10;
     }
+    if (S.sky.on && sky_block) sky_frame_to_radec(S.sky, ch.th_y[9], ch.th_y[10], &ch.th_y[9], &ch.th_y[10]);
     if (prof) {
       const long long t2 = clock64();
       acc_prop += t2 - tk;
@@ -781,7 +788,7 @@ __device__ __noinline__ void ns_boundary(const LikeConst& L, const SamplerConst&
     ch.lx = P.live_logl[s];
     for (int j = 0; j < 2 * SWIG_MAX_DET; ++j) ch.kap[j] = P.live_kap[(size_t)s * 2 * SWIG_MAX_DET + j];
     for (int i = 0; i < SWIG_MAX_DET; ++i) ch.vv[i] = P.live_vv[(size_t)s * SWIG_MAX_DET + i];
-    prior_map(S.prior, ch.x, ch.th);
+    prior_map(S.prior, ch.x, ch.th, &S.sky);
     setup_record(L, ch.th, &P.recx[c]);
     ch.proj_dirty = 0;
     ch.block = ch.step = ch.sweep = 0;
@@ -1200,12 +1207,12 @@ __global__ void k_init_live(SamplerConst S, double* live_u, double* theta) {
     u[j] = u01_from(r);
     live_u[(size_t)i * S.ndim + j] = u[j];
   }
-  prior_map(S.prior, u, theta + (size_t)i * SWIG_N_PARAMS);
+  prior_map(S.prior, u, theta + (size_t)i * SWIG_N_PARAMS, &S.sky);
 }
 
 __global__ void k_dead_theta(SamplerConst S, const double* u, int n, double* theta) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) prior_map(S.prior, u + (size_t)i * S.ndim, theta + (size_t)i * SWIG_N_PARAMS);
+  if (i < n) prior_map(S.prior, u + (size_t)i * S.ndim, theta + (size_t)i * SWIG_N_PARAMS, &S.sky);
 }
 
 // ---------------------------------------------------------------------------
@@ -1348,6 +1355,7 @@ int swig_run(swig_ctx* c, swig_result* out) {
   S.n_ctas = het ? het_ctas : L.n_slices;
   S.het = het ? 1 : 0;
   S.spin_limit = c->wait_limit;
+  if ((rc = make_sky_frame(c, &S.sky))) return rc;
   int nd = 0;
   for (int i = 0; i < SWIG_N_PARAMS; ++i) {
     const swig_param& p = c->params[i];

@@ -69,6 +69,7 @@ SIGNATURES = {
     "swig_inject": (_c_int, [_vp, _dp, _c_double, _dp, _dp, _dp]),
     "swig_loglike_batch_noalloc": (_c_int, [_vp, _vp, _c_i64, _vp, _vp]),
     "swig_get_samples": (_c_int, [_vp, _dp, _dp, _dp, _c_i64, ctypes.POINTER(_c_i64)]),
+    "swig_set_sky_frame": (_c_int, [_vp, _c_int, _c_int]),
     "swig_mlp_init": (_c_int, [_vp, _c_u64, _fp]),
     "swig_mlp_forward": (_c_int, [_vp, _fp, _fp, _c_i64, _fp]),
     "swig_mlp_loss_grad": (_c_int, [_vp, _fp, _fp, _fp, _fp, _c_i64, _c_int, _dp, _fp]),
@@ -255,6 +256,10 @@ class Context:
         out = np.zeros(len(self.PROFILE_KEYS))
         self._check(self.lib.swig_get_profile(self.h, _ptr(out), out.size))
         return dict(zip(self.PROFILE_KEYS, out.tolist()))
+
+    def set_sky_frame(self, det_a=-1, det_b=-1):
+        """Sample the sky as (azimuth, zenith) about the det_b -> det_a baseline."""
+        self._check(self.lib.swig_set_sky_frame(self.h, int(det_a), int(det_b)))
 
     def set_stream(self, stream_ptr):
         self._check(self.lib.swig_set_stream(self.h, _vp(stream_ptr)))
