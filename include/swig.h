@@ -223,6 +223,18 @@ int swig_prior_transform(swig_ctx* ctx, const double* u, int64_t n, double* thet
  * chains per CTA of the persistent kernel.  SWIG_E_TIMEOUT if a bounded
  * device wait expired (the context stays usable). */
 int swig_run(swig_ctx* ctx, swig_result* out);
+/* Run nested sampling for a campaign of n_ctx events (config 4), each a
+ * context set up as for swig_run; outs[i] receives event i's result and each
+ * context keeps its samples.  Consecutive events that can share a launch (full
+ * grid, mixed precision, covariance proposal, same detector count, chains and
+ * device) run up to 4 at a time in one persistent launch: their slices of the
+ * grid share each CTA's shared memory and their chains share the control and
+ * sweep warps, which keeps the GPU busy while one event's chains wait.  Per
+ * event the arithmetic and its order are those of swig_run, so the results
+ * are the same; an event's persistent-kernel time in the profile is the
+ * shared launch time.  Other events run one after another.  A context may
+ * appear once.  Stops at the first failure (that context's error). */
+int swig_run_batch(swig_ctx** ctxs, int n_ctx, swig_result* outs);
 /* Cap, in polling iterations of ~100 ns, on every spin-wait of the persistent
  * kernel (grid barriers).  Default 1e7.  A wait that reaches the cap makes
  * swig_run return SWIG_E_TIMEOUT instead of hanging. */

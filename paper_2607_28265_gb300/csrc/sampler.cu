@@ -56,6 +56,7 @@ constexpr int kMaxShrink = 100;
 constexpr int kMaxSort = 8192;
 constexpr int kMaxChains = 2048;
 
+constexpr int kMaxEvents = 4;    // events per multi-event launch
 constexpr int kFlowThreads = 512;  // dataflow sampler: 16 warps, up to 128 registers per thread
 constexpr int kHetThreads = 512;  // heterodyned sampler: one chain per CTA, 16 warps
 constexpr int kFreeBudget = 8;  // projection-only evaluations per chain per round
@@ -649,7 +650,12 @@ __device__ void block_reduce_max_sum(double* vals, int n, double* out_max, doubl
   __syncthreads();
 }
 
-__device__ __noinline__ void ns_boundary(const LikeConst& L, const SamplerConst& S, const SamplerPtrs& P, unsigned char* smem) {
+// First half of the boundary: write the finished chains back into the live
+// set and apply the launch's iteration limit and the termination rule.  Fills
+// the sort keys in `smem` for the second half.  Returns false (status set)
+// when the run stops here.
+__device__ __noinline__ bool ns_boundary_check(const LikeConst& L, const SamplerConst& S, const SamplerPtrs& P,
+                                               unsigned char* smem) {
   NSGlobal* g = P.g;
   const int tid = threadIdx.x, nt = blockDim.x;
   const int m = S.nlive, k = S.nrep, d = S.ndim;
@@ -668,7 +674,7 @@ __device__ __noinline__ void ns_boundary(const LikeConst& L, const SamplerConst&
   __syncthreads();
   if (g->iters_launch >= S.max_iters) {
     if (tid == 0) g->status = ST_LIMIT;
-    return;
+    return false;
   }
   double* key = reinterpret_cast<double*>(smem);
   int* idx = reinterpret_cast<int*>(key + S.m_pow2);
@@ -685,8 +691,21 @@ __device__ __noinline__ void ns_boundary(const LikeConst& L, const SamplerConst&
   const double logz = g->logz;
   if (isfinite(logz) && logz_live - logz < S.dlogz) {
     if (tid == 0) g->status = ST_TERMINATED;
-    return;
+    return false;
   }
+  return true;
+}
+
+// Second half: sort, retire the k worst points, update log X / log Z and
+// logL*, estimate the block Cholesky factors, start k chains at survivors.
+__device__ __noinline__ void ns_boundary_advance(const LikeConst& L, const SamplerConst& S, const SamplerPtrs& P,
+                                                 unsigned char* smem) {
+  NSGlobal* g = P.g;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int m = S.nlive, k = S.nrep, d = S.ndim;
+  double* key = reinterpret_cast<double*>(smem);
+  int* idx = reinterpret_cast<int*>(key + S.m_pow2);
+  double* tmp = reinterpret_cast<double*>(idx + S.m_pow2);
   // bitonic sort (ascending) of (logL, index)
   for (int kk = 2; kk <= S.m_pow2; kk <<= 1) {
     for (int j = kk >> 1; j > 0; j >>= 1) {
@@ -807,6 +826,10 @@ __device__ __noinline__ void ns_boundary(const LikeConst& L, const SamplerConst&
     g->iters_launch += 1;
     g->need_writeback = 1;
   }
+}
+
+__device__ void ns_boundary(const LikeConst& L, const SamplerConst& S, const SamplerPtrs& P, unsigned char* smem) {
+  if (ns_boundary_check(L, S, P, smem)) ns_boundary_advance(L, S, P, smem);
 }
 
 // ---------------------------------------------------------------------------
@@ -1086,6 +1109,163 @@ __global__ void __launch_bounds__(kFlowThreads, 1)
   }
 }
 
+// ---------------------------------------------------------------------------
+// Several events in one persistent launch (an injection campaign): every CTA
+// holds its slice of each event's grid in shared memory, the control warps
+// serve chains of all events, the sweep warps claim requests of any event.
+// Each event keeps its own NS state and boundary (run by CTA e for event e);
+// the grid meets around the boundaries, and the launch returns as soon as any
+// event leaves the running state, before any event starts new chains, so that
+// the others resume exactly where they stopped.  Per event the arithmetic and
+// its order are those of k_ns_flow: the results equal separate runs.
+// ---------------------------------------------------------------------------
+struct EventDesc {
+  LikeConst L;
+  SamplerConst S;
+  DeviceBuffers B;
+  SamplerPtrs P;
+  int smem_off;  // byte offset of the event's slice data in the CTA's shared memory
+};
+
+template <int NDET>
+__global__ void __launch_bounds__(kFlowThreads, 1)
+    k_ns_multi(const EventDesc* __restrict__ ev, int n_ev, NSGlobal* gb, int n_ctrl, int dyn_off) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ int s_claim[kMaxChains];  // [event][chain]: request number this CTA has taken
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int k = ev[0].S.nrep;
+  const long long spin_limit = ev[0].S.spin_limit;
+  for (int e = 0; e < n_ev; ++e) {
+    const LikeConst& L = ev[e].L;
+    if ((int)blockIdx.x >= L.n_slices) continue;
+    const int b0 = ev[e].B.slice_begin[blockIdx.x], nb = ev[e].B.slice_begin[blockIdx.x + 1] - b0;
+    float2* sd = reinterpret_cast<float2*>(smem + ev[e].smem_off);
+    int* stile = reinterpret_cast<int*>(sd + (size_t)NDET * nb);
+    for (int i = 0; i < NDET; ++i)
+      for (int kq = tid; kq < nb; kq += blockDim.x) sd[i * nb + kq] = ev[e].B.data32[(size_t)i * L.n_bins + b0 + kq];
+    for (int kq = tid; kq < nb; kq += blockDim.x) stile[kq] = ev[e].B.bin_tile[b0 + kq];
+  }
+  __syncthreads();
+  unsigned char* dyn = smem + dyn_off;
+  EvalRecord* rec = reinterpret_cast<EvalRecord*>(dyn) + warp;
+  for (;;) {
+    if (!grid_sync(gb, gridDim.x, spin_limit)) return;
+    if ((int)blockIdx.x < n_ev) ns_boundary_check(ev[blockIdx.x].L, ev[blockIdx.x].S, ev[blockIdx.x].P, dyn);
+    if (!grid_sync(gb, gridDim.x, spin_limit)) return;
+    bool all_run = true;
+    for (int e = 0; e < n_ev; ++e) all_run = all_run && *(volatile int*)&ev[e].P.g->status == ST_RUNNING;
+    if (!all_run) return;
+    if ((int)blockIdx.x < n_ev) ns_boundary_advance(ev[blockIdx.x].L, ev[blockIdx.x].S, ev[blockIdx.x].P, dyn);
+    for (int q = tid; q < n_ev * k; q += blockDim.x) s_claim[q] = 0;
+    if (!grid_sync(gb, gridDim.x, spin_limit)) return;
+
+    long long idle = 0;
+    if (warp < n_ctrl) {
+      // ---- control of the chains homed on (this CTA, this warp)
+      for (;;) {
+        bool all_done = true, progressed = false;
+        for (int q = blockIdx.x + gridDim.x * warp; q < n_ev * k; q += gridDim.x * n_ctrl) {
+          const EventDesc& E = ev[q / k];
+          const int c = q % k;
+          int st = 0;  // 0 done, 1 waiting, 2 ready
+          if (lane == 0) {
+            const ChainState* ch = &E.P.chains[c];
+            if (ch->done)
+              st = 0;
+            else if (ch->pending)
+              st = ld_acquire(&E.P.done_cnt[c]) >= E.L.n_slices ? 2 : 1;
+            else
+              st = 2;
+          }
+          st = __shfl_sync(0xffffffffu, st, 0);
+          if (st == 0) continue;
+          all_done = false;
+          if (st == 1) continue;
+          progressed = true;
+          flow_control<NDET, true>(E.L, E.S, E.B, E.P, c, lane);
+        }
+        if (all_done) break;
+        if (*(volatile int*)&gb->error) break;
+        if (progressed) {
+          idle = 0;
+        } else {
+          if (++idle > spin_limit) {
+            if (lane == 0) atomicCAS(&gb->error, 0, SWIG_E_TIMEOUT);
+            break;
+          }
+          __nanosleep(64);
+        }
+      }
+    } else {
+      // ---- sweep: claim (event, chain, request) and evaluate this CTA's slice
+      for (;;) {
+        bool over = true;
+        for (int e = 0; e < n_ev; ++e) over = over && *(volatile int*)&ev[e].P.g->chains_done >= k;
+        if (over) break;
+        if (*(volatile int*)&gb->error) break;
+        int qq = -1;
+        for (int base = 0; base < n_ev * k && qq < 0; base += 32) {
+          const int q = base + lane;
+          int r = 0;
+          bool cand = false;
+          if (q < n_ev * k && (int)blockIdx.x < ev[q / k].L.n_slices) {
+            r = (*(volatile int*)&ev[q / k].P.req[q % k]) >> 3;
+            cand = r > *(volatile int*)&s_claim[q];
+          }
+          unsigned msk = __ballot_sync(0xffffffffu, cand);
+          while (msk) {
+            const int leader = __ffs(msk) - 1;
+            int won = 0;
+            if (lane == leader) {
+              const int old = *(volatile int*)&s_claim[q];
+              won = (old < r) && atomicCAS(&s_claim[q], old, r) == old;
+            }
+            if (__shfl_sync(0xffffffffu, won, leader)) {
+              qq = base + leader;
+              break;
+            }
+            msk &= ~(1u << leader);
+          }
+        }
+        if (qq < 0) {
+          if (++idle > spin_limit) {
+            if (lane == 0) atomicCAS(&gb->error, 0, SWIG_E_TIMEOUT);
+            break;
+          }
+          __nanosleep(100);
+          continue;
+        }
+        idle = 0;
+        const EventDesc& E = ev[qq / k];
+        const int cc = qq % k;
+        const int slice = blockIdx.x;
+        const int b0 = E.B.slice_begin[slice], nb = E.B.slice_begin[slice + 1] - b0;
+        const float2* sd = reinterpret_cast<const float2*>(smem + E.smem_off);
+        const int* stile = reinterpret_cast<const int*>(sd + (size_t)NDET * nb);
+        const int tf = stile[0];
+        float* row = E.P.anchor_buf + ((size_t)slice * k + cc) * E.S.max_tiles_slice * kAnchorStride;
+        __threadfence();  // acquire: the request word was read relaxed
+        load_record_cg(&E.B.rec[cc], rec, lane);
+        for (int t = lane; t <= stile[nb - 1] - tf; t += 32)
+          compute_anchor(NDET, E.B.tiles[tf + t], E.B.basis[tf + t], *rec, row + (size_t)t * kAnchorStride);
+        __syncwarp();
+        float v[2 * NDET];
+        sweep_warp_mixed<NDET>(E.L, sd, nb, stile, b0, 0, nb, E.B.tiles, row, tf, *rec, lane, v);
+        const size_t pidx = ((size_t)cc * E.L.n_slices + slice) * kPartialStride;
+#pragma unroll
+        for (int j = 0; j < 2 * NDET; ++j)
+          if (lane == j) E.B.partials32[pidx + j] = v[j];
+        __syncwarp();
+        if (lane == 0) {
+          __threadfence();
+          atomicAdd(&E.P.done_cnt[cc], 1);
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
 // Persistent sampler for the heterodyned likelihood (Sec. 3.4).  A
 // heterodyned evaluation is a few hundred to a few thousand bins, so one CTA
 // owns one chain at a time: thread 0 runs the chain's control, then every
@@ -1293,6 +1473,15 @@ void* pick_kernel(int n_det, bool mixed) {
   }
 }
 
+void* pick_multi_kernel(int n_det) {
+  switch (n_det) {
+    case 1: return (void*)k_ns_multi<1>;
+    case 2: return (void*)k_ns_multi<2>;
+    case 3: return (void*)k_ns_multi<3>;
+    default: return (void*)k_ns_multi<4>;
+  }
+}
+
 void* pick_het_kernel(int n_det) {
   switch (n_det) {
     case 1: return (void*)k_ns_het<1>;
@@ -1324,25 +1513,60 @@ int swig_set_wait_limit(swig_ctx* c, long long spins) {
   return SWIG_OK;
 }
 
-int swig_run(swig_ctx* c, swig_result* out) {
-  if (!c) return SWIG_E_ARG;
-  if (!out) return fail(c, SWIG_E_ARG, "null result pointer");
-  std::memset(out, 0, sizeof(*out));
+}  // extern "C"
+
+namespace swig {
+namespace {
+
+// Host state of one sampler run between its set-up and its result.
+struct RunState {
+  SamplerConst S;
+  SamplerState* st = nullptr;
+  size_t smem = 0, fixed = 0;
+  void* kern = nullptr;
+  int threads = 0;
+  bool het = false, mixed = false, learned = false;
+  int m = 0, k = 0, nd = 0;
+  float learn_lr = 0.0f;
+  int learn_steps = 0;
+  std::vector<double> du, dl, dw;
+  NSGlobal gh;
+  long long total_iters = 0;
+  double persistent_ms = 0.0, learn_ms = 0.0;
+  long long persistent_launches = 0, learn_rounds = 0;
+  bool finished = false;
+  std::chrono::steady_clock::time_point t_start;
+};
+
+}  // namespace
+}  // namespace swig
+
+using namespace swig;
+
+namespace {
+
+// Validation, preparation, sampler constants, buffers, the initial live set
+// and the NS state: everything before the first persistent launch.
+int run_setup(swig_ctx* c, RunState& R) {
   if (!c->prior_set) return fail(c, SWIG_E_STATE, "prior not set");
   if (!c->cfg_set) return fail(c, SWIG_E_STATE, "sampler not configured");
   if (c->cfg.nlive > kMaxSort) return fail(c, SWIG_E_ARG, "nlive must be <= 8192 for the device sort");
   if (c->cfg.nrep > kMaxChains) return fail(c, SWIG_E_ARG, "nrep must be <= 2048");
   int rc = prepare(c);
   if (rc) return rc;
-  const auto t_start = std::chrono::steady_clock::now();
+  R.t_start = std::chrono::steady_clock::now();
   const bool het = c->prepared_like == SWIG_LIKE_HET;
   const bool mixed = !het && c->prepared_precision == SWIG_PREC_MIXED;
+  R.het = het;
+  R.mixed = mixed;
   const int m = c->cfg.nlive, k = c->cfg.nrep;
+  R.m = m;
+  R.k = k;
   const LikeConst& L = c->L;
   if (!het && k > 32 * L.n_slices) return fail(c, SWIG_E_ARG, "nrep exceeds 32 chains per CTA");
   const int het_ctas = std::max(1, std::min(c->sm_count, k));
 
-  SamplerConst S;
+  SamplerConst& S = R.S;
   std::memset(&S, 0, sizeof(S));
   S.nlive = m;
   S.nrep = k;
@@ -1363,6 +1587,7 @@ int swig_run(swig_ctx* c, swig_result* out) {
     if (p.mode == SWIG_MODE_SAMPLE) S.slot_of_dim[nd++] = i;
   }
   S.ndim = nd;
+  R.nd = nd;
   // Gibbs blocks in increasing block id
   int ids[kMaxDim], n_ids = 0;
   for (int j = 0; j < nd; ++j) {
@@ -1397,12 +1622,12 @@ int swig_run(swig_ctx* c, swig_result* out) {
   S.max_iters = (int)std::max(1, std::min(64, c->cfg.max_iter));
   S.flow_parts = 1;  // summation parts per slice, at most 4 (the partial buffers hold 4 per slice and theta)
   // learned proposal: retrain every learn_interval iterations (one launch each)
-  const bool learned = c->cfg.proposal == SWIG_PROPOSAL_LEARNED;
+  R.learned = c->cfg.proposal == SWIG_PROPOSAL_LEARNED;
   const double learn_mix = c->cfg.learn_mix > 0.0 ? std::min(1.0, c->cfg.learn_mix) : 0.5;
-  const float learn_lr = c->cfg.learn_lr > 0.0 ? (float)c->cfg.learn_lr : 1e-3f;
-  const int learn_steps = c->cfg.learn_steps > 0 ? c->cfg.learn_steps : 50;
+  R.learn_lr = c->cfg.learn_lr > 0.0 ? (float)c->cfg.learn_lr : 1e-3f;
+  R.learn_steps = c->cfg.learn_steps > 0 ? c->cfg.learn_steps : 50;
   const int learn_interval = c->cfg.learn_interval > 0 ? c->cfg.learn_interval : 8;
-  if (learned) {
+  if (R.learned) {
     if (2 * nd >= m) return fail(c, SWIG_E_ARG, "the learned proposal needs nlive > 2 x sampled dimensions");
     S.max_iters = std::min(S.max_iters, learn_interval);
     S.learn_on = 1;
@@ -1413,6 +1638,7 @@ int swig_run(swig_ctx* c, swig_result* out) {
   S.max_pieces = max_pieces;
   size_t fixed = 0;
   if (mixed) fixed = ((size_t)c->B.max_slice_bins * (L.n_det * sizeof(float2) + sizeof(int)) + 15) & ~(size_t)15;
+  R.fixed = fixed;
   int max_tiles = 1;
   if (mixed) {
     std::vector<int> sb(L.n_slices + 1), bt(L.n_bins);
@@ -1424,8 +1650,8 @@ int swig_run(swig_ctx* c, swig_result* out) {
   const size_t sort_bytes = (size_t)S.m_pow2 * (sizeof(double) + sizeof(int)) + kSweepThreads * sizeof(double) +
                             (size_t)k * sizeof(double) + (kMaxDim + kMaxDim * kMaxDim) * sizeof(float) + 64;
   const size_t rec_bytes = (size_t)(kFlowThreads / 32) * sizeof(EvalRecord);
-  const size_t smem = het ? sort_bytes : fixed + std::max(rec_bytes, sort_bytes);
-  if (smem > 220 * 1024) return fail(c, SWIG_E_ARG, "problem too large for the persistent kernel's shared memory");
+  R.smem = het ? sort_bytes : fixed + std::max(rec_bytes, sort_bytes);
+  if (R.smem > 220 * 1024) return fail(c, SWIG_E_ARG, "problem too large for the persistent kernel's shared memory");
 
   // buffers
   SamplerState* st = c->sampler;
@@ -1462,6 +1688,7 @@ int swig_run(swig_ctx* c, swig_result* out) {
     st->P.harm = st->harm;
     st->P.lw = st->lw;
   }
+  R.st = st;
   st->P.piece_begin = c->B.piece_begin;
   st->P.slice_piece = c->B.slice_piece;
   dfree(st->anchor_buf);
@@ -1470,7 +1697,7 @@ int swig_run(swig_ctx* c, swig_result* out) {
   }
   st->P.anchor_buf = st->anchor_buf;
   st->P.learn_out = nullptr;
-  if (learned) {
+  if (R.learned) {
     if (!c->mlp) c->mlp = new Mlp();
     if (c->mlp->cap < m) SCUDA(mlp_alloc(*c->mlp, std::max(m, 1024)));
   }
@@ -1502,82 +1729,68 @@ int swig_run(swig_ctx* c, swig_result* out) {
   SCUDA(cudaMemsetAsync(st->P.req, 0, sizeof(int) * k, c->stream));
   SCUDA(cudaMemsetAsync(st->P.done_cnt, 0, sizeof(int) * k, c->stream));
   SCUDA(cudaMemsetAsync(st->P.chains, 0, sizeof(ChainState) * k, c->stream));
-
-  void* kern = het ? pick_het_kernel(L.n_det) : pick_kernel(L.n_det, mixed);
-  const int threads = het ? kHetThreads : kFlowThreads;
-  SCUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  int per_sm = 0;
-  SCUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem));
-  if (per_sm < 1 || S.n_ctas > per_sm * c->sm_count)
-    return fail(c, SWIG_E_CUDA, "persistent kernel cannot be co-resident on this device");
-
-  std::vector<double> du, dl, dw;
-  NSGlobal gh;
-  long long total_iters = 0;
-  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-  SCUDA(cudaEventCreate(&ev0));
-  SCUDA(cudaEventCreate(&ev1));
-  double persistent_ms = 0.0, learn_ms = 0.0;
-  long long persistent_launches = 0, learn_rounds = 0;
-  if (learned) SCUDA(mlp_init(*c->mlp, c->cfg.seed ^ 0x4D4C5050ull, c->stream, &c->n_launches));
   c->n_launches += het ? 3 : (mixed ? 5 : 4);  // init draw + batched likelihood
-  for (;;) {
-    // reset per-launch counters
-    NSGlobal gl;
-    SCUDA(cudaMemcpyAsync(&gl, st->P.g, sizeof(gl), cudaMemcpyDeviceToHost, c->stream));
-    SCUDA(cudaStreamSynchronize(c->stream));
-    gl.iters_launch = 0;
-    gl.n_dead = 0;
-    gl.status = ST_RUNNING;
-    gl.error = 0;
-    gl.bar_count = 0;
-    SCUDA(cudaMemcpyAsync(st->P.g, &gl, sizeof(gl), cudaMemcpyHostToDevice, c->stream));
-    if (learned) {
-      // retrain on the current live set, then freeze the output rows of
-      // this snapshot for the launch's iterations
-      Mlp& N = *c->mlp;
-      SCUDA(cudaEventRecord(ev0, c->stream));
-      SCUDA(mlp_targets(N, st->P.live_u, m, nd, 2 * nd, c->stream, &c->n_launches));
-      SCUDA(mlp_train(N, m, nd, learn_rounds == 0 ? 4 * learn_steps : learn_steps, learn_lr, c->stream,
-                      &c->n_launches));
-      SCUDA(mlp_forward(N, m, c->stream, &c->n_launches));
-      SCUDA(cudaEventRecord(ev1, c->stream));
-      SCUDA(cudaEventSynchronize(ev1));
-      float ms = 0.0f;
-      SCUDA(cudaEventElapsedTime(&ms, ev0, ev1));
-      learn_ms += ms;
-      ++learn_rounds;
-      st->P.learn_out = N.out;
-    }
-    void* args[] = {(void*)&L, (void*)&S, (void*)&c->B, (void*)&st->P};
-    SCUDA(cudaEventRecord(ev0, c->stream));
-    SCUDA(cudaLaunchCooperativeKernel(kern, dim3(S.n_ctas), dim3(threads), args, smem, c->stream));
-    SCUDA(cudaEventRecord(ev1, c->stream));
-    SCUDA(cudaMemcpyAsync(&gh, st->P.g, sizeof(gh), cudaMemcpyDeviceToHost, c->stream));
-    SCUDA(cudaStreamSynchronize(c->stream));
-    {
-      float ms = 0.0f;
-      SCUDA(cudaEventElapsedTime(&ms, ev0, ev1));
-      persistent_ms += ms;
-      ++persistent_launches;
-      ++c->n_launches;
-    }
-    if (gh.error) return fail(c, gh.error, gh.error == SWIG_E_TIMEOUT ? "a bounded device wait expired" : "device error");
-    c->d2h_bytes += sizeof(gh);
-    if (gh.n_dead > 0) {
-      c->d2h_bytes += (size_t)gh.n_dead * (nd + 2) * sizeof(double);
-      const size_t n0 = dl.size();
-      du.resize((n0 + gh.n_dead) * nd);
-      dl.resize(n0 + gh.n_dead);
-      dw.resize(n0 + gh.n_dead);
-      SCUDA(cudaMemcpy(du.data() + n0 * nd, st->P.dead_u, sizeof(double) * gh.n_dead * nd, cudaMemcpyDeviceToHost));
-      SCUDA(cudaMemcpy(dl.data() + n0, st->P.dead_logl, sizeof(double) * gh.n_dead, cudaMemcpyDeviceToHost));
-      SCUDA(cudaMemcpy(dw.data() + n0, st->P.dead_logw, sizeof(double) * gh.n_dead, cudaMemcpyDeviceToHost));
-    }
-    total_iters = gh.iter;
-    if (gh.status == ST_TERMINATED) break;
-    if (total_iters >= c->cfg.max_iter) break;
+
+  R.kern = het ? pick_het_kernel(L.n_det) : pick_kernel(L.n_det, mixed);
+  R.threads = het ? kHetThreads : kFlowThreads;
+  if (R.learned) SCUDA(mlp_init(*c->mlp, c->cfg.seed ^ 0x4D4C5050ull, c->stream, &c->n_launches));
+  R.du.clear();
+  R.dl.clear();
+  R.dw.clear();
+  R.total_iters = 0;
+  R.finished = false;
+  return SWIG_OK;
+}
+
+// Reset the per-launch counters of the NS state before a launch.
+int run_reset(swig_ctx* c, RunState& R) {
+  NSGlobal gl;
+  SCUDA(cudaMemcpyAsync(&gl, R.st->P.g, sizeof(gl), cudaMemcpyDeviceToHost, c->stream));
+  SCUDA(cudaStreamSynchronize(c->stream));
+  gl.iters_launch = 0;
+  gl.n_dead = 0;
+  gl.status = ST_RUNNING;
+  gl.error = 0;
+  gl.bar_count = 0;
+  SCUDA(cudaMemcpyAsync(R.st->P.g, &gl, sizeof(gl), cudaMemcpyHostToDevice, c->stream));
+  return SWIG_OK;
+}
+
+// After a launch: the NS state, its dead points, and whether the run is over.
+int run_collect(swig_ctx* c, RunState& R) {
+  SCUDA(cudaMemcpyAsync(&R.gh, R.st->P.g, sizeof(R.gh), cudaMemcpyDeviceToHost, c->stream));
+  SCUDA(cudaStreamSynchronize(c->stream));
+  const NSGlobal& gh = R.gh;
+  if (gh.error) return fail(c, gh.error, gh.error == SWIG_E_TIMEOUT ? "a bounded device wait expired" : "device error");
+  c->d2h_bytes += sizeof(gh);
+  const int nd = R.nd;
+  if (gh.n_dead > 0) {
+    c->d2h_bytes += (size_t)gh.n_dead * (nd + 2) * sizeof(double);
+    const size_t n0 = R.dl.size();
+    R.du.resize((n0 + gh.n_dead) * nd);
+    R.dl.resize(n0 + gh.n_dead);
+    R.dw.resize(n0 + gh.n_dead);
+    SCUDA(cudaMemcpy(R.du.data() + n0 * nd, R.st->P.dead_u, sizeof(double) * gh.n_dead * nd, cudaMemcpyDeviceToHost));
+    SCUDA(cudaMemcpy(R.dl.data() + n0, R.st->P.dead_logl, sizeof(double) * gh.n_dead, cudaMemcpyDeviceToHost));
+    SCUDA(cudaMemcpy(R.dw.data() + n0, R.st->P.dead_logw, sizeof(double) * gh.n_dead, cudaMemcpyDeviceToHost));
   }
+  R.total_iters = gh.iter;
+  R.finished = gh.status == ST_TERMINATED || R.total_iters >= c->cfg.max_iter;
+  return SWIG_OK;
+}
+
+// Final live points, the samples' parameters (and post-hoc distances), the
+// result and the profile counters.
+int run_finish(swig_ctx* c, RunState& R, swig_result* out) {
+  const int m = R.m, k = R.k, nd = R.nd;
+  const bool mixed = R.mixed, het = R.het;
+  const LikeConst& L = c->L;
+  const SamplerConst& S = R.S;
+  SamplerState* st = R.st;
+  const NSGlobal& gh = R.gh;
+  std::vector<double>& du = R.du;
+  std::vector<double>& dl = R.dl;
+  std::vector<double>& dw = R.dw;
   // final live points, X/m each
   std::vector<double> lu((size_t)m * nd), ll(m);
   SCUDA(cudaMemcpy(lu.data(), st->P.live_u, sizeof(double) * lu.size(), cudaMemcpyDeviceToHost));
@@ -1658,7 +1871,7 @@ int swig_run(swig_ctx* c, swig_result* out) {
   out->logz_err = std::sqrt(std::max(info, 0.0) / m);
   out->ess = sum_p2 > 0 ? 1.0 / sum_p2 : 0.0;
   out->n_dead = (int64_t)n_dead;
-  out->n_iter = total_iters;
+  out->n_iter = R.total_iters;
   // evaluations: the initial m plus the chains' counters accumulated on device
   long long ne = m, nf = m;
   for (const ChainState& q : ch) {
@@ -1668,7 +1881,7 @@ int swig_run(swig_ctx* c, swig_result* out) {
   out->n_evals = ne;
   out->n_sweep_evals = nf;
   out->status = gh.status == ST_TERMINATED ? 0 : 1;
-  out->wall_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
+  out->wall_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - R.t_start).count();
   c->last = *out;
   c->profile[0] = (double)gh.rounds;
   c->profile[1] = gh.t_bound * 1e-9;
@@ -1676,8 +1889,8 @@ int swig_run(swig_ctx* c, swig_result* out) {
   c->profile[3] = gh.t_wait_ctrl * 1e-9;
   c->profile[4] = gh.t_sweep * 1e-9;
   c->profile[5] = gh.t_wait_sweep * 1e-9;
-  c->profile[6] = persistent_ms;
-  c->profile[7] = (double)persistent_launches;
+  c->profile[6] = R.persistent_ms;
+  c->profile[7] = (double)R.persistent_launches;
   c->profile[8] = (double)c->n_launches;
   c->profile[9] = (double)c->h2d_bytes;
   c->profile[10] = (double)c->d2h_bytes;
@@ -1691,13 +1904,222 @@ int swig_run(swig_ctx* c, swig_result* out) {
   c->profile[17] = (double)gh.n_free;
   c->profile[18] = (double)gh.n_setup;
   c->profile[19] = (double)gh.n_step;
-  c->profile[20] = learn_ms;
-  c->profile[21] = (double)learn_rounds;
+  c->profile[20] = R.learn_ms;
+  c->profile[21] = (double)R.learn_rounds;
   c->profile[22] = (double)gh.f_units;
   c->profile[23] = (double)gh.f_unit_cyc;
   c->profile[24] = (double)gh.f_idle_cyc;
+  return SWIG_OK;
+}
+
+// The persistent launches of one run until termination or the iteration cap.
+int run_loop_single(swig_ctx* c, RunState& R) {
+  int rc = SWIG_OK;
+  SCUDA(cudaFuncSetAttribute(R.kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)R.smem));
+  int per_sm = 0;
+  SCUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, R.kern, R.threads, R.smem));
+  if (per_sm < 1 || R.S.n_ctas > per_sm * c->sm_count)
+    return fail(c, SWIG_E_CUDA, "persistent kernel cannot be co-resident on this device");
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  SCUDA(cudaEventCreate(&ev0));
+  SCUDA(cudaEventCreate(&ev1));
+  while (!R.finished) {
+    if ((rc = run_reset(c, R))) break;
+    if (R.learned) {
+      // retrain on the current live set, then freeze the output rows of
+      // this snapshot for the launch's iterations
+      Mlp& N = *c->mlp;
+      cudaError_t e = cudaEventRecord(ev0, c->stream);
+      if (e == cudaSuccess) e = mlp_targets(N, R.st->P.live_u, R.m, R.nd, 2 * R.nd, c->stream, &c->n_launches);
+      if (e == cudaSuccess)
+        e = mlp_train(N, R.m, R.nd, R.learn_rounds == 0 ? 4 * R.learn_steps : R.learn_steps, R.learn_lr, c->stream,
+                      &c->n_launches);
+      if (e == cudaSuccess) e = mlp_forward(N, R.m, c->stream, &c->n_launches);
+      if (e == cudaSuccess) e = cudaEventRecord(ev1, c->stream);
+      if (e == cudaSuccess) e = cudaEventSynchronize(ev1);
+      float ms = 0.0f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ev0, ev1);
+      if (e != cudaSuccess) {
+        rc = fail(c, SWIG_E_CUDA, std::string("learned proposal training: ") + cudaGetErrorString(e));
+        break;
+      }
+      R.learn_ms += ms;
+      ++R.learn_rounds;
+      R.st->P.learn_out = N.out;
+    }
+    void* args[] = {(void*)&c->L, (void*)&R.S, (void*)&c->B, (void*)&R.st->P};
+    cudaError_t e = cudaEventRecord(ev0, c->stream);
+    if (e == cudaSuccess)
+      e = cudaLaunchCooperativeKernel(R.kern, dim3(R.S.n_ctas), dim3(R.threads), args, R.smem, c->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(ev1, c->stream);
+    if (e == cudaSuccess) e = cudaEventSynchronize(ev1);
+    float ms = 0.0f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ev0, ev1);
+    if (e != cudaSuccess) {
+      rc = fail(c, SWIG_E_CUDA, std::string("persistent launch: ") + cudaGetErrorString(e));
+      break;
+    }
+    R.persistent_ms += ms;
+    ++R.persistent_launches;
+    ++c->n_launches;
+    if ((rc = run_collect(c, R))) break;
+  }
   cudaEventDestroy(ev0);
   cudaEventDestroy(ev1);
+  return rc;
+}
+
+// Events of one campaign that can share a launch: full grid, mixed precision,
+// covariance proposal, the same detector count, chains per event and device.
+bool batchable(swig_ctx* const* ctxs, const std::vector<RunState>& R, int i0, int i1) {
+  for (int i = i0; i < i1; ++i) {
+    if (R[i].het || !R[i].mixed || R[i].learned) return false;
+    if (ctxs[i]->L.n_det != ctxs[i0]->L.n_det || R[i].k != R[i0].k || ctxs[i]->device != ctxs[i0]->device) return false;
+  }
+  return true;
+}
+
+// One group of events in k_ns_multi launches until every one is finished.
+int run_loop_multi(swig_ctx* const* ctxs, std::vector<RunState>& R, int i0, int i1) {
+  swig_ctx* c0 = ctxs[i0];
+  const int n_det = c0->L.n_det, k = R[i0].k;
+  // shared-memory layout: every event's slice data, then the per-warp records
+  // or the boundary's sort buffers
+  std::vector<int> off(i1 - i0);
+  size_t fixed = 0, tail = 0;
+  int grid = 1;
+  for (int i = i0; i < i1; ++i) {
+    off[i - i0] = (int)fixed;
+    fixed += R[i].fixed;
+    tail = std::max(tail, R[i].smem - R[i].fixed);
+    grid = std::max(grid, ctxs[i]->L.n_slices);
+  }
+  const size_t smem = fixed + tail;
+  void* kern = pick_multi_kernel(n_det);
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int per_sm = 0;
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kFlowThreads, smem);
+  if (e != cudaSuccess) return fail(c0, SWIG_E_CUDA, std::string("multi-event kernel set-up: ") + cudaGetErrorString(e));
+  if (per_sm < 1 || grid > per_sm * c0->sm_count)
+    return fail(c0, SWIG_E_CUDA, "multi-event persistent kernel cannot be co-resident on this device");
+  const int n_ctrl = std::max(1, std::min(4, ((i1 - i0) * k + grid - 1) / grid));
+  NSGlobal* gb = nullptr;
+  EventDesc* evd = nullptr;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  int rc = SWIG_OK;
+  e = cudaMalloc(&gb, sizeof(NSGlobal));
+  if (e == cudaSuccess) e = cudaMalloc(&evd, sizeof(EventDesc) * (i1 - i0));
+  if (e == cudaSuccess) e = cudaEventCreate(&ev0);
+  if (e == cudaSuccess) e = cudaEventCreate(&ev1);
+  std::vector<EventDesc> hd;
+  std::vector<int> idx;
+  while (e == cudaSuccess && rc == SWIG_OK) {
+    hd.clear();
+    idx.clear();
+    for (int i = i0; i < i1; ++i) {
+      if (R[i].finished) continue;
+      if ((rc = run_reset(ctxs[i], R[i]))) break;
+      EventDesc d;
+      d.L = ctxs[i]->L;
+      d.S = R[i].S;
+      d.B = ctxs[i]->B;
+      d.P = R[i].st->P;
+      d.smem_off = off[i - i0];
+      hd.push_back(d);
+      idx.push_back(i);
+    }
+    if (rc || hd.empty()) break;
+    for (int i : idx) {
+      e = cudaStreamSynchronize(ctxs[i]->stream);
+      if (e != cudaSuccess) break;
+    }
+    NSGlobal g0;
+    std::memset(&g0, 0, sizeof(g0));
+    if (e == cudaSuccess) e = cudaMemcpy(gb, &g0, sizeof(g0), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(evd, hd.data(), sizeof(EventDesc) * hd.size(), cudaMemcpyHostToDevice);
+    int n_ev = (int)hd.size();
+    int n_ctrl_arg = n_ctrl;
+    int dyn_off = (int)fixed;
+    void* args[] = {(void*)&evd, (void*)&n_ev, (void*)&gb, (void*)&n_ctrl_arg, (void*)&dyn_off};
+    if (e == cudaSuccess) e = cudaEventRecord(ev0, c0->stream);
+    if (e == cudaSuccess) e = cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(kFlowThreads), args, smem, c0->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(ev1, c0->stream);
+    if (e == cudaSuccess) e = cudaEventSynchronize(ev1);
+    float ms = 0.0f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ev0, ev1);
+    NSGlobal gh;
+    if (e == cudaSuccess) e = cudaMemcpy(&gh, gb, sizeof(gh), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) break;
+    if (gh.error) {
+      rc = fail(c0, gh.error, gh.error == SWIG_E_TIMEOUT ? "a bounded device wait expired" : "device error");
+      break;
+    }
+    for (int i : idx) {
+      R[i].persistent_ms += ms;  // the launch's wall time, shared by its events
+      ++R[i].persistent_launches;
+      if ((rc = run_collect(ctxs[i], R[i]))) break;
+    }
+    ++c0->n_launches;
+  }
+  if (e != cudaSuccess && rc == SWIG_OK)
+    rc = fail(c0, SWIG_E_CUDA, std::string("multi-event launch: ") + cudaGetErrorString(e));
+  if (gb) cudaFree(gb);
+  if (evd) cudaFree(evd);
+  if (ev0) cudaEventDestroy(ev0);
+  if (ev1) cudaEventDestroy(ev1);
+  return rc;
+}
+
+}  // namespace
+
+extern "C" {
+
+int swig_run(swig_ctx* c, swig_result* out) {
+  if (!c) return SWIG_E_ARG;
+  if (!out) return fail(c, SWIG_E_ARG, "null result pointer");
+  std::memset(out, 0, sizeof(*out));
+  RunState R;
+  int rc = run_setup(c, R);
+  if (!rc) rc = run_loop_single(c, R);
+  if (rc) return rc;
+  return run_finish(c, R, out);
+}
+
+int swig_run_batch(swig_ctx** ctxs, int n_ctx, swig_result* outs) {
+  if (!ctxs || !outs || n_ctx < 1) return SWIG_E_ARG;
+  for (int i = 0; i < n_ctx; ++i) {
+    if (!ctxs[i]) return SWIG_E_ARG;
+    for (int j = 0; j < i; ++j)
+      if (ctxs[j] == ctxs[i]) return fail(ctxs[i], SWIG_E_ARG, "a context appears twice in the batch");
+    std::memset(&outs[i], 0, sizeof(outs[i]));
+  }
+  std::vector<RunState> R(n_ctx);
+  for (int i = 0; i < n_ctx; ++i) {
+    const int rc = run_setup(ctxs[i], R[i]);
+    if (rc) return rc;
+  }
+  // greedy groups of consecutive events that share a launch: at most
+  // kMaxEvents, their chains within kMaxChains, their slices within the
+  // shared memory of one CTA
+  int i0 = 0;
+  while (i0 < n_ctx) {
+    int i1 = i0 + 1;
+    if (batchable(ctxs, R, i0, i0 + 1)) {
+      size_t fixed = R[i0].fixed, tail = R[i0].smem - R[i0].fixed;
+      while (i1 < n_ctx && i1 - i0 < kMaxEvents && batchable(ctxs, R, i0, i1 + 1) &&
+             (i1 + 1 - i0) * R[i0].k <= kMaxChains &&
+             fixed + R[i1].fixed + std::max(tail, R[i1].smem - R[i1].fixed) <= 220 * 1024) {
+        fixed += R[i1].fixed;
+        tail = std::max(tail, R[i1].smem - R[i1].fixed);
+        ++i1;
+      }
+    }
+    int rc = i1 - i0 == 1 ? run_loop_single(ctxs[i0], R[i0]) : run_loop_multi(ctxs, R, i0, i1);
+    if (rc) return rc;
+    for (int i = i0; i < i1; ++i)
+      if ((rc = run_finish(ctxs[i], R[i], &outs[i]))) return rc;
+    i0 = i1;
+  }
   return SWIG_OK;
 }
 

@@ -70,6 +70,7 @@ SIGNATURES = {
     "swig_loglike_batch_noalloc": (_c_int, [_vp, _vp, _c_i64, _vp, _vp]),
     "swig_get_samples": (_c_int, [_vp, _dp, _dp, _dp, _c_i64, ctypes.POINTER(_c_i64)]),
     "swig_set_sky_frame": (_c_int, [_vp, _c_int, _c_int]),
+    "swig_run_batch": (_c_int, [ctypes.POINTER(_vp), _c_int, ctypes.POINTER(SwigResult)]),
     "swig_mlp_init": (_c_int, [_vp, _c_u64, _fp]),
     "swig_mlp_forward": (_c_int, [_vp, _fp, _fp, _c_i64, _fp]),
     "swig_mlp_loss_grad": (_c_int, [_vp, _fp, _fp, _fp, _fp, _c_i64, _c_int, _dp, _fp]),
@@ -313,6 +314,22 @@ class Context:
         out = np.empty((n, 26), dtype=np.float32)
         self._check(self.lib.swig_mlp_train(self.h, _ptr(u), n, d, int(steps), float(lr), _fptr(p), _fptr(out)))
         return p, out
+
+
+def run_batch(contexts):
+    """Run a campaign of contexts (swig_run_batch); returns their RunResults."""
+    n = len(contexts)
+    arr = (_vp * n)(*[c.h for c in contexts])
+    res = (SwigResult * n)()
+    rc = load_library().swig_run_batch(arr, n, res)
+    if rc != SWIG_OK:
+        for c in contexts:
+            msg = c.lib.swig_last_error(c.h).decode()
+            if msg:
+                raise SwigError(rc, msg)
+        raise SwigError(rc, "swig_run_batch failed")
+    return [RunResult(r.logz, r.logz_err, r.info, r.ess, r.wall_s, r.n_dead, r.n_iter, r.n_evals, r.n_sweep_evals,
+                      r.status) for r in res]
 
 
 def context_for_workload(wl, data, psds, gmst, device=0, precision=PREC_MIXED, detectors=None):
