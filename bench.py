@@ -13,6 +13,8 @@ them) and wall-seconds per posterior (= ms_per_step / 1000).
   cfg2-het  cfg2 with the heterodyned likelihood, 5,000 bins (Sec. 3.4)
   cfg2-nss  cfg2 without Gibbs blocks (all sampled parameters in one block)
   cfg2-m3   cfg2 with M = 3 Gibbs sweeps per replacement (the paper's High-Res)
+  cfg4      one batch of the injection campaign: four 3-detector events of
+            32/64/128/256 s in one persistent launch (swig_run_batch)
   cfg1      4 s single detector, 4,017 bins, FP64, nlive 100
   cfg3      cfg1 data, heterodyned likelihood, 450 geometric bins, nlive 1000
 
@@ -60,6 +62,9 @@ WORKLOADS = {
                      text="unblocked nested slice sampling (one block of all sampled parameters), full grid, mixed"),
     "cfg2-m3": dict(event="cfg2", precision="mixed", likelihood="full", proposal="cov", sweeps=3,
                     text="plain SwiG, M = 3 Gibbs sweeps per replacement, full grid, mixed"),
+    "cfg4": dict(event="campaign", precision="mixed", likelihood="full", proposal="cov",
+                 text="campaign batch: 4 events (32/64/128/256 s, injections drawn from the prior, SNR 25) "
+                      "in one persistent launch, plain SwiG, full grid, mixed"),
     "cfg1": dict(event="cfg1", precision="fp64", likelihood="full", proposal="cov", nlive=100,
                  text="plain SwiG, full grid, FP64"),
     "cfg3": dict(event="cfg1", precision="mixed", likelihood="het", proposal="cov", nlive=1000, het_bins=450,
@@ -67,8 +72,24 @@ WORKLOADS = {
 }
 
 
+CAMPAIGN_SECONDS = (32, 64, 128, 256)
+
+
+def campaign_workloads(rank=0):
+    """The four events of one campaign batch: 3-detector BNS injections drawn
+    from the prior (seeds 1000 + i), segments of 32/64/128/256 s."""
+    import dataclasses
+    out = []
+    for i, T in enumerate(CAMPAIGN_SECONDS):
+        wl = si.config2(seed_index=10 + i + 100 * rank)
+        out.append(dataclasses.replace(wl, df=1.0 / T, name=f"campaign_{T}s"))
+    return out
+
+
 def make_workload(name):
     spec = WORKLOADS[name]
+    if spec["event"] == "campaign":
+        return campaign_workloads()[2], spec
     wl = si.config2() if spec["event"] == "cfg2" else si.config1(nlive=spec.get("nlive", 100))
     if spec.get("single_block"):
         for p in wl.params:
@@ -141,7 +162,111 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def run_campaign(args, rank, world):
+    """cfg4: each step is one batch of four posteriors in one persistent launch."""
+    import torch
+
+    from paper_2607_28265_gb300 import swig
+    from paper_2607_28265_gb300.workloads import build_context
+
+    torch.cuda.set_device(0 if world == 1 else int(os.environ.get("LOCAL_RANK", rank)))
+    spec = WORKLOADS["cfg4"]
+    wls = campaign_workloads(rank)
+    stream = torch.cuda.current_stream()
+    built = [build_context(wl) for wl in wls]
+    ctxs = [b[0] for b in built]
+    for ctx in ctxs:
+        ctx.set_stream(stream.cuda_stream)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def step():
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        res = swig.run_batch(ctxs)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return res, e0.elapsed_time(e1)
+
+    for _ in range(args.warmup):
+        step()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    launches0 = sum(c.profile()["kernel_launches"] for c in ctxs)
+    with ClockSampler(int(os.environ.get("LOCAL_RANK", 0))) as clocks:
+        out = [step() for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    launches = int(sum(c.profile()["kernel_launches"] for c in ctxs) - launches0)
+    total_ms = sum(ms for _, ms in out)
+    evals = sum(r.n_evals for res, _ in out for r in res)
+    full = sum(r.n_sweep_evals for res, _ in out for r in res)
+    # end to end: data and PSDs from pinned host memory, the batch, the samples back
+    pinned = [[torch.from_numpy(np.ascontiguousarray(d)).pin_memory() for d in b[1]] for b in built]
+    pinned_psd = [[torch.from_numpy(np.ascontiguousarray(p)).pin_memory() for p in b[2]] for b in built]
+    h2d0 = sum(c.profile()["h2d_bytes"] for c in ctxs)
+    d2h0 = sum(c.profile()["d2h_bytes"] for c in ctxs)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for ctx, dd, pp in zip(ctxs, pinned, pinned_psd):
+        for i in range(len(dd)):
+            ctx.set_data(i, dd[i].numpy())
+            ctx.set_psd(i, pp[i].numpy())
+    res = swig.run_batch(ctxs)
+    for ctx in ctxs:
+        ctx.get_samples()
+    torch.cuda.synchronize()
+    e2e_ms = (time.perf_counter() - t0) * 1e3
+    e2e_evals = sum(r.n_evals for r in res)
+    h2d = sum(c.profile()["h2d_bytes"] for c in ctxs) - h2d0
+    d2h = sum(c.profile()["d2h_bytes"] for c in ctxs) - d2h0
+    t_local = np.array([total_ms, evals, e2e_ms, e2e_evals, full], dtype=np.float64)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor(t_local, device="cuda")
+        tmax, tsum = t.clone(), t.clone()
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+        dist.all_reduce(tsum, op=dist.ReduceOp.SUM)
+        total_ms_max, e2e_ms_max = float(tmax[0]), float(tmax[2])
+        evals_all, e2e_all, full_all = float(tsum[1]), float(tsum[3]), float(tsum[4])
+    else:
+        total_ms_max, e2e_ms_max = total_ms, e2e_ms
+        evals_all, e2e_all, full_all = evals, e2e_evals, full
+    if rank != 0:
+        return None
+    n_post = len(wls) * args.steps
+    bindet = sum(r.n_sweep_evals * 3 * wl.n_bins for res, _ in out for r, wl in zip(res, wls))
+    peak = SFU_OPS_PER_CLK_SM * 152 * 2070.0e6 / 1e12
+    achieved = SFU_OPS_PER_BIN_DET * bindet / (total_ms * 1e-3) / 1e12
+    line = {
+        "metric": METRIC, "value": evals_all / (total_ms_max * 1e-3), "unit": "logL evals/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms_max / args.steps,
+        "wall_s_per_posterior": total_ms_max / n_post / 1e3,
+        "full_grid_evals_per_s": full_all / (total_ms_max * 1e-3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "; ".join(f"{wl.name}: {wl.n_bins} bins/det" for wl in wls) + "; " + spec["text"],
+                   "name": "cfg4", "posteriors_per_step": len(wls), "l2": "flushed between steps (256 MB write)",
+                   "parallelism": f"replicas x{world}",
+                   "posteriors": [{"logz": r.logz, "logz_err": r.logz_err, "n_iter": r.n_iter} for r in out[-1][0]]},
+        "e2e": {"value": e2e_all / (e2e_ms_max * 1e-3), "unit": "logL evals/s", "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_ms_max},
+        "gpu_launches": launches,
+        "roofline": {"kernel": "k_ns_multi (campaign persistent kernel)", "bound": "alu", "achieved": achieved,
+                     "peak": peak, "unit": "SFU Top/s", "frac": achieved / peak, "traffic": None,
+                     "work_per_launch": "2 SFU ops x bin-detector evaluations of the four events",
+                     "timing": "CUDA events around each batch (the batch's persistent launches and host steps)",
+                     "peak_source": "16 sin/cos per clk per SM x 152 SMs x 2070 MHz (derived, not measured)"},
+        "clocks": clocks.summary(),
+    }
+    if args.cpu_baseline and world == 1:
+        line["cpu_baseline"] = cpu_baseline("cfg4", seconds=args.cpu_seconds,
+                                            evals_per_posterior=evals / max(1, n_post))
+    return line
+
+
 def run_gpu(args, rank, world):
+    if args.workload == "cfg4":
+        return run_campaign(args, rank, world)
     import torch
 
     from paper_2607_28265_gb300 import swig

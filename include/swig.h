@@ -225,9 +225,10 @@ int swig_prior_transform(swig_ctx* ctx, const double* u, int64_t n, double* thet
 int swig_run(swig_ctx* ctx, swig_result* out);
 /* Run nested sampling for a campaign of n_ctx events (config 4), each a
  * context set up as for swig_run; outs[i] receives event i's result and each
- * context keeps its samples.  Consecutive events that can share a launch (full
- * grid, mixed precision, covariance proposal, same detector count, chains and
- * device) run up to 4 at a time in one persistent launch: their slices of the
+ * context keeps its samples.  Events that can share a launch (full grid, mixed
+ * precision, covariance proposal, same detector count, chains and device) and
+ * whose grids are within 1.5x of each other (the events of a launch advance
+ * their iterations in step) run up to 4 at a time in one persistent launch: their slices of the
  * grid share each CTA's shared memory and their chains share the control and
  * sweep warps, which keeps the GPU busy while one event's chains wait.  Per
  * event the arithmetic and its order are those of swig_run, so the results

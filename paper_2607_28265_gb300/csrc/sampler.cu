@@ -2098,26 +2098,38 @@ int swig_run_batch(swig_ctx** ctxs, int n_ctx, swig_result* outs) {
     const int rc = run_setup(ctxs[i], R[i]);
     if (rc) return rc;
   }
-  // greedy groups of consecutive events that share a launch: at most
-  // kMaxEvents, their chains within kMaxChains, their slices within the
-  // shared memory of one CTA
+  // Events share a launch in groups of similar grid size: the events of a
+  // launch advance their NS iterations in step, so a short event grouped with
+  // a long one would wait for it.  Greedy groups over the events sorted by
+  // grid size: at most kMaxEvents, within 1.5x of the group's smallest grid,
+  // their chains within kMaxChains, their slices within one CTA's shared
+  // memory.
+  std::vector<int> order(n_ctx);
+  for (int i = 0; i < n_ctx; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return ctxs[a]->L.n_bins < ctxs[b]->L.n_bins; });
+  std::vector<swig_ctx*> oc(n_ctx);
+  std::vector<RunState> orr(n_ctx);
+  for (int i = 0; i < n_ctx; ++i) {
+    oc[i] = ctxs[order[i]];
+    orr[i] = R[order[i]];
+  }
   int i0 = 0;
   while (i0 < n_ctx) {
     int i1 = i0 + 1;
-    if (batchable(ctxs, R, i0, i0 + 1)) {
-      size_t fixed = R[i0].fixed, tail = R[i0].smem - R[i0].fixed;
-      while (i1 < n_ctx && i1 - i0 < kMaxEvents && batchable(ctxs, R, i0, i1 + 1) &&
-             (i1 + 1 - i0) * R[i0].k <= kMaxChains &&
-             fixed + R[i1].fixed + std::max(tail, R[i1].smem - R[i1].fixed) <= 220 * 1024) {
-        fixed += R[i1].fixed;
-        tail = std::max(tail, R[i1].smem - R[i1].fixed);
+    if (batchable(oc.data(), orr, i0, i0 + 1)) {
+      size_t fixed = orr[i0].fixed, tail = orr[i0].smem - orr[i0].fixed;
+      while (i1 < n_ctx && i1 - i0 < kMaxEvents && batchable(oc.data(), orr, i0, i1 + 1) &&
+             (i1 + 1 - i0) * orr[i0].k <= kMaxChains && oc[i1]->L.n_bins <= 1.5 * oc[i0]->L.n_bins &&
+             fixed + orr[i1].fixed + std::max(tail, orr[i1].smem - orr[i1].fixed) <= 220 * 1024) {
+        fixed += orr[i1].fixed;
+        tail = std::max(tail, orr[i1].smem - orr[i1].fixed);
         ++i1;
       }
     }
-    int rc = i1 - i0 == 1 ? run_loop_single(ctxs[i0], R[i0]) : run_loop_multi(ctxs, R, i0, i1);
+    int rc = i1 - i0 == 1 ? run_loop_single(oc[i0], orr[i0]) : run_loop_multi(oc.data(), orr, i0, i1);
     if (rc) return rc;
     for (int i = i0; i < i1; ++i)
-      if ((rc = run_finish(ctxs[i], R[i], &outs[i]))) return rc;
+      if ((rc = run_finish(oc[i], orr[i], &outs[order[i]]))) return rc;
     i0 = i1;
   }
   return SWIG_OK;
