@@ -1,6 +1,6 @@
-"""Matched-filter log-likelihood in FP64 (Sec. 3.1, Eq. 2), its phase- and
-distance-marginalised forms (Sec. 3.1) and its heterodyned approximation
-(Sec. 3.4).
+"""Matched-filter log-likelihood in FP64 (Sec. 3.1, Eq. 2), its phase-,
+distance- and time-marginalised forms (Sec. 3.1, App. A) and its heterodyned
+approximation (Sec. 3.4).
 
 Event layout: an ``Event`` holds the frequency grid, per-detector data d_i(f),
 PSDs S_i(f), detector geometry, GMST and the prior description.
@@ -291,16 +291,12 @@ def het_setup(ev: Event, theta_fid, n_bins, spacing="phase"):
     return Het(edges, centers, A0, A1, B0, B1, h0e, theta_fid)
 
 
-def het_loglike(ev: Event, het: Het, theta):
-    """Heterodyned logL: r = h/h0 linear in each bin, r0 at the centre, r1 slope.
+def het_overlap(ev: Event, het: Het, theta):
+    """Heterodyned complex overlap Z = sum_i sum_b (A0 r0 + A1 r1) and <h|h>.
 
-    <d|h> ~ Re sum_b (A0 r0 + A1 r1),  <h|h> ~ sum_b (B0 |r0|^2 + 2 B1 Re(r0 r1*)).
-    The phase-marginalised form uses the complex Z = sum_b (A0 r0 + A1 r1).
-    -1/2 <d|d> is the same constant as in the full likelihood.
+    r = h/h0 at the edges, taken linear in each bin: r0 the mean of the two
+    edge values (the value at the centre), r1 the slope.
     """
-    theta = np.asarray(theta, dtype=np.float64).copy()
-    if ev.phase_marginalised:
-        theta[IDX["phic"]] = 0.0
     z = 0.0 + 0.0j
     hh = 0.0
     for i, det in enumerate(ev.detectors):
@@ -311,8 +307,113 @@ def het_loglike(ev: Event, het: Het, theta):
         r1 = (r[1:] - r[:-1]) / width
         z += complex(np.sum(het.A0[i] * r0 + het.A1[i] * r1))
         hh += float(np.sum(het.B0[i] * np.abs(r0) ** 2 + 2.0 * het.B1[i] * np.real(r0 * np.conj(r1))))
+    return z, hh
+
+
+def het_loglike(ev: Event, het: Het, theta):
+    """Heterodyned logL: r = h/h0 linear in each bin, r0 at the centre, r1 slope.
+
+    <d|h> ~ Re sum_b (A0 r0 + A1 r1),  <h|h> ~ sum_b (B0 |r0|^2 + 2 B1 Re(r0 r1*)).
+    The phase-marginalised form uses the complex Z = sum_b (A0 r0 + A1 r1).
+    -1/2 <d|d> is the same constant as in the full likelihood.
+    """
+    theta = np.asarray(theta, dtype=np.float64).copy()
+    if ev.phase_marginalised:
+        theta[IDX["phic"]] = 0.0
+    z, hh = het_overlap(ev, het, theta)
     dd = sum(inner_product(d, d, s, ev.df) for d, s in zip(ev.data, ev.psds))
     if ev.phase_marginalised:
         x = abs(z)
         return x + math.log(i0e(x)) - 0.5 * hh - 0.5 * dd
     return z.real - 0.5 * hh - 0.5 * dd
+
+
+# --------------------------------------------------------------------------
+# Time marginalisation (Sec. 3.1 and App. A): t_c summed over a grid of time
+# shifts, on the heterodyned bins (the direct sum) and, as its full-resolution
+# analogue, on the whole frequency grid.
+# --------------------------------------------------------------------------
+def time_grid(params, n_nodes):
+    """Midpoint nodes of the uniform t_c prior [lo, hi]:
+    t_j = lo + (j + 1/2) (hi - lo) / N_t, each carrying prior mass 1 / N_t."""
+    p = params[IDX["tc"]]
+    if p.kind != PRIOR_UNIFORM:
+        raise ValueError("time marginalisation needs a uniform t_c prior")
+    return p.lo + (np.arange(n_nodes) + 0.5) * ((p.hi - p.lo) / n_nodes)
+
+
+def _node_log_weight(ev: Event, z):
+    """The t_c-dependent part of logL at one node: log I0(|Z|) with phi_c
+    marginalised, Re Z otherwise."""
+    if ev.phase_marginalised:
+        x = np.abs(z)
+        return x + np.log(i0e(x))
+    return np.real(z)
+
+
+def het_time_overlaps(ev: Event, het: Het, theta, t_nodes):
+    """Z(t_j): the heterodyned overlap of the template moved to t_c = t_j, for
+    every node; and <h|h>, which a time shift leaves unchanged, taken once
+    with t_c at the fiducial's value."""
+    theta = np.asarray(theta, dtype=np.float64).copy()
+    if ev.phase_marginalised:
+        theta[IDX["phic"]] = 0.0
+    theta[IDX["tc"]] = het.theta_fid[IDX["tc"]]
+    _, hh = het_overlap(ev, het, theta)
+    z = np.empty(len(t_nodes), dtype=np.complex128)
+    for j, t in enumerate(t_nodes):
+        theta[IDX["tc"]] = t
+        z[j] = het_overlap(ev, het, theta)[0]
+    return z, hh
+
+
+def het_time_log_weights(ev: Event, het: Het, theta, n_nodes):
+    """log of the conditional weights of t_c on its grid (up to a constant)."""
+    z, _ = het_time_overlaps(ev, het, theta, time_grid(ev.params, n_nodes))
+    return _node_log_weight(ev, z)
+
+
+def het_loglike_time_marg(ev: Event, het: Het, theta, n_nodes):
+    """Heterodyned logL with t_c marginalised over its uniform prior:
+    log( (1/N_t) sum_j exp(logL_het(theta, t_c = t_j)) ), <h|h> at the
+    fiducial's t_c (the theta[tc] passed in is ignored)."""
+    t = time_grid(ev.params, n_nodes)
+    z, hh = het_time_overlaps(ev, het, theta, t)
+    ell = _node_log_weight(ev, z)
+    m = float(np.max(ell))
+    dd = sum(inner_product(d, d, s, ev.df) for d, s in zip(ev.data, ev.psds))
+    return m + math.log(float(np.sum(np.exp(ell - m)))) - math.log(n_nodes) - 0.5 * hh - 0.5 * dd
+
+
+def full_time_overlaps(ev: Event, theta, t_nodes):
+    """Full-grid Z(t_j) = sum_i 4 df sum_f d_i* h_i(t_c = t_j) / S_i and <h|h>."""
+    theta = np.asarray(theta, dtype=np.float64).copy()
+    if ev.phase_marginalised:
+        theta[IDX["phic"]] = 0.0
+    z = np.empty(len(t_nodes), dtype=np.complex128)
+    hh = None
+    for j, t in enumerate(t_nodes):
+        theta[IDX["tc"]] = t
+        hs = strains(ev, theta)
+        z[j] = sum(complex_overlap(d, h, s, ev.df) for d, h, s in zip(ev.data, hs, ev.psds))
+        if hh is None:
+            hh = sum(inner_product(h, h, s, ev.df) for h, s in zip(hs, ev.psds))
+    return z, hh
+
+
+def loglike_time_marg_full(ev: Event, theta, n_nodes):
+    """Full-resolution logL with t_c marginalised on the same midpoint grid."""
+    t = time_grid(ev.params, n_nodes)
+    z, hh = full_time_overlaps(ev, theta, t)
+    ell = _node_log_weight(ev, z)
+    m = float(np.max(ell))
+    dd = sum(inner_product(d, d, s, ev.df) for d, s in zip(ev.data, ev.psds))
+    return m + math.log(float(np.sum(np.exp(ell - m)))) - math.log(n_nodes) - 0.5 * hh - 0.5 * dd
+
+
+def draw_time_node(log_w, q):
+    """Index of the grid node drawn by the uniform q from weights exp(log_w):
+    the first node whose cumulative weight reaches q times the total."""
+    w = np.exp(np.asarray(log_w, dtype=np.float64) - np.max(log_w))
+    c = np.cumsum(w)
+    return int(min(np.searchsorted(c, q * c[-1], side="left"), len(c) - 1))
