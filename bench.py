@@ -11,6 +11,9 @@ them) and wall-seconds per posterior (= ms_per_step / 1000).
   cfg2      128 s H1/L1/V1 BNS, 259,585 bins/det, full grid, plain SwiG, mixed
   cfg5      cfg2 with the learned slice proposal (learned + mixed)
   cfg2-het  cfg2 with the heterodyned likelihood, 5,000 bins (Sec. 3.4)
+  cfg2-het-tm  cfg2-het with t_c marginalised on 2,000 grid nodes over its
+            prior and d_L sampled (Sec. 3.1, App. A; the paper's
+            recommended configuration)
   cfg2-nss  cfg2 without Gibbs blocks (all sampled parameters in one block)
   cfg2-m3   cfg2 with M = 3 Gibbs sweeps per replacement (the paper's High-Res)
   cfg4      one batch of the injection campaign: four 3-detector events of
@@ -58,6 +61,10 @@ WORKLOADS = {
                  text="learned slice proposal (MLP 13-256-256-26, BF16/FP32) + covariance, full grid, mixed"),
     "cfg2-het": dict(event="cfg2", precision="mixed", likelihood="het", proposal="cov", het_bins=5000,
                      het_spacing=0, text="plain SwiG, heterodyned likelihood, 5000 bins of equal phase change"),
+    "cfg2-het-tm": dict(event="cfg2", precision="mixed", likelihood="het", proposal="cov", het_bins=5000,
+                        het_spacing=0, tmarg_nodes=2000,
+                        text="plain SwiG, heterodyned likelihood (5000 bins of equal phase change), t_c "
+                             "marginalised on 2000 nodes over its +-0.1 s prior, d_L sampled"),
     "cfg2-nss": dict(event="cfg2", precision="mixed", likelihood="full", proposal="cov", single_block=True,
                      text="unblocked nested slice sampling (one block of all sampled parameters), full grid, mixed"),
     "cfg2-m3": dict(event="cfg2", precision="mixed", likelihood="full", proposal="cov", sweeps=3,
@@ -97,6 +104,14 @@ def make_workload(name):
                 p.block = 0
     wl.sweeps = spec.get("sweeps", 1)
     return wl, spec
+
+
+def tmarg_params(wl):
+    """The workload's prior with t_c marginalised over the same uniform range."""
+    params = list(wl.params)
+    p = params[si.IDX["tc"]]
+    params[si.IDX["tc"]] = si.Param(si.PRIOR_UNIFORM, p.lo, p.hi, si.MODE_MARG)
+    return params
 
 
 def workload_description(wl, spec):
@@ -277,12 +292,15 @@ def run_gpu(args, rank, world):
     prec = swig.PREC_FP64 if spec["precision"] == "fp64" else swig.PREC_MIXED
     ctx, data, psds, th_inj = build_context(wl, seed_offset=1000 * rank, precision=prec)
     het = spec["likelihood"] == "het"
+    n_tm = spec.get("tmarg_nodes", 0)
+    if n_tm:
+        ctx.set_prior(tmarg_params(wl))  # the same event, t_c now marginalised
     ctx.set_sampler(nlive=wl.nlive, nrep=wl.nrep, sweeps=wl.sweeps, steps_per_dim=wl.steps_per_dim,
                     seed=wl.sampler_seed + 1000 * rank, precision=prec,
                     likelihood=swig.LIKE_HET if het else swig.LIKE_FULL,
                     proposal=swig.PROPOSAL_LEARNED if spec["proposal"] == "learned" else swig.PROPOSAL_COV,
                     het_bins=spec.get("het_bins", 0), het_spacing=spec.get("het_spacing", 0),
-                    het_fiducial=th_inj if het else None)
+                    het_fiducial=th_inj if het else None, tmarg_nodes=n_tm)
     stream = torch.cuda.current_stream()
     ctx.set_stream(stream.cuda_stream)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # > L2 (129 MB)
@@ -406,6 +424,19 @@ def run_gpu(args, rank, world):
         },
         "clocks": clk,
     }
+    if n_tm:
+        # the time pass dominates: per full evaluation and (edge, node) pair one
+        # complex add and one complex rotation, 6 FP32-pipe instructions
+        ops = 6.0 * (spec["het_bins"] + 1) * n_tm * full_evals
+        peak32 = 128 * 152 * sm_mhz_max * 1e6 / 1e12
+        line["roofline"].update({
+            "kernel": "k_ns_het (persistent SwiG kernel, heterodyned, time-marginalised)",
+            "bound": "alu", "achieved": ops / (pers_ms * 1e-3) / 1e12 if pers_ms > 0 else 0.0, "peak": peak32,
+            "unit": "FP32-pipe Top/s", "traffic": None,
+            "work_per_launch": (f"6 FP32 ops x (edge, node) pairs x full evaluations ({spec['het_bins'] + 1} edges x "
+                                f"{n_tm} nodes)"),
+            "peak_source": "128 FP32 lanes per clk per SM x 152 SMs x 2070 MHz (derived, not measured)"})
+        line["roofline"]["frac"] = line["roofline"]["achieved"] / peak32
     if args.cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(args.workload, seconds=args.cpu_seconds,
                                             evals_per_posterior=total_evals / max(1, args.steps))
@@ -429,16 +460,19 @@ def _worker_init(name):
     from oracle import likelihood as L
     wl, spec = make_workload(name)
     ev, th = events.build_event(wl)
+    if spec.get("tmarg_nodes"):
+        ev = L.Event(ev.freqs, ev.df, ev.data, ev.psds, ev.detectors, ev.gmst, tmarg_params(wl))
+        wl.params = ev.params
     het = L.het_setup(ev, th, spec["het_bins"], spacing="phase" if spec.get("het_spacing", 0) == 0 else "geometric") \
         if spec["likelihood"] == "het" else None
-    _EV = (wl, ev, het)
+    _EV = (wl, ev, het, spec.get("tmarg_nodes", 0))
 
 
 def _worker_evals(args):
     seed, n = args
     from oracle import likelihood as L
     from oracle import physics
-    wl, ev, het = _EV
+    wl, ev, het, n_tm = _EV
     rng = np.random.default_rng(seed)
     ns = len(wl.sampled())
     t0 = time.perf_counter()
@@ -446,6 +480,8 @@ def _worker_evals(args):
         t = physics.prior_transform(rng.random(ns), wl.params)[0]
         if het is None:
             L.loglike(ev, t)
+        elif n_tm:
+            L.het_loglike_time_marg(ev, het, t, n_tm)
         else:
             L.het_loglike(ev, het, t)
     return n, time.perf_counter() - t0
@@ -481,6 +517,8 @@ def _sample_text(name, total, cores, extra):
     wl, spec = make_workload(name)
     what = (f"heterodyned logL ({spec['het_bins']} bins)" if spec["likelihood"] == "het"
             else f"logL on the full {len(wl.detectors)} x {wl.n_bins}-bin grid")
+    if spec.get("tmarg_nodes"):
+        what += f" with t_c marginalised on {spec['tmarg_nodes']} nodes"
     return f"{total} FP64 oracle evaluations of {what} at prior draws, {cores} spawned processes, {extra}"
 
 

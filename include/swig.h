@@ -54,7 +54,7 @@ enum swig_prior_kind {       /* Table I prior families, on [lo, hi]          */
 enum swig_param_mode {
   SWIG_MODE_SAMPLE = 0,      /* sampled by the Gibbs kernel                  */
   SWIG_MODE_FIXED = 1,       /* held at `value`                              */
-  SWIG_MODE_MARG = 2         /* marginalised analytically (phi_c only)       */
+  SWIG_MODE_MARG = 2         /* marginalised (phi_c, d_L or t_c; see below)  */
 };
 enum swig_likelihood { SWIG_LIKE_FULL = 0, SWIG_LIKE_HET = 1 };
 enum swig_precision { SWIG_PREC_FP64 = 0, SWIG_PREC_MIXED = 1 };
@@ -92,6 +92,12 @@ typedef struct swig_sampler_cfg {
   double learn_lr;      /* Adam learning rate [1e-3]                     */
   int learn_steps;      /* Adam steps per retraining [50; 4x at start]   */
   int learn_interval;   /* NS iterations between retrainings [8]         */
+  /* t_c marginalised (slot 11 SWIG_MODE_MARG; heterodyned likelihood only,
+   * het_bins <= 16384): nodes of the midpoint grid over the uniform t_c
+   * prior [lo, hi], t_j = lo + (j + 1/2)(hi - lo)/tmarg_nodes, 1..65536.
+   * The spacing should resolve the t_c posterior (its width is roughly
+   * 1 / (2 pi SNR sigma_f), sigma_f the spread of the signal's frequencies). */
+  int tmarg_nodes;
 } swig_sampler_cfg;
 
 typedef struct swig_result {
@@ -131,8 +137,13 @@ int swig_set_data(swig_ctx* ctx, int det, const double* re_im, int64_t n);
  * all finite and > 0, else SWIG_E_NUMERIC). */
 int swig_set_psd(swig_ctx* ctx, int det, const double* psd, int64_t n);
 /* Prior: exactly SWIG_N_PARAMS slots (Table I).  Requires lo < hi for sampled
- * slots; only phi_c may be SWIG_MODE_MARG (closed-form phase marginalisation,
- * Sec. 3.1). */
+ * slots.  Three slots may be SWIG_MODE_MARG (Sec. 3.1, App. A): phi_c (slot
+ * 12, closed-form log I0), d_L (slot 6, uniform or power-law-2 prior on
+ * 0 < lo < hi, quadrature; full-grid likelihood only) and t_c (slot 11,
+ * uniform prior, grid sum over tmarg_nodes time shifts; heterodyned
+ * likelihood only).  The likelihood ignores the theta value of a
+ * marginalised slot; the sampler's returned samples carry a post-hoc draw
+ * from its conditional for d_L and t_c.  Bad kinds or ranges -> SWIG_E_ARG. */
 int swig_set_prior(swig_ctx* ctx, const swig_param* params, int n_params);
 /* Sampler configuration (Table II); validated here (nlive > nrep >= 1, ...). */
 int swig_set_sampler(swig_ctx* ctx, const swig_sampler_cfg* cfg);

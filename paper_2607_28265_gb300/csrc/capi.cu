@@ -223,6 +223,8 @@ void free_problem(DeviceBuffers& B) {
   dfree(B.het_coef);
   dfree(B.het_coefB);
   dfree(B.het_fid);
+  dfree(B.het_tm_g);
+  dfree(B.het_tm_w);
   B.het_nb = 0;
 }
 
@@ -334,6 +336,7 @@ int prepare_het(swig_ctx* c) {
   // summary data per detector and bin
   std::vector<float4> coef((size_t)n_det * nb);
   std::vector<float2> coefB((size_t)n_det * nb);
+  std::vector<double> a01((size_t)n_det * nb * 4);  // FP64 (A0.re, A0.im, A1.re, A1.im) for the edge weights
   std::vector<float> inv_w(nb);
   for (int b = 0; b < nb; ++b) inv_w[b] = (float)(1.0 / (f[idx[b + 1]] - f[idx[b]]));
   for (int i = 0; i < n_det; ++i) {
@@ -355,6 +358,11 @@ int prepare_het(swig_ctx* c) {
         b1.add(hh * off);
       }
       coef[(size_t)i * nb + b] = make_float4((float)a0r.value(), (float)a0i.value(), (float)a1r.value(), (float)a1i.value());
+      double* a = &a01[((size_t)i * nb + b) * 4];
+      a[0] = a0r.value();
+      a[1] = a0i.value();
+      a[2] = a1r.value();
+      a[3] = a1i.value();
       coefB[(size_t)i * nb + b] = make_float2((float)b0.value(), (float)b1.value());
     }
   }
@@ -382,6 +390,38 @@ int prepare_het(swig_ctx* c) {
   CUDA_TRY(c, cudaMemcpy(B.het_coefB, coefB.data(), sizeof(float2) * coefB.size(), cudaMemcpyHostToDevice));
   c->h2d_bytes += sizeof(float) * (eb.size() + ef.size() + inv_w.size()) + sizeof(float4) * coef.size() +
                   sizeof(float2) * coefB.size();
+  if (L.tm_n > 0) {
+    // edge weights g_ie (the bin above contributes A0/2 - A1/w, the bin below
+    // A0/2 + A1/w) and the rotation of each edge per grid step, in FP64
+    std::vector<float2> g((size_t)n_det * ne), w(ne);
+    for (int i = 0; i < n_det; ++i)
+      for (int q = 0; q <= nb; ++q) {
+        double gr = 0.0, gi = 0.0;
+        if (q < nb) {
+          const double* a = &a01[((size_t)i * nb + q) * 4];
+          const double iw = 1.0 / (f[idx[q + 1]] - f[idx[q]]);
+          gr += 0.5 * a[0] - a[2] * iw;
+          gi += 0.5 * a[1] - a[3] * iw;
+        }
+        if (q > 0) {
+          const double* a = &a01[((size_t)i * nb + q - 1) * 4];
+          const double iw = 1.0 / (f[idx[q]] - f[idx[q - 1]]);
+          gr += 0.5 * a[0] + a[2] * iw;
+          gi += 0.5 * a[1] + a[3] * iw;
+        }
+        g[(size_t)i * ne + q] = make_float2((float)gr, (float)gi);
+      }
+    for (int q = 0; q <= nb; ++q) {
+      double ph = f[idx[q]] * L.tm_dt;
+      ph -= std::nearbyint(ph);
+      w[q] = make_float2((float)std::cos(2.0 * kPi * ph), (float)-std::sin(2.0 * kPi * ph));
+    }
+    CUDA_TRY(c, cudaMalloc(&B.het_tm_g, sizeof(float2) * g.size()));
+    CUDA_TRY(c, cudaMalloc(&B.het_tm_w, sizeof(float2) * w.size()));
+    CUDA_TRY(c, cudaMemcpy(B.het_tm_g, g.data(), sizeof(float2) * g.size(), cudaMemcpyHostToDevice));
+    CUDA_TRY(c, cudaMemcpy(B.het_tm_w, w.data(), sizeof(float2) * w.size(), cudaMemcpyHostToDevice));
+    c->h2d_bytes += sizeof(float2) * (g.size() + w.size());
+  }
   B.het_nb = nb;
   return SWIG_OK;
 }
@@ -479,6 +519,22 @@ int prepare(swig_ctx* c) {
   }
   if (L.dist_marg && c->cfg_set && c->cfg.likelihood == SWIG_LIKE_HET)
     return fail(c, SWIG_E_ARG, "distance marginalisation is implemented for the full-grid likelihood only");
+  if (c->prior_set && c->params[11].mode == SWIG_MODE_MARG) {
+    // time marginalisation: midpoint grid over the uniform t_c prior, templates
+    // at the fiducial's t_c shifted to each node (heterodyned bins only)
+    if (!c->cfg_set || c->cfg.likelihood != SWIG_LIKE_HET)
+      return fail(c, SWIG_E_ARG, "time marginalisation is implemented for the heterodyned likelihood only");
+    if (c->cfg.tmarg_nodes < 1) return fail(c, SWIG_E_ARG, "time marginalisation needs tmarg_nodes >= 1");
+    if (c->cfg.het_bins > kMaxTmBins) return fail(c, SWIG_E_ARG, "time marginalisation supports at most 16384 heterodyned bins");
+    if (!std::isfinite(c->cfg.het_fiducial[11])) return fail(c, SWIG_E_ARG, "non-finite fiducial t_c");
+    const swig_param& p = c->params[11];
+    c->params[11].value = c->cfg.het_fiducial[11];
+    L.tm_n = c->cfg.tmarg_nodes;
+    L.tm_lo = p.lo;
+    L.tm_dt = (p.hi - p.lo) / L.tm_n;
+    L.tm_tref = c->cfg.het_fiducial[11];
+    L.tm_t0 = L.tm_lo + 0.5 * L.tm_dt - L.tm_tref;
+  }
   const int prec = current_precision(c);
   L.fast_epilogue = prec == SWIG_PREC_MIXED ? 1 : 0;
 
@@ -808,8 +864,11 @@ int swig_set_prior(swig_ctx* c, const swig_param* params, int n_params) {
   for (int i = 0; i < SWIG_N_PARAMS; ++i) {
     const swig_param& p = params[i];
     if (p.mode < 0 || p.mode > 2 || p.kind < 0 || p.kind > 3) return fail(c, SWIG_E_ARG, "bad prior kind or mode in slot " + std::to_string(i));
-    if (p.mode == SWIG_MODE_MARG && i != 12 && i != 6)
-      return fail(c, SWIG_E_ARG, "only d_L (slot 6) and phi_c (slot 12) can be marginalised");
+    if (p.mode == SWIG_MODE_MARG && i != 12 && i != 6 && i != 11)
+      return fail(c, SWIG_E_ARG, "only d_L (slot 6), t_c (slot 11) and phi_c (slot 12) can be marginalised");
+    if (p.mode == SWIG_MODE_MARG && i == 11 &&
+        (p.kind != SWIG_PRIOR_UNIFORM || !std::isfinite(p.lo) || !std::isfinite(p.hi) || !(p.hi > p.lo)))
+      return fail(c, SWIG_E_ARG, "a marginalised t_c needs a uniform prior with lo < hi");
     if (p.mode == SWIG_MODE_MARG && i == 6 &&
         (!(p.lo > 0.0) || !(p.hi > p.lo) || !std::isfinite(p.hi) ||
          (p.kind != SWIG_PRIOR_UNIFORM && p.kind != SWIG_PRIOR_POWER2)))
@@ -826,6 +885,8 @@ int swig_set_prior(swig_ctx* c, const swig_param* params, int n_params) {
   // a marginalised slot is evaluated at a fixed value: phi_c = 0, d_L = 1 Mpc
   if (c->params[12].mode == SWIG_MODE_MARG) c->params[12].value = 0.0;
   if (c->params[6].mode == SWIG_MODE_MARG) c->params[6].value = 1.0;
+  // t_c marginalised: templates at the heterodyne fiducial's t_c
+  if (c->params[11].mode == SWIG_MODE_MARG) c->params[11].value = c->cfg_set ? c->cfg.het_fiducial[11] : 0.0;
   c->prior_set = true;
   c->n_sampled = n_sampled;
   c->dirty = true;
@@ -844,13 +905,16 @@ int swig_set_sampler(swig_ctx* c, const swig_sampler_cfg* cfg) {
   if (cfg->likelihood == SWIG_LIKE_HET && (cfg->het_bins < 2 || cfg->het_bins > 65536)) return fail(c, SWIG_E_ARG, "het_bins must be in [2, 65536]");
   if (cfg->het_spacing != 0 && cfg->het_spacing != 1) return fail(c, SWIG_E_ARG, "het_spacing must be 0 or 1");
   if (!(cfg->dlogz < 0.0) || cfg->max_iter < 1) return fail(c, SWIG_E_ARG, "need dlogz < 0 and max_iter >= 1");
+  if (cfg->tmarg_nodes < 0 || cfg->tmarg_nodes > kMaxTmNodes) return fail(c, SWIG_E_ARG, "tmarg_nodes must be in [0, 65536]");
   if (c->cfg_set && (c->cfg.precision != cfg->precision || c->cfg.likelihood != cfg->likelihood ||
                      c->cfg.het_bins != cfg->het_bins || c->cfg.het_spacing != cfg->het_spacing ||
+                     c->cfg.tmarg_nodes != cfg->tmarg_nodes ||
                      std::memcmp(c->cfg.het_fiducial, cfg->het_fiducial, sizeof(cfg->het_fiducial)) != 0))
     c->dirty = true;
   if (!c->cfg_set) c->dirty = true;
   c->cfg = *cfg;
   c->cfg_set = true;
+  if (c->prior_set && c->params[11].mode == SWIG_MODE_MARG) c->params[11].value = cfg->het_fiducial[11];
   return SWIG_OK;
 }
 

@@ -11,6 +11,16 @@
 // edge is a double-float sum of (c_j - c0_j) phi_j(f_e) (it can reach hundreds
 // of cycles far from the fiducial); the contraction itself is FP32 per bin with
 // a pairwise (warp-shuffle) reduction and an FP64 epilogue.
+//
+// Time marginalisation (t_c marginalised, Sec. 3.1 and App. A).  Z_i is
+// linear in the edge values, Z_i = sum_e g_ie r_i(e) with hat-function weights
+// g_ie = (A0_ib/2 - A1_ib/w_b) from the bin above the edge plus
+// (A0_ib/2 + A1_ib/w_b) from the bin below.  A common geocentric shift dt
+// multiplies r_i(e) by exp(-2 pi i f_e dt) in every detector, so the network
+// overlap at a grid node is one sum over edges,
+//   Z(dt_j) = sum_e y_e exp(-2 pi i f_e dt_j),   y_e = sum_i g_ie r_i(e),
+// with the templates built at the fiducial's t_c.  <h|h> is the same at every
+// node (a time shift only rotates h) and is taken there once.
 #pragma once
 
 #include "device_common.cuh"
@@ -25,6 +35,8 @@ struct HetTables {
   const float4* coef;         // [n_det][N_b] (A0.re, A0.im, A1.re, A1.im)
   const float2* coefB;        // [n_det][N_b] (B0, B1)
   const EvalRecord* fid;      // fiducial record
+  const float2* tm_g;         // [n_det][N_b + 1] time marginalisation: edge weights g_ie
+  const float2* tm_w;         // [N_b + 1] exp(-2 pi i f_e dt), one grid step
 };
 
 __host__ __device__ inline HetTables het_tables(const DeviceBuffers& B) {
@@ -36,6 +48,8 @@ __host__ __device__ inline HetTables het_tables(const DeviceBuffers& B) {
   H.coef = B.het_coef;
   H.coefB = B.het_coefB;
   H.fid = B.het_fid;
+  H.tm_g = B.het_tm_g;
+  H.tm_w = B.het_tm_w;
   return H;
 }
 
@@ -65,9 +79,11 @@ __device__ inline void het_prepare(const HetTables& H, const EvalRecord& r, HetP
 // Bins [base, base + 31) of the contraction, accumulated into the lane's
 // per-detector sums: lane l holds edge base + l, bin base + l uses edges l and
 // l + 1 (the next edge by a shuffle).  All 32 lanes must call it together.
-template <int NDET>
+// With TM the lanes also store the network edge products y_e of the time
+// marginalisation (each edge once: lanes 0..30, and the last edge).
+template <int NDET, bool TM = false>
 __device__ inline void het_chunk(const HetTables& H, const HetPrep<NDET>& p, int base, int lane, float* zr, float* zi,
-                                 float* hh) {
+                                 float* hh, float2* y = nullptr) {
   const float twopi = 6.283185307179586f;
   const int e = base + lane;
   float er[NDET], ei[NDET];
@@ -85,6 +101,16 @@ __device__ inline void het_chunk(const HetTables& H, const HetPrep<NDET>& p, int
       __sincosf(twopi * ph, &s, &co);  // exp(-2 pi i ph) = co - i s
       er[i] = p.rho_re[i] * co + p.rho_im[i] * s;
       ei[i] = p.rho_im[i] * co - p.rho_re[i] * s;
+    }
+    if (TM && (lane < 31 || e == H.n_bins)) {
+      float yr = 0.0f, yi = 0.0f;
+#pragma unroll
+      for (int i = 0; i < NDET; ++i) {
+        const float2 g = H.tm_g[(size_t)i * ne + e];
+        yr += g.x * er[i] - g.y * ei[i];
+        yi += g.x * ei[i] + g.y * er[i];
+      }
+      y[e] = make_float2(yr, yi);
     }
   } else {
 #pragma unroll
@@ -134,6 +160,114 @@ __device__ inline double het_epilogue(const LikeConst& L, double Z_re, double Z_
 }
 
 __host__ __device__ inline int het_chunks(int n_bins) { return (n_bins + 30) / 31; }
+
+// ---------------------------------------------------------------------------
+// Time pass of the time-marginalised likelihood.
+// ---------------------------------------------------------------------------
+constexpr int kTmNodes = 32;  // grid nodes per warp pass (lane l ends with node j0 + l)
+
+// Log weight of one node: log I0(|Z|) with phi_c marginalised, Re Z otherwise.
+__device__ __forceinline__ float tm_node_logw(const LikeConst& L, float zr, float zi) {
+  if (L.phase_marg) {
+    const float x = sqrtf(zr * zr + zi * zi);
+    return x + log_i0e_f32(x);
+  }
+  return zr;
+}
+
+// One level of the halving reduction: lanes with bit O set keep the upper O
+// nodes, the others the lower O, each adding its partner's copy of them.
+template <int O>
+__device__ __forceinline__ void tm_halve(float* ar, float* ai, int lane) {
+  const bool up = (lane & O) != 0;
+#pragma unroll
+  for (int k = 0; k < O; ++k) {
+    const float sr = up ? ar[k] : ar[k + O], si = up ? ai[k] : ai[k + O];
+    const float kr = up ? ar[k + O] : ar[k], ki = up ? ai[k + O] : ai[k];
+    ar[k] = kr + __shfl_xor_sync(0xffffffffu, sr, O);
+    ai[k] = ki + __shfl_xor_sync(0xffffffffu, si, O);
+  }
+}
+
+// One warp, nodes [j0, j0 + 32): Z(dt_j) = sum_e y_e exp(-2 pi i f_e dt_j).
+// Lane l takes edges l, l + 32, ...: one phasor at dt_j0 from the
+// double-float phase f_e dt_j0, then a rotation by w_e per node (31 steps,
+// FP32 drift ~2e-6 rad).  The 32 node sums are reduced across the warp by
+// halving, after which lane l holds node j0 + l; returns its log weight
+// (-inf past the last node).  All 32 lanes call it together.
+__device__ inline float tm_nodes_warp(const LikeConst& L, const HetTables& H, const float2* __restrict__ y, int j0,
+                                      int lane) {
+  float ar[kTmNodes], ai[kTmNodes];
+#pragma unroll
+  for (int k = 0; k < kTmNodes; ++k) ar[k] = ai[k] = 0.0f;
+  const dfl d0 = df_from_double(L.tm_t0 + (double)j0 * L.tm_dt);
+  const int ne = H.n_bins + 1;
+  const float twopi = 6.283185307179586f;
+  for (int e = lane; e < ne; e += 32) {
+    const dfl fe = {H.edge_f[e], H.edge_f[ne + e]};
+    float s, co;
+    __sincosf(twopi * df_frac(df_mul(fe, d0)), &s, &co);  // exp(-2 pi i f_e dt_j0) = co - i s
+    const float2 yv = y[e];
+    const float2 w = H.tm_w[e];
+    float ur = yv.x * co + yv.y * s, ui = yv.y * co - yv.x * s;
+#pragma unroll
+    for (int k = 0; k < kTmNodes; ++k) {
+      ar[k] += ur;
+      ai[k] += ui;
+      const float t = ur * w.x - ui * w.y;
+      ui = ur * w.y + ui * w.x;
+      ur = t;
+    }
+  }
+  tm_halve<16>(ar, ai, lane);
+  tm_halve<8>(ar, ai, lane);
+  tm_halve<4>(ar, ai, lane);
+  tm_halve<2>(ar, ai, lane);
+  tm_halve<1>(ar, ai, lane);
+  return (j0 + lane < L.tm_n) ? tm_node_logw(L, ar[0], ai[0]) : -INFINITY;
+}
+
+// The warps of a CTA share the grid's 32-node chunks (chunk q to warp
+// q mod n_warps).  Each lane keeps a running max and scaled sum of its
+// nodes' exp(log weight); returns the warp's (max, sum), the same on every
+// lane.  ell (optional) receives every node's log weight.
+__device__ inline void tm_pass(const LikeConst& L, const HetTables& H, const float2* __restrict__ y, int warp,
+                               int n_warps, int lane, float* ell, float& wm, float& ws) {
+  float m = -INFINITY, s = 0.0f;
+  const int nq = (L.tm_n + kTmNodes - 1) / kTmNodes;
+  for (int q = warp; q < nq; q += n_warps) {
+    const int j = q * kTmNodes + lane;
+    const float l = tm_nodes_warp(L, H, y, q * kTmNodes, lane);
+    if (j < L.tm_n) {
+      if (ell) ell[j] = l;
+      if (l > m) {
+        s = s * __expf(m - l) + 1.0f;
+        m = l;
+      } else {
+        s += __expf(l - m);
+      }
+    }
+  }
+  float M = m;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) M = fmaxf(M, __shfl_xor_sync(0xffffffffu, M, o));
+  float S = (m > -INFINITY) ? s * __expf(m - M) : 0.0f;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) S += __shfl_xor_sync(0xffffffffu, S, o);
+  wm = M;
+  ws = S;
+}
+
+// Time-marginalised logL from the warps' (max, sum) pairs (warp order) and
+// the network <h|h>: log((1/N_t) sum_j exp(l_j)) - <h|h>/2 - <d|d>/2.
+__device__ inline double tm_finish(const LikeConst& L, const float (*wms)[2], int n_warps, double HH) {
+  float M = -INFINITY;
+  for (int w = 0; w < n_warps; ++w) M = fmaxf(M, wms[w][0]);
+  double S = 0.0;
+  for (int w = 0; w < n_warps; ++w)
+    if (wms[w][0] > -INFINITY) S += (double)wms[w][1] * exp((double)wms[w][0] - (double)M);
+  return (double)M + log(S) - log((double)L.tm_n) - 0.5 * HH - 0.5 * L.DD;
+}
 
 // Per-detector sums cached for projection-only evaluations: (Z_i / C_i) /
 // inv_scale_i as the chain's kappa, and <h|h>_i / |C_i|^2 times A1^2 (the

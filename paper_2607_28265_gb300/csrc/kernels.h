@@ -26,6 +26,13 @@ struct SkyFrame {
   double gmst;
 };
 
+// Time-marginalised heterodyned likelihood: threads per CTA (one theta or
+// one chain per CTA), the largest bin count (the edge products y_e live in
+// shared memory) and the shared-memory bytes of those products.
+constexpr int kHetTmThreads = 512;
+constexpr int kMaxTmBins = 16384;
+inline size_t het_tm_smem_bytes(int n_bins) { return ((size_t)n_bins + 1) * 2 * sizeof(float); }
+
 // Device buffers owned by a context (all allocated with cudaMalloc).
 struct DeviceBuffers {
   // problem data
@@ -50,6 +57,9 @@ struct DeviceBuffers {
   float4* het_coef = nullptr;       // [n_det][N_b]
   float2* het_coefB = nullptr;      // [n_det][N_b]
   EvalRecord* het_fid = nullptr;    // fiducial record
+  // time marginalisation on the heterodyned bins (t_c marginalised)
+  float2* het_tm_g = nullptr;       // [n_det][N_b + 1] edge weights: Z_i = sum_e g_ie r_i(e)
+  float2* het_tm_w = nullptr;       // [N_b + 1] exp(-2 pi i f_e dt), the step between grid nodes
   // scratch for batched evaluation, sized for `cap` thetas
   int cap = 0;
   EvalRecord* rec = nullptr;     // [cap]
@@ -77,8 +87,16 @@ cudaError_t launch_distance_draw(const LikeConst& L, const DeviceBuffers& B, con
 // Heterodyned logL of n thetas (device pointers), one warp per theta.
 // kappa_out (n x 8) / vv_out (n x 4), optional: the per-detector cache of
 // projection-only evaluations (het.cuh het_cache).
+// With t_c marginalised (L.tm_n > 0) one CTA of kHetTmThreads per theta
+// instead, and ell (optional, n x tm_n) receives each node's log weight.
 cudaError_t launch_loglike_het(const LikeConst& L, const DeviceBuffers& B, const double* theta, int n, double* out,
-                               cudaStream_t st, double* kappa_out = nullptr, double* vv_out = nullptr);
+                               cudaStream_t st, double* kappa_out = nullptr, double* vv_out = nullptr,
+                               float* ell = nullptr);
+// Post-hoc t_c of n time-marginalised samples from their node log weights
+// (records of the same samples in B.rec); sample i uses the Philox counter of
+// global index first + i under key (k0, k1).  Writes theta[i][11].
+cudaError_t launch_time_draw(const LikeConst& L, const DeviceBuffers& B, const float* ell, int n, long long first,
+                             unsigned k0, unsigned k1, double* theta, cudaStream_t st);
 cudaError_t launch_prior_transform(const PriorSlot* slots, int n_sampled, const double* u, int n, double* theta,
                                    cudaStream_t st, SkyFrame sky);
 cudaError_t set_sweep_smem_limit(size_t bytes);

@@ -31,7 +31,8 @@ __global__ void k_setup(LikeConst L, const double* __restrict__ theta, int n, Ev
   if (i >= n) return;
   double th[SWIG_N_PARAMS];
   for (int j = 0; j < SWIG_N_PARAMS; ++j) th[j] = theta[(size_t)SWIG_N_PARAMS * i + j];
-  if (L.dist_marg) th[6] = 1.0;  // the marginal is built from the template at 1 Mpc
+  if (L.dist_marg) th[6] = 1.0;   // the marginal is built from the template at 1 Mpc
+  if (L.tm_n > 0) th[11] = L.tm_tref;  // templates at the fiducial's t_c, shifted node by node
   setup_record(L, th, rec + i);
 }
 
@@ -195,6 +196,71 @@ __global__ void k_distance_draw(LikeConst L, const EvalRecord* __restrict__ rec,
   th[6] = 1.0 / uq;
 }
 
+// ---------------------------------------------------------------------------
+// Post-hoc t_c of time-marginalised samples (App. A): from the node log
+// weights of each sample (k_het_tm's ell), the first grid node whose
+// cumulative weight reaches q x total, q a 53-bit Philox uniform on the
+// sample's global index (stream tag "time").  One warp per sample; the
+// cumulative sums run in 32-node chunks (warp inclusive scan) in the same
+// order for the total and the search, so the search always ends on a node.
+// ---------------------------------------------------------------------------
+__device__ inline double warp_inclusive_scan(double v, int lane) {
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const double u = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += u;
+  }
+  return v;
+}
+
+__global__ void k_time_draw(LikeConst L, const EvalRecord* __restrict__ rec, const float* __restrict__ ell, int n,
+                            long long first, unsigned k0, unsigned k1, double* __restrict__ theta) {
+  const int i = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (i >= n) return;
+  double* th = theta + (size_t)SWIG_N_PARAMS * i;
+  if (!rec[i].valid) {
+    if (lane == 0) th[11] = NAN;
+    return;
+  }
+  const int N = L.tm_n;
+  const float* l = ell + (size_t)i * N;
+  float m = -INFINITY;
+  for (int j = lane; j < N; j += 32) m = fmaxf(m, l[j]);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  double total = 0.0;
+  for (int base = 0; base < N; base += 32) {
+    const int j = base + lane;
+    const double v = warp_inclusive_scan(j < N ? exp((double)l[j] - (double)m) : 0.0, lane);
+    total += __shfl_sync(0xffffffffu, v, 31);
+  }
+  const long long gi = first + i;
+  const uint4 w = philox4x32_10(make_uint4((unsigned)(gi & 0xFFFFFFFFll), (unsigned)(gi >> 32), 0x74696d65u, 5u), k0, k1);
+  const double q = ((double)(w.x >> 5) * 67108864.0 + (double)(w.y >> 6)) * (1.0 / 9007199254740992.0);
+  const double target = q * total;
+  double acc = 0.0;
+  int pick = N - 1;
+  for (int base = 0; base < N; base += 32) {
+    const int j = base + lane;
+    const double v = warp_inclusive_scan(j < N ? exp((double)l[j] - (double)m) : 0.0, lane);
+    const unsigned hit = __ballot_sync(0xffffffffu, j < N && acc + v >= target);
+    if (hit) {
+      pick = base + __ffs(hit) - 1;
+      break;
+    }
+    acc += __shfl_sync(0xffffffffu, v, 31);
+  }
+  if (lane == 0) th[11] = L.tm_lo + ((double)pick + 0.5) * L.tm_dt;
+}
+
+cudaError_t launch_time_draw(const LikeConst& L, const DeviceBuffers& B, const float* ell, int n, long long first,
+                             unsigned k0, unsigned k1, double* theta, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  k_time_draw<<<(n + 3) / 4, 128, 0, st>>>(L, B.rec, ell, n, first, k0, k1, theta);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_distance_draw(const LikeConst& L, const DeviceBuffers& B, const double* kappa, int n,
                                  long long first, unsigned k0, unsigned k1, double* theta, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
@@ -217,10 +283,88 @@ __global__ void k_het(LikeConst L, HetTables H, const EvalRecord* __restrict__ r
   if (lane == 0) out[th] = v;
 }
 
+// Time-marginalised heterodyned likelihood, one CTA per theta (the thread
+// count and the chunk-to-warp assignment of the persistent sampler, so both
+// give the same sums): the warps contract the bins as above, storing the edge
+// products y_e in shared memory, then share the grid's 32-node chunks.
+// ell (optional) receives every node's log weight, [n][tm_n].
+template <int NDET>
+__global__ void __launch_bounds__(kHetTmThreads, 1)
+    k_het_tm(LikeConst L, HetTables H, const EvalRecord* __restrict__ rec, int n, double* __restrict__ out,
+             double* __restrict__ kappa_out, double* __restrict__ vv_out, float* __restrict__ ell) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  float2* y = reinterpret_cast<float2*>(smem);
+  __shared__ float s_hh[kHetTmThreads / 32][NDET];
+  __shared__ float s_tm[kHetTmThreads / 32][2];
+  const int th = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5, n_warps = blockDim.x >> 5;
+  if (th >= n) return;
+  const EvalRecord& r = rec[th];
+  if (threadIdx.x == 0) {
+    // no projection-only reuse under time marginalisation: the caches are zero
+    if (kappa_out)
+      for (int j = 0; j < 2 * SWIG_MAX_DET; ++j) kappa_out[(size_t)th * 2 * SWIG_MAX_DET + j] = 0.0;
+    if (vv_out)
+      for (int i = 0; i < SWIG_MAX_DET; ++i) vv_out[(size_t)th * SWIG_MAX_DET + i] = 0.0;
+  }
+  float* ell_th = ell ? ell + (size_t)th * L.tm_n : nullptr;
+  if (!r.valid) {
+    if (threadIdx.x == 0) out[th] = -INFINITY;
+    if (ell_th)
+      for (int j = threadIdx.x; j < L.tm_n; j += blockDim.x) ell_th[j] = -INFINITY;
+    return;
+  }
+  HetPrep<NDET> p;
+  het_prepare<NDET>(H, r, p);
+  float zr[NDET], zi[NDET], hh[NDET];
+#pragma unroll
+  for (int i = 0; i < NDET; ++i) zr[i] = zi[i] = hh[i] = 0.0f;
+  const int nc = het_chunks(H.n_bins);
+  for (int q = warp; q < nc; q += n_warps) het_chunk<NDET, true>(H, p, 31 * q, lane, zr, zi, hh, y);
+  het_warp_reduce<NDET>(zr, zi, hh);
+  if (lane == 0)
+#pragma unroll
+    for (int i = 0; i < NDET; ++i) s_hh[warp][i] = hh[i];
+  __syncthreads();
+  float wm, ws;
+  tm_pass(L, H, y, warp, n_warps, lane, ell_th, wm, ws);
+  if (lane == 0) {
+    s_tm[warp][0] = wm;
+    s_tm[warp][1] = ws;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double HH = 0.0;
+    for (int i = 0; i < NDET; ++i) {
+      double h = 0.0;
+      for (int w = 0; w < n_warps; ++w) h += (double)s_hh[w][i];
+      HH += h;
+    }
+    out[th] = tm_finish(L, s_tm, n_warps, HH);
+  }
+}
+
+template <int NDET>
+cudaError_t launch_het_tm(const LikeConst& L, const DeviceBuffers& B, int n, double* out, cudaStream_t st,
+                          double* kappa_out, double* vv_out, float* ell) {
+  const size_t bytes = het_tm_smem_bytes(B.het_nb);
+  cudaError_t e = cudaFuncSetAttribute(k_het_tm<NDET>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e != cudaSuccess) return e;
+  k_het_tm<NDET><<<n, kHetTmThreads, bytes, st>>>(L, het_tables(B), B.rec, n, out, kappa_out, vv_out, ell);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_loglike_het(const LikeConst& L, const DeviceBuffers& B, const double* theta, int n, double* out,
-                               cudaStream_t st, double* kappa_out, double* vv_out) {
+                               cudaStream_t st, double* kappa_out, double* vv_out, float* ell) {
   if (n <= 0) return cudaSuccess;
   k_setup<<<(n + 127) / 128, 128, 0, st>>>(L, theta, n, B.rec);
+  if (L.tm_n > 0) {
+    switch (L.n_det) {
+      case 1: return launch_het_tm<1>(L, B, n, out, st, kappa_out, vv_out, ell);
+      case 2: return launch_het_tm<2>(L, B, n, out, st, kappa_out, vv_out, ell);
+      case 3: return launch_het_tm<3>(L, B, n, out, st, kappa_out, vv_out, ell);
+      default: return launch_het_tm<4>(L, B, n, out, st, kappa_out, vv_out, ell);
+    }
+  }
   const HetTables H = het_tables(B);
   const unsigned grid = (unsigned)((n + 3) / 4);
   switch (L.n_det) {

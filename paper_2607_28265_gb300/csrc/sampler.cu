@@ -59,6 +59,7 @@ constexpr int kMaxChains = 2048;
 constexpr int kMaxEvents = 4;    // events per multi-event launch
 constexpr int kFlowThreads = 512;  // dataflow sampler: 16 warps, up to 128 registers per thread
 constexpr int kHetThreads = 512;  // heterodyned sampler: one chain per CTA, 16 warps
+static_assert(kHetThreads == kHetTmThreads, "the sampler and the batched time-marginalised kernel share sum orders");
 constexpr int kFreeBudget = 8;  // projection-only evaluations per chain per round
 enum ChainPhase { PH_NEW = 0, PH_LEFT = 1, PH_RIGHT = 2, PH_SHRINK = 3 };
 // What a Gibbs block moves: waveform coefficients, amplitude A(Mc)/d_L,
@@ -1276,11 +1277,16 @@ __global__ void __launch_bounds__(kFlowThreads, 1)
 // chain's per-detector cache of its last full evaluation, as on the full
 // grid; the set-up follows the mixed-precision sampler (FP64 waveform
 // coefficients and delays, FP32 prior transform, amplitude and projection).
+// With t_c marginalised the bin pass also stores the edge products y_e in
+// shared memory (the boundary's scratch, unused between boundaries) and the
+// warps then share the time grid's 32-node chunks (het.cuh tm_pass); there
+// are no projection-only blocks in that mode.
 template <int NDET>
 __global__ void __launch_bounds__(kHetThreads, 1)
     k_ns_het(LikeConst L, SamplerConst S, DeviceBuffers B, SamplerPtrs P) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ float s_sum[kHetThreads / 32][3 * NDET];
+  __shared__ float s_tm[kHetThreads / 32][2];
   __shared__ int s_done, s_fl;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int n_warps = blockDim.x >> 5;
@@ -1334,7 +1340,12 @@ __global__ void __launch_bounds__(kHetThreads, 1)
         if (valid) {
           HetPrep<NDET> p;
           het_prepare<NDET>(H, r, p);
-          for (int q = warp; q < nc; q += n_warps) het_chunk<NDET>(H, p, 31 * q, lane, zr, zi, hh);
+          if (L.tm_n > 0) {
+            float2* y = reinterpret_cast<float2*>(smem);
+            for (int q = warp; q < nc; q += n_warps) het_chunk<NDET, true>(H, p, 31 * q, lane, zr, zi, hh, y);
+          } else {
+            for (int q = warp; q < nc; q += n_warps) het_chunk<NDET>(H, p, 31 * q, lane, zr, zi, hh);
+          }
           het_warp_reduce<NDET>(zr, zi, hh);
         }
         if (lane == 0) {
@@ -1346,6 +1357,15 @@ __global__ void __launch_bounds__(kHetThreads, 1)
           }
         }
         __syncthreads();
+        if (L.tm_n > 0 && valid) {  // block-uniform
+          float wm, ws;
+          tm_pass(L, H, reinterpret_cast<const float2*>(smem), warp, n_warps, lane, nullptr, wm, ws);
+          if (lane == 0) {
+            s_tm[warp][0] = wm;
+            s_tm[warp][1] = ws;
+          }
+          __syncthreads();
+        }
         if (threadIdx.x == 0) {
           if (!valid) {
             ly = -INFINITY;
@@ -1363,7 +1383,7 @@ __global__ void __launch_bounds__(kHetThreads, 1)
               Z_im += zi;
               HH += hh;
             }
-            ly = het_epilogue(L, Z_re, Z_im, HH);
+            ly = L.tm_n > 0 ? tm_finish(L, s_tm, n_warps, HH) : het_epilogue(L, Z_re, Z_im, HH);
           }
         }
       }
@@ -1614,7 +1634,9 @@ int run_setup(swig_ctx* c, RunState& R) {
         if (slot == 7 || slot == 8 || slot == 9 || slot == 10 || slot == 12) flags |= BF_PROJ;
         if (slot == 9 || slot == 10 || slot == 11) flags |= BF_TAU;
       }
-    S.block_free[b] = free_block ? 1 : 0;
+    // time marginalisation keeps no per-detector cache at every node, so
+    // projection-only blocks take the full evaluation there
+    S.block_free[b] = (free_block && L.tm_n == 0) ? 1 : 0;
     S.block_flags[b] = flags;
   }
   S.m_pow2 = 1;
@@ -1650,7 +1672,8 @@ int run_setup(swig_ctx* c, RunState& R) {
   const size_t sort_bytes = (size_t)S.m_pow2 * (sizeof(double) + sizeof(int)) + kSweepThreads * sizeof(double) +
                             (size_t)k * sizeof(double) + (kMaxDim + kMaxDim * kMaxDim) * sizeof(float) + 64;
   const size_t rec_bytes = (size_t)(kFlowThreads / 32) * sizeof(EvalRecord);
-  R.smem = het ? sort_bytes : fixed + std::max(rec_bytes, sort_bytes);
+  R.smem = het ? std::max(sort_bytes, L.tm_n > 0 ? het_tm_smem_bytes(c->B.het_nb) : (size_t)0)
+              : fixed + std::max(rec_bytes, sort_bytes);
   if (R.smem > 220 * 1024) return fail(c, SWIG_E_ARG, "problem too large for the persistent kernel's shared memory");
 
   // buffers
@@ -1848,6 +1871,34 @@ int run_finish(swig_ctx* c, RunState& R, swig_result* out) {
       }
       if (kap_d) cudaFree(kap_d);
       if (ll_d) cudaFree(ll_d);
+      if (e != cudaSuccess) {
+        cudaFree(du_d);
+        cudaFree(th_d);
+        SCUDA(e);
+      }
+    }
+    if (L.tm_n > 0) {
+      // post-hoc t_c: the node log weights of every sample, then a draw from
+      // its conditional on the time grid
+      const int chunk = (int)std::max<int64_t>(1, std::min<int64_t>(4096, ((int64_t)1 << 26) / L.tm_n));
+      double* ll_d = nullptr;
+      float* ell_d = nullptr;
+      cudaError_t e = cudaMalloc(&ll_d, sizeof(double) * chunk);
+      if (e == cudaSuccess) e = cudaMalloc(&ell_d, sizeof(float) * (size_t)chunk * L.tm_n);
+      for (size_t off = 0; e == cudaSuccess && off < n_dead; off += chunk) {
+        const int mm = (int)std::min<size_t>(chunk, n_dead - off);
+        if (ensure_scratch(c, mm)) {
+          e = cudaErrorMemoryAllocation;
+          break;
+        }
+        e = launch_loglike_het(L, c->B, th_d + off * SWIG_N_PARAMS, mm, ll_d, c->stream, nullptr, nullptr, ell_d);
+        if (e == cudaSuccess)
+          e = launch_time_draw(L, c->B, ell_d, mm, (long long)off, S.key0, S.key1, th_d + off * SWIG_N_PARAMS,
+                               c->stream);
+        c->n_launches += 3;
+      }
+      if (ll_d) cudaFree(ll_d);
+      if (ell_d) cudaFree(ell_d);
       if (e != cudaSuccess) {
         cudaFree(du_d);
         cudaFree(th_d);

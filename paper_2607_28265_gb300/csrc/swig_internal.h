@@ -70,6 +70,7 @@ struct EvalRecord {
 };
 
 constexpr int kGaussLegendre = 64;  // nodes of the distance integral
+constexpr int kMaxTmNodes = 65536;  // largest time-marginalisation grid
 
 struct LikeConst {
   int n_det;
@@ -98,6 +99,12 @@ struct LikeConst {
   int d_kind;
   double d_lo, d_hi;
   double gl_x[kGaussLegendre], gl_w[kGaussLegendre];
+  // time marginalisation (t_c marginalised, heterodyned likelihood): tm_n
+  // midpoint nodes t_j = tm_lo + (j + 1/2) tm_dt over the uniform t_c prior;
+  // templates are built at t_c = tm_tref (the fiducial's) and shifted by
+  // tm_t0 + j tm_dt = t_j - tm_tref
+  int tm_n;
+  double tm_lo, tm_dt, tm_tref, tm_t0;
 };
 
 }  // namespace swig

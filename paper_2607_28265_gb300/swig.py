@@ -39,7 +39,7 @@ class SwigSamplerCfg(ctypes.Structure):
                 ("seed", _c_u64), ("likelihood", _c_int), ("precision", _c_int), ("proposal", _c_int),
                 ("het_bins", _c_int), ("het_spacing", _c_int), ("dlogz", _c_double), ("max_iter", _c_int),
                 ("het_fiducial", _c_double * N_PARAMS), ("learn_mix", _c_double), ("learn_lr", _c_double),
-                ("learn_steps", _c_int), ("learn_interval", _c_int)]
+                ("learn_steps", _c_int), ("learn_interval", _c_int), ("tmarg_nodes", _c_int)]
 
 
 class SwigResult(ctypes.Structure):
@@ -190,7 +190,7 @@ class Context:
     def set_sampler(self, nlive, nrep, sweeps=1, steps_per_dim=5, seed=0, likelihood=LIKE_FULL,
                     precision=PREC_MIXED, proposal=PROPOSAL_COV, het_bins=0, het_spacing=0, dlogz=-3.0,
                     max_iter=100000, het_fiducial=None, learn_mix=0.0, learn_lr=0.0, learn_steps=0,
-                    learn_interval=0):
+                    learn_interval=0, tmarg_nodes=0):
         cfg = SwigSamplerCfg()
         cfg.nlive, cfg.nrep, cfg.sweeps, cfg.steps_per_dim = nlive, nrep, sweeps, steps_per_dim
         cfg.seed, cfg.likelihood, cfg.precision, cfg.proposal = seed, likelihood, precision, proposal
@@ -200,6 +200,7 @@ class Context:
                 cfg.het_fiducial[i] = float(v)
         cfg.learn_mix, cfg.learn_lr = float(learn_mix), float(learn_lr)
         cfg.learn_steps, cfg.learn_interval = int(learn_steps), int(learn_interval)
+        cfg.tmarg_nodes = int(tmarg_nodes)
         self._check(self.lib.swig_set_sampler(self.h, ctypes.byref(cfg)))
 
     # ---- likelihood --------------------------------------------------------

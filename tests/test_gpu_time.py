@@ -1,0 +1,206 @@
+"""Time marginalisation on the heterodyned bins (Sec. 3.1, App. A) on the GPU
+against the oracle: batched marginal likelihoods, the sampler's dead points,
+the post-hoc t_c drawn for them and the evidence.
+
+Tolerance: as for the heterodyned likelihood (1e-6 relative to |logL| plus
+2e-4), which also covers the time pass.  Each node's Z is a fresh FP32 sum
+over the edges.  A term's phasor comes from an exact double-float phase at the
+chunk's first node, then up to 31 FP32 rotation steps.  Each step adds about
+6e-8 of relative error, so no term drifts by more than ~2e-6.  That is
+2e-6 x sum_e |y_e| at worst, a few 1e-3 on the 128 s workload (sum_e |y_e| ~
+3e3), below the 0.78 that 1e-6 |logL| allows there.  The node log weights
+and their log-sum-exp are FP32; the rest of the epilogue is FP64.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import swig_inputs as si
+from oracle import events, physics
+from oracle import likelihood as L
+from oracle.philox import philox4x32_10
+
+pytestmark = pytest.mark.gpu
+
+swig = pytest.importorskip("paper_2607_28265_gb300.swig")
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+TC = si.IDX["tc"]
+
+
+def _tol(want):
+    return 1e-6 * np.abs(want) + 2e-4
+
+
+def _tm_params(wl, lo=-0.1, hi=0.1, phase_marg=False):
+    params = list(wl.params)
+    params[TC] = si.Param(si.PRIOR_UNIFORM, lo, hi, si.MODE_MARG)
+    if phase_marg:
+        params[si.IDX["phic"]] = si.Param(si.PRIOR_UNIFORM, 0.0, 2 * math.pi, si.MODE_MARG)
+    return params
+
+
+def _event(ev, params):
+    return L.Event(ev.freqs, ev.df, ev.data, ev.psds, ev.detectors, ev.gmst, params)
+
+
+def _ctx(wl, ev, params, fid, n_bins, spacing, nt, nlive=100, nrep=10, seed=0):
+    ctx = swig.context_for_workload(wl, ev.data, ev.psds, ev.gmst)
+    ctx.set_prior(params)
+    ctx.set_sampler(nlive=nlive, nrep=nrep, likelihood=swig.LIKE_HET, het_bins=n_bins, het_spacing=spacing,
+                    het_fiducial=fid, tmarg_nodes=nt, seed=seed)
+    return ctx
+
+
+def _thetas(params, th, n, seed, spread):
+    rng = np.random.default_rng(seed)
+    sampled = [i for i, p in enumerate(params) if p.mode == si.MODE_SAMPLE]
+    far = physics.prior_transform(rng.random((n, len(sampled))), params)
+    near = np.repeat(th[None, :], n, axis=0)
+    for s in sampled:
+        p = params[s]
+        if p.kind == si.PRIOR_UNIFORM:
+            near[:, s] = np.clip(th[s] + spread * (p.hi - p.lo) * rng.standard_normal(n), p.lo, p.hi)
+    return np.concatenate([far, near])
+
+
+@pytest.fixture(scope="module")
+def cfg1():
+    wl = si.config1()
+    ev, th = events.build_event(wl)
+    return wl, ev, th
+
+
+@pytest.mark.parametrize("nt,phase_marg", [(100, False), (256, True), (1, False), (33, True)])
+def test_batched_time_marginal_matches_oracle_cfg1(cfg1, nt, phase_marg):
+    """Several 32-node chunks with a ragged last one (100, 33), exact chunks
+    (256) and the one-node grid; plain and phase-marginalised."""
+    wl, ev, th = cfg1
+    params = _tm_params(wl, phase_marg=phase_marg)
+    evt = _event(ev, params)
+    fid = th.copy()
+    fid[TC] += 3e-4  # the fiducial's t_c sets the templates' reference time
+    het = L.het_setup(evt, fid, 450, spacing="geometric")
+    ctx = _ctx(wl, ev, params, fid, 450, 1, nt)
+    thetas = _thetas(params, th, 10, nt, 0.002)
+    got = ctx.loglike_batch(thetas)
+    want = np.array([L.het_loglike_time_marg(evt, het, t, nt) for t in thetas])
+    assert np.all(np.abs(got - want) <= _tol(want)), np.max(np.abs(got - want))
+    # theta[tc] is ignored
+    t2 = thetas.copy()
+    t2[:, TC] = 0.05
+    assert np.array_equal(ctx.loglike_batch(t2), got)
+    ctx.close()
+
+
+def test_batched_time_marginal_full_size_three_detectors():
+    """128 s H1/L1/V1 grid, 5000 bins of equal phase change, phi_c
+    marginalised, 2000 nodes over +-0.1 s: the bench's configuration."""
+    wl = si.config2()
+    ev, th = events.build_event(wl)
+    params = _tm_params(wl)
+    evt = _event(ev, params)
+    het = L.het_setup(evt, th, 5000)
+    ctx = _ctx(wl, ev, params, th, 5000, 0, 2000, nlive=1000, nrep=100)
+    thetas = _thetas(params, th, 1, 3, 0.0003)
+    got = ctx.loglike_batch(thetas)
+    want = np.array([L.het_loglike_time_marg(evt, het, t, 2000) for t in thetas])
+    assert np.all(np.abs(got - want) <= _tol(want)), np.max(np.abs(got - want))
+    ctx.close()
+
+
+def _philox_uniform(i, seed):
+    w = philox4x32_10((i & 0xFFFFFFFF, i >> 32, 0x74696D65, 5), (seed & 0xFFFFFFFF, seed >> 32))
+    return ((w[0] >> 5) * 67108864.0 + (w[1] >> 6)) / 9007199254740992.0
+
+
+def _cdf_bounds(log_w, j):
+    w = np.exp(np.asarray(log_w) - np.max(log_w))
+    c = np.cumsum(w) / np.sum(w)
+    return (c[j - 1] if j > 0 else 0.0), c[j]
+
+
+def test_sampler_dead_points_time_draws_and_evidence(cfg1):
+    """cfg1 data, 450 geometric bins, t_c marginalised on 4096 nodes (49 us,
+    about the width of the t_c likelihood peak): dead-point logL against
+    the oracle, post-hoc t_c against the oracle's draw with the same uniform,
+    and the evidence against the golden evidence of the same heterodyned
+    likelihood with t_c sampled (marginalising t_c on its prior leaves the
+    evidence unchanged; the grid error is ~1e-7 at this spacing)."""
+    wl, ev, th = cfg1
+    nt = 4096
+    params = _tm_params(wl)
+    evt = _event(ev, params)
+    het = L.het_setup(evt, th, 450, spacing="geometric")
+    golden = os.path.join(HERE, "golden", "cfg3_het_is_evidence.txt")
+    vals = {}
+    for line in open(golden):
+        if not line.startswith("#") and line.strip():
+            k, v, e = line.split()
+            vals[k] = (float(v), float(e))
+    logz_true, logz_true_err = vals["geometric"]
+    zs, errs = [], []
+    for seed in (51, 52, 53, 54):
+        ctx = _ctx(wl, ev, params, th, 450, 1, nt, nlive=400, nrep=40, seed=seed)
+        r = ctx.run()
+        thd, ll, lw = ctx.get_samples()
+        zs.append(r.logz)
+        errs.append(r.logz_err)
+        if seed == 51:
+            idx = np.linspace(0, len(ll) - 1, 8).astype(int)
+            want = np.array([L.het_loglike_time_marg(evt, het, thd[i], nt) for i in idx])
+            assert np.all(np.abs(ll[idx] - want) <= _tol(want)), np.max(np.abs(ll[idx] - want))
+            grid = L.time_grid(params, nt)
+            for i in idx:
+                q = _philox_uniform(int(i), seed)
+                lw_i = L.het_time_log_weights(evt, het, thd[i], nt)
+                j_want = L.draw_time_node(lw_i, q)
+                j_got = int(round((thd[i, TC] - grid[0]) / (grid[1] - grid[0])))
+                assert abs(thd[i, TC] - grid[j_got]) < 1e-12
+                if j_got != j_want:
+                    # only where q sits on a boundary of the FP32-weighted CDF
+                    lo, hi = _cdf_bounds(lw_i, j_got)
+                    assert lo - 1e-4 <= q <= hi + 1e-4, (i, q, j_got, j_want)
+            # the reconstructed t_c posterior sits at the injection within its width
+            w = np.exp(lw - r.logz)
+            w /= w.sum()
+            mean = float(np.sum(w * thd[:, TC]))
+            std = math.sqrt(float(np.sum(w * (thd[:, TC] - mean) ** 2)))
+            assert 1e-5 < std < 3e-4
+            assert abs(mean - th[TC]) < 3 * std
+        ctx.close()
+    se = math.hypot(float(np.mean(errs)) / 2.0, logz_true_err)
+    assert abs(np.mean(zs) - logz_true) < 3 * se + 0.05, (zs, logz_true)
+
+
+def test_time_marginal_errors(cfg1):
+    wl, ev, th = cfg1
+    ctx = swig.context_for_workload(wl, ev.data, ev.psds, ev.gmst)
+    bad = list(wl.params)
+    bad[TC] = si.Param(si.PRIOR_SINE, -0.1, 0.1, si.MODE_MARG)
+    with pytest.raises(swig.SwigError):
+        ctx.set_prior(bad)
+    params = _tm_params(wl)
+    ctx.set_prior(params)
+    th1 = th[None, :]
+    # full-grid likelihood: not implemented with t_c marginalised
+    ctx.set_sampler(nlive=100, nrep=10)
+    with pytest.raises(swig.SwigError):
+        ctx.loglike_batch(th1)
+    # no grid
+    ctx.set_sampler(nlive=100, nrep=10, likelihood=swig.LIKE_HET, het_bins=300, het_fiducial=th)
+    with pytest.raises(swig.SwigError):
+        ctx.loglike_batch(th1)
+    # too many bins for the shared-memory edge products
+    ctx.set_sampler(nlive=100, nrep=10, likelihood=swig.LIKE_HET, het_bins=20000, het_fiducial=th, tmarg_nodes=10)
+    with pytest.raises(swig.SwigError):
+        ctx.loglike_batch(th1)
+    with pytest.raises(swig.SwigError):
+        ctx.set_sampler(nlive=100, nrep=10, likelihood=swig.LIKE_HET, het_bins=300, het_fiducial=th,
+                        tmarg_nodes=70000)
+    # a valid configuration still works on the same context
+    ctx.set_sampler(nlive=100, nrep=10, likelihood=swig.LIKE_HET, het_bins=300, het_fiducial=th, tmarg_nodes=8)
+    assert np.isfinite(ctx.loglike_batch(th1)[0])
+    ctx.close()
