@@ -189,12 +189,43 @@ __device__ __forceinline__ void tm_halve(float* ar, float* ai, int lane) {
   }
 }
 
+// One edge's inputs to the time pass: its product y_e, rotation w_e and
+// frequency (double-float); an edge past the end reads as y = 0, w = 1.
+struct TmEdge {
+  float2 y, w;
+  dfl f;
+};
+
+__device__ __forceinline__ TmEdge tm_load_edge(const HetTables& H, const float2* __restrict__ y, int e, int ne) {
+  TmEdge d;
+  if (e < ne) {
+    d.y = y[e];
+    d.w = H.tm_w[e];
+    d.f = {H.edge_f[e], H.edge_f[ne + e]};
+  } else {
+    d.y = make_float2(0.0f, 0.0f);
+    d.w = make_float2(1.0f, 0.0f);
+    d.f = {0.0f, 0.0f};
+  }
+  return d;
+}
+
+// y_e exp(-2 pi i f_e dt): the term at the chunk's first node.
+__device__ __forceinline__ float2 tm_start(const TmEdge& d, dfl dt) {
+  const float twopi = 6.283185307179586f;
+  float s, co;
+  __sincosf(twopi * df_frac(df_mul(d.f, dt)), &s, &co);  // exp(-2 pi i f_e dt) = co - i s
+  return make_float2(d.y.x * co + d.y.y * s, d.y.y * co - d.y.x * s);
+}
+
 // One warp, nodes [j0, j0 + 32): Z(dt_j) = sum_e y_e exp(-2 pi i f_e dt_j).
-// Lane l takes edges l, l + 32, ...: one phasor at dt_j0 from the
-// double-float phase f_e dt_j0, then a rotation by w_e per node (31 steps,
-// FP32 drift ~2e-6 rad).  The 32 node sums are reduced across the warp by
-// halving, after which lane l holds node j0 + l; returns its log weight
-// (-inf past the last node).  All 32 lanes call it together.
+// Lane l takes edges l, l + 32, ... two at a time (e and e + 32, added in
+// that order, so the sums are those of one edge at a time): one phasor at
+// dt_j0 from the double-float phase f_e dt_j0, then a rotation by w_e per
+// node (31 steps, FP32 drift ~2e-6 rad).  The next pair's loads are issued
+// before the current pair's steps.  The 32 node sums are reduced across the
+// warp by halving, after which lane l holds node j0 + l; returns its log
+// weight (-inf past the last node).  All 32 lanes call it together.
 __device__ inline float tm_nodes_warp(const LikeConst& L, const HetTables& H, const float2* __restrict__ y, int j0,
                                       int lane) {
   float ar[kTmNodes], ai[kTmNodes];
@@ -202,21 +233,24 @@ __device__ inline float tm_nodes_warp(const LikeConst& L, const HetTables& H, co
   for (int k = 0; k < kTmNodes; ++k) ar[k] = ai[k] = 0.0f;
   const dfl d0 = df_from_double(L.tm_t0 + (double)j0 * L.tm_dt);
   const int ne = H.n_bins + 1;
-  const float twopi = 6.283185307179586f;
-  for (int e = lane; e < ne; e += 32) {
-    const dfl fe = {H.edge_f[e], H.edge_f[ne + e]};
-    float s, co;
-    __sincosf(twopi * df_frac(df_mul(fe, d0)), &s, &co);  // exp(-2 pi i f_e dt_j0) = co - i s
-    const float2 yv = y[e];
-    const float2 w = H.tm_w[e];
-    float ur = yv.x * co + yv.y * s, ui = yv.y * co - yv.x * s;
+  TmEdge a = tm_load_edge(H, y, lane, ne), b = tm_load_edge(H, y, lane + 32, ne);
+  for (int e = lane; e < ne; e += 64) {
+    const TmEdge ca = a, cb = b;
+    a = tm_load_edge(H, y, e + 64, ne);
+    b = tm_load_edge(H, y, e + 96, ne);
+    float2 u = tm_start(ca, d0), v = tm_start(cb, d0);
 #pragma unroll
     for (int k = 0; k < kTmNodes; ++k) {
-      ar[k] += ur;
-      ai[k] += ui;
-      const float t = ur * w.x - ui * w.y;
-      ui = ur * w.y + ui * w.x;
-      ur = t;
+      ar[k] += u.x;
+      ai[k] += u.y;
+      ar[k] += v.x;
+      ai[k] += v.y;
+      const float tu = u.x * ca.w.x - u.y * ca.w.y;
+      u.y = u.x * ca.w.y + u.y * ca.w.x;
+      u.x = tu;
+      const float tv = v.x * cb.w.x - v.y * cb.w.y;
+      v.y = v.x * cb.w.y + v.y * cb.w.x;
+      v.x = tv;
     }
   }
   tm_halve<16>(ar, ai, lane);
