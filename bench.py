@@ -124,6 +124,22 @@ def workload_description(wl, spec):
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
+def reduce_over_ranks(local, world, device="cuda"):
+    """Elementwise max and sum over the ranks of a vector of per-rank figures
+    (the caller takes times from the max and counts from the sum); a plain
+    copy at world 1.  NCCL on the GPU arm, any backend whose tensors live on
+    `device` (gloo on "cpu" in the tests)."""
+    t = np.asarray(local, dtype=np.float64)
+    if world == 1:
+        return t.copy(), t.copy()
+    import torch
+    import torch.distributed as dist
+    x = torch.tensor(t, device=device)
+    tmax, tsum = x.clone(), x.clone()
+    dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+    dist.all_reduce(tsum, op=dist.ReduceOp.SUM)
+    return tmax.cpu().numpy(), tsum.cpu().numpy()
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled during the timed region."""
 
@@ -235,18 +251,9 @@ def run_campaign(args, rank, world):
     e2e_evals = sum(r.n_evals for r in res)
     h2d = sum(c.profile()["h2d_bytes"] for c in ctxs) - h2d0
     d2h = sum(c.profile()["d2h_bytes"] for c in ctxs) - d2h0
-    t_local = np.array([total_ms, evals, e2e_ms, e2e_evals, full], dtype=np.float64)
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor(t_local, device="cuda")
-        tmax, tsum = t.clone(), t.clone()
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-        dist.all_reduce(tsum, op=dist.ReduceOp.SUM)
-        total_ms_max, e2e_ms_max = float(tmax[0]), float(tmax[2])
-        evals_all, e2e_all, full_all = float(tsum[1]), float(tsum[3]), float(tsum[4])
-    else:
-        total_ms_max, e2e_ms_max = total_ms, e2e_ms
-        evals_all, e2e_all, full_all = evals, e2e_evals, full
+    tmax, tsum = reduce_over_ranks([total_ms, evals, e2e_ms, e2e_evals, full], world)
+    total_ms_max, e2e_ms_max = float(tmax[0]), float(tmax[2])
+    evals_all, e2e_all, full_all = float(tsum[1]), float(tsum[3]), float(tsum[4])
     if rank != 0:
         return None
     n_post = len(wls) * args.steps
@@ -358,20 +365,10 @@ def run_gpu(args, rank, world):
     h2d = (ctx.profile()["h2d_bytes"] - h2d0) / n_e2e
     d2h = (ctx.profile()["d2h_bytes"] - d2h0) / n_e2e
 
-    # max over ranks
-    t_local = np.array([total_ms, total_evals, sum(e2e_ms), e2e_evals, full_evals], dtype=np.float64)
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor(t_local, device="cuda")
-        tmax = t.clone()
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-        tsum = t.clone()
-        dist.all_reduce(tsum, op=dist.ReduceOp.SUM)
-        total_ms_max, e2e_ms_max = float(tmax[0]), float(tmax[2])
-        evals_all, e2e_evals_all, full_all = float(tsum[1]), float(tsum[3]), float(tsum[4])
-    else:
-        total_ms_max, e2e_ms_max = total_ms, sum(e2e_ms)
-        evals_all, e2e_evals_all, full_all = total_evals, e2e_evals, full_evals
+    # max of the times and sum of the counts over ranks
+    tmax, tsum = reduce_over_ranks([total_ms, total_evals, sum(e2e_ms), e2e_evals, full_evals], world)
+    total_ms_max, e2e_ms_max = float(tmax[0]), float(tmax[2])
+    evals_all, e2e_evals_all, full_all = float(tsum[1]), float(tsum[3]), float(tsum[4])
     if rank != 0:
         return None
 
