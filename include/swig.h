@@ -163,7 +163,13 @@ int swig_set_sampler(swig_ctx* ctx, const swig_sampler_cfg* cfg);
  * h/h0 is taken linear in each bin (value at the centre, slope), so
  *   <d|h> ~ Re sum_b (A0 r0 + A1 r1),  <h|h> ~ sum_b (B0 |r0|^2 + 2 B1 Re(r0 r1*)).
  * The per-bin contraction is FP32 with double-float phase differences; the
- * precision setting does not apply.  An invalid fiducial -> SWIG_E_ARG. */
+ * precision setting does not apply.  An invalid fiducial -> SWIG_E_ARG.
+ * With d_L marginalised: the marginal over its prior (64-node quadrature).
+ * With t_c marginalised (heterodyned only): the templates are built at the
+ * fiducial's t_c, Z is formed at each of the tmarg_nodes grid nodes by
+ * rotating the bin-edge ratios, and the result is
+ * log((1/N_t) sum_j exp(l_j)) - <h|h>/2 - <d|d>/2 with l_j = log I0(|Z_j|)
+ * (or Re Z_j), <h|h> taken once at the fiducial's t_c. */
 int swig_loglike_batch(swig_ctx* ctx, const double* theta, int64_t n, double* out_logl);
 /* Same with device pointers on the context's device, enqueued on `stream`
  * (cudaStream_t).  Uses the context's scratch buffers, so calls on one
