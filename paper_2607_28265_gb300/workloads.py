@@ -11,13 +11,15 @@ Run as a module it executes one small case for a profiler capture::
     python -m paper_2607_28265_gb300.workloads loglike --batch 1000
     python -m paper_2607_28265_gb300.workloads het --batch 1000 --bins 1000
     python -m paper_2607_28265_gb300.workloads sampler-het --max-iter 2 --bins 5000
+    python -m paper_2607_28265_gb300.workloads sampler-het --max-iter 2 --bins 5000 --tmarg-nodes 2000
 
 ``sampler``: the persistent nested-sampling kernel on the 128 s H1/L1/V1
 workload for --max-iter outer iterations (one launch); ``loglike``: one batch
 of the full-grid mixed-precision likelihood; ``het``: one batch of the
 heterodyned likelihood; ``sampler-het``: the heterodyned persistent sampler
-kernel (fiducial at the injection).  Each case exits non-zero on any library
-error.
+kernel (fiducial at the injection).  ``--tmarg-nodes N`` marginalises t_c over
+its prior on N grid nodes in the heterodyned cases.  Each case exits non-zero
+on any library error.
 """
 from __future__ import annotations
 
@@ -60,9 +62,10 @@ def build_context(wl, seed_offset=0, precision=swig.PREC_MIXED):
     return ctx, data, psds, th_used
 
 
-def _prior_draws(ctx, wl, n, seed):
+def _prior_draws(ctx, params, n, seed):
     rng = np.random.default_rng(seed)
-    return ctx.prior_transform(rng.random((n, len(wl.sampled()))))
+    n_sampled = sum(1 for p in params if p.mode == si.MODE_SAMPLE)
+    return ctx.prior_transform(rng.random((n, n_sampled)))
 
 
 def main(argv=None):
@@ -72,9 +75,15 @@ def main(argv=None):
     ap.add_argument("--batch", type=int, default=1000)
     ap.add_argument("--bins", type=int, default=1000)
     ap.add_argument("--repeat", type=int, default=1)
+    ap.add_argument("--tmarg-nodes", type=int, default=0)
     a = ap.parse_args(argv)
     wl = si.config2()
     ctx, data, psds, th = build_context(wl)
+    params = list(wl.params)
+    if a.tmarg_nodes:
+        p = params[si.IDX["tc"]]
+        params[si.IDX["tc"]] = si.Param(si.PRIOR_UNIFORM, p.lo, p.hi, si.MODE_MARG)
+        ctx.set_prior(params)
     if a.case == "sampler":
         ctx.set_sampler(nlive=wl.nlive, nrep=wl.nrep, sweeps=wl.sweeps, steps_per_dim=wl.steps_per_dim,
                         seed=wl.sampler_seed, precision=swig.PREC_MIXED, max_iter=a.max_iter)
@@ -84,15 +93,15 @@ def main(argv=None):
     elif a.case == "sampler-het":
         ctx.set_sampler(nlive=wl.nlive, nrep=wl.nrep, sweeps=wl.sweeps, steps_per_dim=wl.steps_per_dim,
                         seed=wl.sampler_seed, likelihood=swig.LIKE_HET, het_bins=a.bins, het_fiducial=th,
-                        max_iter=a.max_iter)
+                        max_iter=a.max_iter, tmarg_nodes=a.tmarg_nodes)
         for _ in range(a.repeat):
             r = ctx.run()
         print(f"sampler-het: n_iter={r.n_iter} n_evals={r.n_evals} logz={r.logz:.3f}")
     else:
         if a.case == "het":
             ctx.set_sampler(nlive=wl.nlive, nrep=wl.nrep, likelihood=swig.LIKE_HET, het_bins=a.bins,
-                            het_fiducial=th)
-        thetas = _prior_draws(ctx, wl, a.batch, 7)
+                            het_fiducial=th, tmarg_nodes=a.tmarg_nodes)
+        thetas = _prior_draws(ctx, params, a.batch, 7)
         for _ in range(a.repeat):
             out = ctx.loglike_batch(thetas)
         print(f"{a.case}: batch={a.batch} finite={int(np.isfinite(out).sum())} max={out.max():.3f}")
