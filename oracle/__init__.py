@@ -12,7 +12,8 @@ Modules
 physics     prior transform (Table I), TaylorF2 phase/amplitude, antenna
             patterns and geocentric time delays (Sec. 3.1, Eq. 2 templates)
 likelihood  noise-weighted inner product and matched-filter log-likelihood
-            (Eq. 2), phase marginalisation (Sec. 3.1), heterodyned likelihood
+            (Eq. 2), phase, distance and time marginalisation and the post-hoc
+            draws of d_L and t_c (Sec. 3.1, App. A), heterodyned likelihood
             (Sec. 3.4)
 nested      nested sampling with batch deletion (Sec. 2.2, Eq. 1) driven by a
             Slice-within-Gibbs kernel (Sec. 2.3, Eq. 3; Sec. 3.2)
