@@ -20,7 +20,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 
 
 def _tol(want):
-    # 1e-6 relative (the benchmark spec's bound) plus the FP32 log-prior/log-i0e
+    # 1e-6 relative (the stated parity bound) plus the FP32 log-prior/log-i0e
     # terms of the quadrature (~1e-6 absolute each, 64 nodes)
     return 1e-6 * np.abs(want) + 1e-4
 

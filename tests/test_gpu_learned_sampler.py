@@ -1,7 +1,7 @@
 """The sampler with the learned slice proposal on the 4 s single-detector
 workload, through the C-ABI: dead points against the oracle likelihood,
 determinism, and evidence/posterior against the same references as plain
-SwiG (plain SwiG is the judge of correctness)."""
+SwiG (plain SwiG is the reference for correctness)."""
 import math
 import os
 

@@ -1,6 +1,6 @@
 """Parity of the CUDA likelihood (through the C-ABI) with the FP64 oracle.
 
-Bar (spec tolerance): |dlogL| <= 1e-6 |logL| + 1e-6 on identical seeded
+Bar (the stated parity tolerance): |dlogL| <= 1e-6 |logL| + 1e-6 on identical seeded
 inputs.  Cases cover FP64 and mixed precision, one and three detectors, the
 full-size 128 s network grid, a grid whose last tile is ragged, phase
 marginalisation on and off, invalid parameters, empty and large batches, and
