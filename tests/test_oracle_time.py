@@ -130,6 +130,9 @@ def test_zero_data_gives_minus_half_hh(cfg1):
 
 
 def test_heterodyned_sum_tracks_the_full_grid(cfg1):
+    """Near the fiducial the heterodyned marginal is within ~5e-5 of the
+    full-grid one; 5e-4 still fails a flipped A1 term (2e-3 .. 2e-2 here) or
+    r0 taken at the left edge instead of the centre (up to 4e-3)."""
     wl, ev, _, th = cfg1
     params = _params(wl, phase_marg=True)
     evt = _event(ev, params)
@@ -141,7 +144,7 @@ def test_heterodyned_sum_tracks_the_full_grid(cfg1):
         theta[1] = min(1.0, theta[1] * (1.0 + 1e-3 * rng.standard_normal()))
         got = L.het_loglike_time_marg(evt, het, theta, 800)
         want = L.loglike_time_marg_full(evt, theta, 800)
-        assert abs(got - want) < 0.01, (got, want)
+        assert abs(got - want) < 5e-4, (got, want)
 
 
 def test_draw_time_node_is_the_inverse_cdf():
