@@ -63,10 +63,15 @@ def test_full_grid_overlap_is_a_dft(cfg1):
 
 
 def test_overlap_peaks_at_the_injected_time(cfg1):
+    """A noise-free injection moved to t_c = 12.3 ms (away from zero, so a
+    flipped shift sign would peak at -12.3 ms): |Z(t)| peaks there."""
     wl, _, ev0, th = cfg1
+    t_inj = 0.0123
+    th_inj = th.copy()
+    th_inj[TC] = t_inj
     evt = _event(ev0, _params(wl, phase_marg=True))
-    t_inj = th[TC]
-    t = t_inj + np.linspace(-2e-3, 2e-3, 401)  # 10 us steps
+    evt.data = L.strains(evt, th_inj)
+    t = np.concatenate([t_inj + np.linspace(-2e-3, 2e-3, 401), -t_inj + np.linspace(-2e-3, 2e-3, 41)])
     z, _ = L.full_time_overlaps(evt, th, t)
     assert abs(t[np.argmax(np.abs(z))] - t_inj) <= 1e-5
 
