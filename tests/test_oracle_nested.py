@@ -61,6 +61,29 @@ def test_prior_volume_shrinkage_law():
     assert abs(np.mean(diffs)) < 3.0 / math.sqrt(len(diffs)) + 0.5
 
 
+def test_run_assigns_the_true_enclosed_volume():
+    """The prior volume a run assigns to its deaths, read from its own
+    weights (X_j = sum over later dead points of exp(logw - logL), the final
+    live points included), against the true enclosed volume of the d-ball on
+    L = -|u - 1/2|.  log X_run - log X_true has mean 0 and variance
+    sum 1/n^2 over the deaths (Skilling 2006); after 200 iterations of
+    k = 10 deaths from m = 100 a per-death shrinkage of 1/m instead of
+    1/(m - j) would sit ~2.3 standard deviations off."""
+    d, m, k, iters = 3, 100, 10, 200
+    ll = lambda u: -float(np.linalg.norm(u - 0.5)) if np.all((u >= 0) & (u <= 1)) else -np.inf
+    vd = math.pi ** (d / 2) / special.gamma(d / 2 + 1)
+    var = sum(1.0 / (m - (i % k)) ** 2 for i in range(iters * k))
+    zs = []
+    for seed in range(8):
+        res = nested.run_nested(ll, d, [[0, 1, 2]], nlive=m, nrep=k, rng=300 + seed, dlogz=-1e9, max_iter=iters)
+        inc = np.exp(res["logw"] - res["logl"])  # X_{j-1} - X_j of each dead point
+        j = iters * k - 1  # the last death before the final live points
+        log_x_run = math.log(float(np.sum(inc[j + 1:])))
+        log_x_true = math.log(vd) + d * math.log(-res["logl"][j])
+        zs.append((log_x_run - log_x_true) / math.sqrt(var))
+    assert abs(np.mean(zs)) < 3.0 / math.sqrt(len(zs)) + 0.3, zs
+
+
 def test_slice_kernel_leaves_constrained_uniform_invariant():
     """Chains started from the constrained prior (uniform in a ball of radius
     r* inside the cube) stay uniform: r^d / r*^d ~ U(0, 1)."""

@@ -118,8 +118,8 @@ def test_spa_time_frequency_relation(mc, q, chi1, chi2):
     v = np.cbrt(math.pi * m_s * f)
     tau = 5.0 * m_s / (256.0 * eta * v**8) * _chirp_time_series(v, eta, beta, sigma)
     newt = 5.0 / 256.0 * mc * physics.MTSUN_S * (math.pi * mc * physics.MTSUN_S * f) ** (-8.0 / 3.0)
-    assert np.allclose(5.0 * m_s / (256.0 * eta * v**8), newt, rtol=1e-12)
-    assert np.allclose(dpsi, -tau, rtol=2e-8)
+    assert np.allclose(5.0 * m_s / (256.0 * eta * v**8), newt, rtol=1e-12, atol=0)
+    assert np.allclose(dpsi, -tau, rtol=2e-8, atol=0)
 
 
 def test_newtonian_only_phase_is_quadrupole_chirp():
@@ -129,7 +129,7 @@ def test_newtonian_only_phase_is_quadrupole_chirp():
     psi = lambda ff: physics.taylorf2_phase_intrinsic(ff, mc, q, 0, 0, 0, 0, orders={0})
     dpsi = (psi(f + h) - psi(f - h)) / (2 * h) / (2 * math.pi)
     mcs = mc * physics.MTSUN_S
-    assert np.allclose(dpsi, -5.0 / 256.0 * mcs * (math.pi * mcs * f) ** (-8.0 / 3.0), rtol=1e-8)
+    assert np.allclose(dpsi, -5.0 / 256.0 * mcs * (math.pi * mcs * f) ** (-8.0 / 3.0), rtol=1e-8, atol=0)
 
 
 def test_tidal_lambda_tilde():
@@ -163,7 +163,7 @@ def test_tidal_phase_terms_enter_as_stated():
                        - physics.taylorf2_phase_intrinsic(f - h, mc, q, 0, 0, lam, lam, orders=o)) / (2 * h) / (2 * math.pi))
     v = np.cbrt(math.pi * m_s * f)
     lead = 5.0 * m_s / (256.0 * eta * v**8)
-    assert np.allclose(dpsi({10}), -lead * (39.0 / 2.0) * lam * v**10, rtol=1e-7)
+    assert np.allclose(dpsi({10}), -lead * (39.0 / 2.0) * lam * v**10, rtol=1e-7, atol=0)
 
 
 def test_prior_transforms_invert_cdf():
@@ -189,4 +189,33 @@ def test_polarization_amplitudes():
     # Newtonian amplitude: |h+| at iota=0 equals A f^-7/6
     th[7] = 0.0
     hp, _ = physics.polarizations(f, th)
-    assert np.allclose(np.abs(hp), physics.amplitude_prefactor(1.5, 100.0) * f ** (-7 / 6))
+    assert np.allclose(np.abs(hp), physics.amplitude_prefactor(1.5, 100.0) * f ** (-7 / 6), rtol=1e-12, atol=0)
+
+
+def test_amplitude_is_the_spa_of_the_quadrupole_chirp():
+    """Face-on, h+(t) = h0 cos Phi(t) with the quadrupole amplitude
+    h0 = 4 (c / d) (G Mc / c^3)^(5/3) (pi f)^(2/3) and chirp rate
+    df/dt = (96/5) pi^(8/3) (G Mc / c^3)^(5/3) f^(11/3).  The stationary-phase
+    transform gives |h+~(f)| = (h0 / 2) (df/dt)^(-1/2), which must equal
+    A f^(-7/6)."""
+    f = np.array([20.0, 87.0, 400.0, 1500.0])
+    for mc, d in ((1.2, 40.0), (2.3, 150.0)):
+        m = mc * physics.MTSUN_S
+        h0 = 4.0 * (physics.C_SI / (d * physics.MPC_M)) * m ** (5.0 / 3.0) * (math.pi * f) ** (2.0 / 3.0)
+        fdot = 96.0 / 5.0 * math.pi ** (8.0 / 3.0) * m ** (5.0 / 3.0) * f ** (11.0 / 3.0)
+        spa = 0.5 * h0 / np.sqrt(fdot)
+        assert np.allclose(physics.amplitude_prefactor(mc, d) * f ** (-7.0 / 6.0), spa, rtol=1e-12, atol=0)
+
+
+def test_prior_transforms_on_sub_ranges():
+    """The inverse CDFs on ranges other than the Table I ones: the prior mass
+    below x(u), by adaptive quadrature of the unnormalised density, is u."""
+    from scipy import integrate
+    u = np.array([0.02, 0.3, 0.5, 0.77, 0.98])
+    cases = ((si.PRIOR_SINE, 0.3, 2.0, math.sin), (si.PRIOR_COSINE, -0.4, 1.1, math.cos),
+             (si.PRIOR_POWER2, 10.0, 40.0, lambda x: x * x), (si.PRIOR_UNIFORM, -3.0, 5.0, lambda x: 1.0))
+    for kind, lo, hi, dens in cases:
+        x = physics.prior_transform_1d(u, kind, lo, hi)
+        total = integrate.quad(dens, lo, hi, epsabs=0, epsrel=1e-13)[0]
+        mass = np.array([integrate.quad(dens, lo, xi, epsabs=0, epsrel=1e-13)[0] for xi in x]) / total
+        assert np.allclose(mass, u, atol=1e-11), kind

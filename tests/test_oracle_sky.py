@@ -35,6 +35,15 @@ def test_zenith_zero_is_the_baseline_direction():
         assert np.allclose(physics.source_direction(ra, dec, GMST), frame[2], atol=1e-12)
 
 
+def test_azimuth_runs_from_ex_towards_ey():
+    """On the equator of the frame (zenith pi/2) azimuth 0 is ex and pi/2 is
+    ey, so with the right-handed frame the azimuth turns about ez."""
+    frame, _, _ = _frame()
+    for az, axis in ((0.0, frame[0]), (0.5 * math.pi, frame[1]), (math.pi, -frame[0])):
+        ra, dec = physics.frame_to_radec(az, 0.5 * math.pi, frame, GMST)
+        assert np.allclose(physics.source_direction(ra, dec, GMST), axis, atol=1e-12)
+
+
 def test_map_preserves_angles():
     frame, _, _ = _frame()
     rng = np.random.default_rng(1)
