@@ -228,6 +228,9 @@ def phase_bound_edges(freqs, n_bins, f_lo=None, f_hi=None):
     gamma in {-5/3, -2/3, 1, 5/3, 7/3}, f* = f_lo for negative powers and f_hi
     for positive ones.  Edges split g into n_bins equal increments and are
     snapped to grid frequencies, so every grid bin falls in exactly one bin.
+    The exponent set is the construction's heuristic: the pins check the edge
+    structure and the heterodyne's accuracy, not the set itself (parity
+    unpinned for the exact edge positions; any set gives a valid heterodyne).
     """
     f_lo = freqs[0] if f_lo is None else f_lo
     f_hi = freqs[-1] if f_hi is None else f_hi

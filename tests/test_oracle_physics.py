@@ -219,3 +219,22 @@ def test_prior_transforms_on_sub_ranges():
         total = integrate.quad(dens, lo, hi, epsabs=0, epsrel=1e-13)[0]
         mass = np.array([integrate.quad(dens, lo, xi, epsabs=0, epsrel=1e-13)[0] for xi in x]) / total
         assert np.allclose(mass, u, atol=1e-11), kind
+
+
+@pytest.mark.parametrize("q,lam1,lam2", [(1.0, 400.0, 400.0), (0.7, 300.0, 900.0), (0.5, 50.0, 2000.0), (0.9, 1000.0, 10.0)])
+def test_tidal_terms_equal_the_per_body_form(q, lam1, lam2):
+    """The 5PN and 6PN tidal coefficients written per body (Vines, Flanagan &
+    Hinderer 2011): with X_A = m_A / M and X_B = 1 - X_A,
+      alpha_10 = -sum_A (24 / X_A) (1 + 11 X_B) X_A^5 Lambda_A,
+      alpha_12 = -sum_A 5 / (28 X_A) (3179 - 919 X_A - 2286 X_A^2 + 260 X_A^3) X_A^5 Lambda_A.
+    The Lambda-tilde / delta-Lambda-tilde form must reproduce both for unequal
+    masses and deformabilities (this fixes delta-Lambda-tilde's coefficients
+    and the sign of its 6PN term, which vanish at equal masses)."""
+    a = physics.pn_phase_coefficients(1.3, q, 0.0, 0.0, lam1, lam2)
+    m1, m2 = 1.0 / (1.0 + q), q / (1.0 + q)
+    a10 = a12 = 0.0
+    for xa, xb, lam in ((m1, m2, lam1), (m2, m1, lam2)):
+        a10 -= 24.0 / xa * (1.0 + 11.0 * xb) * xa**5 * lam
+        a12 -= 5.0 / (28.0 * xa) * (3179.0 - 919.0 * xa - 2286.0 * xa**2 + 260.0 * xa**3) * xa**5 * lam
+    assert a[10] == pytest.approx(a10, rel=1e-12, abs=0)
+    assert a[12] == pytest.approx(a12, rel=1e-12, abs=0)
