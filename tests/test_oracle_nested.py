@@ -109,6 +109,23 @@ def test_slice_kernel_leaves_constrained_uniform_invariant():
     assert stats.kstest((out / rstar) ** d, "uniform").pvalue > 0.01
 
 
+def test_one_slice_step_from_a_fixed_point_is_uniform_on_the_slice():
+    """On a one-dimensional slice (the interval L > L* = (0.3, 0.7)) one
+    stepping-out and shrinkage step from a fixed start lands uniformly on the
+    slice (Neal 2003): shrinkage only removes ground outside it.  20,000
+    independent steps from x0 = 0.32 near the edge: KS against U(0.3, 0.7),
+    and no step may stay at x0."""
+    ll = lambda u: -abs(float(u[0]) - 0.5)
+    chol = np.array([[0.15]])
+    rng = np.random.default_rng(12)
+    cnt = {"evals": 0, "shrink_caps": 0}
+    x0 = np.array([0.32])
+    out = np.array([nested.slice_step(x0, ll(x0), [0], chol, -0.2, ll, rng, cnt)[0][0] for _ in range(20000)])
+    assert cnt["shrink_caps"] == 0 and not np.any(out == x0[0])
+    assert np.all((out > 0.3) & (out < 0.7))
+    assert stats.kstest((out - 0.3) / 0.4, "uniform").pvalue > 1e-3
+
+
 def test_pp_calibration_on_gaussian_toys():
     rng = np.random.default_rng(21)
     levels = []
