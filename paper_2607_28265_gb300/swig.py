@@ -191,6 +191,16 @@ class Context:
                     precision=PREC_MIXED, proposal=PROPOSAL_COV, het_bins=0, het_spacing=0, dlogz=-3.0,
                     max_iter=100000, het_fiducial=None, learn_mix=0.0, learn_lr=0.0, learn_steps=0,
                     learn_interval=0, tmarg_nodes=0):
+        """swig_set_sampler: the fields of swig_sampler_cfg (include/swig.h).
+
+        nlive / nrep: live points m and deletions k per iteration; sweeps (M)
+        and steps_per_dim: Gibbs sweeps per replacement and slice steps per
+        dimension of a block; likelihood LIKE_FULL or LIKE_HET with het_bins,
+        het_spacing (0 equal phase change, 1 geometric) and het_fiducial (13
+        values); precision PREC_FP64 or PREC_MIXED; proposal PROPOSAL_COV or
+        PROPOSAL_LEARNED with learn_* (0 = library default); tmarg_nodes: grid
+        nodes over the t_c prior when t_c is marginalised (heterodyned only).
+        """
         cfg = SwigSamplerCfg()
         cfg.nlive, cfg.nrep, cfg.sweeps, cfg.steps_per_dim = nlive, nrep, sweeps, steps_per_dim
         cfg.seed, cfg.likelihood, cfg.precision, cfg.proposal = seed, likelihood, precision, proposal
