@@ -1,0 +1,65 @@
+// Host-only harness over the library's preparation code, for the CPU tests:
+// it compiles the C-ABI source into a small program that calls the pure host
+// routines (no device call is made, so it runs without a GPU) and prints
+// their results as JSON for comparison with numpy and the oracle.
+//
+//   host_harness edges F_MIN F_MAX DF N_BINS SPACING   heterodyne bin-edge indices
+//   host_harness gl N                                  Gauss-Legendre nodes, weights
+//   host_harness frame AX AY AZ BX BY BZ GMST          detector sky frame (b -> a)
+#include "../paper_2607_28265_gb300/csrc/capi.cu"
+
+#include <cstdlib>
+
+static void print_array(const char* name, const double* v, int n, bool last) {
+  std::printf("\"%s\": [", name);
+  for (int i = 0; i < n; ++i) std::printf("%s%.17g", i ? ", " : "", v[i]);
+  std::printf("]%s", last ? "" : ", ");
+}
+
+int main(int argc, char** argv) {
+  if (argc < 2) return 2;
+  const std::string what = argv[1];
+  if (what == "edges" && argc == 7) {
+    swig_ctx c;
+    if (swig_set_grid(&c, std::atof(argv[2]), std::atof(argv[3]), std::atof(argv[4])) != SWIG_OK) return 3;
+    std::vector<double> f((size_t)c.n_bins);
+    for (int64_t k = 0; k < c.n_bins; ++k) f[(size_t)k] = (double)(c.k_min + k) * c.df;
+    const std::vector<int> idx = het_edge_indices(f, std::atoi(argv[5]), std::atoi(argv[6]));
+    std::printf("{\"k_min\": %lld, \"n_bins\": %lld, \"idx\": [", (long long)c.k_min, (long long)c.n_bins);
+    for (size_t i = 0; i < idx.size(); ++i) std::printf("%s%d", i ? ", " : "", idx[i]);
+    std::printf("]}\n");
+    return 0;
+  }
+  if (what == "gl" && argc == 3) {
+    const int n = std::atoi(argv[2]);
+    std::vector<double> x(n), w(n);
+    gauss_legendre(n, x.data(), w.data());
+    std::printf("{");
+    print_array("x", x.data(), n, false);
+    print_array("w", w.data(), n, true);
+    std::printf("}\n");
+    return 0;
+  }
+  if (what == "frame" && argc == 9) {
+    swig_ctx c;
+    for (int k = 0; k < 3; ++k) {
+      c.vertex[0][k] = std::atof(argv[2 + k]);
+      c.vertex[1][k] = std::atof(argv[5 + k]);
+    }
+    c.det_set[0] = c.det_set[1] = true;
+    c.sky_a = 0;
+    c.sky_b = 1;
+    c.gmst = std::atof(argv[8]);
+    c.params[9] = swig_param{SWIG_PRIOR_UNIFORM, 0.0, 2.0 * kPi, SWIG_MODE_SAMPLE, 0.0, 4};
+    c.params[10] = swig_param{SWIG_PRIOR_SINE, 0.0, kPi, SWIG_MODE_SAMPLE, 0.0, 4};
+    SkyFrame F;
+    if (make_sky_frame(&c, &F) != SWIG_OK) return 4;
+    std::printf("{");
+    print_array("ex", F.ex, 3, false);
+    print_array("ey", F.ey, 3, false);
+    print_array("ez", F.ez, 3, true);
+    std::printf("}\n");
+    return 0;
+  }
+  return 2;
+}

@@ -1,0 +1,97 @@
+"""The library's host-side preparation, checked on the CPU (no GPU needed):
+`host_harness.cu` compiles the C-ABI source into a small program that calls
+the pure host routines, and their results must equal the oracle's and
+numpy's.
+
+* heterodyne bin edges (Sec. 3.4): the grid indices of the equal-dephasing
+  and geometric rules, bit for bit against the oracle (integer work), on the
+  4 s and 128 s grids;
+* the Gauss-Legendre rule of the distance marginal against numpy's leggauss;
+* the detector sky frame against the oracle's detector_frame.
+"""
+import json
+import os
+import shutil
+import subprocess
+
+import numpy as np
+import pytest
+
+import swig_inputs as si
+from oracle import likelihood as L
+from oracle import physics
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def harness(tmp_path_factory):
+    nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    if not os.path.exists(nvcc):
+        pytest.skip("nvcc not available")
+    from paper_2607_28265_gb300 import build, swig
+    if not os.path.exists(swig.LIB_PATH):
+        build.build()
+    lib_dir = os.path.dirname(swig.LIB_PATH)
+    exe = str(tmp_path_factory.mktemp("host") / "host_harness")
+    cmd = [nvcc, "-std=c++17", "-O1", "-gencode", "arch=compute_103a,code=sm_103a",
+           "-I", os.path.join(ROOT, "include"), "-I", os.path.join(ROOT, "paper_2607_28265_gb300", "csrc"),
+           os.path.join(ROOT, "tests", "host_harness.cu"), "-o", exe, "-L", lib_dir, "-lswig",
+           "-Xlinker", "-rpath", "-Xlinker", lib_dir]
+    r = subprocess.run(cmd, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-3000:]
+    return exe
+
+
+def _run(exe, *args):
+    r = subprocess.run([exe] + [str(a) for a in args], capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0, (args, r.returncode, r.stderr)
+    return json.loads(r.stdout)
+
+
+@pytest.mark.parametrize("which,bins", [("cfg1", (10, 150, 300, 451, 600, 1000)), ("cfg2", (1000, 5000))])
+def test_het_edge_indices_equal_the_oracle(harness, which, bins):
+    wl = si.config1() if which == "cfg1" else si.config2()
+    freqs = wl.freqs
+    for nb in bins:
+        for spacing in (0, 1):
+            out = _run(harness, "edges", repr(wl.f_min), repr(wl.f_max), repr(wl.df), nb, spacing)
+            assert out["n_bins"] == freqs.size and out["k_min"] * wl.df == freqs[0]
+            _, want = (L.phase_bound_edges(freqs, nb) if spacing == 0 else L.geometric_edges(freqs, nb))
+            assert np.array_equal(out["idx"], want), (which, nb, spacing)
+
+
+@pytest.mark.parametrize("n", [8, 64])
+def test_gauss_legendre_rule(harness, n):
+    """Against the roots of P_n and the weights 2 / ((1 - x^2) P_n'(x)^2) in
+    40-digit arithmetic (mpmath, Newton from numpy's estimates), and against
+    numpy's leggauss (itself good to ~1e-12 relative in the weights at n = 64)."""
+    mpmath = pytest.importorskip("mpmath")
+    out = _run(harness, "gl", n)
+    xn, wn = np.polynomial.legendre.leggauss(n)
+    with mpmath.workdps(40):
+        xr, wr = [], []
+        for x0 in xn:
+            x = mpmath.mpf(float(x0))
+            for _ in range(60):
+                dp = n * (x * mpmath.legendre(n, x) - mpmath.legendre(n - 1, x)) / (x * x - 1)
+                x -= mpmath.legendre(n, x) / dp
+            dp = n * (x * mpmath.legendre(n, x) - mpmath.legendre(n - 1, x)) / (x * x - 1)
+            xr.append(float(x))
+            wr.append(float(2 / ((1 - x * x) * dp * dp)))
+    assert np.allclose(out["x"], xr, rtol=0, atol=4e-16)
+    assert np.allclose(out["w"], wr, rtol=3e-13, atol=0)
+    assert np.allclose(out["w"], wn, rtol=5e-12, atol=0)
+    assert abs(sum(out["w"]) - 2.0) < 1e-13
+
+
+def test_sky_frame_equals_the_oracle(harness):
+    gmst = si.gmst_from_gps(si.REFERENCE_GPS)
+    for a, b in (("H1", "L1"), ("L1", "V1"), ("V1", "H1")):
+        va, _, _ = si.site_vectors(a)
+        vb, _, _ = si.site_vectors(b)
+        out = _run(harness, "frame", *[repr(float(v)) for v in va], *[repr(float(v)) for v in vb], repr(gmst))
+        ex, ey, ez = physics.detector_frame(va, vb)
+        assert np.allclose(out["ex"], ex, rtol=0, atol=1e-14)
+        assert np.allclose(out["ey"], ey, rtol=0, atol=1e-14)
+        assert np.allclose(out["ez"], ez, rtol=0, atol=1e-14)
