@@ -6,6 +6,7 @@
 //   host_harness edges F_MIN F_MAX DF N_BINS SPACING   heterodyne bin-edge indices
 //   host_harness gl N                                  Gauss-Legendre nodes, weights
 //   host_harness frame AX AY AZ BX BY BZ GMST          detector sky frame (b -> a)
+//   host_harness tiles F_MIN F_MAX DF                  phase tiles of the mixed path
 #include "../paper_2607_28265_gb300/csrc/capi.cu"
 
 #include <cstdlib>
@@ -59,6 +60,41 @@ int main(int argc, char** argv) {
     print_array("ey", F.ey, 3, false);
     print_array("ez", F.ez, 3, true);
     std::printf("}\n");
+    return 0;
+  }
+  if (what == "tiles" && argc == 5) {
+    swig_ctx c;
+    if (swig_set_grid(&c, std::atof(argv[2]), std::atof(argv[3]), std::atof(argv[4])) != SWIG_OK) return 3;
+    double cmax[NBASIS];
+    coefficient_bounds(&c, cmax);
+    std::vector<TileInfo> tiles;
+    std::vector<TileBasis> basis;
+    plan_tiles(&c, tiles, basis);
+    std::printf("{\"k_min\": %lld, ", (long long)c.k_min);
+    print_array("cmax", cmax, NBASIS, false);
+    std::printf("\"tiles\": [");
+    for (size_t t = 0; t < tiles.size(); ++t) {
+      const TileInfo& ti = tiles[t];
+      const TileBasis& tb = basis[t];
+      std::printf("%s{\"k0\": %d, \"nbins\": %d, \"inv_T\": %.9g, ", t ? ", " : "", ti.k0, ti.nbins, ti.inv_T);
+      double v[NBASIS], s[NBASIS];
+      for (int j = 0; j < NBASIS; ++j) {
+        v[j] = (double)tb.val_hi[j] + (double)tb.val_lo[j];
+        s[j] = (double)tb.slope_hi[j] + (double)tb.slope_lo[j];
+      }
+      print_array("val", v, NBASIS, false);
+      print_array("slope", s, NBASIS, false);
+      std::printf("\"poly\": [");
+      for (int m = 0; m < kNumPoly; ++m) {
+        double pm[NBASIS];
+        for (int j = 0; j < NBASIS; ++j) pm[j] = tb.poly[m][j];
+        std::printf("%s[", m ? ", " : "");
+        for (int j = 0; j < NBASIS; ++j) std::printf("%s%.9g", j ? ", " : "", pm[j]);
+        std::printf("]");
+      }
+      std::printf("]}");
+    }
+    std::printf("]}\n");
     return 0;
   }
   return 2;

@@ -10,6 +10,7 @@ numpy's.
 * the detector sky frame against the oracle's detector_frame.
 """
 import json
+import math
 import os
 import shutil
 import subprocess
@@ -95,3 +96,71 @@ def test_sky_frame_equals_the_oracle(harness):
         assert np.allclose(out["ex"], ex, rtol=0, atol=1e-14)
         assert np.allclose(out["ey"], ey, rtol=0, atol=1e-14)
         assert np.allclose(out["ez"], ez, rtol=0, atol=1e-14)
+
+
+# The phase basis P(f) = sum_j c_j phi_j(f) of the mixed path, in the
+# library's order: f^-5/3, f^-1, f^-2/3, f^-1/3, ln f, f^1/3, f^1/3 ln f,
+# f^2/3, f^5/3, f^7/3, 1 (power, carries ln f).
+_BASIS = [(-5 / 3, 0), (-1.0, 0), (-2 / 3, 0), (-1 / 3, 0), (0.0, 1), (1 / 3, 0), (1 / 3, 1), (2 / 3, 0),
+          (5 / 3, 0), (7 / 3, 0), (0.0, 0)]
+
+
+def _falling(p, n):
+    out = 1.0
+    for i in range(n):
+        out *= p - i
+    return out
+
+
+def _deriv(p, lg, n, f):
+    """n-th derivative of f^p (ln f)^lg, by the Leibniz rule with
+    d^k ln f = (-1)^(k-1) (k-1)! f^-k."""
+    f = np.asarray(f, dtype=np.float64)
+    if not lg:
+        return _falling(p, n) * f ** (p - n)
+    s = sum(math.comb(n, k) * _falling(p, n - k) * (-1) ** (k - 1) * math.factorial(k - 1) for k in range(1, n + 1))
+    return f ** (p - n) * (_falling(p, n) * np.log(f) + s)
+
+
+@pytest.mark.parametrize("which", ["cfg1", "cfg2"])
+def test_tile_plan_meets_its_remainder_bound(harness, which):
+    """The tiles of the mixed-precision phase: they cover the grid in powers of
+    two (2048 at most, aligned to 32-bin chunks), their stored basis values are
+    the analytic derivatives, and over every tile the degree-6 Taylor
+    remainder, summed over the basis with the coefficient bounds of the prior
+    box, stays below 1e-8 cycles."""
+    wl = si.config1() if which == "cfg1" else si.config2()
+    out = _run(harness, "tiles", repr(wl.f_min), repr(wl.f_max), repr(wl.df))
+    tiles, cmax = out["tiles"], np.array(out["cmax"])
+    n = wl.freqs.size
+    k = 0
+    for i, t in enumerate(tiles):
+        assert t["k0"] == k
+        span = 1 << max(0, (t["nbins"] - 1).bit_length())
+        assert span <= 2048 and t["inv_T"] == 1.0 / span
+        if i < len(tiles) - 1:
+            assert t["nbins"] == span
+        assert t["k0"] % min(span, 32) == 0
+        k += t["nbins"]
+    assert k == n
+    worst = 0.0
+    for t in tiles:
+        fa = (out["k_min"] + t["k0"]) * wl.df
+        x = np.arange(t["nbins"], dtype=np.float64)
+        f = fa + x * wl.df
+        span = 1.0 / t["inv_T"]
+        r = 0.0
+        for j, (p, lg) in enumerate(_BASIS):
+            if p == 0.0 and not lg:
+                continue
+            d = [float(_deriv(p, lg, m, fa)) for m in range(7)]
+            assert t["val"][j] == pytest.approx(d[0], rel=1e-14, abs=0)
+            assert t["slope"][j] == pytest.approx(d[1] * wl.df, rel=1e-14, abs=0)
+            for m in range(5):
+                want = d[m + 2] * (wl.df * span) ** (m + 2) / math.factorial(m + 2)
+                assert t["poly"][m][j] == pytest.approx(want, rel=2e-7, abs=1e-300)
+            taylor = sum(d[m] * (x * wl.df) ** m / math.factorial(m) for m in range(7))
+            exact = _deriv(p, lg, 0, f)
+            r += cmax[j] * float(np.max(np.abs(exact - taylor)))
+        worst = max(worst, r)
+    assert worst < 1e-8, worst
