@@ -7,6 +7,8 @@
 //   host_harness gl N                                  Gauss-Legendre nodes, weights
 //   host_harness frame AX AY AZ BX BY BZ GMST          detector sky frame (b -> a)
 //   host_harness tiles F_MIN F_MAX DF                  phase tiles of the mixed path
+//   host_harness coeffs MC Q CHI1 CHI2 LAM1 LAM2       TaylorF2 phase-basis coefficients
+//                                                      (the host/device set-up code)
 #include "../paper_2607_28265_gb300/csrc/capi.cu"
 
 #include <cstdlib>
@@ -59,6 +61,15 @@ int main(int argc, char** argv) {
     print_array("ex", F.ex, 3, false);
     print_array("ey", F.ey, 3, false);
     print_array("ez", F.ez, 3, true);
+    std::printf("}\n");
+    return 0;
+  }
+  if (what == "coeffs" && argc == 8) {
+    double cc[NBASIS];
+    taylorf2_basis_coeffs(std::atof(argv[2]), std::atof(argv[3]), std::atof(argv[4]), std::atof(argv[5]),
+                          std::atof(argv[6]), std::atof(argv[7]), cc);
+    std::printf("{");
+    print_array("c", cc, NBASIS, true);
     std::printf("}\n");
     return 0;
   }

@@ -164,3 +164,17 @@ def test_tile_plan_meets_its_remainder_bound(harness, which):
             r += cmax[j] * float(np.max(np.abs(exact - taylor)))
         worst = max(worst, r)
     assert worst < 1e-8, worst
+
+
+@pytest.mark.parametrize("theta", [(1.2, 0.8, 0.0, 0.0, 0.0, 0.0), (1.5, 0.5, 0.05, -0.05, 0.0, 5000.0),
+                                   (2.5, 1.0, -0.05, 0.05, 5000.0, 0.0), (1.87, 0.71, 0.013, -0.037, 812.0, 2240.0)])
+def test_phase_coefficients_equal_the_oracle_phase(harness, theta):
+    """The TaylorF2 phase in cycles, sum_j c_j(theta) phi_j(f) with the
+    coefficients of the set-up code the device also runs, equals the oracle's
+    Psi_int(f) / 2 pi over 20-2048 Hz (h ~ exp(-2 pi i (P(f) + f tau)))."""
+    mc, q, chi1, chi2, lam1, lam2 = theta
+    c = np.array(_run(harness, "coeffs", *[repr(float(v)) for v in theta])["c"])
+    f = np.geomspace(20.0, 2048.0, 3001)
+    P = sum(c[j] * _deriv(p, lg, 0, f) for j, (p, lg) in enumerate(_BASIS))
+    want = physics.taylorf2_phase_intrinsic(f, mc, q, chi1, chi2, lam1, lam2) / (2 * math.pi)
+    assert np.allclose(P, want, rtol=1e-12, atol=1e-9)
