@@ -9,6 +9,11 @@
 //   host_harness tiles F_MIN F_MAX DF                  phase tiles of the mixed path
 //   host_harness coeffs MC Q CHI1 CHI2 LAM1 LAM2       TaylorF2 phase-basis coefficients
 //                                                      (the host/device set-up code)
+//   host_harness amp MC                                SPA amplitude at 1 Mpc
+//   host_harness logi0 X...                            log I0(x) (FP64) and log(I0(x) e^-x) (FP32)
+//   host_harness distmarg KIND LO HI PM ZRE ZIM H DD   distance-marginal logL (64-node rule)
+//   host_harness prior KIND LO HI U...                 prior inverse CDF of one slot
+//   host_harness sky AX AY AZ BX BY BZ GMST AZI ZEN    frame (azimuth, zenith) -> (RA, Dec)
 #include "../paper_2607_28265_gb300/csrc/capi.cu"
 
 #include <cstdlib>
@@ -71,6 +76,63 @@ int main(int argc, char** argv) {
     std::printf("{");
     print_array("c", cc, NBASIS, true);
     std::printf("}\n");
+    return 0;
+  }
+  if (what == "amp" && argc == 3) {
+    std::printf("{\"amp\": %.17g}\n", amplitude_per_mpc(std::atof(argv[2])));
+    return 0;
+  }
+  if (what == "logi0" && argc >= 3) {
+    std::vector<double> a, b;
+    for (int i = 2; i < argc; ++i) {
+      const double x = std::atof(argv[i]);
+      a.push_back(log_bessel_i0(x));
+      b.push_back((double)log_i0e_f32((float)x));
+    }
+    std::printf("{");
+    print_array("log_i0", a.data(), (int)a.size(), false);
+    print_array("log_i0e_f32", b.data(), (int)b.size(), true);
+    std::printf("}\n");
+    return 0;
+  }
+  if (what == "distmarg" && argc == 10) {
+    LikeConst L{};
+    L.dist_marg = 1;
+    L.d_kind = std::atoi(argv[2]);
+    L.d_lo = std::atof(argv[3]);
+    L.d_hi = std::atof(argv[4]);
+    L.phase_marg = std::atoi(argv[5]);
+    L.DD = std::atof(argv[9]);
+    gauss_legendre(kGaussLegendre, L.gl_x, L.gl_w);
+    std::printf("{\"logl\": %.17g}\n", distance_marg_logl(L, std::atof(argv[6]), std::atof(argv[7]), std::atof(argv[8])));
+    return 0;
+  }
+  if (what == "prior" && argc >= 6) {
+    const PriorSlot s = make_prior_slot(std::atoi(argv[2]), SWIG_MODE_SAMPLE, std::atof(argv[3]), std::atof(argv[4]), 0.0);
+    std::vector<double> x;
+    for (int i = 5; i < argc; ++i) x.push_back(prior_slot_inverse(s, std::atof(argv[i])));
+    std::printf("{");
+    print_array("x", x.data(), (int)x.size(), true);
+    std::printf("}\n");
+    return 0;
+  }
+  if (what == "sky" && argc == 11) {
+    swig_ctx c;
+    for (int k = 0; k < 3; ++k) {
+      c.vertex[0][k] = std::atof(argv[2 + k]);
+      c.vertex[1][k] = std::atof(argv[5 + k]);
+    }
+    c.det_set[0] = c.det_set[1] = true;
+    c.sky_a = 0;
+    c.sky_b = 1;
+    c.gmst = std::atof(argv[8]);
+    c.params[9] = swig_param{SWIG_PRIOR_UNIFORM, 0.0, 2.0 * kPi, SWIG_MODE_SAMPLE, 0.0, 4};
+    c.params[10] = swig_param{SWIG_PRIOR_SINE, 0.0, kPi, SWIG_MODE_SAMPLE, 0.0, 4};
+    SkyFrame F;
+    if (make_sky_frame(&c, &F) != SWIG_OK) return 4;
+    double ra, dec;
+    sky_frame_to_radec(F, std::atof(argv[9]), std::atof(argv[10]), &ra, &dec);
+    std::printf("{\"ra\": %.17g, \"dec\": %.17g}\n", ra, dec);
     return 0;
   }
   if (what == "tiles" && argc == 5) {

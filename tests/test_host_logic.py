@@ -178,3 +178,65 @@ def test_phase_coefficients_equal_the_oracle_phase(harness, theta):
     P = sum(c[j] * _deriv(p, lg, 0, f) for j, (p, lg) in enumerate(_BASIS))
     want = physics.taylorf2_phase_intrinsic(f, mc, q, chi1, chi2, lam1, lam2) / (2 * math.pi)
     assert np.allclose(P, want, rtol=1e-12, atol=1e-9)
+
+
+def test_amplitude_equals_the_oracle(harness):
+    for mc in (0.9, 1.2, 1.87, 2.9):
+        got = _run(harness, "amp", repr(mc))["amp"]
+        assert got == pytest.approx(physics.amplitude_prefactor(mc, 1.0), rel=1e-14, abs=0)
+
+
+def test_log_bessel_i0_forms(harness):
+    """log I0 (FP64, both branches and their seam at x = 20) against scipy's
+    i0e: within 2e-14 relative, and 1e-12 absolute just past the seam, where the
+    asymptotic series' truncation (~3e-13) is largest.  The FP32
+    log(I0(x) e^-x) of the mixed epilogues within 2e-6: FP32 summation of the
+    power series below x = 20, ~1e-6 there."""
+    from scipy.special import i0e
+    xs = [0.0, 1e-3, 0.5, 5.0, 19.99, 20.01, 25.0, 100.0, 700.0, 5000.0]
+    out = _run(harness, "logi0", *[repr(x) for x in xs])
+    want = np.log(i0e(xs))
+    assert np.allclose(out["log_i0"], want + np.array(xs), rtol=2e-14, atol=1e-12)
+    assert np.allclose(out["log_i0e_f32"], want, rtol=0, atol=2e-6)
+
+
+@pytest.mark.parametrize("kind,lo,hi", [(si.PRIOR_POWER2, 30.0, 150.0), (si.PRIOR_UNIFORM, 20.0, 200.0)])
+@pytest.mark.parametrize("phase_marg", [0, 1])
+def test_distance_marginal_epilogue_equals_the_oracle(harness, kind, lo, hi, phase_marg):
+    """The 64-node distance marginal of the epilogues (template at 1 Mpc: Z1,
+    H1) against the oracle's adaptive quadrature, from no signal to a peak
+    inside, at and beyond the prior edges; tolerance as on the GPU."""
+    p = si.Param(kind, lo, hi, si.MODE_MARG)
+    dd = 4.0e3
+    for snr2_at_100, d_peak in ((0.0, 100.0), (50.0, 80.0), (400.0, 100.0), (900.0, 35.0), (600.0, 140.0),
+                                (400.0, 20.0), (400.0, 400.0), (3.0, 60.0)):
+        h1 = snr2_at_100 * 100.0 ** 2
+        z1 = complex(h1 / d_peak, 0.3 * h1 / d_peak) if phase_marg else complex(h1 / d_peak, 0.0)
+        got = _run(harness, "distmarg", kind, repr(lo), repr(hi), phase_marg, repr(z1.real), repr(z1.imag),
+                   repr(h1), repr(dd))["logl"]
+        want = L.log_distance_integral(z1, h1, dd, p, bool(phase_marg))
+        assert abs(got - want) <= 1e-6 * abs(want) + 1e-4, (snr2_at_100, d_peak, got, want)
+
+
+def test_prior_inverse_cdfs_equal_the_oracle(harness):
+    u = [0.0, 0.013, 0.25, 0.5, 0.77, 0.999, 1.0]
+    for kind, lo, hi in ((si.PRIOR_UNIFORM, -0.1, 0.1), (si.PRIOR_SINE, 0.0, math.pi), (si.PRIOR_SINE, 0.3, 2.0),
+                         (si.PRIOR_COSINE, -math.pi / 2, math.pi / 2), (si.PRIOR_COSINE, -0.4, 1.1),
+                         (si.PRIOR_POWER2, 30.0, 150.0)):
+        got = _run(harness, "prior", kind, repr(lo), repr(hi), *[repr(x) for x in u])["x"]
+        want = physics.prior_transform_1d(np.array(u), kind, lo, hi)
+        assert np.allclose(got, want, rtol=1e-13, atol=1e-14), kind
+
+
+def test_sky_frame_map_equals_the_oracle(harness):
+    gmst = si.gmst_from_gps(si.REFERENCE_GPS)
+    va, _, _ = si.site_vectors("H1")
+    vb, _, _ = si.site_vectors("L1")
+    frame = physics.detector_frame(va, vb)
+    rng = np.random.default_rng(4)
+    for az, zen in zip(rng.random(6) * 2 * math.pi, np.arccos(1 - 2 * rng.random(6))):
+        got = _run(harness, "sky", *[repr(float(v)) for v in va], *[repr(float(v)) for v in vb], repr(gmst),
+                   repr(float(az)), repr(float(zen)))
+        ra, dec = physics.frame_to_radec(az, zen, frame, gmst)
+        assert abs(got["dec"] - dec) < 1e-12
+        assert abs(math.remainder(got["ra"] - ra, 2 * math.pi)) < 1e-12
