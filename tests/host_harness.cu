@@ -14,6 +14,8 @@
 //   host_harness distmarg KIND LO HI PM ZRE ZIM H DD   distance-marginal logL (64-node rule)
 //   host_harness prior KIND LO HI U...                 prior inverse CDF of one slot
 //   host_harness sky AX AY AZ BX BY BZ GMST AZI ZEN    frame (azimuth, zenith) -> (RA, Dec)
+//   host_harness priormap < SLOTS ROWS                 13 slots (kind mode lo hi value) then
+//                                                      rows of sampled unit-cube coordinates
 #include "../paper_2607_28265_gb300/csrc/capi.cu"
 
 #include <cstdlib>
@@ -133,6 +135,31 @@ int main(int argc, char** argv) {
     double ra, dec;
     sky_frame_to_radec(F, std::atof(argv[9]), std::atof(argv[10]), &ra, &dec);
     std::printf("{\"ra\": %.17g, \"dec\": %.17g}\n", ra, dec);
+    return 0;
+  }
+  if (what == "priormap" && argc == 2) {
+    PriorSlot slots[SWIG_N_PARAMS];
+    int n_sampled = 0;
+    for (int i = 0; i < SWIG_N_PARAMS; ++i) {
+      int kind, mode;
+      double lo, hi, value;
+      if (std::scanf("%d %d %lf %lf %lf", &kind, &mode, &lo, &hi, &value) != 5) return 5;
+      slots[i] = make_prior_slot(kind, mode, lo, hi, value);
+      n_sampled += mode == SWIG_MODE_SAMPLE;
+    }
+    std::printf("{\"theta\": [");
+    for (int row = 0;; ++row) {
+      double u[SWIG_N_PARAMS];
+      int got = 0;
+      for (int j = 0; j < n_sampled; ++j) got += std::scanf("%lf", &u[j]);
+      if (got != n_sampled) break;
+      double th[SWIG_N_PARAMS];
+      prior_map(slots, u, th);
+      std::printf("%s[", row ? ", " : "");
+      for (int j = 0; j < SWIG_N_PARAMS; ++j) std::printf("%s%.17g", j ? ", " : "", th[j]);
+      std::printf("]");
+    }
+    std::printf("]}\n");
     return 0;
   }
   if (what == "tiles" && argc == 5) {

@@ -240,3 +240,23 @@ def test_sky_frame_map_equals_the_oracle(harness):
         ra, dec = physics.frame_to_radec(az, zen, frame, gmst)
         assert abs(got["dec"] - dec) < 1e-12
         assert abs(math.remainder(got["ra"] - ra, 2 * math.pi)) < 1e-12
+
+
+def test_prior_map_places_sampled_and_fixed_slots_like_the_oracle(harness):
+    """The full 13-slot map of the sampler and the batched transform (sampled
+    coordinates in slot order, fixed slots at their values) against the
+    oracle's prior_transform, on the 128 s and 4 s workloads' priors."""
+    rng = np.random.default_rng(6)
+    for wl in (si.config2(), si.config1()):
+        params = wl.params
+        spec = "\n".join(f"{p.kind} {p.mode} {p.lo!r} {p.hi!r} {p.value!r}" for p in params)
+        u = rng.random((5, len(wl.sampled())))
+        rows = "\n".join(" ".join(repr(float(v)) for v in r) for r in u)
+        r = subprocess.run([harness, "priormap"], input=spec + "\n" + rows + "\n", capture_output=True, text=True,
+                           timeout=60)
+        assert r.returncode == 0, r.stderr
+        got = np.array(json.loads(r.stdout)["theta"])
+        want = physics.prior_transform(u, params)
+        keep = [i for i, p in enumerate(params) if p.mode != si.MODE_MARG]
+        assert got.shape == want.shape
+        assert np.allclose(got[:, keep], want[:, keep], rtol=1e-13, atol=1e-14)
