@@ -16,9 +16,13 @@
 //   host_harness sky AX AY AZ BX BY BZ GMST AZI ZEN    frame (azimuth, zenith) -> (RA, Dec)
 //   host_harness priormap < SLOTS ROWS                 13 slots (kind mode lo hi value) then
 //                                                      rows of sampled unit-cube coordinates
+//   host_harness abi                                   sizes and field offsets of the C-ABI structs
 #include "../paper_2607_28265_gb300/csrc/capi.cu"
 
+#include <cstddef>
 #include <cstdlib>
+
+#define SWIG_FIELD(T, f) std::printf("%s[\"%s\", %zu]", first ? "" : ", ", #f, offsetof(T, f)), first = false
 
 static void print_array(const char* name, const double* v, int n, bool last) {
   std::printf("\"%s\": [", name);
@@ -160,6 +164,31 @@ int main(int argc, char** argv) {
       std::printf("]");
     }
     std::printf("]}\n");
+    return 0;
+  }
+  if (what == "abi" && argc == 2) {
+    bool first = true;
+    std::printf("{\"swig_param\": {\"size\": %zu, \"fields\": [", sizeof(swig_param));
+    SWIG_FIELD(swig_param, kind); SWIG_FIELD(swig_param, lo); SWIG_FIELD(swig_param, hi);
+    SWIG_FIELD(swig_param, mode); SWIG_FIELD(swig_param, value); SWIG_FIELD(swig_param, block);
+    first = true;
+    std::printf("]}, \"swig_sampler_cfg\": {\"size\": %zu, \"fields\": [", sizeof(swig_sampler_cfg));
+    SWIG_FIELD(swig_sampler_cfg, nlive); SWIG_FIELD(swig_sampler_cfg, nrep); SWIG_FIELD(swig_sampler_cfg, sweeps);
+    SWIG_FIELD(swig_sampler_cfg, steps_per_dim); SWIG_FIELD(swig_sampler_cfg, seed);
+    SWIG_FIELD(swig_sampler_cfg, likelihood); SWIG_FIELD(swig_sampler_cfg, precision);
+    SWIG_FIELD(swig_sampler_cfg, proposal); SWIG_FIELD(swig_sampler_cfg, het_bins);
+    SWIG_FIELD(swig_sampler_cfg, het_spacing); SWIG_FIELD(swig_sampler_cfg, dlogz);
+    SWIG_FIELD(swig_sampler_cfg, max_iter); SWIG_FIELD(swig_sampler_cfg, het_fiducial);
+    SWIG_FIELD(swig_sampler_cfg, learn_mix); SWIG_FIELD(swig_sampler_cfg, learn_lr);
+    SWIG_FIELD(swig_sampler_cfg, learn_steps); SWIG_FIELD(swig_sampler_cfg, learn_interval);
+    SWIG_FIELD(swig_sampler_cfg, tmarg_nodes);
+    first = true;
+    std::printf("]}, \"swig_result\": {\"size\": %zu, \"fields\": [", sizeof(swig_result));
+    SWIG_FIELD(swig_result, logz); SWIG_FIELD(swig_result, logz_err); SWIG_FIELD(swig_result, info);
+    SWIG_FIELD(swig_result, ess); SWIG_FIELD(swig_result, wall_s); SWIG_FIELD(swig_result, n_dead);
+    SWIG_FIELD(swig_result, n_iter); SWIG_FIELD(swig_result, n_evals); SWIG_FIELD(swig_result, n_sweep_evals);
+    SWIG_FIELD(swig_result, status);
+    std::printf("]}}\n");
     return 0;
   }
   if (what == "tiles" && argc == 5) {

@@ -9,6 +9,7 @@ numpy's.
 * the Gauss-Legendre rule of the distance marginal against numpy's leggauss;
 * the detector sky frame against the oracle's detector_frame.
 """
+import ctypes
 import json
 import math
 import os
@@ -260,3 +261,18 @@ def test_prior_map_places_sampled_and_fixed_slots_like_the_oracle(harness):
         keep = [i for i, p in enumerate(params) if p.mode != si.MODE_MARG]
         assert got.shape == want.shape
         assert np.allclose(got[:, keep], want[:, keep], rtol=1e-13, atol=1e-14)
+
+
+def test_binding_structs_match_the_c_abi(harness):
+    """The ctypes structures of the Python binding have the C structs' field
+    order, offsets and sizes (compiled from include/swig.h), and every field
+    the header declares."""
+    from paper_2607_28265_gb300 import swig
+    out = _run(harness, "abi")
+    for cname, py in (("swig_param", swig.SwigParam), ("swig_sampler_cfg", swig.SwigSamplerCfg),
+                      ("swig_result", swig.SwigResult)):
+        c = out[cname]
+        assert c["size"] == ctypes.sizeof(py), cname
+        assert [f for f, _ in c["fields"]] == [f[0] for f in py._fields_], cname
+        for f, off in c["fields"]:
+            assert getattr(py, f).offset == off, (cname, f)
