@@ -21,7 +21,8 @@ them) and wall-seconds per posterior (= ms_per_step / 1000).
   cfg1      4 s single detector, 4,017 bins, FP64, nlive 100
   cfg3      cfg1 data, heterodyned likelihood, 450 geometric bins, nlive 1000
 
-Output: one JSON line on rank 0.  ``--impl reference`` times the FP64 CPU
+Output: one JSON line on rank 0 (with ``sampler_profile``, the sampler's
+device phase timers averaged over the timed posteriors).  ``--impl reference`` times the FP64 CPU
 oracle on the same workload instead (bounded samples of likelihood
 evaluations per step on the host cores).
 """
@@ -437,6 +438,12 @@ def run_gpu(args, rank, world):
     if args.cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(args.workload, seconds=args.cpu_seconds,
                                             evals_per_posterior=total_evals / max(1, args.steps))
+    # the sampler's own device counters, averaged over the timed posteriors:
+    # phase times, chain 0's control cycles by part, sweep-unit cycles
+    prof_keys = ("rounds", "boundary_s", "control_s", "wait_control_s", "sweep_s", "wait_sweep_s", "cyc_result",
+                 "cyc_step", "cyc_prop", "cyc_free", "cyc_setup", "n_free", "n_setup", "n_step", "f_units",
+                 "f_unit_cyc", "f_idle_cyc")
+    line["sampler_profile"] = {k: float(np.mean([p.get(k, 0.0) for _, _, p in results])) for k in prof_keys}
     if prof_learn := sum(p.get("learn_ms", 0.0) for _, _, p in results):
         line["learned"] = {"train_ms_per_posterior": prof_learn / args.steps,
                            "retrainings_per_posterior": sum(p.get("learn_rounds", 0) for _, _, p in results) / args.steps}
