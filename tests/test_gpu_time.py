@@ -7,8 +7,9 @@ Tolerance: as for the heterodyned likelihood (1e-6 relative to |logL| plus
 over the edges.  A term's phasor comes from an exact double-float phase at the
 chunk's first node, then up to 31 FP32 rotation steps.  Each step adds about
 6e-8 of relative error, so no term drifts by more than ~2e-6.  That is
-2e-6 x sum_e |y_e| at worst, a few 1e-3 on the 128 s workload (sum_e |y_e| ~
-3e3), below the 0.78 that 1e-6 |logL| allows there.  The node log weights
+2e-6 x sum_e |y_e| at worst, 2.4e-3 on the 128 s workload (sum_e |y_e| = 1.2e3
+at the fiducial, the oracle's summary data), below the 0.78 that 1e-6 |logL|
+allows there.  The node log weights
 and their log-sum-exp are FP32; the rest of the epilogue is FP64.
 """
 import math
