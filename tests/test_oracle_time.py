@@ -174,3 +174,35 @@ def test_time_grid_is_the_midpoint_rule():
         bad = list(wl.params)
         bad[TC] = si.Param(si.PRIOR_SINE, 0.0, 1.0, si.MODE_MARG)
         L.time_grid(bad, 3)
+
+
+def test_collapsed_edge_sum_equals_the_binned_overlap():
+    """The form the device evaluates: with hat weights
+    g_ie = [A0_ib/2 - A1_ib/w_b]_(b = e) + [A0_ib/2 + A1_ib/w_b]_(b = e - 1) and
+    y_e = sum_i g_ie r_i(e) (ratios at the fiducial's t_c), the overlap at a
+    shift dt is sum_e y_e exp(-2 pi i f_e dt); it must equal the per-bin
+    heterodyned overlap of the template moved by dt (128 s, H1/L1/V1)."""
+    from oracle import physics
+    wl = si.config2()
+    ev, th = events.build_event(wl)
+    params = _params(wl, phase_marg=True)
+    evt = _event(ev, params)
+    het = L.het_setup(evt, th, 1000)
+    theta = th.copy()
+    theta[0] *= 1.0 + 3e-6
+    theta[si.IDX["ra"]] += 0.01
+    nodes = th[TC] + np.array([-2e-3, -1e-4, 0.0, 3e-5, 7e-4])
+    z_bins, _ = L.het_time_overlaps(evt, het, theta, nodes)
+    w = het.edges[1:] - het.edges[:-1]
+    th_ref = theta.copy()
+    th_ref[TC] = th[TC]
+    th_ref[si.IDX["phic"]] = 0.0
+    y = np.zeros(het.edges.size, complex)
+    for i, det in enumerate(evt.detectors):
+        r = physics.detector_strain(het.edges, th_ref, det, evt.gmst) / het.h0_edges[i]
+        g = np.zeros(het.edges.size, complex)
+        g[:-1] += 0.5 * het.A0[i] - het.A1[i] / w
+        g[1:] += 0.5 * het.A0[i] + het.A1[i] / w
+        y += g * r
+    z_edges = np.array([np.sum(y * np.exp(-2j * math.pi * het.edges * (t - th[TC]))) for t in nodes])
+    assert np.allclose(z_edges, z_bins, rtol=1e-11, atol=1e-9 * np.max(np.abs(z_bins)))
