@@ -293,6 +293,40 @@ std::vector<int> het_edge_indices(const std::vector<double>& f, int nb, int spac
   return idx;
 }
 
+// Tables of the time-marginalised heterodyne, in FP64 and stored FP32: the
+// edge weights g_ie (Z_i = sum_e g_ie r_i(e): the bin above an edge gives
+// A0/2 - A1/w, the bin below A0/2 + A1/w) from a01 = (A0.re, A0.im, A1.re,
+// A1.im) per detector and bin, and the rotation exp(-2 pi i f_e dt) of each
+// edge per grid step.  f[idx[q]] is the frequency of edge q.
+void het_tm_tables(const std::vector<double>& a01, const std::vector<double>& f, const std::vector<int>& idx,
+                   int nb, int n_det, double dt, std::vector<float2>& g, std::vector<float2>& w) {
+  const size_t ne = (size_t)nb + 1;
+  g.assign((size_t)n_det * ne, make_float2(0.0f, 0.0f));
+  w.assign(ne, make_float2(0.0f, 0.0f));
+  for (int i = 0; i < n_det; ++i)
+    for (int q = 0; q <= nb; ++q) {
+      double gr = 0.0, gi = 0.0;
+      if (q < nb) {
+        const double* a = &a01[((size_t)i * nb + q) * 4];
+        const double iw = 1.0 / (f[idx[q + 1]] - f[idx[q]]);
+        gr += 0.5 * a[0] - a[2] * iw;
+        gi += 0.5 * a[1] - a[3] * iw;
+      }
+      if (q > 0) {
+        const double* a = &a01[((size_t)i * nb + q - 1) * 4];
+        const double iw = 1.0 / (f[idx[q]] - f[idx[q - 1]]);
+        gr += 0.5 * a[0] + a[2] * iw;
+        gi += 0.5 * a[1] + a[3] * iw;
+      }
+      g[(size_t)i * ne + q] = make_float2((float)gr, (float)gi);
+    }
+  for (int q = 0; q <= nb; ++q) {
+    double ph = f[idx[q]] * dt;
+    ph -= std::nearbyint(ph);
+    w[q] = make_float2((float)std::cos(2.0 * kPi * ph), (float)-std::sin(2.0 * kPi * ph));
+  }
+}
+
 }  // namespace
 
 namespace swig {
@@ -391,31 +425,8 @@ int prepare_het(swig_ctx* c) {
   c->h2d_bytes += sizeof(float) * (eb.size() + ef.size() + inv_w.size()) + sizeof(float4) * coef.size() +
                   sizeof(float2) * coefB.size();
   if (L.tm_n > 0) {
-    // edge weights g_ie (the bin above contributes A0/2 - A1/w, the bin below
-    // A0/2 + A1/w) and the rotation of each edge per grid step, in FP64
-    std::vector<float2> g((size_t)n_det * ne), w(ne);
-    for (int i = 0; i < n_det; ++i)
-      for (int q = 0; q <= nb; ++q) {
-        double gr = 0.0, gi = 0.0;
-        if (q < nb) {
-          const double* a = &a01[((size_t)i * nb + q) * 4];
-          const double iw = 1.0 / (f[idx[q + 1]] - f[idx[q]]);
-          gr += 0.5 * a[0] - a[2] * iw;
-          gi += 0.5 * a[1] - a[3] * iw;
-        }
-        if (q > 0) {
-          const double* a = &a01[((size_t)i * nb + q - 1) * 4];
-          const double iw = 1.0 / (f[idx[q]] - f[idx[q - 1]]);
-          gr += 0.5 * a[0] + a[2] * iw;
-          gi += 0.5 * a[1] + a[3] * iw;
-        }
-        g[(size_t)i * ne + q] = make_float2((float)gr, (float)gi);
-      }
-    for (int q = 0; q <= nb; ++q) {
-      double ph = f[idx[q]] * L.tm_dt;
-      ph -= std::nearbyint(ph);
-      w[q] = make_float2((float)std::cos(2.0 * kPi * ph), (float)-std::sin(2.0 * kPi * ph));
-    }
+    std::vector<float2> g, w;
+    het_tm_tables(a01, f, idx, nb, n_det, L.tm_dt, g, w);
     CUDA_TRY(c, cudaMalloc(&B.het_tm_g, sizeof(float2) * g.size()));
     CUDA_TRY(c, cudaMalloc(&B.het_tm_w, sizeof(float2) * w.size()));
     CUDA_TRY(c, cudaMemcpy(B.het_tm_g, g.data(), sizeof(float2) * g.size(), cudaMemcpyHostToDevice));

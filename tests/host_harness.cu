@@ -17,6 +17,7 @@
 //   host_harness priormap < SLOTS ROWS                 13 slots (kind mode lo hi value) then
 //                                                      rows of sampled unit-cube coordinates
 //   host_harness abi                                   sizes and field offsets of the C-ABI structs
+//   host_harness tmtables < NB NDET DT EDGES A01       time-marginalisation edge tables
 #include "../paper_2607_28265_gb300/csrc/capi.cu"
 
 #include <cstddef>
@@ -163,6 +164,27 @@ int main(int argc, char** argv) {
       for (int j = 0; j < SWIG_N_PARAMS; ++j) std::printf("%s%.17g", j ? ", " : "", th[j]);
       std::printf("]");
     }
+    std::printf("]}\n");
+    return 0;
+  }
+  if (what == "tmtables" && argc == 2) {
+    int nb, n_det;
+    double dt;
+    if (std::scanf("%d %d %lf", &nb, &n_det, &dt) != 3) return 5;
+    std::vector<double> f(nb + 1), a01((size_t)n_det * nb * 4);
+    std::vector<int> idx(nb + 1);
+    for (int q = 0; q <= nb; ++q) {
+      if (std::scanf("%lf", &f[q]) != 1) return 5;
+      idx[q] = q;
+    }
+    for (double& v : a01)
+      if (std::scanf("%lf", &v) != 1) return 5;
+    std::vector<float2> g, w;
+    het_tm_tables(a01, f, idx, nb, n_det, dt, g, w);
+    std::printf("{\"g\": [");
+    for (size_t k = 0; k < g.size(); ++k) std::printf("%s%.9g, %.9g", k ? ", " : "", g[k].x, g[k].y);
+    std::printf("], \"w\": [");
+    for (size_t k = 0; k < w.size(); ++k) std::printf("%s%.9g, %.9g", k ? ", " : "", w[k].x, w[k].y);
     std::printf("]}\n");
     return 0;
   }

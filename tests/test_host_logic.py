@@ -276,3 +276,35 @@ def test_binding_structs_match_the_c_abi(harness):
         assert [f for f, _ in c["fields"]] == [f[0] for f in py._fields_], cname
         for f, off in c["fields"]:
             assert getattr(py, f).offset == off, (cname, f)
+
+
+def test_time_marginalisation_tables_equal_the_hat_weights(harness):
+    """The library's edge weights g_ie and per-step rotations from the
+    oracle's summary data: g_ie is the coefficient of r_i(e) in the per-bin
+    overlap (the linear-in-bin ratio's hat functions), w_e = exp(-2 pi i f_e dt);
+    FP32 storage."""
+    wl = si.config2()
+    from oracle import events
+    ev, th = events.build_event(wl)
+    het = L.het_setup(ev, th, 300)
+    nb, nd, dt = het.edges.size - 1, len(ev.detectors), 0.2 / 2000
+    a01 = np.concatenate([np.stack([het.A0[i].real, het.A0[i].imag, het.A1[i].real, het.A1[i].imag], axis=1).ravel()
+                          for i in range(nd)])
+    text = f"{nb} {nd} {dt!r}\n" + " ".join(repr(float(x)) for x in het.edges) + "\n" + \
+        " ".join(repr(float(x)) for x in a01) + "\n"
+    r = subprocess.run([harness, "tmtables"], input=text, capture_output=True, text=True, timeout=60)
+    assert r.returncode == 0, r.stderr
+    out = json.loads(r.stdout)
+    g = np.array(out["g"]).reshape(nd, nb + 1, 2)
+    w = np.array(out["w"]).reshape(nb + 1, 2)
+    # coefficient of r(e) in sum_b A0 (r_b + r_b+1)/2 + A1 (r_b+1 - r_b)/width_b, by unit vectors
+    width = het.edges[1:] - het.edges[:-1]
+    for i in range(nd):
+        for e in (0, 1, nb // 2, nb - 1, nb):
+            r_unit = np.zeros(nb + 1)
+            r_unit[e] = 1.0
+            want = np.sum(het.A0[i] * 0.5 * (r_unit[:-1] + r_unit[1:]) + het.A1[i] * (r_unit[1:] - r_unit[:-1]) / width)
+            scale = np.max(np.abs(het.A0[i]))
+            assert abs(complex(*g[i, e]) - want) <= 1e-6 * scale, (i, e)
+    want_w = np.exp(-2j * math.pi * het.edges * dt)
+    assert np.allclose(w[:, 0] + 1j * w[:, 1], want_w, rtol=0, atol=2e-7)
