@@ -293,6 +293,50 @@ std::vector<int> het_edge_indices(const std::vector<double>& f, int nb, int spac
   return idx;
 }
 
+// Summary data of the heterodyned likelihood (Sec. 3.4) per detector and bin:
+// bin b holds the grid bins idx[b] <= k < idx[b + 1] (the last bin also the
+// last grid bin); with the centre f_c and w = 4 df / S,
+//   A0 = sum conj(d) h0 w,  A1 = sum conj(d) h0 w (f - f_c),
+//   B0 = sum |h0|^2 w,      B1 = sum |h0|^2 w (f - f_c),
+// compensated FP64 sums stored FP32 (coef: A0, A1; coefB: B0, B1) and kept in
+// FP64 in a01 (A0.re, A0.im, A1.re, A1.im).  data[i] holds re, im interleaved;
+// h0 is [n_det][n] on the grid.
+void het_summary(const std::vector<double>& f, const std::vector<int>& idx, int nb, int n_det, double df,
+                 const std::vector<double>* data, const std::vector<double>* psd, const std::vector<double2>& h0,
+                 std::vector<float4>& coef, std::vector<float2>& coefB, std::vector<double>& a01) {
+  const int n = (int)f.size();
+  coef.assign((size_t)n_det * nb, make_float4(0.0f, 0.0f, 0.0f, 0.0f));
+  coefB.assign((size_t)n_det * nb, make_float2(0.0f, 0.0f));
+  a01.assign((size_t)n_det * nb * 4, 0.0);
+  for (int i = 0; i < n_det; ++i) {
+    for (int b = 0; b < nb; ++b) {
+      const int k_end = (b == nb - 1) ? n : idx[b + 1];
+      const double fc = 0.5 * (f[idx[b]] + f[idx[b + 1]]);
+      NSum a0r, a0i, a1r, a1i, b0, b1;
+      for (int k = idx[b]; k < k_end; ++k) {
+        const double w = 4.0 * df / psd[i][k];
+        const double dr = data[i][2 * k], di = data[i][2 * k + 1];
+        const double hr = h0[(size_t)i * n + k].x, hi = h0[(size_t)i * n + k].y;
+        const double pr = (dr * hr + di * hi) * w, pi = (dr * hi - di * hr) * w;  // conj(d) h0 w
+        const double hh = (hr * hr + hi * hi) * w, off = f[k] - fc;
+        a0r.add(pr);
+        a0i.add(pi);
+        a1r.add(pr * off);
+        a1i.add(pi * off);
+        b0.add(hh);
+        b1.add(hh * off);
+      }
+      coef[(size_t)i * nb + b] = make_float4((float)a0r.value(), (float)a0i.value(), (float)a1r.value(), (float)a1i.value());
+      double* a = &a01[((size_t)i * nb + b) * 4];
+      a[0] = a0r.value();
+      a[1] = a0i.value();
+      a[2] = a1r.value();
+      a[3] = a1i.value();
+      coefB[(size_t)i * nb + b] = make_float2((float)b0.value(), (float)b1.value());
+    }
+  }
+}
+
 // Tables of the time-marginalised heterodyne, in FP64 and stored FP32: the
 // edge weights g_ie (Z_i = sum_e g_ie r_i(e): the bin above an edge gives
 // A0/2 - A1/w, the bin below A0/2 + A1/w) from a01 = (A0.re, A0.im, A1.re,
@@ -368,38 +412,12 @@ int prepare_het(swig_ctx* c) {
     if (!(fid.cre[i] * fid.cre[i] + fid.cim[i] * fid.cim[i] > 0.0))
       return fail(c, SWIG_E_ARG, "fiducial waveform vanishes in detector " + std::to_string(i));
   // summary data per detector and bin
-  std::vector<float4> coef((size_t)n_det * nb);
-  std::vector<float2> coefB((size_t)n_det * nb);
-  std::vector<double> a01((size_t)n_det * nb * 4);  // FP64 (A0.re, A0.im, A1.re, A1.im) for the edge weights
+  std::vector<float4> coef;
+  std::vector<float2> coefB;
+  std::vector<double> a01;  // FP64 (A0.re, A0.im, A1.re, A1.im) for the edge weights
+  het_summary(f, idx, nb, n_det, c->df, c->data, c->psd, h0, coef, coefB, a01);
   std::vector<float> inv_w(nb);
   for (int b = 0; b < nb; ++b) inv_w[b] = (float)(1.0 / (f[idx[b + 1]] - f[idx[b]]));
-  for (int i = 0; i < n_det; ++i) {
-    for (int b = 0; b < nb; ++b) {
-      const int k_end = (b == nb - 1) ? n : idx[b + 1];
-      const double fc = 0.5 * (f[idx[b]] + f[idx[b + 1]]);
-      NSum a0r, a0i, a1r, a1i, b0, b1;
-      for (int k = idx[b]; k < k_end; ++k) {
-        const double w = 4.0 * c->df / c->psd[i][k];
-        const double dr = c->data[i][2 * k], di = c->data[i][2 * k + 1];
-        const double hr = h0[(size_t)i * n + k].x, hi = h0[(size_t)i * n + k].y;
-        const double pr = (dr * hr + di * hi) * w, pi = (dr * hi - di * hr) * w;  // conj(d) h0 w
-        const double hh = (hr * hr + hi * hi) * w, off = f[k] - fc;
-        a0r.add(pr);
-        a0i.add(pi);
-        a1r.add(pr * off);
-        a1i.add(pi * off);
-        b0.add(hh);
-        b1.add(hh * off);
-      }
-      coef[(size_t)i * nb + b] = make_float4((float)a0r.value(), (float)a0i.value(), (float)a1r.value(), (float)a1i.value());
-      double* a = &a01[((size_t)i * nb + b) * 4];
-      a[0] = a0r.value();
-      a[1] = a0i.value();
-      a[2] = a1r.value();
-      a[3] = a1i.value();
-      coefB[(size_t)i * nb + b] = make_float2((float)b0.value(), (float)b1.value());
-    }
-  }
   std::vector<float> eb((size_t)(nb + 1) * 2 * NBASIS), ef((size_t)(nb + 1) * 2);
   // transposed (row per basis function and hi/lo part) so that a warp reads
   // 32 consecutive edges of a row

@@ -18,6 +18,7 @@
 //                                                      rows of sampled unit-cube coordinates
 //   host_harness abi                                   sizes and field offsets of the C-ABI structs
 //   host_harness tmtables < NB NDET DT EDGES A01       time-marginalisation edge tables
+//   host_harness hetsum < N NB NDET DF F IDX (DATA PSD H0)xNDET   heterodyne summary data
 #include "../paper_2607_28265_gb300/csrc/capi.cu"
 
 #include <cstddef>
@@ -165,6 +166,43 @@ int main(int argc, char** argv) {
       std::printf("]");
     }
     std::printf("]}\n");
+    return 0;
+  }
+  if (what == "hetsum" && argc == 2) {
+    int n, nb, n_det;
+    double df;
+    if (std::scanf("%d %d %d %lf", &n, &nb, &n_det, &df) != 4 || n_det < 1 || n_det > SWIG_MAX_DET) return 5;
+    std::vector<double> f(n);
+    std::vector<int> idx(nb + 1);
+    for (double& v : f)
+      if (std::scanf("%lf", &v) != 1) return 5;
+    for (int& v : idx)
+      if (std::scanf("%d", &v) != 1) return 5;
+    std::vector<double> data[SWIG_MAX_DET], psd[SWIG_MAX_DET];
+    std::vector<double2> h0((size_t)n_det * n);
+    for (int i = 0; i < n_det; ++i) {
+      data[i].resize(2 * (size_t)n);
+      psd[i].resize(n);
+      for (double& v : data[i])
+        if (std::scanf("%lf", &v) != 1) return 5;
+      for (double& v : psd[i])
+        if (std::scanf("%lf", &v) != 1) return 5;
+      for (int k = 0; k < n; ++k)
+        if (std::scanf("%lf %lf", &h0[(size_t)i * n + k].x, &h0[(size_t)i * n + k].y) != 2) return 5;
+    }
+    std::vector<float4> coef;
+    std::vector<float2> coefB;
+    std::vector<double> a01;
+    het_summary(f, idx, nb, n_det, df, data, psd, h0, coef, coefB, a01);
+    std::printf("{");
+    print_array("a01", a01.data(), (int)a01.size(), false);
+    std::vector<double> bb;
+    for (const float2& v : coefB) {
+      bb.push_back(v.x);
+      bb.push_back(v.y);
+    }
+    print_array("b01", bb.data(), (int)bb.size(), true);
+    std::printf("}\n");
     return 0;
   }
   if (what == "tmtables" && argc == 2) {

@@ -308,3 +308,35 @@ def test_time_marginalisation_tables_equal_the_hat_weights(harness):
             assert abs(complex(*g[i, e]) - want) <= 1e-6 * scale, (i, e)
     want_w = np.exp(-2j * math.pi * het.edges * dt)
     assert np.allclose(w[:, 0] + 1j * w[:, 1], want_w, rtol=0, atol=2e-7)
+
+
+def test_heterodyne_summary_data_equal_the_oracle(harness):
+    """The library's summary data (compensated FP64 sums) from the oracle's own
+    fiducial waveform, data and PSDs against the oracle's het_setup: A0, A1
+    to 1e-12 of each detector's largest |A0|, |A1|; B0, B1 to FP32 storage."""
+    from oracle import events
+    wl = si.config1()
+    ev, th = events.build_event(wl)
+    het = L.het_setup(ev, th, 300)
+    _, idx = L.phase_bound_edges(ev.freqs, 300)
+    nb, n = idx.size - 1, ev.freqs.size
+    h0 = L.strains(ev, th)
+    parts = [f"{n} {nb} {len(ev.detectors)} {ev.df!r}", " ".join(repr(float(x)) for x in ev.freqs),
+             " ".join(str(int(k)) for k in idx)]
+    for d, s, h in zip(ev.data, ev.psds, h0):
+        parts.append(" ".join(repr(float(x)) for x in np.stack([d.real, d.imag], axis=1).ravel()))
+        parts.append(" ".join(repr(float(x)) for x in s))
+        parts.append(" ".join(repr(float(x)) for x in np.stack([h.real, h.imag], axis=1).ravel()))
+    r = subprocess.run([harness, "hetsum"], input="\n".join(parts) + "\n", capture_output=True, text=True,
+                       timeout=120)
+    assert r.returncode == 0, r.stderr
+    out = json.loads(r.stdout)
+    a01 = np.array(out["a01"]).reshape(len(ev.detectors), nb, 4)
+    b01 = np.array(out["b01"]).reshape(len(ev.detectors), nb, 2)
+    for i in range(len(ev.detectors)):
+        A0 = a01[i, :, 0] + 1j * a01[i, :, 1]
+        A1 = a01[i, :, 2] + 1j * a01[i, :, 3]
+        assert np.max(np.abs(A0 - het.A0[i])) <= 1e-12 * np.max(np.abs(het.A0[i]))
+        assert np.max(np.abs(A1 - het.A1[i])) <= 1e-12 * np.max(np.abs(het.A1[i]))
+        assert np.allclose(b01[i, :, 0], het.B0[i], rtol=1e-7, atol=0)
+        assert np.max(np.abs(b01[i, :, 1] - het.B1[i])) <= 1e-7 * np.max(np.abs(het.B1[i]))
