@@ -293,6 +293,35 @@ std::vector<int> het_edge_indices(const std::vector<double>& f, int nb, int spac
   return idx;
 }
 
+// Weighted data of the full-grid likelihood (Eq. 2 expanded): D_i(k) =
+// 4 df conj(d_i) f^-7/6 / S_i (dre, dim: [n_det][n_bins]), K_i = 4 df sum
+// f^-7/3 / S_i, <d|d> summed over the detectors (compensated FP64 sums), and
+// the largest |D_i| of each detector (the mixed path's data scale).
+void weight_data(const swig_ctx* c, int n_det, std::vector<double>& dre, std::vector<double>& dim, double* K,
+                 double* dd, double* dmax) {
+  const int64_t n = c->n_bins;
+  dre.assign((size_t)n_det * n, 0.0);
+  dim.assign((size_t)n_det * n, 0.0);
+  NSum dsum;
+  for (int i = 0; i < n_det; ++i) {
+    NSum Ks;
+    dmax[i] = 0.0;
+    for (int64_t k = 0; k < n; ++k) {
+      const double f = (double)(c->k_min + k) * c->df;
+      const double w = 4.0 * c->df / c->psd[i][k];
+      const double re = c->data[i][2 * k], im = c->data[i][2 * k + 1];
+      const double a = w * std::pow(f, -7.0 / 6.0);
+      dre[i * n + k] = a * re;
+      dim[i * n + k] = -a * im;
+      Ks.add(w * std::pow(f, -7.0 / 3.0));
+      dsum.add(w * (re * re + im * im));
+      dmax[i] = std::max(dmax[i], std::hypot(re, im) * a);
+    }
+    K[i] = Ks.value();
+  }
+  *dd = dsum.value();
+}
+
 // Summary data of the heterodyned likelihood (Sec. 3.4) per detector and bin:
 // bin b holds the grid bins idx[b] <= k < idx[b + 1] (the last bin also the
 // last grid bin); with the centre f_c and w = 4 df / S,
@@ -568,24 +597,11 @@ int prepare(swig_ctx* c) {
   L.fast_epilogue = prec == SWIG_PREC_MIXED ? 1 : 0;
 
   // D_i(k) = 4 df conj(d_i) f^-7/6 / S_i,  K_i = 4 df sum f^-7/3 / S_i,  <d|d>
-  std::vector<double> dre((size_t)n_det * n), dim((size_t)n_det * n);
-  NSum dd;
+  std::vector<double> dre, dim;
+  double dmax[SWIG_MAX_DET], dd_sum = 0.0;
+  weight_data(c, n_det, dre, dim, L.K, &dd_sum, dmax);
   for (int i = 0; i < n_det; ++i) {
-    NSum K;
-    double dmax = 0.0;
-    for (int64_t k = 0; k < n; ++k) {
-      const double f = (double)(c->k_min + k) * c->df;
-      const double w = 4.0 * c->df / c->psd[i][k];
-      const double re = c->data[i][2 * k], im = c->data[i][2 * k + 1];
-      const double a = w * std::pow(f, -7.0 / 6.0);
-      dre[i * n + k] = a * re;
-      dim[i * n + k] = -a * im;
-      K.add(w * std::pow(f, -7.0 / 3.0));
-      dd.add(w * (re * re + im * im));
-      dmax = std::max(dmax, std::hypot(re, im) * a);
-    }
-    L.K[i] = K.value();
-    L.inv_scale[i] = prec == SWIG_PREC_MIXED ? (dmax > 0.0 ? dmax : 1.0) : 1.0;
+    L.inv_scale[i] = prec == SWIG_PREC_MIXED ? (dmax[i] > 0.0 ? dmax[i] : 1.0) : 1.0;
     for (int r = 0; r < 3; ++r) L.vertex[i][r] = c->vertex[i][r];
     const double* x = c->xarm[i];
     const double* y = c->yarm[i];
@@ -596,7 +612,7 @@ int prepare(swig_ctx* c) {
     L.dten[i][4] = 0.5 * (x[1] * x[2] - y[1] * y[2]);
     L.dten[i][5] = 0.5 * (x[2] * x[2] - y[2] * y[2]);
   }
-  L.DD = dd.value();
+  L.DD = dd_sum;
   {
     const double a1 = std::sqrt(5.0 / 24.0) * std::pow(kPi, -2.0 / 3.0) * std::pow(kMtsunS, 5.0 / 6.0) * kCSI / kMpcM;
     for (int i = 0; i < n_det; ++i) {

@@ -19,6 +19,7 @@
 //   host_harness abi                                   sizes and field offsets of the C-ABI structs
 //   host_harness tmtables < NB NDET DT EDGES A01       time-marginalisation edge tables
 //   host_harness hetsum < N NB NDET DF F IDX (DATA PSD H0)xNDET   heterodyne summary data
+//   host_harness weights F_MIN F_MAX DF NDET STRIDE < (DATA PSD)xNDET   full-grid data weights
 #include "../paper_2607_28265_gb300/csrc/capi.cu"
 
 #include <cstddef>
@@ -166,6 +167,34 @@ int main(int argc, char** argv) {
       std::printf("]");
     }
     std::printf("]}\n");
+    return 0;
+  }
+  if (what == "weights" && argc == 7) {
+    swig_ctx c;
+    if (swig_set_grid(&c, std::atof(argv[2]), std::atof(argv[3]), std::atof(argv[4])) != SWIG_OK) return 3;
+    const int n_det = std::atoi(argv[5]), stride = std::atoi(argv[6]);
+    const int64_t n = c.n_bins;
+    for (int i = 0; i < n_det; ++i) {
+      std::vector<double> d(2 * (size_t)n), s((size_t)n);
+      for (double& v : d)
+        if (std::scanf("%lf", &v) != 1) return 5;
+      for (double& v : s)
+        if (std::scanf("%lf", &v) != 1) return 5;
+      if (swig_set_data(&c, i, d.data(), n) != SWIG_OK || swig_set_psd(&c, i, s.data(), n) != SWIG_OK) return 6;
+    }
+    std::vector<double> dre, dim, sre, sim;
+    double K[SWIG_MAX_DET], dmax[SWIG_MAX_DET], dd;
+    weight_data(&c, n_det, dre, dim, K, &dd, dmax);
+    for (size_t k = 0; k < dre.size(); k += (size_t)stride) {
+      sre.push_back(dre[k]);
+      sim.push_back(dim[k]);
+    }
+    std::printf("{\"dd\": %.17g, ", dd);
+    print_array("K", K, n_det, false);
+    print_array("dmax", dmax, n_det, false);
+    print_array("dre", sre.data(), (int)sre.size(), false);
+    print_array("dim", sim.data(), (int)sim.size(), true);
+    std::printf("}\n");
     return 0;
   }
   if (what == "hetsum" && argc == 2) {

@@ -340,3 +340,32 @@ def test_heterodyne_summary_data_equal_the_oracle(harness):
         assert np.max(np.abs(A1 - het.A1[i])) <= 1e-12 * np.max(np.abs(het.A1[i]))
         assert np.allclose(b01[i, :, 0], het.B0[i], rtol=1e-7, atol=0)
         assert np.max(np.abs(b01[i, :, 1] - het.B1[i])) <= 1e-7 * np.max(np.abs(het.B1[i]))
+
+
+def test_full_grid_data_weights_equal_the_inner_products(harness):
+    """The weighted data of the full-grid likelihood against the oracle's
+    inner products: K_i = <f^-7/6 | f^-7/6>_i, <d|d> summed over detectors,
+    D_i(f) = 4 df conj(d_i) f^-7/6 / S_i at sampled bins, max |D_i|."""
+    from oracle import events
+    wl = si.config2()
+    ev, _ = events.build_event(wl)
+    stride = 997
+    text = []
+    for d, s in zip(ev.data, ev.psds):
+        text.append(" ".join(repr(float(x)) for x in np.stack([d.real, d.imag], axis=1).ravel()))
+        text.append(" ".join(repr(float(x)) for x in s))
+    r = subprocess.run([harness, "weights", repr(wl.f_min), repr(wl.f_max), repr(wl.df), str(len(ev.data)), str(stride)],
+                       input="\n".join(text) + "\n", capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stderr
+    out = json.loads(r.stdout)
+    f = ev.freqs
+    amp = f ** (-7.0 / 6.0)
+    dd = sum(L.inner_product(d, d, s, ev.df) for d, s in zip(ev.data, ev.psds))
+    assert out["dd"] == pytest.approx(dd, rel=1e-12, abs=0)
+    D = np.concatenate([4.0 * ev.df * np.conj(d) * amp / s for d, s in zip(ev.data, ev.psds)])
+    for i, s in enumerate(ev.psds):
+        assert out["K"][i] == pytest.approx(L.inner_product(amp, amp, s, ev.df), rel=1e-12, abs=0)
+        Di = D[i * f.size:(i + 1) * f.size]
+        assert out["dmax"][i] == pytest.approx(np.max(np.abs(Di)), rel=1e-14, abs=0)
+    sample = D[::stride]
+    assert np.allclose(np.array(out["dre"]) + 1j * np.array(out["dim"]), sample, rtol=1e-14, atol=0)
