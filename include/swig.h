@@ -98,6 +98,12 @@ typedef struct swig_sampler_cfg {
    * The spacing should resolve the t_c posterior (its width is roughly
    * 1 / (2 pi SNR sigma_f), sigma_f the spread of the signal's frequencies). */
   int tmarg_nodes;
+  /* 1: evaluate every proposal in full, also for the blocks that only move
+   * the projection factors (d_L, iota, psi, phi_c), which otherwise reuse the
+   * chain's cached per-detector sums of its last full evaluation (exact in C_i,
+   * see Sec. 3.2 on fast and slow blocks).  A verification switch: the cached
+   * and uncached samplers must agree in distribution.  0 = the cache. */
+  int cache_off;
 } swig_sampler_cfg;
 
 typedef struct swig_result {

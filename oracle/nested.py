@@ -17,7 +17,7 @@ with L_b the Cholesky factor of the covariance of the m live points at the
 start of the iteration restricted to block b.  Each update follows Neal (2003)
 stepping-out and shrinkage along n with unit width and random initial offset.
 
-Readings where the paper is silent (listed in the design doc): start points are
+Readings where the paper is silent (this module's own choices): start points are
 drawn uniformly with replacement among the survivors; stepping-out and
 shrinkage are capped at 100 moves (on a shrink cap the chain keeps its point);
 bounded unit-cube coordinates (no wrapping for periodic angles).

@@ -68,17 +68,20 @@ extern "C" int swig_loglike_batch_noalloc(swig_ctx* c, const double* theta_dev, 
              "swig_run call with the current problem (preparation allocates; this entry point does not)";
     return SWIG_E_STATE;
   }
+  // Capacity first, from the per-vector bytes (three 256-byte roundings at
+  // most on top), so that no size below is formed from an unchecked n.
+  const size_t per_theta = sizeof(EvalRecord) + sizeof(float) * kAnchorStride * (size_t)c->L.n_tiles +
+                           sizeof(float) * kPartialStride * (size_t)c->L.n_slices * 4;
+  const int64_t cap = (int64_t)((kNoAllocScratchBytes - 3 * 256) / per_theta);
+  if (n > cap) {
+    c->err = "batch of " + std::to_string(n) + " exceeds the fixed scratch of this entry point (" +
+             std::to_string(kNoAllocScratchBytes >> 20) + " MiB, " + std::to_string(cap) +
+             " parameter vectors for this grid); split the batch";
+    return SWIG_E_ARG;
+  }
   // layout: [records][anchors][partials], each 256-byte aligned
   const size_t rec_b = round_up(sizeof(EvalRecord) * (size_t)n);
   const size_t anc_b = round_up(sizeof(float) * kAnchorStride * (size_t)c->L.n_tiles * (size_t)n);
-  const size_t par_b = round_up(sizeof(float) * kPartialStride * (size_t)c->L.n_slices * 4 * (size_t)n);
-  const size_t per_theta = (rec_b + anc_b + par_b) / (size_t)n + 1;
-  if (rec_b + anc_b + par_b > kNoAllocScratchBytes) {
-    c->err = "batch of " + std::to_string(n) + " exceeds the fixed scratch of this entry point (" +
-             std::to_string(kNoAllocScratchBytes >> 20) + " MiB, about " +
-             std::to_string(kNoAllocScratchBytes / per_theta) + " parameter vectors for this grid); split the batch";
-    return SWIG_E_ARG;
-  }
   cudaError_t e = cudaSetDevice(c->device);
   void* base = nullptr;
   if (e == cudaSuccess) e = scratch_address(c->device, &base);

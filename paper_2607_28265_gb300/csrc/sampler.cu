@@ -1635,8 +1635,9 @@ int run_setup(swig_ctx* c, RunState& R) {
         if (slot == 9 || slot == 10 || slot == 11) flags |= BF_TAU;
       }
     // time marginalisation keeps no per-detector cache at every node, so
-    // projection-only blocks take the full evaluation there
-    S.block_free[b] = (free_block && L.tm_n == 0) ? 1 : 0;
+    // projection-only blocks take the full evaluation there (and everywhere
+    // when the cache is switched off)
+    S.block_free[b] = (free_block && L.tm_n == 0 && !c->cfg.cache_off) ? 1 : 0;
     S.block_flags[b] = flags;
   }
   S.m_pow2 = 1;

@@ -39,7 +39,8 @@ class SwigSamplerCfg(ctypes.Structure):
                 ("seed", _c_u64), ("likelihood", _c_int), ("precision", _c_int), ("proposal", _c_int),
                 ("het_bins", _c_int), ("het_spacing", _c_int), ("dlogz", _c_double), ("max_iter", _c_int),
                 ("het_fiducial", _c_double * N_PARAMS), ("learn_mix", _c_double), ("learn_lr", _c_double),
-                ("learn_steps", _c_int), ("learn_interval", _c_int), ("tmarg_nodes", _c_int)]
+                ("learn_steps", _c_int), ("learn_interval", _c_int), ("tmarg_nodes", _c_int),
+                ("cache_off", _c_int)]
 
 
 class SwigResult(ctypes.Structure):
@@ -190,7 +191,7 @@ class Context:
     def set_sampler(self, nlive, nrep, sweeps=1, steps_per_dim=5, seed=0, likelihood=LIKE_FULL,
                     precision=PREC_MIXED, proposal=PROPOSAL_COV, het_bins=0, het_spacing=0, dlogz=-3.0,
                     max_iter=100000, het_fiducial=None, learn_mix=0.0, learn_lr=0.0, learn_steps=0,
-                    learn_interval=0, tmarg_nodes=0):
+                    learn_interval=0, tmarg_nodes=0, cache_off=0):
         """swig_set_sampler: the fields of swig_sampler_cfg (include/swig.h).
 
         nlive / nrep: live points m and deletions k per iteration; sweeps (M)
@@ -199,7 +200,9 @@ class Context:
         het_spacing (0 equal phase change, 1 geometric) and het_fiducial (13
         values); precision PREC_FP64 or PREC_MIXED; proposal PROPOSAL_COV or
         PROPOSAL_LEARNED with learn_* (0 = library default); tmarg_nodes: grid
-        nodes over the t_c prior when t_c is marginalised (heterodyned only).
+        nodes over the t_c prior when t_c is marginalised (heterodyned only);
+        cache_off=1 evaluates projection-only proposals in full (no reuse of
+        the chain's cached per-detector sums).
         """
         cfg = SwigSamplerCfg()
         cfg.nlive, cfg.nrep, cfg.sweeps, cfg.steps_per_dim = nlive, nrep, sweeps, steps_per_dim
@@ -211,6 +214,7 @@ class Context:
         cfg.learn_mix, cfg.learn_lr = float(learn_mix), float(learn_lr)
         cfg.learn_steps, cfg.learn_interval = int(learn_steps), int(learn_interval)
         cfg.tmarg_nodes = int(tmarg_nodes)
+        cfg.cache_off = int(cache_off)
         self._check(self.lib.swig_set_sampler(self.h, ctypes.byref(cfg)))
 
     # ---- likelihood --------------------------------------------------------
