@@ -96,3 +96,39 @@ def test_het_phase_edges_cover_grid(cfg1_noisy):
     assert np.all(np.diff(idx) > 0)
     # equal increments of the phase-bound function, before snapping to the grid
     assert 250 <= edges.size - 1 <= 300
+
+
+def test_heterodyne_is_second_order_for_an_amplitude_varying_template(cfg1_noisy, monkeypatch):
+    """Summary-data signs (A1, B1) against the exact inner products.
+
+    Every template of this model has |h / h0| constant in f, and then
+    Re(r0 r1*) = (|r_hi|^2 - |r_lo|^2) / (2 w) = 0 in every bin, so B1 never
+    contributes.  To fix its sign the template here is the fiducial times a
+    real amplitude ramp a(f) = 1 + eps (f - f_ref) / f_ref, which is linear in
+    f, so r is exactly linear in each bin.  Then, from the definitions:
+    * Z = sum_b (A0 r0 + A1 r1) equals the full-grid 4 df sum d* h / S to
+      rounding (Z is linear in r);
+    * <h|h>_het = sum_b (B0 |r0|^2 + 2 B1 Re(r0 r1*)) misses only
+      sum_b |r1|^2 sum_(f in b) |h0|^2 w (f - f_c)^2 >= 0, which is second order
+      in eps: the error is negative and quadruples when eps doubles.  A B1 of
+      the wrong sign leaves a first-order error (the ratio would be ~2)."""
+    ev, th = cfg1_noisy
+    het = L.het_setup(ev, th, 300, spacing="phase")
+    f_ref = 100.0
+    base = physics.detector_strain
+    errs = []
+    for eps in (0.01, 0.02):
+        def ramp(f, theta, det, gmst, eps=eps):
+            return base(f, theta, det, gmst) * (1.0 + eps * (np.asarray(f) - f_ref) / f_ref)
+
+        monkeypatch.setattr(physics, "detector_strain", ramp)
+        z_het, hh_het = L.het_overlap(ev, het, th)
+        h = L.strains(ev, np.asarray(th))
+        monkeypatch.setattr(physics, "detector_strain", base)
+        z_ex = sum(L.complex_overlap(d, hi, s, ev.df) for d, hi, s in zip(ev.data, h, ev.psds))
+        hh_ex = sum(L.inner_product(hi, hi, s, ev.df) for hi, s in zip(h, ev.psds))
+        assert abs(z_het - z_ex) <= 1e-10 * abs(z_ex)
+        errs.append(hh_het - hh_ex)
+    assert errs[0] < 0.0 and errs[1] < 0.0
+    assert errs[1] / errs[0] == pytest.approx(4.0, rel=0.02)
+    assert abs(errs[1]) < 1e-4 * hh_ex

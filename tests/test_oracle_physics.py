@@ -238,3 +238,33 @@ def test_tidal_terms_equal_the_per_body_form(q, lam1, lam2):
         a12 -= 5.0 / (28.0 * xa) * (3179.0 - 919.0 * xa - 2286.0 * xa**2 + 260.0 * xa**3) * xa**5 * lam
     assert a[10] == pytest.approx(a10, rel=1e-12, abs=0)
     assert a[12] == pytest.approx(a12, rel=1e-12, abs=0)
+
+
+@pytest.mark.parametrize("q,chi1,chi2", [(0.55, 0.04, -0.03), (0.8, -0.05, -0.02), (0.93, 0.05, 0.05), (1.0, 0.03, -0.01)])
+def test_spin_terms_against_independent_forms(q, chi1, chi2):
+    """The aligned-spin parts of alpha_3 and alpha_4, against two published
+    forms written in other variables (so a wrong 113/12, 25/4, 79/8 or a swapped
+    mass weight fails):
+
+    * 1.5PN spin-orbit in the symmetric/antisymmetric spins chi_s = (chi1 +
+      chi2)/2, chi_a = (chi1 - chi2)/2, delta = (m1 - m2)/M, as Ajith (2011,
+      PRD 84, 084037) writes the non-precessing TaylorF2 phase:
+      alpha_3 spin part = (113/3)(chi_s + delta chi_a) - (76/3) eta chi_s;
+    * 2PN spin-spin from Kidder (1995, PRD 52, 821):
+      sigma = eta/48 [721 (L.chi1)(L.chi2) - 247 chi1.chi2], which for spins
+      along L is eta (721 - 247)/48 chi1 chi2; alpha_4 spin part = -10 sigma.
+    """
+    mc = 1.7
+    eta = physics.symmetric_mass_ratio(q)
+    m1, m2 = 1 / (1 + q), q / (1 + q)
+    delta = m1 - m2
+    a_spin = physics.pn_phase_coefficients(mc, q, chi1, chi2, 0.0, 0.0)
+    a_zero = physics.pn_phase_coefficients(mc, q, 0.0, 0.0, 0.0, 0.0)
+    chi_s, chi_a = 0.5 * (chi1 + chi2), 0.5 * (chi1 - chi2)
+    so = 113.0 / 3.0 * (chi_s + delta * chi_a) - 76.0 / 3.0 * eta * chi_s
+    assert a_spin[3] - a_zero[3] == pytest.approx(so, rel=1e-12, abs=1e-15)
+    sigma = eta / 48.0 * (721.0 * chi1 * chi2 - 247.0 * chi1 * chi2)
+    assert a_spin[4] - a_zero[4] == pytest.approx(-10.0 * sigma, rel=1e-12, abs=1e-15)
+    # the other orders do not see the spins
+    for k in (0, 2, 5, 6, 7):
+        assert a_spin[k] == a_zero[k]
