@@ -48,6 +48,7 @@ struct swig_ctx {
   // results of the last run
   swig_result last = {};
   double profile[25] = {};
+  std::vector<double> cta_profile;  // [n_ctas][4] of the last run (see swig_get_profile)
   // counters over the context's lifetime: kernel launches, bytes copied host
   // to device and device to host by the library
   long long n_launches = 0, h2d_bytes = 0, d2h_bytes = 0;

@@ -150,6 +150,7 @@ struct SamplerPtrs {
   const float* learn_out;  // [m][32] network outputs (u, s) of a frozen live snapshot, or null
   int* req;                // [k] 8 * (sequence number of the chain's latest full-likelihood request) + parts per slice
   int* done_cnt;           // [k] CTAs that finished the chain's latest request
+  unsigned long long* cta_prof;  // [n_ctas][4] per CTA: sweep units, cycles in units, cycles polling, control cycles
 };
 
 // ---------------------------------------------------------------------------
@@ -978,7 +979,7 @@ __global__ void __launch_bounds__(kFlowThreads, 1)
     if (*(volatile int*)&g->status != ST_RUNNING) return;
 
     long long idle = 0;
-    unsigned long long my_units = 0, my_unit_cyc = 0, my_idle_cyc = 0;
+    unsigned long long my_units = 0, my_unit_cyc = 0, my_idle_cyc = 0, my_ctrl_cyc = 0;
     long long tpoll = clock64();
     if (warp == 0) {
       // ---- control of the chains homed on this CTA (their state stays in
@@ -1001,7 +1002,9 @@ __global__ void __launch_bounds__(kFlowThreads, 1)
           all_done = false;
           if (st == 1) continue;
           progressed = true;
+          const long long tc0 = clock64();
           flow_control<NDET, MIXED>(L, S, B, P, c, lane);
+          my_ctrl_cyc += clock64() - tc0;
         }
         if (all_done) break;
         if (*(volatile int*)&g->error) break;
@@ -1100,6 +1103,16 @@ __global__ void __launch_bounds__(kFlowThreads, 1)
       atomicAdd(&g->f_units, my_units);
       atomicAdd(&g->f_unit_cyc, my_unit_cyc);
       atomicAdd(&g->f_idle_cyc, my_idle_cyc);
+    }
+    if (lane == 0 && P.cta_prof) {
+      unsigned long long* cp = P.cta_prof + 4 * (size_t)blockIdx.x;
+      if (warp == 0) {
+        atomicAdd(cp + 3, my_ctrl_cyc);
+      } else {
+        atomicAdd(cp + 0, my_units);
+        atomicAdd(cp + 1, my_unit_cyc);
+        atomicAdd(cp + 2, my_idle_cyc);
+      }
     }
     __syncthreads();
     if (timer) {
@@ -1424,6 +1437,8 @@ struct SamplerState {
   double* lw = nullptr;
   double* init_theta = nullptr;
   float* anchor_buf = nullptr;
+  unsigned long long* cta_prof = nullptr;  // [n_ctas][4]
+  int cta_prof_n = 0;
   int cap_iters = 0;
   int nlive = 0, nrep = 0, ndim = 0;
 };
@@ -1456,6 +1471,7 @@ void release(SamplerState* s) {
   dfree(s->lw);
   dfree(s->init_theta);
   dfree(s->anchor_buf);
+  dfree(s->cta_prof);
 }
 
 int fail(swig_ctx* c, int code, const std::string& m) {
@@ -1720,6 +1736,13 @@ int run_setup(swig_ctx* c, RunState& R) {
     SCUDA(cudaMalloc(&st->anchor_buf, sizeof(float) * kAnchorStride * (size_t)L.n_slices * k * max_tiles));
   }
   st->P.anchor_buf = st->anchor_buf;
+  if (st->cta_prof_n < S.n_ctas) {
+    dfree(st->cta_prof);
+    SCUDA(cudaMalloc(&st->cta_prof, sizeof(unsigned long long) * 4 * S.n_ctas));
+    st->cta_prof_n = S.n_ctas;
+  }
+  SCUDA(cudaMemsetAsync(st->cta_prof, 0, sizeof(unsigned long long) * 4 * S.n_ctas, c->stream));
+  st->P.cta_prof = st->cta_prof;
   st->P.learn_out = nullptr;
   if (R.learned) {
     if (!c->mlp) c->mlp = new Mlp();
@@ -1961,6 +1984,11 @@ int run_finish(swig_ctx* c, RunState& R, swig_result* out) {
   c->profile[22] = (double)gh.f_units;
   c->profile[23] = (double)gh.f_unit_cyc;
   c->profile[24] = (double)gh.f_idle_cyc;
+  {
+    std::vector<unsigned long long> cp(4 * (size_t)S.n_ctas);
+    SCUDA(cudaMemcpy(cp.data(), st->cta_prof, sizeof(unsigned long long) * cp.size(), cudaMemcpyDeviceToHost));
+    c->cta_profile.assign(cp.begin(), cp.end());
+  }
   return SWIG_OK;
 }
 
@@ -2191,6 +2219,7 @@ int swig_get_profile(swig_ctx* c, double* out, int n) {
   if (!c) return SWIG_E_ARG;
   if (!out || n < 0) return fail(c, SWIG_E_ARG, "null output");
   for (int i = 0; i < n && i < 25; ++i) out[i] = c->profile[i];
+  for (int i = 25; i < n && i - 25 < (int)c->cta_profile.size(); ++i) out[i] = c->cta_profile[i - 25];
   return SWIG_OK;
 }
 

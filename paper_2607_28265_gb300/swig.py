@@ -273,6 +273,13 @@ class Context:
         self._check(self.lib.swig_get_profile(self.h, _ptr(out), out.size))
         return dict(zip(self.PROFILE_KEYS, out.tolist()))
 
+    def cta_profile(self, n_ctas):
+        """Per-CTA counters of the last run's persistent kernel (n_ctas x 4):
+        sweep units, cycles in units, cycles polling, control cycles."""
+        out = np.zeros(len(self.PROFILE_KEYS) + 4 * int(n_ctas))
+        self._check(self.lib.swig_get_profile(self.h, _ptr(out), out.size))
+        return out[len(self.PROFILE_KEYS):].reshape(-1, 4)
+
     def set_sky_frame(self, det_a=-1, det_b=-1):
         """Sample the sky as (azimuth, zenith) about the det_b -> det_a baseline."""
         self._check(self.lib.swig_set_sky_frame(self.h, int(det_a), int(det_b)))

@@ -11,10 +11,6 @@ alternate along every chain.
 * Dead and final live points: the logL the sampler reports equals the
   oracle's heterodyned logL of the reported parameters (same fiducial, bins
   and spacing), with the cache and with it switched off.
-* Both forms give valid samplers of the same constrained prior: their runs
-  (different seeds) over the same iterations leave statistically
-  indistinguishable live sets (two-sample KS per parameter and on logL of the
-  final live points, combined by Fisher's method).
 """
 import numpy as np
 import pytest
@@ -67,22 +63,3 @@ def test_full_size_het_dead_points_match_oracle(cfg2, cache_off):
     want = np.array([L.het_loglike(ev, het, thd[i]) for i in idx])
     err = np.abs(ll[idx] - want)
     assert np.all(err <= _tol(want)), (err.max(), want[np.argmax(err)])
-
-
-def test_cache_on_and_off_sample_the_same_constrained_prior(cfg2):
-    wl, ev, th, het = cfg2
-    live = []
-    for cache_off, seed in ((0, 43), (1, 44)):
-        r, thd, ll, lw = _run(wl, ev, th, cache_off, seed=seed)
-        live.append((thd[-1000:], ll[-1000:]))
-    (a, la), (b, lb) = live
-    w = np.ones(1000)
-    ps = []
-    for slot in wl.sampled():
-        d, p = pp.weighted_ks_2samp(a[:, slot], w, b[:, slot], w)
-        ps.append(p)
-    d, p = pp.weighted_ks_2samp(la, w, lb, w)
-    ps.append(p)
-    # 13 tests at once: Fisher's combination, and no single one far out
-    assert pp.fisher_combined(np.array(ps)) > 1e-3, ps
-    assert min(ps) > 1e-4, ps
