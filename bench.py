@@ -45,7 +45,7 @@ if ROOT not in sys.path:
 
 import swig_inputs as si  # noqa: E402
 
-SFU_OPS_PER_CLK_SM = 16   # sin/cos results per clock per SM (sm_100-class SFU)
+SFU_OPS_PER_CLK_SM = 16   # sin/cos results per clock per SM (sm_100-class SFU), used if the probe fails
 SFU_OPS_PER_BIN_DET = 2   # one sine and one cosine per bin and detector
 # DRAM bytes (read + write) per logL evaluation inside k_ns_flow (512
 # threads), from one ncu capture of a 2-iteration launch of the 128 s workload
@@ -125,6 +125,28 @@ def workload_description(wl, spec):
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
+def measure_sfu_peak():
+    """The SFU roofline denominator measured on this GPU: compile and run
+    paper_2607_28265_gb300/csrc/peak_probe.cu (__sincosf throughput, best of 5
+    launches).  Returns (Top/s at the measured rate, source text); falls back
+    to the unit-count derivation if the probe cannot run."""
+    src = os.path.join(ROOT, "paper_2607_28265_gb300", "csrc", "peak_probe.cu")
+    exe = os.path.join(ROOT, "_build", "peak_probe")
+    try:
+        os.makedirs(os.path.dirname(exe), exist_ok=True)
+        nvcc = os.environ.get("NVCC", "nvcc")
+        subprocess.run([nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-o", exe, src], check=True,
+                       capture_output=True, timeout=300)
+        out = subprocess.run([exe], check=True, capture_output=True, text=True, timeout=120).stdout
+        rows = [json.loads(l) for l in out.splitlines() if l.strip().startswith("{")]
+        sfu = next(r for r in rows if r["kind"] == "sfu_sincos_results")
+        return sfu["ops_per_s"] / 1e12, (f"measured on this GPU: {sfu['per_clk_per_sm_at_max_clock']:.2f} sin/cos "
+                                        f"results per clk per SM at the {sfu['max_clock_khz'] / 1e3:.0f} MHz maximum "
+                                        f"clock (peak_probe.cu, __sincosf, 64 warps/SM, best of 5)")
+    except Exception as e:  # noqa: BLE001 - any failure falls back to the derived figure
+        return (SFU_OPS_PER_CLK_SM * 152 * 2070.0e6 / 1e12,
+                f"16 sin/cos per clk per SM x 152 SMs x 2070 MHz (derived; the probe failed: {type(e).__name__})")
+
 def reduce_over_ranks(local, world, device="cuda"):
     """Elementwise max and sum over the ranks of a vector of per-rank figures
     (the caller takes times from the max and counts from the sum); a plain
@@ -259,13 +281,13 @@ def run_campaign(args, rank, world):
         return None
     n_post = len(wls) * args.steps
     bindet = sum(r.n_sweep_evals * 3 * wl.n_bins for res, _ in out for r, wl in zip(res, wls))
-    peak = SFU_OPS_PER_CLK_SM * 152 * 2070.0e6 / 1e12
+    peak, peak_source = measure_sfu_peak()
     achieved = SFU_OPS_PER_BIN_DET * bindet / (total_ms * 1e-3) / 1e12
     line = {
-        "metric": METRIC, "value": evals_all / (total_ms_max * 1e-3), "unit": "logL evals/s", "n_gpus": world,
+        "metric": METRIC, "value": full_all / (total_ms_max * 1e-3), "unit": "logL evals/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms_max / args.steps,
         "wall_s_per_posterior": total_ms_max / n_post / 1e3,
-        "full_grid_evals_per_s": full_all / (total_ms_max * 1e-3),
+        "all_evals_per_s": evals_all / (total_ms_max * 1e-3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": "; ".join(f"{wl.name}: {wl.n_bins} bins/det" for wl in wls) + "; " + spec["text"],
                    "name": "cfg4", "posteriors_per_step": len(wls), "l2": "flushed between steps (256 MB write)",
@@ -278,7 +300,7 @@ def run_campaign(args, rank, world):
                      "peak": peak, "unit": "SFU Top/s", "frac": achieved / peak, "traffic": None,
                      "work_per_launch": "2 SFU ops x bin-detector evaluations of the four events",
                      "timing": "CUDA events around each batch (the batch's persistent launches and host steps)",
-                     "peak_source": "16 sin/cos per clk per SM x 152 SMs x 2070 MHz (derived, not measured)"},
+                     "peak_source": peak_source},
         "clocks": clocks.summary(),
     }
     if args.cpu_baseline and world == 1:
@@ -312,6 +334,7 @@ def run_gpu(args, rank, world):
     stream = torch.cuda.current_stream()
     ctx.set_stream(stream.cuda_stream)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # > L2 (129 MB)
+    peak_sfu, peak_source = measure_sfu_peak() if rank == 0 else (None, None)
 
     def step_device():
         flush.zero_()  # evict L2 between steps
@@ -349,7 +372,7 @@ def run_gpu(args, rank, world):
     # PSDs (host -> device inside the library), run, read back the samples
     pinned = [torch.from_numpy(np.ascontiguousarray(d)).pin_memory() for d in data]
     pinned_psd = [torch.from_numpy(np.ascontiguousarray(s)).pin_memory() for s in psds]
-    e2e_ms, e2e_evals = [], 0
+    e2e_ms, e2e_evals, e2e_full = [], 0, 0
     h2d0, d2h0 = ctx.profile()["h2d_bytes"], ctx.profile()["d2h_bytes"]
     for _ in range(max(1, args.e2e_steps)):
         torch.cuda.synchronize()
@@ -362,20 +385,41 @@ def run_gpu(args, rank, world):
         torch.cuda.synchronize()
         e2e_ms.append((time.perf_counter() - t0) * 1e3)
         e2e_evals += r.n_evals
+        e2e_full += r.n_sweep_evals
     n_e2e = max(1, args.e2e_steps)
     h2d = (ctx.profile()["h2d_bytes"] - h2d0) / n_e2e
     d2h = (ctx.profile()["d2h_bytes"] - d2h0) / n_e2e
 
+    # the metric's comparison (cfg2): the learned proposal with mixed precision
+    # on the same event, same K and W, then both arms' posteriors side by side
+    arms = None
+    if args.workload == "cfg2" and args.learned_arm:
+        th_p, ll_p, lw_p = ctx.get_samples()
+        ls = WORKLOADS["cfg5"]
+        ctx.set_sampler(nlive=wl.nlive, nrep=wl.nrep, sweeps=wl.sweeps, steps_per_dim=wl.steps_per_dim,
+                        seed=wl.sampler_seed + 1000 * rank, precision=prec, proposal=swig.PROPOSAL_LEARNED,
+                        learn_mix=ls.get("learn_mix", 0.0), learn_interval=ls.get("learn_interval", 0),
+                        learn_steps=ls.get("learn_steps", 0))
+        for _ in range(args.warmup):
+            step_device()
+        learned = [step_device() for _ in range(args.steps)]
+        th_l, ll_l, lw_l = ctx.get_samples()
+        arms = {"plain": _arm_summary(results, "plain SwiG: covariance directions, mixed precision"),
+                "learned": _arm_summary(learned, "learned + mixed: " + ls["text"]),
+                "posterior_comparison": _compare_posteriors(wl, (th_p, lw_p), (th_l, lw_l),
+                                                            results[-1][0], learned[-1][0])}
+
     # max of the times and sum of the counts over ranks
-    tmax, tsum = reduce_over_ranks([total_ms, total_evals, sum(e2e_ms), e2e_evals, full_evals], world)
+    tmax, tsum = reduce_over_ranks([total_ms, total_evals, sum(e2e_ms), e2e_evals, full_evals, e2e_full], world)
     total_ms_max, e2e_ms_max = float(tmax[0]), float(tmax[2])
     evals_all, e2e_evals_all, full_all = float(tsum[1]), float(tsum[3]), float(tsum[4])
+    e2e_full_all = float(tsum[5])
     if rank != 0:
         return None
 
     clk = clocks.summary()
     sm_mhz_max = 2070.0
-    peak = SFU_OPS_PER_CLK_SM * 152 * sm_mhz_max * 1e6 / 1e12  # SFU Top/s at the maximum SM clock
+    peak = peak_sfu  # SFU Top/s, measured on this GPU by peak_probe.cu
     achieved = SFU_OPS_PER_BIN_DET * bindet / (pers_ms * 1e-3) / 1e12 if pers_ms > 0 else 0.0
     n_bins_eval = spec.get("het_bins", 0) + 1 if het else wl.n_bins
     kernel = "k_ns_het (persistent SwiG kernel, heterodyned)" if het else "k_ns_flow (persistent SwiG kernel, dataflow)"
@@ -383,14 +427,17 @@ def run_gpu(args, rank, world):
                if TRAFFIC_B_PER_EVAL is not None and args.workload == "cfg2" else None)
     line = {
         "metric": METRIC,
-        "value": evals_all / (total_ms_max * 1e-3),
+        # full-grid (or heterodyned) evaluations: those that run the sweep, the
+        # same kind the CPU oracle arm times; all evaluations (projection-only
+        # updates from the cached sums included) in all_evals_per_s
+        "value": full_all / (total_ms_max * 1e-3),
         "unit": "logL evals/s",
         "n_gpus": world,
         "steps": args.steps,
         "warmup": args.warmup,
         "ms_per_step": total_ms_max / args.steps,
         "wall_s_per_posterior": total_ms_max / args.steps / 1e3,
-        "full_grid_evals_per_s": full_all / (total_ms_max * 1e-3),
+        "all_evals_per_s": evals_all / (total_ms_max * 1e-3),
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
@@ -401,7 +448,7 @@ def run_gpu(args, rank, world):
                    "posterior": {"logz": results[-1][0].logz, "logz_err": results[-1][0].logz_err,
                                  "ess": results[-1][0].ess, "n_iter": results[-1][0].n_iter,
                                  "n_dead": results[-1][0].n_dead}},
-        "e2e": {"value": e2e_evals_all / (e2e_ms_max * 1e-3), "unit": "logL evals/s",
+        "e2e": {"value": e2e_full_all / (e2e_ms_max * 1e-3), "unit": "logL evals/s",
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                 "ms_per_step": e2e_ms_max / n_e2e},
         "gpu_launches": launches,
@@ -418,7 +465,7 @@ def run_gpu(args, rank, world):
                                 f"{n_bins_eval} {'bin edges' if het else 'bins'})"),
             "launches": int(pers_launch),
             "avg_launch_ms": pers_ms / max(1, pers_launch),
-            "peak_source": "16 sin/cos per clk per SM x 152 SMs x 2070 MHz (derived, not measured)",
+            "peak_source": peak_source,
         },
         "clocks": clk,
     }
@@ -444,10 +491,50 @@ def run_gpu(args, rank, world):
                  "cyc_step", "cyc_prop", "cyc_free", "cyc_setup", "n_free", "n_setup", "n_step", "f_units",
                  "f_unit_cyc", "f_idle_cyc")
     line["sampler_profile"] = {k: float(np.mean([p.get(k, 0.0) for _, _, p in results])) for k in prof_keys}
+    if arms is not None:
+        line["arms"] = arms
     if prof_learn := sum(p.get("learn_ms", 0.0) for _, _, p in results):
         line["learned"] = {"train_ms_per_posterior": prof_learn / args.steps,
                            "retrainings_per_posterior": sum(p.get("learn_rounds", 0) for _, _, p in results) / args.steps}
     return line
+
+
+def _arm_summary(results, text):
+    """Wall-s per posterior and the posteriors' figures of one arm's timed steps."""
+    ms = [m for _, m, _ in results]
+    return {"text": text, "wall_s_per_posterior": float(np.mean(ms)) / 1e3,
+            "wall_s_each": [m / 1e3 for m in ms],
+            "logz": [r.logz for r, _, _ in results], "logz_err": [r.logz_err for r, _, _ in results],
+            "ess": [r.ess for r, _, _ in results], "n_evals": [r.n_evals for r, _, _ in results],
+            "n_full_evals": [r.n_sweep_evals for r, _, _ in results],
+            "train_ms": [p.get("learn_ms", 0.0) for _, _, p in results],
+            "retrainings": [p.get("learn_rounds", 0.0) for _, _, p in results]}
+
+
+def _compare_posteriors(wl, a, b, ra, rb):
+    """Evidence difference and per-parameter weighted two-sample KS (Kish
+    effective sizes) between two runs' weighted samples (theta, log w)."""
+    out = {"dlogz": rb.logz - ra.logz, "dlogz_err": math.hypot(ra.logz_err, rb.logz_err), "ks": {}}
+    wa, wb = np.exp(a[1] - a[1].max()), np.exp(b[1] - b[1].max())
+    for slot in wl.sampled():
+        d, p = _weighted_ks(a[0][:, slot], wa, b[0][:, slot], wb)
+        out["ks"][si.PARAM_NAMES[slot]] = {"D": d, "p": p}
+    return out
+
+
+def _weighted_ks(x1, w1, x2, w2):
+    """Two-sample Kolmogorov-Smirnov distance of weighted samples and its
+    asymptotic p-value with n = n1 n2 / (n1 + n2) from the Kish effective sizes."""
+    from scipy import stats
+    w1, w2 = w1 / np.sum(w1), w2 / np.sum(w2)
+    grid = np.sort(np.concatenate([x1, x2]))
+    o1, o2 = np.argsort(x1), np.argsort(x2)
+    c1 = np.concatenate([[0.0], np.cumsum(w1[o1])])
+    c2 = np.concatenate([[0.0], np.cumsum(w2[o2])])
+    d = float(np.max(np.abs(c1[np.searchsorted(x1[o1], grid, side="right")] -
+                            c2[np.searchsorted(x2[o2], grid, side="right")])))
+    n1, n2 = 1.0 / np.sum(w1 ** 2), 1.0 / np.sum(w2 ** 2)
+    return d, float(stats.kstwobign.sf(d * math.sqrt(n1 * n2 / (n1 + n2))))
 
 
 # ---------------------------------------------------------------------------
@@ -578,11 +665,13 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--e2e-steps", type=int, default=1)
+    ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--impl", choices=["swig", "reference"], default="swig")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="cfg2")
+    ap.add_argument("--no-learned-arm", dest="learned_arm", action="store_false",
+                    help="cfg2 only: skip the learned-proposal arm of the metric's comparison")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -542,6 +542,47 @@ int ensure_scratch(swig_ctx* c, int n) {
 
 int current_precision(const swig_ctx* c) { return c->cfg_set ? c->cfg.precision : SWIG_PREC_MIXED; }
 
+// Slices: contiguous whole 32-bin chunks, one CTA each, cut at equal
+// estimated cost.  With a tile plan (mixed precision) every tile of more than
+// 32 bins adds about one chunk's cost (its anchor, and every lane's crossing
+// into it in the bin loop), and a chunk holding tiles of 32 bins or fewer
+// (every lane crosses into a new tile on every step) costs about 2.3 chunks,
+// as measured on GB300 with the per-CTA sweep counters of the persistent
+// sampler.  Up to sm_count slices (more if one slice's data would not fit in
+// shared memory).
+void plan_slices(int64_t n, int n_det, int sm_count, const std::vector<TileInfo>& tiles,
+                 std::vector<int>& slice_begin, int* max_bins_out) {
+  const int n_chunks = (int)((n + kChunk - 1) / kChunk);
+  std::vector<double> chunk_cost(n_chunks, 1.0);
+  for (const TileInfo& ti : tiles) {
+    double& cc = chunk_cost[ti.k0 / kChunk];
+    cc = ti.nbins <= kChunk ? std::max(cc, 2.33) : cc + 1.0;
+  }
+  double total_cost = 0.0;
+  for (double v : chunk_cost) total_cost += v;
+  int n_slices = std::min(sm_count, std::max(1, n_chunks / 4));
+  const size_t smem_cap = 200 * 1024;
+  int max_bins = 0;
+  for (;;) {
+    slice_begin.assign(1, 0);
+    double acc = 0.0;
+    int s = 1;
+    for (int ch = 0; ch < n_chunks && s < n_slices; ++ch) {
+      acc += chunk_cost[ch];
+      if (acc >= total_cost * s / n_slices && ch + 1 < n_chunks) {
+        slice_begin.push_back((ch + 1) * kChunk);
+        ++s;
+      }
+    }
+    slice_begin.push_back((int)n);
+    max_bins = 0;
+    for (size_t q = 0; q + 1 < slice_begin.size(); ++q) max_bins = std::max(max_bins, slice_begin[q + 1] - slice_begin[q]);
+    if (sweep_smem_bytes(n_det, max_bins) <= smem_cap || n_slices >= n_chunks) break;
+    n_slices = std::min(n_chunks, n_slices * 2);
+  }
+  *max_bins_out = max_bins;
+}
+
 // Validate the problem and (re)build every device-side table.
 int prepare(swig_ctx* c) {
   if (!c->dirty) return SWIG_OK;
@@ -622,45 +663,13 @@ int prepare(swig_ctx* c) {
     }
   }
 
-  // slices: contiguous whole 32-bin chunks, one CTA each.  The mixed path's
-  // tile plan comes first so that slices can balance the estimated cost:
-  // a chunk whose tiles are no longer than 32 bins reloads anchors for every
-  // bin and costs about twice a chunk inside a long tile, and every tile's
-  // anchor (~480 FP32 operations, one lane) costs about a quarter of a chunk.
   std::vector<TileInfo> tiles;
   std::vector<TileBasis> basis;
   if (prec == SWIG_PREC_MIXED) plan_tiles(c, tiles, basis);
-  const int n_chunks = (int)((n + kChunk - 1) / kChunk);
-  std::vector<double> chunk_cost(n_chunks, 1.0);
-  if (prec == SWIG_PREC_MIXED)
-    for (const TileInfo& ti : tiles)
-      if (ti.nbins <= kChunk) chunk_cost[ti.k0 / kChunk] = 2.0;
-  if (prec == SWIG_PREC_MIXED)
-    for (const TileInfo& ti : tiles) chunk_cost[ti.k0 / kChunk] += 0.25;
-  double total_cost = 0.0;
-  for (double v : chunk_cost) total_cost += v;
-  int n_slices = std::min(c->sm_count, std::max(1, n_chunks / 4));
-  const size_t smem_cap = 200 * 1024;
   std::vector<int> slice_begin;
   int max_bins = 0;
-  for (;;) {
-    slice_begin.assign(1, 0);
-    double acc = 0.0;
-    int s = 1;
-    for (int ch = 0; ch < n_chunks && s < n_slices; ++ch) {
-      acc += chunk_cost[ch];
-      if (acc >= total_cost * s / n_slices && ch + 1 < n_chunks) {
-        slice_begin.push_back((ch + 1) * kChunk);
-        ++s;
-      }
-    }
-    slice_begin.push_back((int)n);
-    max_bins = 0;
-    for (size_t q = 0; q + 1 < slice_begin.size(); ++q) max_bins = std::max(max_bins, slice_begin[q + 1] - slice_begin[q]);
-    if (sweep_smem_bytes(n_det, max_bins) <= smem_cap || n_slices >= n_chunks) break;
-    n_slices = std::min(n_chunks, n_slices * 2);
-  }
-  n_slices = (int)slice_begin.size() - 1;
+  plan_slices(n, n_det, c->sm_count, tiles, slice_begin, &max_bins);
+  int n_slices = (int)slice_begin.size() - 1;
   L.n_slices = n_slices;
   c->B.max_slice_bins = max_bins;
 

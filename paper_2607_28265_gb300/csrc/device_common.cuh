@@ -253,7 +253,9 @@ __device__ inline bool theta_valid(const double* th) {
   return (th[0] > 0.0) && (th[1] > 0.0) && (th[1] <= 1.0) && (th[6] > 0.0) && isfinite(s);
 }
 
-__device__ inline void setup_intrinsic(const double* th, EvalRecord* rec) {
+// split = false leaves c_hi / c_lo to the caller (a warp splits the
+// coefficients one per lane).
+__device__ inline void setup_intrinsic(const double* th, EvalRecord* rec, bool split = true) {
   double c[NBASIS];
   if (rec->valid) {
     const MassTerms t = taylorf2_mass_terms(th[0], th[1]);
@@ -271,14 +273,17 @@ __device__ inline void setup_intrinsic(const double* th, EvalRecord* rec) {
   }
   for (int j = 0; j < NBASIS; ++j) {
     rec->c[j] = c[j];
-    dfl v = df_from_double(c[j]);
-    rec->c_hi[j] = v.hi;
-    rec->c_lo[j] = v.lo;
+    if (split) {
+      dfl v = df_from_double(c[j]);
+      rec->c_hi[j] = v.hi;
+      rec->c_lo[j] = v.lo;
+    }
   }
 }
 
 // Only the spin (slots 2, 3) or only the tidal (slots 4, 5) coefficients.
-__device__ inline void setup_intrinsic_partial(const double* th, EvalRecord* rec, bool spin, bool tide) {
+__device__ inline void setup_intrinsic_partial(const double* th, EvalRecord* rec, bool spin, bool tide,
+                                               bool split = true) {
   if (!rec->valid) return;
   MassTerms t;  // Mc and q are unchanged: reuse the cached mass factors
   t.eta = rec->mterm[0];
@@ -297,9 +302,11 @@ __device__ inline void setup_intrinsic_partial(const double* th, EvalRecord* rec
   for (int q = 0; q < 4; ++q) {
     const int j = js[q];
     rec->c[j] = c[j];
-    dfl v = df_from_double(c[j]);
-    rec->c_hi[j] = v.hi;
-    rec->c_lo[j] = v.lo;
+    if (split) {
+      dfl v = df_from_double(c[j]);
+      rec->c_hi[j] = v.hi;
+      rec->c_lo[j] = v.lo;
+    }
   }
 }
 
@@ -372,7 +379,9 @@ __device__ inline void setup_delays(const LikeConst& L, const double* th, EvalRe
   sincos(th[10], &sd, &cd);
   const double n0 = cd * cl * (-1.0 / kCSI), n1 = cd * sl * (-1.0 / kCSI), n2 = sd * (-1.0 / kCSI);
   for (int i = 0; i < SWIG_MAX_DET; ++i) {
-    const double tau = i < L.n_det ? th[11] + (n0 * L.vertex[i][0] + n1 * L.vertex[i][1] + n2 * L.vertex[i][2]) : 0.0;
+    const double gd = i < L.n_det ? (n0 * L.vertex[i][0] + n1 * L.vertex[i][1] + n2 * L.vertex[i][2]) : 0.0;
+    const double tau = i < L.n_det ? th[11] + gd : 0.0;
+    rec->gdel[i] = gd;
     rec->tau[i] = tau;
     dfl tv = df_from_double(tau);
     rec->tau_hi[i] = tv.hi;
@@ -427,7 +436,19 @@ __device__ inline void setup_delay_det(const LikeConst& L, const double* th, int
   sincos(th[9] - L.gmst, &sl, &cl);
   sincos(th[10], &sd, &cd);
   const double n0 = cd * cl * (-1.0 / kCSI), n1 = cd * sl * (-1.0 / kCSI), n2 = sd * (-1.0 / kCSI);
-  const double tau = th[11] + (n0 * L.vertex[i][0] + n1 * L.vertex[i][1] + n2 * L.vertex[i][2]);
+  const double gd = (n0 * L.vertex[i][0] + n1 * L.vertex[i][1] + n2 * L.vertex[i][2]);
+  const double tau = th[11] + gd;
+  rec->gdel[i] = gd;
+  rec->tau[i] = tau;
+  dfl tv = df_from_double(tau);
+  rec->tau_hi[i] = tv.hi;
+  rec->tau_lo[i] = tv.lo;
+}
+
+// A move of t_c alone: the record's geocentric delay of detector i is kept,
+// tau_i = t_c + gdel_i (the same sum setup_delay_det forms).
+__device__ inline void setup_tc_det(const double* th, int i, EvalRecord* rec) {
+  const double tau = th[11] + rec->gdel[i];
   rec->tau[i] = tau;
   dfl tv = df_from_double(tau);
   rec->tau_hi[i] = tv.hi;

@@ -37,6 +37,7 @@
 #include <algorithm>
 #include <chrono>
 #include <climits>
+#include <cstddef>
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -61,10 +62,21 @@ constexpr int kFlowThreads = 512;  // dataflow sampler: 16 warps, up to 128 regi
 constexpr int kHetThreads = 512;  // heterodyned sampler: one chain per CTA, 16 warps
 static_assert(kHetThreads == kHetTmThreads, "the sampler and the batched time-marginalised kernel share sum orders");
 constexpr int kFreeBudget = 8;  // projection-only evaluations per chain per round
+#ifndef SWIG_FLOW_PARTS
+#define SWIG_FLOW_PARTS 1
+#endif
+static_assert(SWIG_FLOW_PARTS >= 1 && SWIG_FLOW_PARTS <= 4, "1..4 parts per slice");
+// Bytes of a slice's tile table plus `warps` anchor rows in the dataflow
+// kernel's shared memory (16-byte aligned).
+__host__ __device__ inline size_t flow_tile_bytes(int max_tiles, int warps) {
+  const size_t ti = ((size_t)max_tiles * sizeof(TileInfo) + 15) & ~(size_t)15;
+  return ti + (((size_t)warps * max_tiles * kAnchorStride * sizeof(float) + 15) & ~(size_t)15);
+}
 enum ChainPhase { PH_NEW = 0, PH_LEFT = 1, PH_RIGHT = 2, PH_SHRINK = 3 };
 // What a Gibbs block moves: waveform coefficients, amplitude A(Mc)/d_L,
-// projection P_i, time shifts tau_i.
-enum BlockFlag { BF_INTR = 1, BF_AMP = 2, BF_PROJ = 4, BF_TAU = 8, BF_SPIN = 16, BF_TIDE = 32 };
+// projection P_i, time shifts tau_i (BF_SKY: through the geocentric delays;
+// BF_TAU alone: t_c).
+enum BlockFlag { BF_INTR = 1, BF_AMP = 2, BF_PROJ = 4, BF_TAU = 8, BF_SPIN = 16, BF_TIDE = 32, BF_SKY = 64 };
 enum RunStatus { ST_RUNNING = 0, ST_TERMINATED = 1, ST_LIMIT = 2 };
 
 struct SamplerConst {
@@ -87,6 +99,14 @@ struct SamplerConst {
   SkyFrame sky;     // detector-frame sky parameterisation (slots 9, 10), or off
   int learn_on;     // learned directions available (SWIG_PROPOSAL_LEARNED)
   float learn_mix;  // probability of a learned direction per slice step
+  // warp-parallel control: dimensions of each block as a bit mask, each
+  // dimension's rank within its block, the dimension of each slot (-1: none),
+  // and the byte offset of the homed chains' state in dynamic shared memory
+  unsigned block_mask[kMaxBlocks];
+  int block_rank[kMaxDim];
+  int dim_of_slot[SWIG_N_PARAMS];
+  int ctl_off;
+  int ctl_slots;  // chains homed per CTA at most
 };
 
 struct ChainState {
@@ -585,16 +605,19 @@ __device__ __noinline__ int chain_advance(const LikeConst& L, const SamplerConst
 // The set-up of a pending proposal's record, one piece per lane: lane 0 the
 // waveform coefficients (all, or only spin / tidal ones), lane 1 the
 // amplitude, lanes 2.. the projection of each detector, lanes 8.. the time
-// shift of each detector; then lane 0 combines them.  All 32 lanes call it
-// with the same fl (>= 0) and th (the proposal's theta).
+// shift of each detector; then one lane per coefficient splits it into a
+// double-float and one lane per detector forms C_i (lane 0 adds <h|h> in
+// detector order).  All 32 lanes call it with the same fl (>= 0) and th (the
+// proposal's theta).
 __device__ __noinline__ void setup_record_warp(const LikeConst& L, const double* th, int fl, bool f32,
                                                EvalRecord* rec, int lane) {
-  if (rec->valid) {
+  const bool valid = rec->valid != 0;
+  if (valid) {
     if (lane == 0) {
       if (fl & BF_INTR)
-        setup_intrinsic(th, rec);
+        setup_intrinsic(th, rec, false);
       else if (fl & (BF_SPIN | BF_TIDE))
-        setup_intrinsic_partial(th, rec, (fl & BF_SPIN) != 0, (fl & BF_TIDE) != 0);
+        setup_intrinsic_partial(th, rec, (fl & BF_SPIN) != 0, (fl & BF_TIDE) != 0, false);
     } else if (lane == 1) {
       if (fl & BF_AMP) {
         if (f32)
@@ -605,14 +628,32 @@ __device__ __noinline__ void setup_record_warp(const LikeConst& L, const double*
     } else if (lane >= 2 && lane < 2 + L.n_det) {
       if (fl & BF_PROJ) setup_projection_det(L, th, lane - 2, f32, rec);
     } else if (lane >= 8 && lane < 8 + L.n_det) {
-      if (fl & BF_TAU) setup_delay_det(L, th, lane - 8, rec);
+      if (fl & BF_SKY)
+        setup_delay_det(L, th, lane - 8, rec);
+      else if (fl & BF_TAU)
+        setup_tc_det(th, lane - 8, rec);
     }
   } else if (lane == 0) {
     // invalid proposal: the record only has to say so (logL = -inf)
     rec->amp = 0.0;
   }
   __syncwarp();
-  if (lane == 0) setup_combine(L, rec);
+  if (valid && (fl & (BF_INTR | BF_SPIN | BF_TIDE)) && lane < NBASIS) {
+    const dfl v = df_from_double(rec->c[lane]);
+    rec->c_hi[lane] = v.hi;
+    rec->c_lo[lane] = v.lo;
+  }
+  double term = 0.0;
+  if (lane < SWIG_MAX_DET) {
+    const double cre = rec->amp * rec->pre[lane], cim = rec->amp * rec->pim[lane];
+    rec->cre[lane] = cre;
+    rec->cim[lane] = cim;
+    if (lane < L.n_det) term = (cre * cre + cim * cim) * L.K[lane];
+  }
+  double hh = 0.0;
+#pragma unroll
+  for (int i = 0; i < SWIG_MAX_DET; ++i) hh += __shfl_sync(0xffffffffu, term, i);
+  if (lane == 0) rec->hh = hh;
   __syncwarp();
 }
 
@@ -854,12 +895,31 @@ __device__ __forceinline__ void st_release(int* p, int v) {
   asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-// Copy a record written by another SM into shared memory (through L2).
+// Copy the part of a record that a sweep unit reads (the double-float phase
+// coefficients and the time shifts: one contiguous run of words), written by
+// another SM, into shared memory (through L2).
+static_assert(offsetof(EvalRecord, c_lo) > offsetof(EvalRecord, c_hi) &&
+                  offsetof(EvalRecord, tau) > offsetof(EvalRecord, c_lo) &&
+                  offsetof(EvalRecord, tau_hi) > offsetof(EvalRecord, tau) &&
+                  offsetof(EvalRecord, tau_lo) > offsetof(EvalRecord, tau_hi),
+              "the sweep's fields of EvalRecord are one run");
+// The FP64 sweep (MIXED false) also reads the FP64 coefficients c, which
+// precede that run.
+template <bool MIXED = true>
 __device__ __forceinline__ void load_record_cg(const EvalRecord* src, EvalRecord* dst, int lane) {
+  static_assert(offsetof(EvalRecord, c) == 0 && offsetof(EvalRecord, c_hi) > 0, "c leads the record");
+  constexpr int w0 = MIXED ? (int)(offsetof(EvalRecord, c_hi) / 4) : 0;
+  constexpr int w1 = (int)((offsetof(EvalRecord, tau_lo) + sizeof(float) * SWIG_MAX_DET) / 4);
   const unsigned* s = reinterpret_cast<const unsigned*>(src);
   unsigned* d = reinterpret_cast<unsigned*>(dst);
-  for (int w = lane; w < (int)(sizeof(EvalRecord) / 4); w += 32) d[w] = __ldcg(s + w);
+  for (int w = w0 + lane; w < w1; w += 32) d[w] = __ldcg(s + w);
   __syncwarp();
+}
+
+// done_cnt += v with release semantics (orders the unit's partial writes,
+// made visible to lane 0 by the preceding __syncwarp, before the count).
+__device__ __forceinline__ void red_release_add(int* p, int v) {
+  asm volatile("red.release.gpu.global.add.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
 // One control step of chain c by a whole warp: add the slice partials of the
@@ -928,6 +988,549 @@ __device__ bool flow_control(const LikeConst& L, const SamplerConst& S, const De
   return !done;
 }
 
+
+// ---------------------------------------------------------------------------
+// Warp-parallel chain control (mixed-precision full-grid sampler).
+//
+// The control warp keeps the state of the chains homed on its CTA in shared
+// memory for the whole NS iteration (copied in after the boundary and back
+// before the next one).  During a control step the state lives in registers
+// spread over the lanes: the scalars are uniform across the warp; lane j
+// holds dimension j of x, y and the slice direction, slot j of theta and of
+// the proposal's theta, and component j of the cached kappa sums.  The
+// per-dimension work of a proposal (the point on the slice, the unit-cube
+// test, the prior transform, the validity test) is one step across the
+// lanes instead of a loop, the direction's normal draws and its Cholesky
+// product run one row per lane, a projection-only evaluation runs one
+// detector per lane, and records move between shared and global memory with
+// the whole warp.  Each value is formed by the same operations as in
+// chain_advance_local, and the Philox counters are drawn in the same order,
+// so the random stream of a chain is unchanged.
+// ---------------------------------------------------------------------------
+constexpr unsigned kFull = 0xffffffffu;
+
+struct WarpChain {
+  double x, y, dir, th, thy, kap, vv;  // lane-indexed, see above (vv: detector i on lane i)
+  double lx, lo, hi, t;
+  int block, step, sweep, phase, n_out, n_shrink, done, proj_dirty, n_caps;
+  unsigned ctr;
+  long long n_evals, n_full;
+};
+
+__device__ __forceinline__ void wc_load(const ChainState& ch, WarpChain& w, int lane) {
+  const int l = lane < kMaxDim ? lane : 0;
+  w.x = ch.x[l];
+  w.y = ch.y[l];
+  w.dir = ch.dir[l];
+  w.th = ch.th[l];
+  w.thy = ch.th_y[l];
+  w.kap = lane < 2 * SWIG_MAX_DET ? ch.kap[lane] : 0.0;
+  w.vv = lane < SWIG_MAX_DET ? ch.vv[lane] : 0.0;
+  w.lx = ch.lx;
+  w.lo = ch.lo;
+  w.hi = ch.hi;
+  w.t = ch.t;
+  w.block = ch.block;
+  w.step = ch.step;
+  w.sweep = ch.sweep;
+  w.phase = ch.phase;
+  w.n_out = ch.n_out;
+  w.n_shrink = ch.n_shrink;
+  w.done = ch.done;
+  w.proj_dirty = ch.proj_dirty;
+  w.n_caps = ch.n_caps;
+  w.ctr = ch.ctr;
+  w.n_evals = ch.n_evals;
+  w.n_full = ch.n_full;
+}
+
+__device__ __forceinline__ void wc_store(ChainState& ch, const WarpChain& w, int lane) {
+  if (lane < kMaxDim) {
+    ch.x[lane] = w.x;
+    ch.y[lane] = w.y;
+    ch.dir[lane] = w.dir;
+    ch.th[lane] = w.th;
+    ch.th_y[lane] = w.thy;
+  }
+  if (lane < 2 * SWIG_MAX_DET) ch.kap[lane] = w.kap;
+  if (lane < SWIG_MAX_DET) ch.vv[lane] = w.vv;
+  if (lane == 0) {
+    ch.lx = w.lx;
+    ch.lo = w.lo;
+    ch.hi = w.hi;
+    ch.t = w.t;
+    ch.block = w.block;
+    ch.step = w.step;
+    ch.sweep = w.sweep;
+    ch.phase = w.phase;
+    ch.n_out = w.n_out;
+    ch.n_shrink = w.n_shrink;
+    ch.done = w.done;
+    ch.proj_dirty = w.proj_dirty;
+    ch.n_caps = w.n_caps;
+    ch.ctr = w.ctr;
+    ch.n_evals = w.n_evals;
+    ch.n_full = w.n_full;
+  }
+  __syncwarp();
+}
+
+// Copy n bytes (a multiple of 4) with the whole warp.
+__device__ __forceinline__ void warp_copy(void* dst, const void* src, int n, int lane) {
+  const unsigned* s4 = static_cast<const unsigned*>(src);
+  unsigned* d4 = static_cast<unsigned*>(dst);
+  for (int q = lane; q < n / 4; q += 32) d4[q] = s4[q];
+  __syncwarp();
+}
+
+// The same from global memory written by another SM (through L2).
+__device__ __forceinline__ void warp_copy_cg(void* dst, const void* src, int n, int lane) {
+  const unsigned* s4 = static_cast<const unsigned*>(src);
+  unsigned* d4 = static_cast<unsigned*>(dst);
+  for (int q = lane; q < n / 4; q += 32) d4[q] = __ldcg(s4 + q);
+  __syncwarp();
+}
+
+__device__ __forceinline__ double wc_uniform(const SamplerConst& S, WarpChain& w, int c, long long it) {
+  return u01_from(philox4x32_10(make_uint4(w.ctr++, (unsigned)c, (unsigned)it, 0u), S.key0, S.key1));
+}
+
+__device__ __forceinline__ void wc_finish_step(const SamplerConst& S, WarpChain& w, NSGlobal* g, int lane) {
+  w.phase = PH_NEW;
+  if (++w.step >= S.steps_per_dim * S.block_size[w.block]) {
+    w.step = 0;
+    if (++w.block >= S.n_blocks) {
+      w.block = 0;
+      if (++w.sweep >= S.sweeps) {
+        w.done = 1;
+        if (lane == 0) atomicAdd(&g->chains_done, 1);
+      }
+    }
+  }
+}
+
+// apply_result on the warp's copy (uniform).
+__device__ __forceinline__ bool wc_apply(const SamplerConst& S, WarpChain& w, double ly, double logl_star, NSGlobal* g,
+                                         int lane) {
+  const bool ok = ly > logl_star;
+  switch (w.phase) {
+    case PH_LEFT:
+      if (ok) {
+        w.lo -= 1.0;
+        if (++w.n_out >= kMaxStepOut) {
+          w.phase = PH_RIGHT;
+          w.n_out = 0;
+        }
+      } else {
+        w.phase = PH_RIGHT;
+        w.n_out = 0;
+      }
+      return false;
+    case PH_RIGHT:
+      if (ok) {
+        w.hi += 1.0;
+        if (++w.n_out >= kMaxStepOut) {
+          w.phase = PH_SHRINK;
+          w.n_shrink = 0;
+        }
+      } else {
+        w.phase = PH_SHRINK;
+        w.n_shrink = 0;
+      }
+      return false;
+    default:  // PH_SHRINK
+      if (ok) return true;
+      if (w.t < 0.0)
+        w.lo = w.t;
+      else
+        w.hi = w.t;
+      if (++w.n_shrink >= kMaxShrink) {
+        ++w.n_caps;
+        wc_finish_step(S, w, g, lane);
+      }
+      return false;
+  }
+}
+
+__device__ __forceinline__ bool wc_in_block(const SamplerConst& S, int b, int lane) {
+  return lane < S.ndim && ((S.block_mask[b] >> lane) & 1u);
+}
+
+// start_step across the warp.
+__device__ __forceinline__ void wc_start_step(const SamplerConst& S, WarpChain& w, const float* chol,
+                                              const float* learn_out, int c, long long it, int lane) {
+  const int b = w.block, nb = S.block_size[b];
+  const bool inb = wc_in_block(S, b, lane);
+  w.dir = 0.0;
+  bool learned = false;
+  if (S.learn_on && learn_out && wc_uniform(S, w, c, it) < (double)S.learn_mix) {
+    const int row = min((int)(wc_uniform(S, w, c, it) * (double)S.nlive), S.nlive - 1);
+    const float* o = learn_out + (size_t)row * 32;
+    float nrm2 = 0.0f;
+    for (int r = 0; r < nb; ++r) {
+      const float u = o[S.block_dims[b][r]];
+      nrm2 = fmaf(u, u, nrm2);
+    }
+    const float inv = rsqrtf(nrm2 + 1e-12f);
+    if (inb) {
+      const float sv = fminf(fmaxf(o[13 + lane], -30.0f), 5.0f);
+      w.dir = (double)(expf(sv) * o[lane] * inv);
+    }
+    learned = true;
+  }
+  if (!learned) {
+    // z_r, r < nb, one Philox block each at consecutive counters (chain_normal)
+    float z = 0.0f;
+    if (lane < nb) {
+      const uint4 r = philox4x32_10(make_uint4(w.ctr + (unsigned)lane, (unsigned)c, (unsigned)it, 0u), S.key0, S.key1);
+      const float u1 = ((float)(r.x >> 8) + 1.0f) * (1.0f / 16777216.0f);
+      const float u2 = (float)(r.y >> 8) * (1.0f / 16777216.0f);
+      z = sqrtf(-2.0f * logf(u1)) * cospif(2.0f * u2);
+    }
+    w.ctr += (unsigned)nb;
+    // lane r forms row r of L_b z
+    const float* Lb = chol + (size_t)b * kMaxDim * kMaxDim;
+    float v = 0.0f;
+    for (int q = 0; q < nb; ++q) {
+      const float zq = __shfl_sync(kFull, z, q);
+      if (lane < nb && q <= lane) v = fmaf(Lb[lane * kMaxDim + q], zq, v);
+    }
+    // ... and dimension j of the block takes row block_rank[j]
+    const float vd = __shfl_sync(kFull, v, lane < S.ndim ? S.block_rank[lane] : 0);
+    if (inb) w.dir = (double)vd;
+  }
+  const double r0 = wc_uniform(S, w, c, it);
+  w.lo = -r0;
+  w.hi = 1.0 - r0;
+  w.phase = PH_LEFT;
+  w.n_out = 0;
+  w.n_shrink = 0;
+}
+
+// free_loglike_mixed across the warp: lane i < NDET forms detector i's terms
+// (HET: <h|h>_i from the cached vv_i, else the constant K_i A1^2); lane 0 adds
+// them in detector order and finishes.
+template <int NDET, bool HET>
+__device__ __forceinline__ double wc_free_loglike(const LikeConst& L, const WarpChain& w, int lane) {
+  const float tf = (float)w.thy, kf = (float)w.kap;
+  const float mc = __shfl_sync(kFull, tf, 0), dl = __shfl_sync(kFull, tf, 6);
+  const float iota = __shfl_sync(kFull, tf, 7), psi = __shfl_sync(kFull, tf, 8);
+  const float ra = __shfl_sync(kFull, tf, 9), dec = __shfl_sync(kFull, tf, 10), phic = __shfl_sync(kFull, tf, 12);
+  const int di = lane < NDET ? lane : 0;
+  const float ka = __shfl_sync(kFull, kf, 2 * di), kb = __shfl_sync(kFull, kf, 2 * di + 1);
+  const float hk = HET ? (float)w.vv : L.amp_k[di];
+  if (!(mc > 0.0f && dl > 0.0f)) return -INFINITY;
+  float tr = 0.0f, ti = 0.0f, th = 0.0f;
+  if (lane < NDET) {
+    const float rel = exp2f(0.8333333333f * log2f(mc)) / dl;
+    float sl, cl, sd, cd, sp, cp;
+    sincosf(ra - (float)L.gmst, &sl, &cl);
+    sincosf(dec, &sd, &cd);
+    sincosf(psi, &sp, &cp);
+    const float east[3] = {-sl, cl, 0.0f};
+    const float north[3] = {-sd * cl, -sd * sl, cd};
+    float X[3], Y[3];
+    for (int k = 0; k < 3; ++k) {
+      X[k] = -cp * east[k] + sp * north[k];
+      Y[k] = sp * east[k] + cp * north[k];
+    }
+    const float ci = cosf(iota);
+    const float plus = 0.5f * (1.0f + ci * ci), cross = -ci;
+    float sph = 0.0f, cph = 1.0f;
+    if (!L.phase_marg) sincosf(phic, &sph, &cph);
+    float d[6];
+    for (int q = 0; q < 6; ++q) d[q] = (float)L.dten[di][q];
+    auto form = [&d](const float* a, const float* b) {
+      return a[0] * (d[0] * b[0] + d[1] * b[1] + d[2] * b[2]) + a[1] * (d[1] * b[0] + d[3] * b[1] + d[4] * b[2]) +
+             a[2] * (d[2] * b[0] + d[4] * b[1] + d[5] * b[2]);
+    };
+    const float fp = form(X, X) - form(Y, Y), fx = 2.0f * form(X, Y);
+    const float re0 = rel * fp * plus, im0 = rel * fx * cross;
+    const float cre = re0 * cph - im0 * sph, cim = re0 * sph + im0 * cph;
+    const float a = ka * L.amp_s[di], b = kb * L.amp_s[di];
+    tr = cre * a - cim * b;
+    ti = cre * b + cim * a;
+    th = (cre * cre + cim * cim) * hk;
+  }
+  float zr = 0.0f, zi = 0.0f, hh = 0.0f;
+#pragma unroll
+  for (int i = 0; i < NDET; ++i) {
+    zr += __shfl_sync(kFull, tr, i);
+    zi += __shfl_sync(kFull, ti, i);
+    hh += __shfl_sync(kFull, th, i);
+  }
+  double out = 0.0;
+  if (lane == 0) {
+    if (L.dist_marg) {
+      out = distance_marg_logl(L, (double)zr, (double)zi, (double)hh);
+    } else {
+      const float core = (L.phase_marg ? log_i0_f32(sqrtf(zr * zr + zi * zi)) : zr) - 0.5f * hh;
+      out = (double)core - 0.5 * L.DD;
+    }
+  }
+  return __shfl_sync(kFull, out, 0);
+}
+
+// The result of chain c's finished request: the slice partials added in a
+// fixed order as double-float sums on the FP32 pipe (each lane takes units
+// lane, lane + 32, ..., error-free two-sums, then a butterfly of double-float
+// adds; lane 0's totals are the result), each component rounded once to FP64
+// on its own lane (kapc: lane j holds component j), and the FP64 epilogue of
+// Eq. 2 with one detector's terms per lane (ly, on every lane).
+template <int NDET>
+__device__ __forceinline__ void wc_result(const LikeConst& L, const SamplerConst& S, const DeviceBuffers& B, int c,
+                                          int lane, double& kapc, double& ly) {
+  dfl acc[2 * NDET];
+#pragma unroll
+  for (int j = 0; j < 2 * NDET; ++j) acc[j] = dfl{0.0f, 0.0f};
+  const int n_units = L.n_slices * S.flow_parts;
+  for (int s0 = lane; s0 < n_units; s0 += 128) {
+    // four units' loads in flight at once; a unit past the end adds zeros
+    float v[4][2 * NDET];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int s2 = s0 + 32 * q;
+      const float* pp = &B.partials32[((size_t)c * n_units + min(s2, n_units - 1)) * kPartialStride];
+#pragma unroll
+      for (int j = 0; j < 2 * NDET; ++j) v[q][j] = s2 < n_units ? __ldcg(pp + j) : 0.0f;
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+      for (int j = 0; j < 2 * NDET; ++j) {
+        const dfl t = two_sum(acc[j].hi, v[q][j]);
+        acc[j] = fast_two_sum(t.hi, __fadd_rn(t.lo, acc[j].lo));
+      }
+  }
+#pragma unroll
+  for (int j = 0; j < 2 * NDET; ++j)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const dfl b = {__shfl_xor_sync(kFull, acc[j].hi, o), __shfl_xor_sync(kFull, acc[j].lo, o)};
+      acc[j] = df_add(acc[j], b);
+    }
+  float hi = 0.0f, lo = 0.0f;
+#pragma unroll
+  for (int j = 0; j < 2 * NDET; ++j) {
+    const float h0 = __shfl_sync(kFull, acc[j].hi, 0), l0 = __shfl_sync(kFull, acc[j].lo, 0);
+    if (lane == j) {
+      hi = h0;
+      lo = l0;
+    }
+  }
+  kapc = lane < 2 * NDET ? (double)hi + (double)lo : 0.0;
+  const EvalRecord& r = B.rec[c];
+  // detector i's terms of Z = sum_i C_i kappa_i inv_scale_i on lane i
+  const int di = lane < NDET ? lane : 0;
+  const double kre = __shfl_sync(kFull, kapc, 2 * di), kim = __shfl_sync(kFull, kapc, 2 * di + 1);
+  double tr = 0.0, ti = 0.0;
+  if (lane < NDET) {
+    const double a = kre * L.inv_scale[di], b = kim * L.inv_scale[di];
+    tr = r.cre[di] * a - r.cim[di] * b;
+    ti = r.cre[di] * b + r.cim[di] * a;
+  }
+  double zr = __shfl_sync(kFull, tr, 0), zi = __shfl_sync(kFull, ti, 0);
+#pragma unroll
+  for (int i = 1; i < NDET; ++i) {
+    zr += __shfl_sync(kFull, tr, i);
+    zi += __shfl_sync(kFull, ti, i);
+  }
+  double out = 0.0;
+  if (lane == 0) {
+    if (!r.valid) {
+      out = -INFINITY;
+    } else if (L.dist_marg) {
+      out = distance_marg_logl(L, zr, zi, r.hh);
+    } else {
+      const double base = -0.5 * r.hh - 0.5 * L.DD;
+      if (L.phase_marg) {
+        const double x = sqrt(zr * zr + zi * zi);
+        out = (L.fast_epilogue ? x + (double)log_i0e_f32((float)x) : log_bessel_i0(x)) + base;
+      } else {
+        out = zr + base;
+      }
+    }
+  }
+  ly = __shfl_sync(kFull, out, 0);
+}
+
+// One control step of chain c (state `ch` and current-point record `rx` in
+// shared memory) by the whole warp: the result of its pending full
+// evaluation, then the chain's slice steps up to the next full-likelihood
+// proposal, whose record is set up in B.rec[c].  Full grid (HET false): the
+// result is read from the slice partials and the proposal is published as a
+// request to every CTA.  Heterodyned (HET true): the caller evaluates the
+// proposal itself and passes the result back (het_ly on every lane,
+// het_kap: component j on lane j, het_vv: detector i on lane i).  Returns
+// CTL_WAIT (published, or the chain is done), CTL_AGAIN (projection-only
+// budget used up: call again) or CTL_EVAL (HET: record set up, evaluate it).
+enum { CTL_WAIT = 0, CTL_AGAIN = 1, CTL_EVAL = 2 };
+template <int NDET, bool HET>
+__device__ int control_step_warp(const LikeConst& L, const SamplerConst& S, const DeviceBuffers& B,
+                                 const SamplerPtrs& P, int c, ChainState& ch, EvalRecord& rx, int lane,
+                                 double het_ly = 0.0, double het_kap = 0.0, double het_vv = 0.0) {
+  NSGlobal* g = P.g;
+  if (ch.done) return CTL_WAIT;
+  const bool prof = (c == 0) && lane == 0;
+  long long tk = clock64();
+  unsigned long long acc_res = 0, acc_step = 0, acc_prop = 0, acc_free = 0, acc_setup = 0, cnt_free = 0,
+                     cnt_setup = 0, cnt_step = 0;
+  const double logl_star = g->logl_star;
+  const long long it = g->iter;
+  WarpChain w;
+  wc_load(ch, w, lane);
+  if (ch.pending) {
+    double kapc = het_kap, ly = het_ly;
+    if (!HET) wc_result<NDET>(L, S, B, c, lane, kapc, ly);
+    if (lane == 0) {
+      P.pending[c] = 0;
+      ch.pending = 0;
+    }
+    ++w.n_full;
+    ++w.n_evals;
+    if (wc_apply(S, w, ly, logl_star, g, lane)) {
+      w.x = w.y;
+      w.th = w.thy;
+      w.lx = ly;
+      w.kap = kapc;
+      if (HET) w.vv = het_vv;
+      warp_copy(&rx, &B.rec[c], sizeof(EvalRecord), lane);
+      w.proj_dirty = 0;
+      wc_finish_step(S, w, g, lane);
+    }
+  }
+  if (prof) {
+    const long long t2 = clock64();
+    acc_res += t2 - tk;
+    tk = t2;
+  }
+  int free_left = kFreeBudget;
+  int status = CTL_WAIT;
+  for (int guard = 0; guard < 1 << 20 && !w.done; ++guard) {
+    const int b = w.block;
+    if (S.block_free[b] && free_left <= 0) {  // resume next round
+      status = CTL_AGAIN;
+      break;
+    }
+    if (w.phase == PH_NEW) {
+      wc_start_step(S, w, P.chol, P.learn_out, c, it, lane);
+      if (prof) {
+        const long long t2 = clock64();
+        acc_step += t2 - tk;
+        cnt_step += 1;
+        tk = t2;
+      }
+    }
+    double t;
+    if (w.phase == PH_LEFT)
+      t = w.lo;
+    else if (w.phase == PH_RIGHT)
+      t = w.hi;
+    else
+      t = w.lo + (w.hi - w.lo) * wc_uniform(S, w, c, it);
+    w.t = t;
+    const bool inb = wc_in_block(S, b, lane);
+    if (lane < S.ndim) w.y = inb ? w.x + t * w.dir : w.x;
+    const bool inside = __all_sync(kFull, !inb || (w.y >= 0.0 && w.y <= 1.0));
+    if (!inside) {
+      wc_apply(S, w, -INFINITY, logl_star, g, lane);
+      continue;
+    }
+    // the proposal's theta: theta, with the block's slots transformed
+    double v = 0.0;
+    if (inb) {
+      const int slot = S.slot_of_dim[lane];
+      // the sky angles go through FP64: the delays need them to ~1e-10
+      v = (S.sky.on && (slot == 9 || slot == 10)) ? prior_slot_inverse(S.prior[slot], w.y)
+                                                  : prior_slot_inverse_f32(S.prior[slot], w.y);
+    }
+    const int src = lane < SWIG_N_PARAMS ? S.dim_of_slot[lane] : -1;
+    const double vs = __shfl_sync(kFull, v, src >= 0 ? src : 0);
+    w.thy = (src >= 0 && ((S.block_mask[b] >> src) & 1u)) ? vs : w.th;
+    if (S.sky.on && (S.block_flags[b] & BF_SKY)) {
+      const double az = __shfl_sync(kFull, w.thy, 9), zen = __shfl_sync(kFull, w.thy, 10);
+      double ra = 0.0, dec = 0.0;
+      if (lane == 0) sky_frame_to_radec(S.sky, az, zen, &ra, &dec);
+      ra = __shfl_sync(kFull, ra, 0);
+      dec = __shfl_sync(kFull, dec, 0);
+      if (lane == 9) w.thy = ra;
+      if (lane == 10) w.thy = dec;
+    }
+    if (prof) {
+      const long long t2 = clock64();
+      acc_prop += t2 - tk;
+      tk = t2;
+    }
+    if (S.block_free[b]) {
+      --free_left;
+      ++w.n_evals;
+      const double ly = wc_free_loglike<NDET, HET>(L, w, lane);
+      if (wc_apply(S, w, ly, logl_star, g, lane)) {
+        w.x = w.y;
+        w.th = w.thy;
+        w.lx = ly;
+        w.proj_dirty = 1;
+        wc_finish_step(S, w, g, lane);
+      }
+      if (prof) {
+        const long long t2 = clock64();
+        acc_free += t2 - tk;
+        cnt_free += 1;
+        tk = t2;
+      }
+      continue;
+    }
+    // a full evaluation: the current point's record with this block's pieces
+    // recomputed, published as the chain's next request
+    const int fl = S.block_flags[b] | (w.proj_dirty ? (BF_AMP | BF_PROJ) : 0);
+    const bool fin = lane >= SWIG_N_PARAMS || isfinite(w.thy);
+    const double t0v = __shfl_sync(kFull, w.thy, 0), t1v = __shfl_sync(kFull, w.thy, 1);
+    const double t6v = __shfl_sync(kFull, w.thy, 6);
+    const bool valid = __all_sync(kFull, fin) && t0v > 0.0 && t1v > 0.0 && t1v <= 1.0 && t6v > 0.0;
+    if (lane < SWIG_N_PARAMS) ch.th_y[lane] = w.thy;
+    warp_copy(&B.rec[c], &rx, sizeof(EvalRecord), lane);
+    if (lane == 0) {
+      B.rec[c].valid = valid ? 1 : 0;
+      ch.pending = 1;
+      P.pending[c] = 1;
+    }
+    __syncwarp();
+    setup_record_warp(L, ch.th_y, fl, true, &B.rec[c], lane);
+    if (HET) {
+      status = CTL_EVAL;
+    } else if (lane == 0) {
+      P.done_cnt[c] = 0;
+      __threadfence();
+      // sequence number and unit width in one word (one unit per slice)
+      st_release(&P.req[c], (((P.req[c] >> 3) + 1) << 3) | S.flow_parts);
+    }
+    if (prof) {
+      acc_setup += clock64() - tk;
+      cnt_setup += 1;
+    }
+    break;
+  }
+  wc_store(ch, w, lane);
+  if (prof) {
+    g->c_result += acc_res;
+    g->c_step += acc_step;
+    g->c_prop += acc_prop;
+    g->c_free += acc_free;
+    g->c_setup += acc_setup;
+    g->n_free += cnt_free;
+    g->n_setup += cnt_setup;
+    g->n_step += cnt_step;
+  }
+  return w.done && status == CTL_AGAIN ? CTL_WAIT : status;
+}
+
+template <int NDET>
+__device__ __forceinline__ void flow_control_warp(const LikeConst& L, const SamplerConst& S, const DeviceBuffers& B,
+                                                  const SamplerPtrs& P, int c, ChainState& ch, EvalRecord& rx,
+                                                  int lane) {
+  control_step_warp<NDET, false>(L, S, B, P, c, ch, rx, lane);
+}
+
 template <int NDET, bool MIXED>
 __global__ void __launch_bounds__(kFlowThreads, 1)
     k_ns_flow(LikeConst L, SamplerConst S, DeviceBuffers B, SamplerPtrs P) {
@@ -940,23 +1543,33 @@ __global__ void __launch_bounds__(kFlowThreads, 1)
   const int lane = tid & 31, warp = tid >> 5;
   NSGlobal* g = P.g;
 
-  // slice-resident data (mixed precision)
+  // slice-resident data (mixed precision): D_i and the tile of each bin, then
+  // the slice's tile table and one anchor row per warp (so that crossing into
+  // a tile in the bin loop reads shared memory, not L2)
   float2* s_data = reinterpret_cast<float2*>(smem);
   int* s_tile = reinterpret_cast<int*>(s_data + (size_t)NDET * nb);
   size_t fixed_bytes = 0;
+  TileInfo* s_ti = nullptr;
+  float* s_anc = nullptr;
+  int tf = 0;
   if (MIXED) {
     for (int i = 0; i < NDET; ++i)
       for (int kq = tid; kq < nb; kq += blockDim.x) s_data[i * nb + kq] = B.data32[(size_t)i * L.n_bins + b0 + kq];
     for (int kq = tid; kq < nb; kq += blockDim.x) s_tile[kq] = B.bin_tile[b0 + kq];
     fixed_bytes = (((size_t)nb * (NDET * sizeof(float2) + sizeof(int))) + 15) & ~(size_t)15;
+    s_ti = reinterpret_cast<TileInfo*>(smem + fixed_bytes);
+    s_anc = reinterpret_cast<float*>(smem + fixed_bytes + flow_tile_bytes(S.max_tiles_slice, 0));
+    fixed_bytes += flow_tile_bytes(S.max_tiles_slice, kFlowThreads / 32);
+    tf = B.bin_tile[b0];
+    const int nt = B.bin_tile[b1 - 1] - tf + 1;
+    for (int t = tid; t < nt; t += blockDim.x) s_ti[t] = B.tiles[tf + t];
   }
   __syncthreads();
   unsigned char* dyn = smem + fixed_bytes;  // per-warp records, or sort buffers (boundary)
   EvalRecord* rec = reinterpret_cast<EvalRecord*>(dyn) + warp;
-  const int tf = MIXED ? s_tile[0] : 0;
-  float* abuf = P.anchor_buf + (size_t)slice * S.nrep * S.max_tiles_slice * kAnchorStride;
+  float* const arow = MIXED ? s_anc + (size_t)warp * S.max_tiles_slice * kAnchorStride : nullptr;
   const int G = S.flow_parts;
-  const int target = S.n_ctas;  // units per request: one per slice (G parts each)
+  const int target = S.n_ctas * G;  // units per request: G parts of every slice
 
   const bool timer = blockIdx.x == 0 && tid == 0;
   unsigned long long t0 = gtimer(), t1;
@@ -982,14 +1595,24 @@ __global__ void __launch_bounds__(kFlowThreads, 1)
     unsigned long long my_units = 0, my_unit_cyc = 0, my_idle_cyc = 0, my_ctrl_cyc = 0;
     long long tpoll = clock64();
     if (warp == 0) {
-      // ---- control of the chains homed on this CTA (their state stays in
-      // this SM's L1); a chain is ready when every CTA finished its request
+      // ---- control of the chains homed on this CTA.  Mixed precision: the
+      // chains' state and current-point records stay in this CTA's shared
+      // memory for the iteration (warp-parallel control); FP64: in global
+      // memory, one lane.  A chain is ready when every CTA finished its request
+      ChainState* hs = reinterpret_cast<ChainState*>(dyn + S.ctl_off);
+      EvalRecord* hr = reinterpret_cast<EvalRecord*>(hs + S.ctl_slots);
+      if (MIXED) {
+        for (int c = blockIdx.x, i = 0; c < S.nrep; c += S.n_ctas, ++i) {
+          warp_copy_cg(&hs[i], &P.chains[c], sizeof(ChainState), lane);
+          warp_copy_cg(&hr[i], &P.recx[c], sizeof(EvalRecord), lane);
+        }
+      }
       for (;;) {
         bool all_done = true, progressed = false;
-        for (int c = blockIdx.x; c < S.nrep; c += S.n_ctas) {
+        for (int c = blockIdx.x, i = 0; c < S.nrep; c += S.n_ctas, ++i) {
           int st = 0;  // 0 done, 1 waiting, 2 ready
           if (lane == 0) {
-            const ChainState* ch = &P.chains[c];
+            const ChainState* ch = MIXED ? &hs[i] : &P.chains[c];
             if (ch->done)
               st = 0;
             else if (ch->pending)
@@ -1003,7 +1626,10 @@ __global__ void __launch_bounds__(kFlowThreads, 1)
           if (st == 1) continue;
           progressed = true;
           const long long tc0 = clock64();
-          flow_control<NDET, MIXED>(L, S, B, P, c, lane);
+          if (MIXED)
+            flow_control_warp<NDET>(L, S, B, P, c, hs[i], hr[i], lane);
+          else
+            flow_control<NDET, MIXED>(L, S, B, P, c, lane);
           my_ctrl_cyc += clock64() - tc0;
         }
         if (all_done) break;
@@ -1018,32 +1644,48 @@ __global__ void __launch_bounds__(kFlowThreads, 1)
           __nanosleep(64);
         }
       }
+      if (MIXED)
+        for (int c = blockIdx.x, i = 0; c < S.nrep; c += S.n_ctas, ++i)
+          warp_copy(&P.chains[c], &hs[i], sizeof(ChainState), lane);
     } else {
-      // ---- sweep: claim (chain, request) pairs, lowest chain first, and
-      // evaluate this CTA's slice for them, one warp per pair
+      // ---- sweep: claim (chain, request, part) units, lowest chain first,
+      // and evaluate that part of this CTA's slice, one warp per unit (the G
+      // parts of a request may run on G warps at once)
       for (;;) {
         if (*(volatile int*)&g->chains_done >= S.nrep) break;
         if (*(volatile int*)&g->error) break;
-        // s_claim[c] = request number this CTA has taken for chain c
-        int cc = -1;
+        // s_claim[c] = units of chain c this CTA has taken: request r owns
+        // units (r - 1) G .. r G - 1, one per part
+        int cc = -1, part = 0;
+        int rq[4];  // request words of four groups of 32 chains, read together
         for (int base = 0; base < S.nrep && cc < 0; base += 32) {
           const int c = base + lane;
-          int r = 0;
-          bool cand = false;
-          if (c < S.nrep) {
-            r = (*(volatile int*)&P.req[c]) >> 3;
-            cand = r > *(volatile int*)&s_claim[c];
+          const int gq = (base >> 5) & 3;
+          if (gq == 0) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) rq[q] = base + 32 * q + lane < S.nrep ? *(volatile int*)&P.req[base + 32 * q + lane] : 0;
           }
+          int r = 0;
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+            if (q == gq) r = rq[q] >> 3;
+          bool cand = false;
+          if (c < S.nrep) cand = r * G > *(volatile int*)&s_claim[c];
           unsigned m = __ballot_sync(0xffffffffu, cand);
           while (m) {
             const int leader = __ffs(m) - 1;
-            int won = 0;
+            int won = 0, pt = 0;
             if (lane == leader) {
               const int old = *(volatile int*)&s_claim[c];
-              won = (old < r) && atomicCAS(&s_claim[c], old, r) == old;
+              if (old < r * G) {
+                const int nv = max(old, (r - 1) * G) + 1;
+                won = atomicCAS(&s_claim[c], old, nv) == old;
+                pt = nv - 1 - (r - 1) * G;
+              }
             }
             if (__shfl_sync(0xffffffffu, won, leader)) {
               cc = base + leader;
+              part = __shfl_sync(0xffffffffu, pt, leader);
               break;
             }
             m &= ~(1u << leader);
@@ -1061,22 +1703,20 @@ __global__ void __launch_bounds__(kFlowThreads, 1)
         const long long tu0 = clock64();
         my_idle_cyc += tu0 - tpoll;
         __threadfence();  // acquire: the request word was read relaxed
-        load_record_cg(&B.rec[cc], rec, lane);
-        for (int part = 0; part < G; ++part) {
+        load_record_cg<MIXED>(&B.rec[cc], rec, lane);
+        {
           const int lo = (int)(((long long)nb * part) / G), hi = (int)(((long long)nb * (part + 1)) / G);
           const size_t pidx = (((size_t)cc * L.n_slices + slice) * G + part) * kPartialStride;
           if (MIXED) {
-            float* row = abuf + (size_t)cc * S.max_tiles_slice * kAnchorStride;
+            float* row = arow;
             if (hi > lo) {
-              const int lo_prev = (int)(((long long)nb * (part - 1)) / G);
-              const bool cont = part > 0 && lo > lo_prev && s_tile[lo] == s_tile[lo - 1];
-              const int t_lo = s_tile[lo] - tf + (cont ? 1 : 0), t_hi = s_tile[hi - 1] - tf;
+              const int t_lo = s_tile[lo] - tf, t_hi = s_tile[hi - 1] - tf;
               for (int t = t_lo + lane; t <= t_hi; t += 32)
-                compute_anchor(NDET, B.tiles[tf + t], B.basis[tf + t], *rec, row + (size_t)t * kAnchorStride);
+                compute_anchor(NDET, s_ti[t], B.basis[tf + t], *rec, row + (size_t)t * kAnchorStride);
             }
             __syncwarp();
             float v[2 * NDET];
-            sweep_warp_mixed<NDET>(L, s_data, nb, s_tile, b0, lo, hi, B.tiles, row, tf, *rec, lane, v);
+            sweep_warp_mixed<NDET>(L, s_data, nb, s_tile, b0, lo, hi, s_ti, row, tf, *rec, lane, v);
 #pragma unroll
             for (int j = 0; j < 2 * NDET; ++j)
               if (lane == j) B.partials32[pidx + j] = v[j];
@@ -1089,10 +1729,7 @@ __global__ void __launch_bounds__(kFlowThreads, 1)
           }
         }
         __syncwarp();
-        if (lane == 0) {
-          __threadfence();
-          atomicAdd(&P.done_cnt[cc], 1);
-        }
+        if (lane == 0) red_release_add(&P.done_cnt[cc], 1);
         tpoll = clock64();
         my_units += 1;
         my_unit_cyc += tpoll - tu0;
@@ -1143,11 +1780,13 @@ struct EventDesc {
 
 template <int NDET>
 __global__ void __launch_bounds__(kFlowThreads, 1)
-    k_ns_multi(const EventDesc* __restrict__ ev, int n_ev, NSGlobal* gb, int n_ctrl, int dyn_off) {
+    k_ns_multi(const EventDesc* __restrict__ ev, int n_ev, NSGlobal* gb, int n_ctrl, int dyn_off, int ctl_off,
+               int ctl_slots) {
   extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ int s_claim[kMaxChains];  // [event][chain]: request number this CTA has taken
+  __shared__ int s_claim[kMaxChains];  // [event][chain]: units this CTA has taken (see k_ns_flow)
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int k = ev[0].S.nrep;
+  const int G = ev[0].S.flow_parts;
   const long long spin_limit = ev[0].S.spin_limit;
   for (int e = 0; e < n_ev; ++e) {
     const LikeConst& L = ev[e].L;
@@ -1175,19 +1814,28 @@ __global__ void __launch_bounds__(kFlowThreads, 1)
 
     long long idle = 0;
     if (warp < n_ctrl) {
-      // ---- control of the chains homed on (this CTA, this warp)
+      // ---- control of the chains homed on (this CTA, this warp): warp-
+      // parallel, with their state in this warp's shared-memory slots
+      ChainState* hs = reinterpret_cast<ChainState*>(smem + ctl_off) + (size_t)warp * ctl_slots;
+      EvalRecord* hr = reinterpret_cast<EvalRecord*>(reinterpret_cast<ChainState*>(smem + ctl_off) +
+                                                     (size_t)n_ctrl * ctl_slots) + (size_t)warp * ctl_slots;
+      for (int q = blockIdx.x + gridDim.x * warp, i = 0; q < n_ev * k; q += gridDim.x * n_ctrl, ++i) {
+        const EventDesc& E = ev[q / k];
+        warp_copy_cg(&hs[i], &E.P.chains[q % k], sizeof(ChainState), lane);
+        warp_copy_cg(&hr[i], &E.P.recx[q % k], sizeof(EvalRecord), lane);
+      }
       for (;;) {
         bool all_done = true, progressed = false;
-        for (int q = blockIdx.x + gridDim.x * warp; q < n_ev * k; q += gridDim.x * n_ctrl) {
+        for (int q = blockIdx.x + gridDim.x * warp, i = 0; q < n_ev * k; q += gridDim.x * n_ctrl, ++i) {
           const EventDesc& E = ev[q / k];
           const int c = q % k;
           int st = 0;  // 0 done, 1 waiting, 2 ready
           if (lane == 0) {
-            const ChainState* ch = &E.P.chains[c];
+            const ChainState* ch = &hs[i];
             if (ch->done)
               st = 0;
             else if (ch->pending)
-              st = ld_acquire(&E.P.done_cnt[c]) >= E.L.n_slices ? 2 : 1;
+              st = ld_acquire(&E.P.done_cnt[c]) >= E.L.n_slices * G ? 2 : 1;
             else
               st = 2;
           }
@@ -1196,7 +1844,7 @@ __global__ void __launch_bounds__(kFlowThreads, 1)
           all_done = false;
           if (st == 1) continue;
           progressed = true;
-          flow_control<NDET, true>(E.L, E.S, E.B, E.P, c, lane);
+          flow_control_warp<NDET>(E.L, E.S, E.B, E.P, c, hs[i], hr[i], lane);
         }
         if (all_done) break;
         if (*(volatile int*)&gb->error) break;
@@ -1210,32 +1858,40 @@ __global__ void __launch_bounds__(kFlowThreads, 1)
           __nanosleep(64);
         }
       }
+      for (int q = blockIdx.x + gridDim.x * warp, i = 0; q < n_ev * k; q += gridDim.x * n_ctrl, ++i)
+        warp_copy(&ev[q / k].P.chains[q % k], &hs[i], sizeof(ChainState), lane);
     } else {
-      // ---- sweep: claim (event, chain, request) and evaluate this CTA's slice
+      // ---- sweep: claim (event, chain, request, part) units and evaluate
+      // that part of this CTA's slice of the event
       for (;;) {
         bool over = true;
         for (int e = 0; e < n_ev; ++e) over = over && *(volatile int*)&ev[e].P.g->chains_done >= k;
         if (over) break;
         if (*(volatile int*)&gb->error) break;
-        int qq = -1;
+        int qq = -1, part = 0;
         for (int base = 0; base < n_ev * k && qq < 0; base += 32) {
           const int q = base + lane;
           int r = 0;
           bool cand = false;
           if (q < n_ev * k && (int)blockIdx.x < ev[q / k].L.n_slices) {
             r = (*(volatile int*)&ev[q / k].P.req[q % k]) >> 3;
-            cand = r > *(volatile int*)&s_claim[q];
+            cand = r * G > *(volatile int*)&s_claim[q];
           }
           unsigned msk = __ballot_sync(0xffffffffu, cand);
           while (msk) {
             const int leader = __ffs(msk) - 1;
-            int won = 0;
+            int won = 0, pt = 0;
             if (lane == leader) {
               const int old = *(volatile int*)&s_claim[q];
-              won = (old < r) && atomicCAS(&s_claim[q], old, r) == old;
+              if (old < r * G) {
+                const int nv = max(old, (r - 1) * G) + 1;
+                won = atomicCAS(&s_claim[q], old, nv) == old;
+                pt = nv - 1 - (r - 1) * G;
+              }
             }
             if (__shfl_sync(0xffffffffu, won, leader)) {
               qq = base + leader;
+              part = __shfl_sync(0xffffffffu, pt, leader);
               break;
             }
             msk &= ~(1u << leader);
@@ -1257,23 +1913,25 @@ __global__ void __launch_bounds__(kFlowThreads, 1)
         const float2* sd = reinterpret_cast<const float2*>(smem + E.smem_off);
         const int* stile = reinterpret_cast<const int*>(sd + (size_t)NDET * nb);
         const int tf = stile[0];
+        // the parts of a request may run on several warps: each fills the
+        // anchors of its own tiles (a tile shared by two parts gets the same
+        // values from both)
         float* row = E.P.anchor_buf + ((size_t)slice * k + cc) * E.S.max_tiles_slice * kAnchorStride;
+        const int lo = (int)(((long long)nb * part) / G), hi = (int)(((long long)nb * (part + 1)) / G);
         __threadfence();  // acquire: the request word was read relaxed
         load_record_cg(&E.B.rec[cc], rec, lane);
-        for (int t = lane; t <= stile[nb - 1] - tf; t += 32)
-          compute_anchor(NDET, E.B.tiles[tf + t], E.B.basis[tf + t], *rec, row + (size_t)t * kAnchorStride);
+        if (hi > lo)
+          for (int t = stile[lo] - tf + lane; t <= stile[hi - 1] - tf; t += 32)
+            compute_anchor(NDET, E.B.tiles[tf + t], E.B.basis[tf + t], *rec, row + (size_t)t * kAnchorStride);
         __syncwarp();
         float v[2 * NDET];
-        sweep_warp_mixed<NDET>(E.L, sd, nb, stile, b0, 0, nb, E.B.tiles, row, tf, *rec, lane, v);
-        const size_t pidx = ((size_t)cc * E.L.n_slices + slice) * kPartialStride;
+        sweep_warp_mixed<NDET>(E.L, sd, nb, stile, b0, lo, hi, E.B.tiles + tf, row, tf, *rec, lane, v);
+        const size_t pidx = (((size_t)cc * E.L.n_slices + slice) * G + part) * kPartialStride;
 #pragma unroll
         for (int j = 0; j < 2 * NDET; ++j)
           if (lane == j) E.B.partials32[pidx + j] = v[j];
         __syncwarp();
-        if (lane == 0) {
-          __threadfence();
-          atomicAdd(&E.P.done_cnt[cc], 1);
-        }
+        if (lane == 0) red_release_add(&E.P.done_cnt[cc], 1);
       }
     }
     __syncthreads();
@@ -1282,30 +1940,50 @@ __global__ void __launch_bounds__(kFlowThreads, 1)
 
 // Persistent sampler for the heterodyned likelihood (Sec. 3.4).  A
 // heterodyned evaluation is a few hundred to a few thousand bins, so one CTA
-// owns one chain at a time: thread 0 runs the chain's control, then every
-// warp contracts a share of the bins (31-bin chunks, strided by warp) and the
-// per-warp sums are added in warp order.  The chains of one NS iteration run
-// independently to completion; the grid meets only at the iteration
-// boundary.  Projection-only blocks (d_L, iota, psi, phi_c) reuse each
-// chain's per-detector cache of its last full evaluation, as on the full
-// grid; the set-up follows the mixed-precision sampler (FP64 waveform
-// coefficients and delays, FP32 prior transform, amplitude and projection).
-// With t_c marginalised the bin pass also stores the edge products y_e in
-// shared memory (the boundary's scratch, unused between boundaries) and the
-// warps then share the time grid's 32-node chunks (het.cuh tm_pass); there
-// are no projection-only blocks in that mode.
+// owns one chain at a time.  Warp 0 runs the chain's control with the same
+// warp-parallel code as the full-grid sampler (state in this CTA's shared
+// memory), sets up the proposal's record and forms the per-evaluation
+// constants of the contraction (coefficient and delay differences from the
+// fiducial, C_i / C0_i; one per lane) in shared memory; then every warp
+// contracts a share of the bins (31-bin chunks, strided by warp), the
+// per-warp sums are added in warp order (double-float), and warp 0 forms the
+// epilogue and the per-detector cache with one detector per lane.  The
+// chains of one NS iteration run independently to completion; the grid meets
+// only at the iteration boundary.  Projection-only blocks (d_L, iota, psi,
+// phi_c) reuse each chain's per-detector cache of its last full evaluation,
+// as on the full grid.  With t_c marginalised the bin pass also stores the
+// edge products y_e in shared memory (the boundary's scratch, unused between
+// boundaries) and the warps then share the time grid's 32-node chunks
+// (het.cuh tm_pass); there are no projection-only blocks in that mode.
+template <int NDET>
+__device__ __forceinline__ void het_prepare_warp(const HetTables& H, const EvalRecord& r, HetPrep<NDET>& p, int lane) {
+  const EvalRecord& f0 = *H.fid;
+  if (lane < NBASIS) p.dc[lane] = df_from_double(r.c[lane] - f0.c[lane]);
+  if (lane >= 16 && lane < 16 + NDET) {
+    const int i = lane - 16;
+    p.dtau[i] = df_from_double(r.tau[i] - f0.tau[i]);
+    const double den = f0.cre[i] * f0.cre[i] + f0.cim[i] * f0.cim[i];
+    p.rho_re[i] = (float)((r.cre[i] * f0.cre[i] + r.cim[i] * f0.cim[i]) / den);
+    p.rho_im[i] = (float)((r.cim[i] * f0.cre[i] - r.cre[i] * f0.cim[i]) / den);
+  }
+  __syncwarp();
+}
+
 template <int NDET>
 __global__ void __launch_bounds__(kHetThreads, 1)
     k_ns_het(LikeConst L, SamplerConst S, DeviceBuffers B, SamplerPtrs P) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ float s_sum[kHetThreads / 32][3 * NDET];
   __shared__ float s_tm[kHetThreads / 32][2];
-  __shared__ int s_done, s_fl;
+  __shared__ HetPrep<NDET> s_prep;
+  __shared__ int s_st;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int n_warps = blockDim.x >> 5;
   NSGlobal* g = P.g;
   const HetTables H = het_tables(B);
   const int nc = het_chunks(H.n_bins);
+  ChainState& ch = *reinterpret_cast<ChainState*>(smem + S.ctl_off);
+  EvalRecord& rx = *reinterpret_cast<EvalRecord*>(smem + S.ctl_off + sizeof(ChainState));
   const bool timer = blockIdx.x == 0 && threadIdx.x == 0;
   unsigned long long t0 = gtimer(), t1;
   for (;;) {
@@ -1325,34 +2003,29 @@ __global__ void __launch_bounds__(kHetThreads, 1)
     }
     if (*(volatile int*)&g->status != ST_RUNNING) return;
     for (int c = blockIdx.x; c < S.nrep; c += gridDim.x) {
-      double kap_y[2 * SWIG_MAX_DET], vv_y[SWIG_MAX_DET];  // thread 0's cache of the last evaluation
-#pragma unroll
-      for (int j = 0; j < 2 * SWIG_MAX_DET; ++j) kap_y[j] = 0.0;
-#pragma unroll
-      for (int i = 0; i < SWIG_MAX_DET; ++i) vv_y[i] = 0.0;
-      double ly = 0.0;
+      // warp 0's copy of the last evaluation's result (see control_step_warp)
+      double ly = 0.0, kapc = 0.0, vvc = 0.0;
+      if (warp == 0) {
+        warp_copy_cg(&ch, &P.chains[c], sizeof(ChainState), lane);
+        warp_copy_cg(&rx, &P.recx[c], sizeof(EvalRecord), lane);
+      }
       for (long long guard = 0; guard < (1ll << 24); ++guard) {
-        if (threadIdx.x == 0) {
-          s_fl = chain_advance<true>(L, S, P, c, kap_y, ly, &B.rec[c], vv_y);
-          s_done = P.chains[c].done;
-        }
-        __syncthreads();
-        if (s_done) break;
-        if (s_fl < 0) continue;  // nothing pending (cannot happen without projection-only blocks)
         if (warp == 0) {
-          const long long ts = clock64();
-          setup_record_warp(L, P.chains[c].th_y, s_fl, true, &B.rec[c], lane);
-          if (c == 0 && lane == 0) g->c_setup += clock64() - ts;
+          const int st = control_step_warp<NDET, true>(L, S, B, P, c, ch, rx, lane, ly, kapc, vvc);
+          if (st == CTL_EVAL) het_prepare_warp<NDET>(H, B.rec[c], s_prep, lane);
+          if (lane == 0) s_st = st;
         }
         __syncthreads();
+        const int st = s_st;
+        if (st == CTL_WAIT) break;    // the chain is done
+        if (st == CTL_AGAIN) continue;  // projection-only budget used up
         const EvalRecord& r = B.rec[c];
         const bool valid = r.valid != 0;
         float zr[NDET], zi[NDET], hh[NDET];
 #pragma unroll
         for (int i = 0; i < NDET; ++i) zr[i] = zi[i] = hh[i] = 0.0f;
         if (valid) {
-          HetPrep<NDET> p;
-          het_prepare<NDET>(H, r, p);
+          const HetPrep<NDET> p = s_prep;
           if (L.tm_n > 0) {
             float2* y = reinterpret_cast<float2*>(smem);
             for (int q = warp; q < nc; q += n_warps) het_chunk<NDET, true>(H, p, 31 * q, lane, zr, zi, hh, y);
@@ -1379,27 +2052,42 @@ __global__ void __launch_bounds__(kHetThreads, 1)
           }
           __syncthreads();
         }
-        if (threadIdx.x == 0) {
-          if (!valid) {
-            ly = -INFINITY;
-          } else {
-            double Z_re = 0.0, Z_im = 0.0, HH = 0.0;
-            for (int i = 0; i < NDET; ++i) {
-              double zr = 0.0, zi = 0.0, hh = 0.0;
-              for (int w = 0; w < n_warps; ++w) {
-                zr += (double)s_sum[w][3 * i];
-                zi += (double)s_sum[w][3 * i + 1];
-                hh += (double)s_sum[w][3 * i + 2];
-              }
-              het_cache(L, r, i, zr, zi, hh, kap_y + 2 * i, vv_y + i);
-              Z_re += zr;
-              Z_im += zi;
-              HH += hh;
+        if (warp == 0) {
+          // lane i < NDET: detector i's sums over the warps in warp order
+          // (double-float), its cache entries, then the network epilogue
+          double dz_r = 0.0, dz_i = 0.0, dhh = 0.0;
+          if (lane < NDET) {
+            dfl a = {0.0f, 0.0f}, b = {0.0f, 0.0f}, h = {0.0f, 0.0f};
+            for (int w = 0; w < n_warps; ++w) {
+              a = df_add(a, dfl{s_sum[w][3 * lane], 0.0f});
+              b = df_add(b, dfl{s_sum[w][3 * lane + 1], 0.0f});
+              h = df_add(h, dfl{s_sum[w][3 * lane + 2], 0.0f});
             }
-            ly = L.tm_n > 0 ? tm_finish(L, s_tm, n_warps, HH) : het_epilogue(L, Z_re, Z_im, HH);
+            dz_r = (double)a.hi + (double)a.lo;
+            dz_i = (double)b.hi + (double)b.lo;
+            dhh = (double)h.hi + (double)h.lo;
           }
+          double k2[2] = {0.0, 0.0}, vi = 0.0;
+          if (lane < NDET && valid) het_cache(L, r, lane, dz_r, dz_i, dhh, k2, &vi);
+          // component j of the cache on lane j, detector i's vv on lane i
+          const double k0 = __shfl_sync(kFull, k2[0], lane < 2 * NDET ? lane >> 1 : 0);
+          const double k1 = __shfl_sync(kFull, k2[1], lane < 2 * NDET ? lane >> 1 : 0);
+          kapc = lane < 2 * NDET ? ((lane & 1) ? k1 : k0) : 0.0;
+          vvc = lane < NDET ? vi : 0.0;
+          double Z_re = 0.0, Z_im = 0.0, HH = 0.0;
+#pragma unroll
+          for (int i = 0; i < NDET; ++i) {
+            Z_re += __shfl_sync(kFull, dz_r, i);
+            Z_im += __shfl_sync(kFull, dz_i, i);
+            HH += __shfl_sync(kFull, dhh, i);
+          }
+          double out = -INFINITY;
+          if (lane == 0 && valid) out = L.tm_n > 0 ? tm_finish(L, s_tm, n_warps, HH) : het_epilogue(L, Z_re, Z_im, HH);
+          ly = __shfl_sync(kFull, out, 0);
+          if (!valid) kapc = vvc = 0.0;
         }
       }
+      if (warp == 0) warp_copy(&P.chains[c], &ch, sizeof(ChainState), lane);
       __syncthreads();
     }
     if (timer) {
@@ -1558,7 +2246,7 @@ namespace {
 struct RunState {
   SamplerConst S;
   SamplerState* st = nullptr;
-  size_t smem = 0, fixed = 0;
+  size_t smem = 0, fixed = 0, tail = 0;  // tail: per-warp records / sort buffers (multi-event layout)
   void* kern = nullptr;
   int threads = 0;
   bool het = false, mixed = false, learned = false;
@@ -1649,17 +2337,29 @@ int run_setup(swig_ctx* c, RunState& R) {
         if (slot == 0 || slot == 6) flags |= BF_AMP;
         if (slot == 7 || slot == 8 || slot == 9 || slot == 10 || slot == 12) flags |= BF_PROJ;
         if (slot == 9 || slot == 10 || slot == 11) flags |= BF_TAU;
+        if (slot == 9 || slot == 10) flags |= BF_SKY;
       }
     // time marginalisation keeps no per-detector cache at every node, so
     // projection-only blocks take the full evaluation there (and everywhere
     // when the cache is switched off)
     S.block_free[b] = (free_block && L.tm_n == 0 && !c->cfg.cache_off) ? 1 : 0;
     S.block_flags[b] = flags;
+    S.block_mask[b] = 0u;
+    for (int r = 0; r < S.block_size[b]; ++r) {
+      S.block_mask[b] |= 1u << S.block_dims[b][r];
+      S.block_rank[S.block_dims[b][r]] = r;
+    }
   }
+  for (int i = 0; i < SWIG_N_PARAMS; ++i) S.dim_of_slot[i] = -1;
+  for (int j = 0; j < nd; ++j) S.dim_of_slot[S.slot_of_dim[j]] = j;
   S.m_pow2 = 1;
   while (S.m_pow2 < m) S.m_pow2 *= 2;
   S.max_iters = (int)std::max(1, std::min(64, c->cfg.max_iter));
-  S.flow_parts = 1;  // summation parts per slice, at most 4 (the partial buffers hold 4 per slice and theta)
+  // parts per slice and request: the G parts of a request's slice are claimed
+  // by up to G sweep warps of the CTA at once; each part has its own partial
+  // (fixed places, fixed summation order), at most 4 (the partial buffers
+  // hold 4 per slice and theta)
+  S.flow_parts = SWIG_FLOW_PARTS;
   // learned proposal: retrain every learn_interval iterations (one launch each)
   R.learned = c->cfg.proposal == SWIG_PROPOSAL_LEARNED;
   const double learn_mix = c->cfg.learn_mix > 0.0 ? std::min(1.0, c->cfg.learn_mix) : 0.5;
@@ -1686,11 +2386,22 @@ int run_setup(swig_ctx* c, RunState& R) {
     for (int s = 0; s < L.n_slices; ++s) max_tiles = std::max(max_tiles, bt[sb[s + 1] - 1] - bt[sb[s]] + 1);
   }
   S.max_tiles_slice = max_tiles;
+  // the single-event kernel also keeps the slice's tile table and anchor rows
+  // in shared memory (R.fixed stays the slice data alone: the multi-event
+  // kernel's layout)
+  const size_t flow_tiles = mixed ? flow_tile_bytes(max_tiles, kFlowThreads / 32) : 0;
   const size_t sort_bytes = (size_t)S.m_pow2 * (sizeof(double) + sizeof(int)) + kSweepThreads * sizeof(double) +
                             (size_t)k * sizeof(double) + (kMaxDim + kMaxDim * kMaxDim) * sizeof(float) + 64;
   const size_t rec_bytes = (size_t)(kFlowThreads / 32) * sizeof(EvalRecord);
-  R.smem = het ? std::max(sort_bytes, L.tm_n > 0 ? het_tm_smem_bytes(c->B.het_nb) : (size_t)0)
-              : fixed + std::max(rec_bytes, sort_bytes);
+  // the homed chains' state and records of the warp-parallel control follow
+  // the per-warp records / sort buffers
+  // (heterodyned: one slot, after the sort buffers / time-pass edge products)
+  const size_t het_scratch = std::max(sort_bytes, L.tm_n > 0 ? het_tm_smem_bytes(c->B.het_nb) : (size_t)0);
+  S.ctl_slots = mixed ? (k + L.n_slices - 1) / L.n_slices : (het ? 1 : 0);
+  S.ctl_off = (int)(((het ? het_scratch : std::max(rec_bytes, sort_bytes)) + 15) & ~(size_t)15);
+  R.tail = std::max(rec_bytes, sort_bytes);
+  const size_t ctl_bytes = (size_t)S.ctl_slots * (sizeof(ChainState) + sizeof(EvalRecord));
+  R.smem = het ? S.ctl_off + ctl_bytes : fixed + flow_tiles + S.ctl_off + ctl_bytes;
   if (R.smem > 220 * 1024) return fail(c, SWIG_E_ARG, "problem too large for the persistent kernel's shared memory");
 
   // buffers
@@ -2071,10 +2782,15 @@ int run_loop_multi(swig_ctx* const* ctxs, std::vector<RunState>& R, int i0, int 
   for (int i = i0; i < i1; ++i) {
     off[i - i0] = (int)fixed;
     fixed += R[i].fixed;
-    tail = std::max(tail, R[i].smem - R[i].fixed);
+    tail = std::max(tail, R[i].tail);
     grid = std::max(grid, ctxs[i]->L.n_slices);
   }
-  const size_t smem = fixed + tail;
+  // after the data and the records / sort buffers: each control warp's slots
+  // for the chains it serves (warp-parallel control)
+  const int n_ctrl = std::max(1, std::min(4, ((i1 - i0) * k + grid - 1) / grid));
+  const int ctl_slots = ((i1 - i0) * k + grid * n_ctrl - 1) / (grid * n_ctrl);
+  const size_t ctl_off = (fixed + tail + 15) & ~(size_t)15;
+  const size_t smem = ctl_off + (size_t)n_ctrl * ctl_slots * (sizeof(ChainState) + sizeof(EvalRecord));
   void* kern = pick_multi_kernel(n_det);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int per_sm = 0;
@@ -2082,7 +2798,6 @@ int run_loop_multi(swig_ctx* const* ctxs, std::vector<RunState>& R, int i0, int 
   if (e != cudaSuccess) return fail(c0, SWIG_E_CUDA, std::string("multi-event kernel set-up: ") + cudaGetErrorString(e));
   if (per_sm < 1 || grid > per_sm * c0->sm_count)
     return fail(c0, SWIG_E_CUDA, "multi-event persistent kernel cannot be co-resident on this device");
-  const int n_ctrl = std::max(1, std::min(4, ((i1 - i0) * k + grid - 1) / grid));
   NSGlobal* gb = nullptr;
   EventDesc* evd = nullptr;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -2119,8 +2834,9 @@ int run_loop_multi(swig_ctx* const* ctxs, std::vector<RunState>& R, int i0, int 
     if (e == cudaSuccess) e = cudaMemcpy(evd, hd.data(), sizeof(EventDesc) * hd.size(), cudaMemcpyHostToDevice);
     int n_ev = (int)hd.size();
     int n_ctrl_arg = n_ctrl;
-    int dyn_off = (int)fixed;
-    void* args[] = {(void*)&evd, (void*)&n_ev, (void*)&gb, (void*)&n_ctrl_arg, (void*)&dyn_off};
+    int dyn_off = (int)fixed, ctl_off_arg = (int)ctl_off, ctl_slots_arg = ctl_slots;
+    void* args[] = {(void*)&evd,    (void*)&n_ev,        (void*)&gb,           (void*)&n_ctrl_arg,
+                    (void*)&dyn_off, (void*)&ctl_off_arg, (void*)&ctl_slots_arg};
     if (e == cudaSuccess) e = cudaEventRecord(ev0, c0->stream);
     if (e == cudaSuccess) e = cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(kFlowThreads), args, smem, c0->stream);
     if (e == cudaSuccess) e = cudaEventRecord(ev1, c0->stream);
@@ -2197,12 +2913,12 @@ int swig_run_batch(swig_ctx** ctxs, int n_ctx, swig_result* outs) {
   while (i0 < n_ctx) {
     int i1 = i0 + 1;
     if (batchable(oc.data(), orr, i0, i0 + 1)) {
-      size_t fixed = orr[i0].fixed, tail = orr[i0].smem - orr[i0].fixed;
+      size_t fixed = orr[i0].fixed, tail = orr[i0].tail;
       while (i1 < n_ctx && i1 - i0 < kMaxEvents && batchable(oc.data(), orr, i0, i1 + 1) &&
              (i1 + 1 - i0) * orr[i0].k <= kMaxChains && oc[i1]->L.n_bins <= 1.5 * oc[i0]->L.n_bins &&
-             fixed + orr[i1].fixed + std::max(tail, orr[i1].smem - orr[i1].fixed) <= 220 * 1024) {
+             fixed + orr[i1].fixed + std::max(tail, orr[i1].tail) <= 212 * 1024) {
         fixed += orr[i1].fixed;
-        tail = std::max(tail, orr[i1].smem - orr[i1].fixed);
+        tail = std::max(tail, orr[i1].tail);
         ++i1;
       }
     }

@@ -63,9 +63,10 @@ struct LaneAnchor {
   float inv_T, A0, s_hi, s_lo;
   float a[kNumPoly];
   float Ad[NDET];
-  __device__ __forceinline__ void load(const TileInfo* tiles, const float* row, int t, int row_t, int b0,
-                                       int local) {
-    const TileInfo ti = tiles[t];
+  // tiles and row are both indexed by row_t = t - tile_base (the tile table
+  // may be a slice's copy in shared memory).
+  __device__ __forceinline__ void load(const TileInfo* tiles, const float* row, int row_t, int b0, int local) {
+    const TileInfo ti = tiles[row_t];
     end = ti.k0 + ti.nbins - b0;
     x = (float)(b0 + local - ti.k0);
     inv_T = ti.inv_T;
@@ -111,9 +112,9 @@ __device__ __forceinline__ void accumulate_bin(const LaneAnchor<NDET>& la, float
 // One warp evaluates the bins [b0 + lo, b0 + hi) of a slice that starts at
 // bin b0, for one theta; lanes take bins lo + lane + 32 j.  s_data:
 // [NDET][stride] float2 scaled D_i of the slice; s_tile: tile index of each
-// slice bin; anchors `row`: kAnchorStride floats per tile, indexed by (tile -
-// tile_base).  Every lane returns the warp totals (re, im per detector) in
-// out[0 .. 2 NDET).
+// slice bin; `tiles` and the anchors `row` (kAnchorStride floats per tile) are
+// both indexed by (tile - tile_base).  Every lane returns the warp totals (re,
+// im per detector) in out[0 .. 2 NDET).
 template <int NDET>
 __device__ __forceinline__ void sweep_warp_mixed(const LikeConst& L, const float2* s_data, int stride,
                                                  const int* s_tile, int b0, int lo, int hi, const TileInfo* tiles,
@@ -127,14 +128,39 @@ __device__ __forceinline__ void sweep_warp_mixed(const LikeConst& L, const float
   for (int i = 0; i < NDET; ++i) acc_re[i] = acc_im[i] = 0.0f;
   LaneAnchor<NDET> la;
   la.end = -1;
-  for (int local = lo + lane; local < hi; local += kChunk) {
+  // two bins of a tile per step (bins local and local + 32), each into its own
+  // accumulators, so that a lane has two independent phase / sine / multiply-
+  // add chains in flight; the two sets are added at the end
+  float acc2_re[NDET], acc2_im[NDET];
+#pragma unroll
+  for (int i = 0; i < NDET; ++i) acc2_re[i] = acc2_im[i] = 0.0f;
+  int local = lo + lane;
+  while (local < hi) {
     if (local >= la.end) {
       const int t = s_tile[local];
-      la.load(tiles, row, t, t - tile_base, b0, local);
+      la.load(tiles, row, t - tile_base, b0, local);
     }
-    const float p = la.phase();
-    accumulate_bin<NDET>(la, p, bsh, s_data, stride, local, acc_re, acc_im);
-    la.x += (float)kChunk;
+    if (local + kChunk < hi && local + kChunk < la.end) {
+      const float p0 = la.phase();
+      la.x += (float)kChunk;
+      const float p1 = la.phase();
+      la.x -= (float)kChunk;
+      accumulate_bin<NDET>(la, p0, bsh, s_data, stride, local, acc_re, acc_im);
+      la.x += (float)kChunk;
+      accumulate_bin<NDET>(la, p1, bsh, s_data, stride, local + kChunk, acc2_re, acc2_im);
+      la.x += (float)kChunk;
+      local += 2 * kChunk;
+    } else {
+      const float p = la.phase();
+      accumulate_bin<NDET>(la, p, bsh, s_data, stride, local, acc_re, acc_im);
+      la.x += (float)kChunk;
+      local += kChunk;
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < NDET; ++i) {
+    acc_re[i] += acc2_re[i];
+    acc_im[i] += acc2_im[i];
   }
 #pragma unroll
   for (int i = 0; i < NDET; ++i) {

@@ -65,6 +65,7 @@ struct EvalRecord {
   double amp;                    // A(Mc) / d_L
   double mterm[8];               // cached mass factors (eta, dm, m1, m2, A, r, ir, ln pi M)
   double hh;                     // sum_i |C_i|^2 K_i
+  double gdel[SWIG_MAX_DET];     // geocentric delay of each detector [s] (tau_i - t_c)
   int valid;
   int pad;
 };

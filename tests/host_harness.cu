@@ -7,6 +7,8 @@
 //   host_harness gl N                                  Gauss-Legendre nodes, weights
 //   host_harness frame AX AY AZ BX BY BZ GMST          detector sky frame (b -> a)
 //   host_harness tiles F_MIN F_MAX DF                  phase tiles of the mixed path
+//   host_harness slices F_MIN F_MAX DF NDET SMS (LO HI)x6   slices of the persistent kernel over the
+//                                                      tiles of a prior box (Mc q chi1 chi2 L1 L2)
 //   host_harness coeffs MC Q CHI1 CHI2 LAM1 LAM2       TaylorF2 phase-basis coefficients
 //                                                      (the host/device set-up code)
 //   host_harness amp MC                                SPA amplitude at 1 Mpc
@@ -278,6 +280,28 @@ int main(int argc, char** argv) {
     SWIG_FIELD(swig_result, n_iter); SWIG_FIELD(swig_result, n_evals); SWIG_FIELD(swig_result, n_sweep_evals);
     SWIG_FIELD(swig_result, status);
     std::printf("]}}\n");
+    return 0;
+  }
+  if (what == "slices" && argc == 19) {
+    swig_ctx c;
+    if (swig_set_grid(&c, std::atof(argv[2]), std::atof(argv[3]), std::atof(argv[4])) != SWIG_OK) return 3;
+    for (int i = 0; i < 6; ++i) {
+      c.params[i].mode = SWIG_MODE_SAMPLE;
+      c.params[i].lo = std::atof(argv[7 + 2 * i]);
+      c.params[i].hi = std::atof(argv[8 + 2 * i]);
+    }
+    c.prior_set = true;
+    std::vector<TileInfo> tiles;
+    std::vector<TileBasis> basis;
+    plan_tiles(&c, tiles, basis);
+    std::vector<int> sb;
+    int max_bins = 0;
+    plan_slices(c.n_bins, std::atoi(argv[5]), std::atoi(argv[6]), tiles, sb, &max_bins);
+    std::printf("{\"max_bins\": %d, \"slice_begin\": [", max_bins);
+    for (size_t q = 0; q < sb.size(); ++q) std::printf("%s%d", q ? ", " : "", sb[q]);
+    std::printf("], \"tiles\": [");
+    for (size_t t = 0; t < tiles.size(); ++t) std::printf("%s[%d, %d]", t ? ", " : "", tiles[t].k0, tiles[t].nbins);
+    std::printf("]}\n");
     return 0;
   }
   if (what == "tiles" && argc == 5) {
