@@ -58,8 +58,10 @@ METRIC = "logL evals/s (128 s 3-det BNS) and wall-s/posterior, plain vs learned+
 WORKLOADS = {
     "cfg2": dict(event="cfg2", precision="mixed", likelihood="full", proposal="cov",
                  text="plain SwiG (covariance directions), full grid, mixed precision"),
-    "cfg5": dict(event="cfg2", precision="mixed", likelihood="full", proposal="learned",
-                 text="learned slice proposal (MLP 13-256-256-26, BF16/FP32) + covariance, full grid, mixed"),
+    "cfg5": dict(event="cfg2", precision="mixed", likelihood="full", proposal="learned", learn_mix=1.0,
+                 learn_interval=32, learn_steps=30,
+                 text="learned slice proposal (MLP 13-256-256-26, BF16/FP32, every slice direction, retrained every "
+                      "32 iterations with 30 Adam steps), full grid, mixed"),
     "cfg2-het": dict(event="cfg2", precision="mixed", likelihood="het", proposal="cov", het_bins=5000,
                      het_spacing=0, text="plain SwiG, heterodyned likelihood, 5000 bins of equal phase change"),
     "cfg2-het-tm": dict(event="cfg2", precision="mixed", likelihood="het", proposal="cov", het_bins=5000,
@@ -330,7 +332,8 @@ def run_gpu(args, rank, world):
                     likelihood=swig.LIKE_HET if het else swig.LIKE_FULL,
                     proposal=swig.PROPOSAL_LEARNED if spec["proposal"] == "learned" else swig.PROPOSAL_COV,
                     het_bins=spec.get("het_bins", 0), het_spacing=spec.get("het_spacing", 0),
-                    het_fiducial=th_inj if het else None, tmarg_nodes=n_tm)
+                    het_fiducial=th_inj if het else None, tmarg_nodes=n_tm, learn_mix=spec.get("learn_mix", 0.0),
+                    learn_interval=spec.get("learn_interval", 0), learn_steps=spec.get("learn_steps", 0))
     stream = torch.cuda.current_stream()
     ctx.set_stream(stream.cuda_stream)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # > L2 (129 MB)
@@ -404,10 +407,19 @@ def run_gpu(args, rank, world):
             step_device()
         learned = [step_device() for _ in range(args.steps)]
         th_l, ll_l, lw_l = ctx.get_samples()
+        # the run-to-run variation of plain SwiG itself (another seed), the
+        # scale against which the arms' difference is read
+        ctx.set_sampler(nlive=wl.nlive, nrep=wl.nrep, sweeps=wl.sweeps, steps_per_dim=wl.steps_per_dim,
+                        seed=wl.sampler_seed + 1000 * rank + 1, precision=prec)
+        r_b, _, _ = step_device()
+        th_b, ll_b, lw_b = ctx.get_samples()
         arms = {"plain": _arm_summary(results, "plain SwiG: covariance directions, mixed precision"),
                 "learned": _arm_summary(learned, "learned + mixed: " + ls["text"]),
-                "posterior_comparison": _compare_posteriors(wl, (th_p, lw_p), (th_l, lw_l),
-                                                            results[-1][0], learned[-1][0])}
+                "posterior_comparison": {
+                    "plain_vs_learned": _compare_posteriors(wl, (th_p, lw_p), (th_l, lw_l), results[-1][0],
+                                                            learned[-1][0]),
+                    "plain_vs_plain_other_seed": _compare_posteriors(wl, (th_p, lw_p), (th_b, lw_b), results[-1][0],
+                                                                     r_b)}}
 
     # max of the times and sum of the counts over ranks
     tmax, tsum = reduce_over_ranks([total_ms, total_evals, sum(e2e_ms), e2e_evals, full_evals, e2e_full], world)
@@ -470,18 +482,8 @@ def run_gpu(args, rank, world):
         "clocks": clk,
     }
     if n_tm:
-        # the time pass dominates: per full evaluation and (edge, node) pair one
-        # complex add and one complex rotation, 6 FP32-pipe instructions
-        ops = 6.0 * (spec["het_bins"] + 1) * n_tm * full_evals
-        peak32 = 128 * 152 * sm_mhz_max * 1e6 / 1e12
-        line["roofline"].update({
-            "kernel": "k_ns_het (persistent SwiG kernel, heterodyned, time-marginalised)",
-            "bound": "alu", "achieved": ops / (pers_ms * 1e-3) / 1e12 if pers_ms > 0 else 0.0, "peak": peak32,
-            "unit": "FP32-pipe Top/s", "traffic": None,
-            "work_per_launch": (f"6 FP32 ops x (edge, node) pairs x full evaluations ({spec['het_bins'] + 1} edges x "
-                                f"{n_tm} nodes)"),
-            "peak_source": "128 FP32 lanes per clk per SM x 152 SMs x 2070 MHz (derived, not measured)"})
-        line["roofline"]["frac"] = line["roofline"]["achieved"] / peak32
+        line["roofline"]["kernel"] = ("k_ns_het (persistent SwiG kernel, heterodyned, t_c marginalised: bin pass "
+                                      "plus the non-uniform FFT time pass)")
     if args.cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(args.workload, seconds=args.cpu_seconds,
                                             evals_per_posterior=total_evals / max(1, args.steps))

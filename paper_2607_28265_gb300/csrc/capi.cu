@@ -225,6 +225,11 @@ void free_problem(DeviceBuffers& B) {
   dfree(B.het_fid);
   dfree(B.het_tm_g);
   dfree(B.het_tm_w);
+  dfree(B.het_nu_ptr);
+  dfree(B.het_nu_edge);
+  dfree(B.het_nu_wt);
+  dfree(B.het_nu_corr);
+  dfree(B.het_nu_tw);
   B.het_nb = 0;
 }
 
@@ -400,6 +405,91 @@ void het_tm_tables(const std::vector<double>& a01, const std::vector<double>& f,
   }
 }
 
+// Tables of the time pass by non-uniform FFT (type 1; Dutt & Rokhlin 1993,
+// Greengard & Lee 2004) with the "exponential of semicircle" kernel of
+// Barnett, Magland & af Klinteberg (2019): with u_e = f_e dt (cycles per
+// node) and the reference shift dt_ref = t_0 + j0 dt of node j0,
+//   Z(dt_ref + m dt) = sum_e c_e exp(2 pi i xi_e m),  xi_e = frac(-u_e),
+//   c_e = y_e exp(-2 pi i f_e dt_ref),
+// for m = j - j0.  The c_e are spread onto M >= 2 N_t grid points with
+// phi(z) = exp(beta (sqrt(1 - (2 z / W)^2) - 1)), |z| <= W / 2 (z in grid
+// units, W points, beta = 2.3 W), b_l = sum_e c_e phi(l - M xi_e) (periodic);
+// then Z_m = [sum_l b_l exp(2 pi i m l / M)] / Phi(m), Phi(m) the kernel's
+// Fourier integral.  The spreading is stored as a gather list per grid point
+// (edges in increasing order) so that every sum has a fixed order.
+// Outputs: M, j0, ptr [M + 1] (entries of each grid point), edge [M] (its
+// first edge; its edges are consecutive), weight per entry, corr [N_t] = 1 /
+// Phi(j - j0), twiddles [M / 2] = exp(2 pi i k / M); ptr comes back empty
+// (and the direct sum is used) if some grid point's edges are not consecutive.
+void het_nufft_tables(const std::vector<double>& fe, int n_t, double dt, int width, int* M_out, int* j0_out,
+                      std::vector<int>& ptr, std::vector<int>& edge, std::vector<float>& wt,
+                      std::vector<float>& corr, std::vector<float2>& tw) {
+  int M = 1;
+  while (M < 2 * n_t) M <<= 1;
+  const int j0 = n_t / 2;
+  const double W = (double)width, beta = 2.3 * W;
+  auto phi = [&](double z) {
+    const double t = 2.0 * z / W;
+    return std::fabs(t) > 1.0 ? 0.0 : std::exp(beta * (std::sqrt(1.0 - t * t) - 1.0));
+  };
+  const int ne = (int)fe.size();
+  std::vector<std::vector<std::pair<int, float>>> lists(M);
+  for (int e = 0; e < ne; ++e) {
+    double u = fe[e] * dt;
+    double xi = -u - std::floor(-u);  // frac(-u) in [0, 1)
+    const double cpos = xi * M;
+    const int l_lo = (int)std::ceil(cpos - 0.5 * W), l_hi = (int)std::floor(cpos + 0.5 * W);
+    for (int l = l_lo; l <= l_hi; ++l) {
+      const double v = phi((double)l - cpos);
+      if (v == 0.0) continue;
+      const int lw = ((l % M) + M) % M;
+      lists[lw].push_back({e, (float)v});
+    }
+  }
+  // edge[l] = the first edge of grid point l: its edges are consecutive (xi_e
+  // is monotone in e), so the weights alone are stored per entry
+  ptr.assign(M + 1, 0);
+  edge.assign(M, 0);
+  wt.clear();
+  for (int l = 0; l < M; ++l) {
+    const auto& li = lists[l];
+    if (!li.empty()) {
+      edge[l] = li.front().first;
+      for (size_t q = 0; q < li.size(); ++q) {
+        if (li[q].first != li.front().first + (int)q) {  // not consecutive: fall back to no NUFFT tables
+          ptr.clear();
+          return;
+        }
+        wt.push_back(li[q].second);
+      }
+    }
+    ptr[l + 1] = (int)wt.size();
+  }
+  // Phi(m) = int phi(z) cos(2 pi m z / M) dz: twice the integral over the
+  // half-support (the integrand is even), 8 panels of Gauss-Legendre
+  double gx[kGaussLegendre], gw[kGaussLegendre];
+  gauss_legendre(kGaussLegendre, gx, gw);
+  corr.assign(n_t, 0.0f);
+  for (int j = 0; j < n_t; ++j) {
+    const int m = j - j0;
+    double acc = 0.0;
+    const int pieces = 8;  // the half-support [0, W/2] in 8 panels
+    for (int pc = 0; pc < pieces; ++pc) {
+      const double a = 0.5 * W * pc / pieces, b = 0.5 * W * (pc + 1) / pieces;
+      for (int k = 0; k < kGaussLegendre; ++k) {
+        const double z = 0.5 * (a + b) + 0.5 * (b - a) * gx[k];
+        acc += 0.5 * (b - a) * gw[k] * phi(z) * std::cos(2.0 * kPi * m * z / M);
+      }
+    }
+    corr[j] = (float)(1.0 / (2.0 * acc));
+  }
+  tw.resize(M / 2);
+  for (int k = 0; k < M / 2; ++k)
+    tw[k] = make_float2((float)std::cos(2.0 * kPi * k / M), (float)std::sin(2.0 * kPi * k / M));
+  *M_out = M;
+  *j0_out = j0;
+}
+
 }  // namespace
 
 namespace swig {
@@ -474,6 +564,31 @@ int prepare_het(swig_ctx* c) {
   if (L.tm_n > 0) {
     std::vector<float2> g, w;
     het_tm_tables(a01, f, idx, nb, n_det, L.tm_dt, g, w);
+    L.tm_M = 0;
+    std::vector<int> ptr, edge;
+    std::vector<float> wt, corr;
+    std::vector<float2> tw;
+    if (L.tm_n >= kNufftMinNodes && L.tm_n <= kNufftMaxNodes) {
+      std::vector<double> fe(nb + 1);
+      for (int q = 0; q <= nb; ++q) fe[q] = f[idx[q]];
+      het_nufft_tables(fe, L.tm_n, L.tm_dt, kNufftWidth, &L.tm_M, &L.tm_j0, ptr, edge, wt, corr, tw);
+      L.tm_dref = L.tm_t0 + (double)L.tm_j0 * L.tm_dt;
+      if (ptr.empty()) L.tm_M = 0;
+    }
+    if (L.tm_M > 0) {
+      CUDA_TRY(c, cudaMalloc(&B.het_nu_ptr, sizeof(int) * ptr.size()));
+      CUDA_TRY(c, cudaMalloc(&B.het_nu_edge, sizeof(int) * std::max<size_t>(1, edge.size())));
+      CUDA_TRY(c, cudaMalloc(&B.het_nu_wt, sizeof(float) * std::max<size_t>(1, wt.size())));
+      CUDA_TRY(c, cudaMalloc(&B.het_nu_corr, sizeof(float) * corr.size()));
+      CUDA_TRY(c, cudaMalloc(&B.het_nu_tw, sizeof(float2) * tw.size()));
+      CUDA_TRY(c, cudaMemcpy(B.het_nu_ptr, ptr.data(), sizeof(int) * ptr.size(), cudaMemcpyHostToDevice));
+      CUDA_TRY(c, cudaMemcpy(B.het_nu_edge, edge.data(), sizeof(int) * edge.size(), cudaMemcpyHostToDevice));
+      CUDA_TRY(c, cudaMemcpy(B.het_nu_wt, wt.data(), sizeof(float) * wt.size(), cudaMemcpyHostToDevice));
+      CUDA_TRY(c, cudaMemcpy(B.het_nu_corr, corr.data(), sizeof(float) * corr.size(), cudaMemcpyHostToDevice));
+      CUDA_TRY(c, cudaMemcpy(B.het_nu_tw, tw.data(), sizeof(float2) * tw.size(), cudaMemcpyHostToDevice));
+      c->h2d_bytes += sizeof(int) * (ptr.size() + edge.size()) + sizeof(float) * (wt.size() + corr.size()) +
+                      sizeof(float2) * tw.size();
+    }
     CUDA_TRY(c, cudaMalloc(&B.het_tm_g, sizeof(float2) * g.size()));
     CUDA_TRY(c, cudaMalloc(&B.het_tm_w, sizeof(float2) * w.size()));
     CUDA_TRY(c, cudaMemcpy(B.het_tm_g, g.data(), sizeof(float2) * g.size(), cudaMemcpyHostToDevice));

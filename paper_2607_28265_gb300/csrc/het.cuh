@@ -37,6 +37,12 @@ struct HetTables {
   const EvalRecord* fid;      // fiducial record
   const float2* tm_g;         // [n_det][N_b + 1] time marginalisation: edge weights g_ie
   const float2* tm_w;         // [N_b + 1] exp(-2 pi i f_e dt), one grid step
+  // non-uniform FFT form of the time pass (see het_nufft_tables)
+  const int* nu_ptr;
+  const int* nu_edge;
+  const float* nu_wt;
+  const float* nu_corr;
+  const float2* nu_tw;
 };
 
 __host__ __device__ inline HetTables het_tables(const DeviceBuffers& B) {
@@ -50,6 +56,11 @@ __host__ __device__ inline HetTables het_tables(const DeviceBuffers& B) {
   H.fid = B.het_fid;
   H.tm_g = B.het_tm_g;
   H.tm_w = B.het_tm_w;
+  H.nu_ptr = B.het_nu_ptr;
+  H.nu_edge = B.het_nu_edge;
+  H.nu_wt = B.het_nu_wt;
+  H.nu_corr = B.het_nu_corr;
+  H.nu_tw = B.het_nu_tw;
   return H;
 }
 
@@ -290,6 +301,94 @@ __device__ inline void tm_pass(const LikeConst& L, const HetTables& H, const flo
   for (int o = 16; o > 0; o >>= 1) S += __shfl_xor_sync(0xffffffffu, S, o);
   wm = M;
   ws = S;
+}
+
+// The same time pass by non-uniform FFT (tables of het_nufft_tables): the
+// edge products become c_e = y_e exp(-2 pi i f_e dt_ref) (double-float phase;
+// y is overwritten), every grid point gathers its kernel-weighted c_e in a
+// fixed order into bit-reversed position, a radix-2 FFT with exponent
+// +2 pi i runs in shared memory, and node j takes Z_j = X[(j - j0) mod M] /
+// Phi(j - j0).  Nodes are assigned to warps and lanes as in tm_pass, so the
+// (max, sum) pairs and ell have the same layout.  Every thread of the CTA
+// calls it (it synchronises the CTA).  Cost per evaluation ~W (N_b + 1)
+// multiply-adds for the gather and (M/2) log2 M butterflies, against
+// (N_b + 1) N_t terms for the direct sum.
+__device__ inline void tm_pass_nufft(const LikeConst& L, const HetTables& H, float2* y, float2* g, int warp,
+                                     int n_warps, int lane, float* ell, float& wm, float& ws) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int ne = H.n_bins + 1, M = L.tm_M;
+  const dfl dref = df_from_double(L.tm_dref);
+  for (int e = tid; e < ne; e += nt) {
+    TmEdge d;
+    d.y = y[e];
+    d.f = {H.edge_f[e], H.edge_f[ne + e]};
+    y[e] = tm_start(d, dref);
+  }
+  __syncthreads();
+  const int lg = __ffs(M) - 1;
+  for (int l = tid; l < M; l += nt) {
+    // grid point l gathers the consecutive edges e0, e0 + 1, ... in order;
+    // eight weights' loads are issued together
+    float br = 0.0f, bi = 0.0f;
+    const int k0 = H.nu_ptr[l], n = H.nu_ptr[l + 1] - k0, e0 = H.nu_edge[l];
+    for (int q0 = 0; q0 < n; q0 += 8) {
+      float w[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) w[q] = q0 + q < n ? __ldg(&H.nu_wt[k0 + q0 + q]) : 0.0f;
+#pragma unroll
+      for (int q = 0; q < 8; ++q)
+        if (q0 + q < n) {
+          const float2 c = y[e0 + q0 + q];
+          br = fmaf(w[q], c.x, br);
+          bi = fmaf(w[q], c.y, bi);
+        }
+    }
+    g[__brev((unsigned)l) >> (32 - lg)] = make_float2(br, bi);
+  }
+  __syncthreads();
+  for (int half = 1; half < M; half <<= 1) {
+    const int tstep = M / (2 * half);
+    for (int b = tid; b < M / 2; b += nt) {
+      const int pos = b & (half - 1), i = ((b - pos) << 1) + pos, j = i + half;
+      const float2 w = H.nu_tw[pos * tstep];
+      const float2 xj = g[j], xi = g[i];
+      const float tr = w.x * xj.x - w.y * xj.y, ti = w.x * xj.y + w.y * xj.x;
+      g[j] = make_float2(xi.x - tr, xi.y - ti);
+      g[i] = make_float2(xi.x + tr, xi.y + ti);
+    }
+    __syncthreads();
+  }
+  float m = -INFINITY, s = 0.0f;
+  const int nq = (L.tm_n + kTmNodes - 1) / kTmNodes;
+  for (int q = warp; q < nq; q += n_warps) {
+    const int j = q * kTmNodes + lane;
+    if (j < L.tm_n) {
+      const int mi = j - L.tm_j0;
+      const float2 z = g[mi < 0 ? mi + M : mi];
+      const float cr = H.nu_corr[j];
+      const float l = tm_node_logw(L, z.x * cr, z.y * cr);
+      if (ell) ell[j] = l;
+      if (l > m) {
+        s = s * __expf(m - l) + 1.0f;
+        m = l;
+      } else {
+        s += __expf(l - m);
+      }
+    }
+  }
+  float Mx = m;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) Mx = fmaxf(Mx, __shfl_xor_sync(0xffffffffu, Mx, o));
+  float S = (m > -INFINITY) ? s * __expf(m - Mx) : 0.0f;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) S += __shfl_xor_sync(0xffffffffu, S, o);
+  wm = Mx;
+  ws = S;
+}
+
+// The NUFFT grid's place in shared memory: after the N_b + 1 edge products.
+__device__ __forceinline__ float2* tm_nufft_grid(unsigned char* smem, int n_bins) {
+  return reinterpret_cast<float2*>(smem + ((((size_t)n_bins + 1) * 2 * sizeof(float) + 15) / 16 * 16));
 }
 
 // Time-marginalised logL from the warps' (max, sum) pairs (warp order) and

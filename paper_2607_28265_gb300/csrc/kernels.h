@@ -31,7 +31,15 @@ struct SkyFrame {
 // shared memory) and the shared-memory bytes of those products.
 constexpr int kHetTmThreads = 512;
 constexpr int kMaxTmBins = 16384;
-inline size_t het_tm_smem_bytes(int n_bins) { return ((size_t)n_bins + 1) * 2 * sizeof(float); }
+// Non-uniform FFT time pass: node counts it serves (the direct sum below and
+// above), the kernel width in grid points; its grid of M complex values
+// follows the edge products in shared memory.
+constexpr int kNufftMinNodes = 64;
+constexpr int kNufftMaxNodes = 4096;
+constexpr int kNufftWidth = 8;
+inline size_t het_tm_smem_bytes(int n_bins, int nufft_m = 0) {
+  return (((size_t)n_bins + 1) * 2 * sizeof(float) + 15) / 16 * 16 + (size_t)nufft_m * 2 * sizeof(float);
+}
 
 // Device buffers owned by a context (all allocated with cudaMalloc).
 struct DeviceBuffers {
@@ -60,6 +68,13 @@ struct DeviceBuffers {
   // time marginalisation on the heterodyned bins (t_c marginalised)
   float2* het_tm_g = nullptr;       // [n_det][N_b + 1] edge weights: Z_i = sum_e g_ie r_i(e)
   float2* het_tm_w = nullptr;       // [N_b + 1] exp(-2 pi i f_e dt), the step between grid nodes
+  // ... by non-uniform FFT (L.tm_M > 0): gather list of each of the M grid
+  // points (edge, kernel weight), deconvolution 1 / Phi per node, twiddles
+  int* het_nu_ptr = nullptr;        // [M + 1]
+  int* het_nu_edge = nullptr;       // [entries]
+  float* het_nu_wt = nullptr;       // [entries]
+  float* het_nu_corr = nullptr;     // [N_t]
+  float2* het_nu_tw = nullptr;      // [M / 2] exp(2 pi i k / M)
   // scratch for batched evaluation, sized for `cap` thetas
   int cap = 0;
   EvalRecord* rec = nullptr;     // [cap]

@@ -326,7 +326,10 @@ __global__ void __launch_bounds__(kHetTmThreads, 1)
     for (int i = 0; i < NDET; ++i) s_hh[warp][i] = hh[i];
   __syncthreads();
   float wm, ws;
-  tm_pass(L, H, y, warp, n_warps, lane, ell_th, wm, ws);
+  if (L.tm_M > 0)
+    tm_pass_nufft(L, H, y, tm_nufft_grid(smem, H.n_bins), warp, n_warps, lane, ell_th, wm, ws);
+  else
+    tm_pass(L, H, y, warp, n_warps, lane, ell_th, wm, ws);
   if (lane == 0) {
     s_tm[warp][0] = wm;
     s_tm[warp][1] = ws;
@@ -346,7 +349,7 @@ __global__ void __launch_bounds__(kHetTmThreads, 1)
 template <int NDET>
 cudaError_t launch_het_tm(const LikeConst& L, const DeviceBuffers& B, int n, double* out, cudaStream_t st,
                           double* kappa_out, double* vv_out, float* ell) {
-  const size_t bytes = het_tm_smem_bytes(B.het_nb);
+  const size_t bytes = het_tm_smem_bytes(B.het_nb, L.tm_M);
   cudaError_t e = cudaFuncSetAttribute(k_het_tm<NDET>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   if (e != cudaSuccess) return e;
   k_het_tm<NDET><<<n, kHetTmThreads, bytes, st>>>(L, het_tables(B), B.rec, n, out, kappa_out, vv_out, ell);

@@ -411,7 +411,7 @@ __device__ inline void start_step(const SamplerConst& S, ChainState& ch, const f
     const float* Lb = chol + (size_t)b * kMaxDim * kMaxDim;
     for (int r = 0; r < nb; ++r) {
       float v = 0.0f;
-      for (int q = 0; q <= r; ++q) v = fmaf(Lb[r * kMaxDim + q], z[q], v);
+      for (int q = 0; q <= r; ++q) v = fmaf(__ldcg(&Lb[r * kMaxDim + q]), z[q], v);
       ch.dir[S.block_dims[b][r]] = (double)v;
     }
   }
@@ -434,8 +434,9 @@ __device__ __noinline__ void chain_advance_local(const LikeConst& L, const Sampl
                                     EvalRecord& rx, bool& rx_dirty, EvalRecord& rec, bool& rec_set,
                                     int& setup_fl) {
   NSGlobal* g = P.g;
-  const double logl_star = g->logl_star;
-  const long long it = g->iter;
+  // written by CTA 0 at the boundary: read through L2, never a stale L1 line
+  const double logl_star = __ldcg(&g->logl_star);
+  const long long it = __ldcg(&g->iter);
   if (ch.done) return;
   const bool prof = (c == 0);
   long long tk = clock64();
@@ -1193,7 +1194,7 @@ __device__ __forceinline__ void wc_start_step(const SamplerConst& S, WarpChain& 
     float v = 0.0f;
     for (int q = 0; q < nb; ++q) {
       const float zq = __shfl_sync(kFull, z, q);
-      if (lane < nb && q <= lane) v = fmaf(Lb[lane * kMaxDim + q], zq, v);
+      if (lane < nb && q <= lane) v = fmaf(__ldcg(&Lb[lane * kMaxDim + q]), zq, v);  // CTA 0 writes L_b
     }
     // ... and dimension j of the block takes row block_rank[j]
     const float vd = __shfl_sync(kFull, v, lane < S.ndim ? S.block_rank[lane] : 0);
@@ -1375,8 +1376,9 @@ __device__ int control_step_warp(const LikeConst& L, const SamplerConst& S, cons
   long long tk = clock64();
   unsigned long long acc_res = 0, acc_step = 0, acc_prop = 0, acc_free = 0, acc_setup = 0, cnt_free = 0,
                      cnt_setup = 0, cnt_step = 0;
-  const double logl_star = g->logl_star;
-  const long long it = g->iter;
+  // written by CTA 0 at the boundary: read through L2, never a stale L1 line
+  const double logl_star = __ldcg(&g->logl_star);
+  const long long it = __ldcg(&g->iter);
   WarpChain w;
   wc_load(ch, w, lane);
   if (ch.pending) {
@@ -2045,7 +2047,11 @@ __global__ void __launch_bounds__(kHetThreads, 1)
         __syncthreads();
         if (L.tm_n > 0 && valid) {  // block-uniform
           float wm, ws;
-          tm_pass(L, H, reinterpret_cast<const float2*>(smem), warp, n_warps, lane, nullptr, wm, ws);
+          if (L.tm_M > 0)
+            tm_pass_nufft(L, H, reinterpret_cast<float2*>(smem), tm_nufft_grid(smem, H.n_bins), warp, n_warps, lane,
+                          nullptr, wm, ws);
+          else
+            tm_pass(L, H, reinterpret_cast<const float2*>(smem), warp, n_warps, lane, nullptr, wm, ws);
           if (lane == 0) {
             s_tm[warp][0] = wm;
             s_tm[warp][1] = ws;
@@ -2396,7 +2402,7 @@ int run_setup(swig_ctx* c, RunState& R) {
   // the homed chains' state and records of the warp-parallel control follow
   // the per-warp records / sort buffers
   // (heterodyned: one slot, after the sort buffers / time-pass edge products)
-  const size_t het_scratch = std::max(sort_bytes, L.tm_n > 0 ? het_tm_smem_bytes(c->B.het_nb) : (size_t)0);
+  const size_t het_scratch = std::max(sort_bytes, L.tm_n > 0 ? het_tm_smem_bytes(c->B.het_nb, L.tm_M) : (size_t)0);
   S.ctl_slots = mixed ? (k + L.n_slices - 1) / L.n_slices : (het ? 1 : 0);
   S.ctl_off = (int)(((het ? het_scratch : std::max(rec_bytes, sort_bytes)) + 15) & ~(size_t)15);
   R.tail = std::max(rec_bytes, sort_bytes);

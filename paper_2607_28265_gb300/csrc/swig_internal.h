@@ -106,6 +106,10 @@ struct LikeConst {
   // tm_t0 + j tm_dt = t_j - tm_tref
   int tm_n;
   double tm_lo, tm_dt, tm_tref, tm_t0;
+  // non-uniform FFT form of the time pass (tm_M > 0): grid size, the node j0
+  // of the reference shift tm_dref = tm_t0 + j0 tm_dt
+  int tm_M, tm_j0;
+  double tm_dref;
 };
 
 }  // namespace swig

@@ -172,7 +172,12 @@ def unit_to_prior_draw(rng: np.random.Generator, n: int) -> np.ndarray:
 
 
 def config1(nlive: int = 100) -> Workload:
-    """One H1-like detector, 4 s, 20-1024 Hz, df = 0.25 Hz, FP64, 4 free params."""
+    """One H1-like detector, 4 s, 20-1024 Hz, df = 0.25 Hz, FP64, 4 free params.
+
+    Gibbs blocks {Mc, q, t_c} and {d_L}: the chirp mass and the coalescence
+    time are strongly correlated on this short segment, and a joint block lets
+    the covariance-directed slice move along that ridge (a separate t_c block
+    mixed it much more slowly)."""
     P = Param
     params = [
         P(PRIOR_UNIFORM, 1.1, 1.3, block=0),
@@ -186,7 +191,7 @@ def config1(nlive: int = 100) -> Workload:
         P(PRIOR_UNIFORM, 0, 0, MODE_FIXED, 0.3),
         P(PRIOR_UNIFORM, 0, 0, MODE_FIXED, 1.2),
         P(PRIOR_UNIFORM, 0, 0, MODE_FIXED, 0.5),
-        P(PRIOR_UNIFORM, -0.1, 0.1, block=2),
+        P(PRIOR_UNIFORM, -0.1, 0.1, block=0),
         P(PRIOR_UNIFORM, 0, 0, MODE_FIXED, 0.0),
     ]
     inj = np.array([1.2, 0.8, 0, 0, 0, 0, 100.0, 0.4, 0.3, 1.2, 0.5, 0.0, 0.0])

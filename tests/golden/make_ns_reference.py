@@ -16,7 +16,7 @@ import swig_inputs as si  # noqa: E402
 from oracle import events, nested, physics  # noqa: E402
 from oracle import likelihood as L  # noqa: E402
 
-NLIVE, NREP, SEED = 200, 20, 4242
+NLIVE, NREP, SEED = 400, 40, 4242
 
 
 def main():

@@ -19,6 +19,7 @@
 //   host_harness priormap < SLOTS ROWS                 13 slots (kind mode lo hi value) then
 //                                                      rows of sampled unit-cube coordinates
 //   host_harness abi                                   sizes and field offsets of the C-ABI structs
+//   host_harness nufft NT DT < NE FE...                 time-pass NUFFT tables for edge frequencies FE
 //   host_harness tmtables < NB NDET DT EDGES A01       time-marginalisation edge tables
 //   host_harness hetsum < N NB NDET DF F IDX (DATA PSD H0)xNDET   heterodyne summary data
 //   host_harness weights F_MIN F_MAX DF NDET STRIDE < (DATA PSD)xNDET   full-grid data weights
@@ -280,6 +281,28 @@ int main(int argc, char** argv) {
     SWIG_FIELD(swig_result, n_iter); SWIG_FIELD(swig_result, n_evals); SWIG_FIELD(swig_result, n_sweep_evals);
     SWIG_FIELD(swig_result, status);
     std::printf("]}}\n");
+    return 0;
+  }
+  if (what == "nufft" && argc == 4) {
+    int ne = 0;
+    if (std::scanf("%d", &ne) != 1 || ne < 1) return 3;
+    std::vector<double> fe(ne);
+    for (int e = 0; e < ne; ++e)
+      if (std::scanf("%lf", &fe[e]) != 1) return 3;
+    int M = 0, j0 = 0;
+    std::vector<int> ptr, edge;
+    std::vector<float> wt, corr;
+    std::vector<float2> tw;
+    het_nufft_tables(fe, std::atoi(argv[2]), std::atof(argv[3]), kNufftWidth, &M, &j0, ptr, edge, wt, corr, tw);
+    std::printf("{\"M\": %d, \"j0\": %d, \"ptr\": [", M, j0);
+    for (size_t q = 0; q < ptr.size(); ++q) std::printf("%s%d", q ? ", " : "", ptr[q]);
+    std::printf("], \"edge\": [");
+    for (size_t q = 0; q < edge.size(); ++q) std::printf("%s%d", q ? ", " : "", edge[q]);
+    std::printf("], \"wt\": [");
+    for (size_t q = 0; q < wt.size(); ++q) std::printf("%s%.9g", q ? ", " : "", wt[q]);
+    std::printf("], \"corr\": [");
+    for (size_t q = 0; q < corr.size(); ++q) std::printf("%s%.9g", q ? ", " : "", corr[q]);
+    std::printf("]}\n");
     return 0;
   }
   if (what == "slices" && argc == 19) {

@@ -30,12 +30,23 @@ def _thetas(wl, th_inj, n_prior, n_near, seed):
     rng = np.random.default_rng(seed)
     ns = len(wl.sampled())
     out = [physics.prior_transform(rng.random(ns), wl.params)[0] for _ in range(n_prior)]
+    # near the injection every sampled parameter moves: Mc and t_c by about
+    # their posterior widths' scale, the others by a percent or so of their
+    # prior range (spins and tides enter the phase basis, the extrinsic ones
+    # the projection and delays), clipped to the prior
+    scale = {0: None, 1: 0.01, 2: 0.005, 3: 0.005, 4: 50.0, 5: 50.0, 6: None, 7: 0.02, 8: 0.02, 9: 0.005, 10: 0.005,
+             11: 1e-3, 12: 0.05}
     for _ in range(n_near):
         t = th_inj.copy()
-        t[0] *= 1 + rng.normal(0, 3e-4)
-        t[11] += rng.normal(0, 1e-3)
-        if wl.params[1].mode == si.MODE_SAMPLE:
-            t[1] = min(1.0, t[1] * (1 + rng.normal(0, 0.01)))
+        for s in wl.sampled():
+            p = wl.params[s]
+            if s == 0:
+                t[0] *= 1 + rng.normal(0, 3e-4)
+            elif s == 6:
+                t[6] *= 1 + rng.normal(0, 0.02)
+            else:
+                t[s] += rng.normal(0, scale[s])
+            t[s] = min(max(t[s], p.lo), p.hi)
         out.append(t)
     return np.array(out)
 
@@ -78,6 +89,11 @@ def test_cfg2_full_size_parity(cfg2):
     want = np.array([L.loglike(ev, t) for t in thetas])
     err = np.abs(got - want)
     assert np.all(err <= _tol(want)), f"max err {err.max():.3e}"
+    # the stated bound is 0.78 here (|logL| ~ 7.8e5 from -<d|d>/2); the error
+    # on the log-likelihood ratio logL + <d|d>/2 (|.| up to SNR^2 / 2 ~ 300)
+    # is what the mixed path controls: FP32 sweep and epilogue, measured
+    # below 2e-4 on this grid
+    assert err.max() < 2e-3, f"max err {err.max():.3e}"
     # the log-likelihood ratio logL + <d|d>/2 (|value| ~ SNR^2/2) is reported,
     # and must stay well inside the same absolute budget
     assert err.max() < 0.05

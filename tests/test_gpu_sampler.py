@@ -128,13 +128,14 @@ def test_dead_points_match_oracle_and_runs_are_deterministic(cfg1):
 
 
 def test_posterior_and_evidence_against_oracle(cfg1):
-    """Four-parameter workload.  The evidence is compared with its exact value
-    (importance sampling of the oracle likelihood, tests/golden/
-    make_is_evidence.py); single runs scatter by ~1 nat, more than sqrt(H/m),
-    because 5 slice steps per dimension leave the Mc-q-t_c correlation across
-    Gibbs blocks partly unmixed, so the mean of four seeds is tested.  The
-    posterior is compared with the oracle's own run by a weighted two-sample
-    KS test per parameter (Kish effective sizes)."""
+    """Four-parameter workload, blocks {Mc, q, t_c} and {d_L}.  The evidence is
+    compared with its exact value (importance sampling of the oracle
+    likelihood, tests/golden/make_is_evidence.py, error 0.014): the mean of four
+    seeds within three standard errors of the run-to-run scatter measured for
+    this configuration (0.36 nat per run over eight seeds; the per-run estimate
+    sqrt(H/m) is 0.22), each run within three times that scatter.  The
+    posterior is compared with the oracle's own run by a weighted two-sample KS
+    test per parameter (Kish effective sizes)."""
     post = os.path.join(HERE, "golden", "cfg1_oracle_posterior.csv")
     isf = os.path.join(HERE, "golden", "cfg1_is_evidence.txt")
     logz_true = float(open(isf).readlines()[-1].split()[0])
@@ -152,7 +153,9 @@ def test_posterior_and_evidence_against_oracle(cfg1):
                                             np.exp(ref[:, -1] - ref_logz))
                 assert p > 1e-3, (si.PARAM_NAMES[slot], d, p)
         ctx.close()
-    assert abs(np.mean(zs) - logz_true) < 2.0, (zs, logz_true)
+    scatter = 0.36
+    assert abs(np.mean(zs) - logz_true) < 3.0 * scatter / math.sqrt(len(zs)) + 0.014, (zs, logz_true)
+    assert np.all(np.abs(np.array(zs) - logz_true) < 3.0 * scatter + 0.014), (zs, logz_true)
 
 
 def test_full_size_dead_points_match_oracle():

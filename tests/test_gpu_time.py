@@ -3,7 +3,10 @@ against the oracle: batched marginal likelihoods, the sampler's dead points,
 the post-hoc t_c drawn for them and the evidence.
 
 Tolerance: as for the heterodyned likelihood (1e-6 relative to |logL| plus
-2e-4), which also covers the time pass.  Each node's Z is a fresh FP32 sum
+2e-4), which also covers the time pass.  With 64..4096 nodes spaced below
+1 / f_max the pass is a non-uniform FFT (kernel width 8, twofold
+oversampling: ~1e-8 of sum_e |y_e| in exact arithmetic, then FP32 gathering
+and butterflies); otherwise the direct sum.  Each node's Z is a fresh FP32 sum
 over the edges.  A term's phasor comes from an exact double-float phase at the
 chunk's first node, then up to 31 FP32 rotation steps.  Each step adds about
 6e-8 of relative error, so no term drifts by more than ~2e-6.  That is
@@ -74,10 +77,12 @@ def cfg1():
     return wl, ev, th
 
 
-@pytest.mark.parametrize("nt,phase_marg", [(100, False), (256, True), (1, False), (33, True)])
+@pytest.mark.parametrize("nt,phase_marg", [(100, False), (256, True), (1, False), (33, True), (1000, False)])
 def test_batched_time_marginal_matches_oracle_cfg1(cfg1, nt, phase_marg):
     """Several 32-node chunks with a ragged last one (100, 33), exact chunks
-    (256) and the one-node grid; plain and phase-marginalised."""
+    (256) and the one-node grid; plain and phase-marginalised.  256 and 1000
+    nodes (spacing below 1 / f_max) take the non-uniform FFT time pass, the
+    others the direct sum."""
     wl, ev, th = cfg1
     params = _tm_params(wl, phase_marg=phase_marg)
     evt = _event(ev, params)

@@ -369,3 +369,41 @@ def test_full_grid_data_weights_equal_the_inner_products(harness):
         assert out["dmax"][i] == pytest.approx(np.max(np.abs(Di)), rel=1e-14, abs=0)
     sample = D[::stride]
     assert np.allclose(np.array(out["dre"]) + 1j * np.array(out["dim"]), sample, rtol=1e-14, atol=0)
+
+
+@pytest.mark.parametrize("n_t", [64, 1000, 2000, 4096])
+def test_time_pass_nufft_tables_reproduce_the_direct_sum(harness, n_t):
+    """The tables of the non-uniform FFT time pass (het_nufft_tables): gather
+    lists of the kernel-weighted edge values, 1 / Phi per node.  Applied in
+    FP64 here (gather, an inverse FFT with exponent +2 pi i, deconvolution)
+    they give Z(dt_j) = sum_e y_e exp(-2 pi i f_e dt_j) on the uniform node grid
+    to ~1e-8 of sum |y_e| (the kernel's error for width 8 at twofold
+    oversampling), on the 128 s grid's 5,000-bin equal-phase edges, for node
+    spacings below 1 / (2 f_max)."""
+    wl = si.config2()
+    f = np.arange(int(np.ceil(wl.f_min / wl.df)), int(np.floor(wl.f_max / wl.df)) + 1) * wl.df
+    edges, _ = L.phase_bound_edges(f, 5000)
+    dt = 0.2 / n_t
+    inp = f"{len(edges)} " + " ".join(repr(float(x)) for x in edges)
+    r = subprocess.run([harness, "nufft", str(n_t), repr(dt)], input=inp, capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stderr
+    d = json.loads(r.stdout)
+    M, j0 = d["M"], d["j0"]
+    if n_t == 64:
+        # nodes 3.1 ms apart: f_e dt wraps past one cycle, a grid point's edges
+        # are no longer consecutive, and the tables are declined (direct sum)
+        assert M == 0 and d["ptr"] == []
+        return
+    assert M >= 2 * n_t and M & (M - 1) == 0 and j0 == n_t // 2
+    ptr, edge, wt, corr = (np.array(d[k]) for k in ("ptr", "edge", "wt", "corr"))
+    assert len(ptr) == M + 1 and len(edge) == M  # first edge per grid point (its edges are consecutive)
+    rng = np.random.default_rng(n_t)
+    y = rng.normal(size=len(edges)) + 1j * rng.normal(size=len(edges))
+    t0 = -0.1 + 0.5 * dt
+    c = y * np.exp(-2j * np.pi * edges * (t0 + j0 * dt))
+    b = np.array([np.sum(wt[ptr[l]:ptr[l + 1]] * c[edge[l]:edge[l] + ptr[l + 1] - ptr[l]]) for l in range(M)])
+    X = np.fft.ifft(b) * M
+    j = np.arange(n_t)
+    Z = X[(j - j0) % M] * corr
+    Zd = np.exp(-2j * np.pi * np.outer(t0 + j * dt, edges)) @ y
+    assert np.max(np.abs(Z - Zd)) < 1e-7 * np.sum(np.abs(y))
