@@ -66,13 +66,20 @@ constexpr int kFreeBudget = 8;  // projection-only evaluations per chain per rou
 #define SWIG_FLOW_PARTS 1
 #endif
 static_assert(SWIG_FLOW_PARTS >= 1 && SWIG_FLOW_PARTS <= 4, "1..4 parts per slice");
+// 1: both ends of a bracket step out at once in the full-grid dataflow kernel
+// (same evaluations and results as one end after the other, two requests in
+// flight per chain); 0: one end at a time
+#ifndef SWIG_PAR_OUT
+#define SWIG_PAR_OUT 1
+#endif
 // Bytes of a slice's tile table plus `warps` anchor rows in the dataflow
 // kernel's shared memory (16-byte aligned).
 __host__ __device__ inline size_t flow_tile_bytes(int max_tiles, int warps) {
   const size_t ti = ((size_t)max_tiles * sizeof(TileInfo) + 15) & ~(size_t)15;
   return ti + (((size_t)warps * max_tiles * kAnchorStride * sizeof(float) + 15) & ~(size_t)15);
 }
-enum ChainPhase { PH_NEW = 0, PH_LEFT = 1, PH_RIGHT = 2, PH_SHRINK = 3 };
+// PH_OUT: both ends of the bracket stepping out at once (two requests in flight)
+enum ChainPhase { PH_NEW = 0, PH_LEFT = 1, PH_RIGHT = 2, PH_SHRINK = 3, PH_OUT = 4 };
 // What a Gibbs block moves: waveform coefficients, amplitude A(Mc)/d_L,
 // projection P_i, time shifts tau_i (BF_SKY: through the geocentric delays;
 // BF_TAU alone: t_c).
@@ -107,6 +114,10 @@ struct SamplerConst {
   int dim_of_slot[SWIG_N_PARAMS];
   int ctl_off;
   int ctl_slots;  // chains homed per CTA at most
+  // parallel stepping-out (full-grid dataflow kernel): the left end of a
+  // chain's bracket uses request slot c, the right end slot nrep + c
+  int par_out;
+  int n_slots;    // request slots: nrep, or 2 nrep with par_out
 };
 
 struct ChainState {
@@ -120,6 +131,8 @@ struct ChainState {
   unsigned ctr;
   int n_caps;
   long long n_evals, n_full;
+  int side;     // PH_OUT: bit 0 the left end still stepping, bit 1 the right end
+  int n_out_r;  // PH_OUT: expansions of the right end
 };
 
 struct NSGlobal {
@@ -859,9 +872,15 @@ __device__ __noinline__ void ns_boundary_advance(const LikeConst& L, const Sampl
     ch.pending = 0;
     ch.done = 0;
     ch.ctr = 0;
+    ch.side = 0;
+    ch.n_out_r = 0;
     P.pending[c] = 0;
     P.req[c] = 0;
     P.done_cnt[c] = 0;
+    if (S.par_out) {
+      P.req[k + c] = 0;
+      P.done_cnt[k + c] = 0;
+    }
   }
   __syncthreads();
   if (tid == 0) {
@@ -1013,7 +1032,7 @@ constexpr unsigned kFull = 0xffffffffu;
 struct WarpChain {
   double x, y, dir, th, thy, kap, vv;  // lane-indexed, see above (vv: detector i on lane i)
   double lx, lo, hi, t;
-  int block, step, sweep, phase, n_out, n_shrink, done, proj_dirty, n_caps;
+  int block, step, sweep, phase, n_out, n_shrink, done, proj_dirty, n_caps, side, n_out_r;
   unsigned ctr;
   long long n_evals, n_full;
 };
@@ -1040,6 +1059,8 @@ __device__ __forceinline__ void wc_load(const ChainState& ch, WarpChain& w, int 
   w.done = ch.done;
   w.proj_dirty = ch.proj_dirty;
   w.n_caps = ch.n_caps;
+  w.side = ch.side;
+  w.n_out_r = ch.n_out_r;
   w.ctr = ch.ctr;
   w.n_evals = ch.n_evals;
   w.n_full = ch.n_full;
@@ -1069,6 +1090,8 @@ __device__ __forceinline__ void wc_store(ChainState& ch, const WarpChain& w, int
     ch.done = w.done;
     ch.proj_dirty = w.proj_dirty;
     ch.n_caps = w.n_caps;
+    ch.side = w.side;
+    ch.n_out_r = w.n_out_r;
     ch.ctr = w.ctr;
     ch.n_evals = w.n_evals;
     ch.n_full = w.n_full;
@@ -1203,8 +1226,12 @@ __device__ __forceinline__ void wc_start_step(const SamplerConst& S, WarpChain& 
   const double r0 = wc_uniform(S, w, c, it);
   w.lo = -r0;
   w.hi = 1.0 - r0;
-  w.phase = PH_LEFT;
+  // both ends at once where the evaluations are requests to the sweep (the
+  // same evaluations and decisions as left, then right)
+  w.phase = (S.par_out && !S.block_free[b]) ? PH_OUT : PH_LEFT;
+  w.side = 3;
   w.n_out = 0;
+  w.n_out_r = 0;
   w.n_shrink = 0;
 }
 
@@ -1366,8 +1393,76 @@ __device__ __forceinline__ void wc_result(const LikeConst& L, const SamplerConst
 // CTL_WAIT (published, or the chain is done), CTL_AGAIN (projection-only
 // budget used up: call again) or CTL_EVAL (HET: record set up, evaluate it).
 enum { CTL_WAIT = 0, CTL_AGAIN = 1, CTL_EVAL = 2 };
+
+// The proposal at bracket coordinate t of block b: the point y = x + t n on
+// the block's dimensions (lane j: dimension j) and its theta (lane s: slot s).
+// Returns false (and leaves theta alone) when y leaves the unit cube.
+__device__ __forceinline__ bool wc_proposal(const SamplerConst& S, WarpChain& w, int b, double t, int lane) {
+  const bool inb = wc_in_block(S, b, lane);
+  if (lane < S.ndim) w.y = inb ? w.x + t * w.dir : w.x;
+  const bool inside = __all_sync(kFull, !inb || (w.y >= 0.0 && w.y <= 1.0));
+  if (!inside) return false;
+  double v = 0.0;
+  if (inb) {
+    const int slot = S.slot_of_dim[lane];
+    // the sky angles go through FP64: the delays need them to ~1e-10
+    v = (S.sky.on && (slot == 9 || slot == 10)) ? prior_slot_inverse(S.prior[slot], w.y)
+                                                : prior_slot_inverse_f32(S.prior[slot], w.y);
+  }
+  const int src = lane < SWIG_N_PARAMS ? S.dim_of_slot[lane] : -1;
+  const double vs = __shfl_sync(kFull, v, src >= 0 ? src : 0);
+  w.thy = (src >= 0 && ((S.block_mask[b] >> src) & 1u)) ? vs : w.th;
+  if (S.sky.on && (S.block_flags[b] & BF_SKY)) {
+    const double az = __shfl_sync(kFull, w.thy, 9), zen = __shfl_sync(kFull, w.thy, 10);
+    double ra = 0.0, dec = 0.0;
+    if (lane == 0) sky_frame_to_radec(S.sky, az, zen, &ra, &dec);
+    ra = __shfl_sync(kFull, ra, 0);
+    dec = __shfl_sync(kFull, dec, 0);
+    if (lane == 9) w.thy = ra;
+    if (lane == 10) w.thy = dec;
+  }
+  return true;
+}
+
+// Set up the record of the proposal in w.thy in request slot `slot` (the
+// current point's record with block b's pieces recomputed) and, unless the
+// caller evaluates it itself (HET), publish it to every CTA.
+template <bool HET>
+__device__ __forceinline__ void wc_publish(const LikeConst& L, const SamplerConst& S, const DeviceBuffers& B,
+                                           const SamplerPtrs& P, int slot, int b, ChainState& ch,
+                                           const EvalRecord& rx, const WarpChain& w, int lane) {
+  const int fl = S.block_flags[b] | (w.proj_dirty ? (BF_AMP | BF_PROJ) : 0);
+  const bool fin = lane >= SWIG_N_PARAMS || isfinite(w.thy);
+  const double t0v = __shfl_sync(kFull, w.thy, 0), t1v = __shfl_sync(kFull, w.thy, 1);
+  const double t6v = __shfl_sync(kFull, w.thy, 6);
+  const bool valid = __all_sync(kFull, fin) && t0v > 0.0 && t1v > 0.0 && t1v <= 1.0 && t6v > 0.0;
+  if (lane < SWIG_N_PARAMS) ch.th_y[lane] = w.thy;
+  warp_copy(&B.rec[slot], &rx, sizeof(EvalRecord), lane);
+  if (lane == 0) B.rec[slot].valid = valid ? 1 : 0;
+  __syncwarp();
+  setup_record_warp(L, ch.th_y, fl, true, &B.rec[slot], lane);
+  if (!HET && lane == 0) {
+    P.done_cnt[slot] = 0;
+    __threadfence();
+    // sequence number and unit width in one word
+    st_release(&P.req[slot], (((P.req[slot] >> 3) + 1) << 3) | S.flow_parts);
+  }
+}
+
+// One control step of chain c (state `ch` and current-point record `rx` in
+// shared memory) by the whole warp: the results of its finished full
+// evaluations, then the chain's slice steps up to the next full-likelihood
+// proposal(s), whose records are set up in B.rec.  Full grid (HET false): a
+// result is read from the slice partials and a proposal is published as a
+// request to every CTA; with S.par_out the two ends of a bracket step out at
+// once (left end in slot c, right end in slot nrep + c, ch.pending bits 0 and
+// 1).  Heterodyned (HET true): the caller evaluates the proposal itself and
+// passes the result back (het_ly on every lane, het_kap: component j on lane
+// j, het_vv: detector i on lane i).  Returns CTL_WAIT (published, or the
+// chain is done), CTL_AGAIN (projection-only budget used up: call again) or
+// CTL_EVAL (HET: record set up, evaluate it).
 template <int NDET, bool HET>
-__device__ int control_step_warp(const LikeConst& L, const SamplerConst& S, const DeviceBuffers& B,
+__device__ __noinline__ int control_step_warp(const LikeConst& L, const SamplerConst& S, const DeviceBuffers& B,
                                  const SamplerPtrs& P, int c, ChainState& ch, EvalRecord& rx, int lane,
                                  double het_ly = 0.0, double het_kap = 0.0, double het_vv = 0.0) {
   NSGlobal* g = P.g;
@@ -1379,15 +1474,36 @@ __device__ int control_step_warp(const LikeConst& L, const SamplerConst& S, cons
   // written by CTA 0 at the boundary: read through L2, never a stale L1 line
   const double logl_star = __ldcg(&g->logl_star);
   const long long it = __ldcg(&g->iter);
+  const int target = L.n_slices * S.flow_parts;
   WarpChain w;
   wc_load(ch, w, lane);
-  if (ch.pending) {
+  int pend = ch.pending;
+  if (pend && w.phase == PH_OUT) {
+    // the ends whose requests have finished: extend while inside the slice
+    for (int sd = 0; sd < 2; ++sd) {
+      if (!((pend >> sd) & 1)) continue;
+      const int slot = sd ? S.nrep + c : c;
+      int fin = 0;
+      if (lane == 0) fin = ld_acquire(&P.done_cnt[slot]) >= target;
+      if (!__shfl_sync(kFull, fin, 0)) continue;
+      double kapc, ly;
+      wc_result<NDET>(L, S, B, slot, lane, kapc, ly);
+      pend &= ~(1 << sd);
+      ++w.n_full;
+      ++w.n_evals;
+      const bool ok = ly > logl_star;
+      if (sd == 0) {
+        if (ok) w.lo -= 1.0;
+        if (!ok || ++w.n_out >= kMaxStepOut) w.side &= ~1;
+      } else {
+        if (ok) w.hi += 1.0;
+        if (!ok || ++w.n_out_r >= kMaxStepOut) w.side &= ~2;
+      }
+    }
+  } else if (pend) {
     double kapc = het_kap, ly = het_ly;
     if (!HET) wc_result<NDET>(L, S, B, c, lane, kapc, ly);
-    if (lane == 0) {
-      P.pending[c] = 0;
-      ch.pending = 0;
-    }
+    pend = 0;
     ++w.n_full;
     ++w.n_evals;
     if (wc_apply(S, w, ly, logl_star, g, lane)) {
@@ -1410,6 +1526,25 @@ __device__ int control_step_warp(const LikeConst& L, const SamplerConst& S, cons
   int status = CTL_WAIT;
   for (int guard = 0; guard < 1 << 20 && !w.done; ++guard) {
     const int b = w.block;
+    if (w.phase == PH_OUT) {
+      // issue the ends that are still stepping and have no request in flight
+      for (int sd = 0; sd < 2; ++sd) {
+        if (!((w.side >> sd) & 1) || ((pend >> sd) & 1)) continue;
+        if (!wc_proposal(S, w, b, sd ? w.hi : w.lo, lane)) {
+          w.side &= ~(1 << sd);  // this end left the unit cube
+          continue;
+        }
+        wc_publish<false>(L, S, B, P, sd ? S.nrep + c : c, b, ch, rx, w, lane);
+        pend |= 1 << sd;
+        if (prof) cnt_setup += 1;
+      }
+      if (pend) break;  // wait for the requests in flight
+      if (w.side == 0) {  // both ends done: shrink
+        w.phase = PH_SHRINK;
+        w.n_shrink = 0;
+      }
+      continue;
+    }
     if (S.block_free[b] && free_left <= 0) {  // resume next round
       status = CTL_AGAIN;
       break;
@@ -1422,6 +1557,7 @@ __device__ int control_step_warp(const LikeConst& L, const SamplerConst& S, cons
         cnt_step += 1;
         tk = t2;
       }
+      continue;
     }
     double t;
     if (w.phase == PH_LEFT)
@@ -1431,32 +1567,9 @@ __device__ int control_step_warp(const LikeConst& L, const SamplerConst& S, cons
     else
       t = w.lo + (w.hi - w.lo) * wc_uniform(S, w, c, it);
     w.t = t;
-    const bool inb = wc_in_block(S, b, lane);
-    if (lane < S.ndim) w.y = inb ? w.x + t * w.dir : w.x;
-    const bool inside = __all_sync(kFull, !inb || (w.y >= 0.0 && w.y <= 1.0));
-    if (!inside) {
+    if (!wc_proposal(S, w, b, t, lane)) {
       wc_apply(S, w, -INFINITY, logl_star, g, lane);
       continue;
-    }
-    // the proposal's theta: theta, with the block's slots transformed
-    double v = 0.0;
-    if (inb) {
-      const int slot = S.slot_of_dim[lane];
-      // the sky angles go through FP64: the delays need them to ~1e-10
-      v = (S.sky.on && (slot == 9 || slot == 10)) ? prior_slot_inverse(S.prior[slot], w.y)
-                                                  : prior_slot_inverse_f32(S.prior[slot], w.y);
-    }
-    const int src = lane < SWIG_N_PARAMS ? S.dim_of_slot[lane] : -1;
-    const double vs = __shfl_sync(kFull, v, src >= 0 ? src : 0);
-    w.thy = (src >= 0 && ((S.block_mask[b] >> src) & 1u)) ? vs : w.th;
-    if (S.sky.on && (S.block_flags[b] & BF_SKY)) {
-      const double az = __shfl_sync(kFull, w.thy, 9), zen = __shfl_sync(kFull, w.thy, 10);
-      double ra = 0.0, dec = 0.0;
-      if (lane == 0) sky_frame_to_radec(S.sky, az, zen, &ra, &dec);
-      ra = __shfl_sync(kFull, ra, 0);
-      dec = __shfl_sync(kFull, dec, 0);
-      if (lane == 9) w.thy = ra;
-      if (lane == 10) w.thy = dec;
     }
     if (prof) {
       const long long t2 = clock64();
@@ -1482,35 +1595,19 @@ __device__ int control_step_warp(const LikeConst& L, const SamplerConst& S, cons
       }
       continue;
     }
-    // a full evaluation: the current point's record with this block's pieces
-    // recomputed, published as the chain's next request
-    const int fl = S.block_flags[b] | (w.proj_dirty ? (BF_AMP | BF_PROJ) : 0);
-    const bool fin = lane >= SWIG_N_PARAMS || isfinite(w.thy);
-    const double t0v = __shfl_sync(kFull, w.thy, 0), t1v = __shfl_sync(kFull, w.thy, 1);
-    const double t6v = __shfl_sync(kFull, w.thy, 6);
-    const bool valid = __all_sync(kFull, fin) && t0v > 0.0 && t1v > 0.0 && t1v <= 1.0 && t6v > 0.0;
-    if (lane < SWIG_N_PARAMS) ch.th_y[lane] = w.thy;
-    warp_copy(&B.rec[c], &rx, sizeof(EvalRecord), lane);
-    if (lane == 0) {
-      B.rec[c].valid = valid ? 1 : 0;
-      ch.pending = 1;
-      P.pending[c] = 1;
-    }
-    __syncwarp();
-    setup_record_warp(L, ch.th_y, fl, true, &B.rec[c], lane);
-    if (HET) {
-      status = CTL_EVAL;
-    } else if (lane == 0) {
-      P.done_cnt[c] = 0;
-      __threadfence();
-      // sequence number and unit width in one word (one unit per slice)
-      st_release(&P.req[c], (((P.req[c] >> 3) + 1) << 3) | S.flow_parts);
-    }
+    // a full evaluation: published as the chain's next request (slot c)
+    wc_publish<HET>(L, S, B, P, c, b, ch, rx, w, lane);
+    pend = 1;
+    if (HET) status = CTL_EVAL;
     if (prof) {
       acc_setup += clock64() - tk;
       cnt_setup += 1;
     }
     break;
+  }
+  if (lane == 0) {
+    ch.pending = pend;
+    P.pending[c] = pend;
   }
   wc_store(ch, w, lane);
   if (prof) {
@@ -1537,7 +1634,7 @@ template <int NDET, bool MIXED>
 __global__ void __launch_bounds__(kFlowThreads, 1)
     k_ns_flow(LikeConst L, SamplerConst S, DeviceBuffers B, SamplerPtrs P) {
   extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ int s_claim[kMaxChains];
+  __shared__ int s_claim[2 * kMaxChains];  // per request slot
   const int slice = blockIdx.x;
   const int b0 = B.slice_begin[slice], b1 = B.slice_begin[slice + 1];
   const int nb = b1 - b0;
@@ -1584,7 +1681,7 @@ __global__ void __launch_bounds__(kFlowThreads, 1)
       g->rounds += 1;
     }
     if (blockIdx.x == 0) ns_boundary(L, S, P, dyn);
-    for (int c = tid; c < S.nrep; c += blockDim.x) s_claim[c] = 0;
+    for (int c = tid; c < S.n_slots; c += blockDim.x) s_claim[c] = 0;
     if (!grid_sync(g, S.n_ctas, S.spin_limit)) return;
     if (timer) {
       t1 = gtimer();
@@ -1615,10 +1712,14 @@ __global__ void __launch_bounds__(kFlowThreads, 1)
           int st = 0;  // 0 done, 1 waiting, 2 ready
           if (lane == 0) {
             const ChainState* ch = MIXED ? &hs[i] : &P.chains[c];
+            const int pm = ch->pending;  // bit 0: slot c, bit 1: slot nrep + c (two-ended stepping-out)
             if (ch->done)
               st = 0;
-            else if (ch->pending)
-              st = ld_acquire(&P.done_cnt[c]) >= target ? 2 : 1;
+            else if (pm)
+              st = ((pm & 1) && ld_acquire(&P.done_cnt[c]) >= target) ||
+                           ((pm & 2) && ld_acquire(&P.done_cnt[S.nrep + c]) >= target)
+                       ? 2
+                       : 1;
             else
               st = 2;
           }
@@ -1659,20 +1760,21 @@ __global__ void __launch_bounds__(kFlowThreads, 1)
         // s_claim[c] = units of chain c this CTA has taken: request r owns
         // units (r - 1) G .. r G - 1, one per part
         int cc = -1, part = 0;
-        int rq[4];  // request words of four groups of 32 chains, read together
-        for (int base = 0; base < S.nrep && cc < 0; base += 32) {
+        int rq[4];  // request words of four groups of 32 slots, read together
+        for (int base = 0; base < S.n_slots && cc < 0; base += 32) {
           const int c = base + lane;
           const int gq = (base >> 5) & 3;
           if (gq == 0) {
 #pragma unroll
-            for (int q = 0; q < 4; ++q) rq[q] = base + 32 * q + lane < S.nrep ? *(volatile int*)&P.req[base + 32 * q + lane] : 0;
+            for (int q = 0; q < 4; ++q)
+              rq[q] = base + 32 * q + lane < S.n_slots ? *(volatile int*)&P.req[base + 32 * q + lane] : 0;
           }
           int r = 0;
 #pragma unroll
           for (int q = 0; q < 4; ++q)
             if (q == gq) r = rq[q] >> 3;
           bool cand = false;
-          if (c < S.nrep) cand = r * G > *(volatile int*)&s_claim[c];
+          if (c < S.n_slots) cand = r * G > *(volatile int*)&s_claim[c];
           unsigned m = __ballot_sync(0xffffffffu, cand);
           while (m) {
             const int leader = __ffs(m) - 1;
@@ -2366,6 +2468,9 @@ int run_setup(swig_ctx* c, RunState& R) {
   // (fixed places, fixed summation order), at most 4 (the partial buffers
   // hold 4 per slice and theta)
   S.flow_parts = SWIG_FLOW_PARTS;
+  // two-ended stepping-out: the full-grid mixed-precision dataflow kernel
+  S.par_out = mixed ? SWIG_PAR_OUT : 0;
+  S.n_slots = S.par_out ? 2 * k : k;
   // learned proposal: retrain every learn_interval iterations (one launch each)
   R.learned = c->cfg.proposal == SWIG_PROPOSAL_LEARNED;
   const double learn_mix = c->cfg.learn_mix > 0.0 ? std::min(1.0, c->cfg.learn_mix) : 0.5;
@@ -2427,8 +2532,8 @@ int run_setup(swig_ctx* c, RunState& R) {
     SCUDA(cudaMalloc(&st->P.chains, sizeof(ChainState) * k));
     SCUDA(cudaMalloc(&st->P.recx, sizeof(EvalRecord) * k));
     SCUDA(cudaMalloc(&st->P.pending, sizeof(int) * k));
-    SCUDA(cudaMalloc(&st->P.req, sizeof(int) * k));
-    SCUDA(cudaMalloc(&st->P.done_cnt, sizeof(int) * k));
+    SCUDA(cudaMalloc(&st->P.req, sizeof(int) * 2 * k));  // two request slots per chain
+    SCUDA(cudaMalloc(&st->P.done_cnt, sizeof(int) * 2 * k));
     SCUDA(cudaMalloc(&st->P.chol, sizeof(float) * kMaxBlocks * kMaxDim * kMaxDim));
     SCUDA(cudaMalloc(&st->P.g, sizeof(NSGlobal)));
     SCUDA(cudaMalloc(&st->P.dead_u, sizeof(double) * (size_t)S.max_iters * k * nd));
@@ -2465,7 +2570,7 @@ int run_setup(swig_ctx* c, RunState& R) {
     if (!c->mlp) c->mlp = new Mlp();
     if (c->mlp->cap < m) SCUDA(mlp_alloc(*c->mlp, std::max(m, 1024)));
   }
-  if ((rc = ensure_scratch(c, std::max(m, k)))) return rc;
+  if ((rc = ensure_scratch(c, std::max(m, 2 * k)))) return rc;  // records and partials of 2k request slots
 
   // initial live set and its likelihoods (with the per-detector sums)
   SCUDA(cudaSetDevice(c->device));
@@ -2490,8 +2595,8 @@ int run_setup(swig_ctx* c, RunState& R) {
   g0.status = ST_RUNNING;
   SCUDA(cudaMemcpyAsync(st->P.g, &g0, sizeof(g0), cudaMemcpyHostToDevice, c->stream));
   SCUDA(cudaMemsetAsync(st->P.pending, 0, sizeof(int) * k, c->stream));
-  SCUDA(cudaMemsetAsync(st->P.req, 0, sizeof(int) * k, c->stream));
-  SCUDA(cudaMemsetAsync(st->P.done_cnt, 0, sizeof(int) * k, c->stream));
+  SCUDA(cudaMemsetAsync(st->P.req, 0, sizeof(int) * 2 * k, c->stream));
+  SCUDA(cudaMemsetAsync(st->P.done_cnt, 0, sizeof(int) * 2 * k, c->stream));
   SCUDA(cudaMemsetAsync(st->P.chains, 0, sizeof(ChainState) * k, c->stream));
   c->n_launches += het ? 3 : (mixed ? 5 : 4);  // init draw + batched likelihood
 
@@ -2823,6 +2928,8 @@ int run_loop_multi(swig_ctx* const* ctxs, std::vector<RunState>& R, int i0, int 
       EventDesc d;
       d.L = ctxs[i]->L;
       d.S = R[i].S;
+      d.S.par_out = 0;  // the campaign kernel steps out one end at a time (same evaluations and results)
+      d.S.n_slots = d.S.nrep;
       d.B = ctxs[i]->B;
       d.P = R[i].st->P;
       d.smem_off = off[i - i0];

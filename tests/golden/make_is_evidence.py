@@ -1,5 +1,8 @@
 """Write the exact evidence of the 4 s single-detector workload by importance
-sampling of the FP64 oracle likelihood (tests/golden/cfg1_is_evidence.txt).
+sampling of the FP64 oracle likelihood (tests/golden/cfg1_is_evidence.txt),
+and the importance-weighted draws themselves as the reference posterior
+(tests/golden/cfg1_is_posterior.csv: independent draws, each with its exact
+weight L pi / q, so the only error is the Monte Carlo one of the weights).
 
 Proposal: a multivariate t (5 degrees of freedom) fitted to the oracle's own
 nested-sampling posterior (tests/golden/cfg1_oracle_posterior.csv), with its
@@ -54,6 +57,19 @@ def main():
     r = np.exp(lw - m)
     logz = m + math.log(r.mean())
     err = r.std(ddof=1) / math.sqrt(N) / r.mean()
+    ok = np.isfinite(lw)
+    ess = 1.0 / np.sum((r[ok] / r[ok].sum()) ** 2)
+    # draws below 1e-4 of the largest weight carry 3e-5 of the mass: not kept
+    ok &= r >= 1e-4
+    lwn = lw[ok] - math.log(N)  # normalised: logsumexp = log Z (up to the dropped mass)
+    with open(os.path.join(HERE, "cfg1_is_posterior.csv"), "w") as f:
+        f.write("# importance-sampled posterior, config 1 (H1, 4 s), oracle likelihood\n")
+        f.write(f"# logz={logz:.6f} logz_err={err:.6f} ess={ess:.1f} n_draws={N} kept={int(ok.sum())}\n")
+        f.write("mc,q,dl,tc,logl,logw\n")
+        for x, l in zip(S[ok], lwn):
+            t = th.copy()
+            t[slots] = x
+            f.write(",".join(f"{v:.10g}" for v in list(x) + [L.loglike(ev, t), l]) + "\n")
     with open(os.path.join(HERE, "cfg1_is_evidence.txt"), "w") as f:
         f.write("# exact log-evidence of config 1 (H1, 4 s) by importance sampling of the FP64 oracle\n")
         f.write(f"# draws={N} seed={SEED} proposal=multivariate-t(df=5, 4x posterior covariance)\n")

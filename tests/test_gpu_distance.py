@@ -101,7 +101,7 @@ def test_sampler_marginal_dead_points_distances_and_evidence(cfg1):
     params = _marg_params(wl, si.PRIOR_UNIFORM, 20.0, 200.0)
     evm = _event(ev, params)
     logz_true = float(open(os.path.join(HERE, "golden", "cfg1_is_evidence.txt")).readlines()[-1].split()[0])
-    post = os.path.join(HERE, "golden", "cfg1_oracle_posterior.csv")
+    post = os.path.join(HERE, "golden", "cfg1_is_posterior.csv")
     ref_logz = float(open(post).readlines()[1].split("logz=")[1].split()[0])
     ref = np.loadtxt(post, delimiter=",", comments="#", skiprows=3)
     zs = []

@@ -8,7 +8,7 @@
   sampling of the oracle's heterodyned likelihood, tests/golden/
   make_het_is_evidence.py; mean of four seeds, as in the full-grid test, since
   5 slice steps per dimension leave single runs scattered by ~1 nat), and the
-  marginals against the oracle's full-grid nested-sampling posterior by a
+  marginals against the importance-sampled full-grid posterior by a
   weighted two-sample KS test.
 """
 import math
@@ -71,7 +71,7 @@ def test_het_posterior_and_evidence(cfg1):
     wl, ev, th = cfg1
     rows = [l.split() for l in open(os.path.join(HERE, "golden", "cfg3_het_is_evidence.txt")) if not l.startswith("#")]
     logz_true = {r[0]: float(r[1]) for r in rows}["geometric"]
-    post = os.path.join(HERE, "golden", "cfg1_oracle_posterior.csv")
+    post = os.path.join(HERE, "golden", "cfg1_is_posterior.csv")
     ref_logz = float(open(post).readlines()[1].split("logz=")[1].split()[0])
     ref = np.loadtxt(post, delimiter=",", comments="#", skiprows=3)
     zs = []

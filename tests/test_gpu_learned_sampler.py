@@ -55,7 +55,7 @@ def test_learned_dead_points_match_oracle_and_are_deterministic(cfg1):
 def test_learned_posterior_and_evidence(cfg1):
     isf = os.path.join(HERE, "golden", "cfg1_is_evidence.txt")
     logz_true = float(open(isf).readlines()[-1].split()[0])
-    post = os.path.join(HERE, "golden", "cfg1_oracle_posterior.csv")
+    post = os.path.join(HERE, "golden", "cfg1_is_posterior.csv")
     ref_logz = float(open(post).readlines()[1].split("logz=")[1].split()[0])
     ref = np.loadtxt(post, delimiter=",", comments="#", skiprows=3)
     wl, ev, th = cfg1

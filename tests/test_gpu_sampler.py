@@ -4,8 +4,10 @@
   versions of the 4 s workload (independent of any nested-sampling code).
 * Sampled dead points: the logL the sampler reports equals the oracle's logL of
   the reported parameters (full-size 128 s, three-detector workload included).
-* Posterior agreement with the oracle's own nested-sampling run (stored by
-  tests/golden/make_ns_reference.py): log Z within combined error, weighted KS.
+* Posterior agreement with the importance-sampled posterior of the oracle
+  likelihood (independent exactly weighted draws, stored by
+  tests/golden/make_is_evidence.py): log Z within the measured scatter,
+  weighted KS.
 * Determinism for a fixed seed; bounded waits return SWIG_E_TIMEOUT and leave
   the context usable.
 """
@@ -134,9 +136,10 @@ def test_posterior_and_evidence_against_oracle(cfg1):
     seeds within three standard errors of the run-to-run scatter measured for
     this configuration (0.36 nat per run over eight seeds; the per-run estimate
     sqrt(H/m) is 0.22), each run within three times that scatter.  The
-    posterior is compared with the oracle's own run by a weighted two-sample KS
-    test per parameter (Kish effective sizes)."""
-    post = os.path.join(HERE, "golden", "cfg1_oracle_posterior.csv")
+    posterior is compared with the importance-sampled posterior of the oracle
+    likelihood by a weighted two-sample KS test per parameter (Kish effective
+    sizes)."""
+    post = os.path.join(HERE, "golden", "cfg1_is_posterior.csv")
     isf = os.path.join(HERE, "golden", "cfg1_is_evidence.txt")
     logz_true = float(open(isf).readlines()[-1].split()[0])
     head = open(post).readlines()[1]
