@@ -278,10 +278,13 @@ int swig_set_wait_limit(swig_ctx* ctx, long long spins);
  * and out[21] the number of retrainings; out[22..24] for the first CTA's
  * sweep warps: (chain, slice) units evaluated, clock cycles spent in them and
  * cycles spent polling for work.  Then, for each CTA s of the last run's
- * persistent kernel (full-grid sampler; zeros elsewhere), out[25 + 4 s ..
- * 25 + 4 s + 3]: its sweep warps' units, their cycles in units and polling,
- * and its control warp's cycles advancing chains.  Writes min(n, 25 + 4 x
- * CTAs) values. */
+ * persistent kernel (single-event sampler), out[25 + 4 s .. 25 + 4 s + 3]:
+ * its sweep warps' units, their cycles in units and polling, and its control
+ * warp's cycles advancing chains.  In the heterodyned sampler a unit is one
+ * contraction of a chain's proposal by the whole CTA (bin pass, time pass,
+ * reductions), and the polling cycles are those the contracting warps wait
+ * for the control warp (control and epilogue).  Writes min(n, 25 + 4 x CTAs)
+ * values. */
 int swig_get_profile(swig_ctx* ctx, double* out, int n);
 /* Use `stream` (a cudaStream_t on the context's device, owned by the caller)
  * for all later work of this context; NULL restores a private stream. */

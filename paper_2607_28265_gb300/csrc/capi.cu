@@ -220,6 +220,9 @@ void free_problem(DeviceBuffers& B) {
   dfree(B.het_edge_basis);
   dfree(B.het_edge_f);
   dfree(B.het_inv_width);
+  dfree(B.het_chunk);
+  dfree(B.het_dfe);
+  B.het_nc = 0;
   dfree(B.het_coef);
   dfree(B.het_coefB);
   dfree(B.het_fid);
@@ -549,6 +552,58 @@ int prepare_het(swig_ctx* c) {
     }
     split_df(fe, &ef[q], &ef[ne + q]);
   }
+  // chunk anchor tables (kernels.h HetChunkRow): chunk q holds edges
+  // 31 q .. 31 q + 31, anchored at its first edge
+  const int nc = (nb + 30) / 31;
+  std::vector<float> ct((size_t)HC_ROWS * nc, 0.0f), dfe((size_t)nc * kHetChunkEdges, 0.0f);
+  {
+    double cmax[NBASIS];
+    coefficient_bounds(c, cmax);
+    const int order = kTaylorDeg + 1;
+    double fact = 1.0;
+    for (int i = 2; i <= order; ++i) fact *= i;
+    const double eps = 1e-7;  // cycles: Taylor remainder of the phase difference
+    for (int q = 0; q < nc; ++q) {
+      const int e0 = 31 * q, e1 = std::min(31 * q + 31, nb);
+      const double fa = f[idx[e0]], fb = f[idx[e1]], span = fb - fa;
+      auto put = [&](int row, double v) { ct[(size_t)row * nc + q] = (float)v; };
+      float hi, lo;
+      split_df(fa, &hi, &lo);
+      put(HC_FA_HI, hi);
+      put(HC_FA_LO, lo);
+      put(HC_INV_S, span > 0.0 ? 1.0 / span : 0.0);
+      // |c - c0| <= 2 cmax over the prior box
+      double R = 0.0;
+      for (int j = 0; j < NBASIS - 1; ++j)
+        R += 2.0 * cmax[j] * basis_derivative_bound(kBasisPow[j], kBasisLog[j], order, fa, fb);
+      R *= std::pow(span, order) / fact;
+      put(HC_EXACT, R > eps ? 1.0 : 0.0);
+      for (int j = 0; j < NBASIS; ++j) {
+        const bool one = j == B_ONE;
+        split_df(one ? 1.0 : basis_derivative(kBasisPow[j], kBasisLog[j], 0, fa), &hi, &lo);
+        put(HC_VAL_HI + j, hi);
+        put(HC_VAL_LO + j, lo);
+        split_df(one ? 0.0 : basis_derivative(kBasisPow[j], kBasisLog[j], 1, fa) * span, &hi, &lo);
+        put(HC_D1_HI + j, hi);
+        put(HC_D1_LO + j, lo);
+        double nf = 1.0;
+        for (int m = 0; m < kNumPoly; ++m) {
+          const int nn = m + 2;
+          nf *= nn;
+          put(HC_POLY + m * NBASIS + j,
+              one ? 0.0 : basis_derivative(kBasisPow[j], kBasisLog[j], nn, fa) * std::pow(span, nn) / nf);
+        }
+      }
+      for (int l = 0; l < kHetChunkEdges && e0 + l <= nb; ++l) dfe[(size_t)q * kHetChunkEdges + l] = (float)(f[idx[e0 + l]] - fa);
+    }
+  }
+  CUDA_TRY(c, cudaMalloc(&B.het_chunk, sizeof(float) * ct.size()));
+  CUDA_TRY(c, cudaMalloc(&B.het_dfe, sizeof(float) * dfe.size()));
+  CUDA_TRY(c, cudaMemcpy(B.het_chunk, ct.data(), sizeof(float) * ct.size(), cudaMemcpyHostToDevice));
+  CUDA_TRY(c, cudaMemcpy(B.het_dfe, dfe.data(), sizeof(float) * dfe.size(), cudaMemcpyHostToDevice));
+  c->h2d_bytes += sizeof(float) * (ct.size() + dfe.size());
+  B.het_nc = nc;
+  for (int i = 0; i < n_det; ++i) L.het_fid_iden[i] = 1.0 / (fid.cre[i] * fid.cre[i] + fid.cim[i] * fid.cim[i]);
   CUDA_TRY(c, cudaMalloc(&B.het_edge_basis, sizeof(float) * eb.size()));
   CUDA_TRY(c, cudaMalloc(&B.het_edge_f, sizeof(float) * ef.size()));
   CUDA_TRY(c, cudaMalloc(&B.het_inv_width, sizeof(float) * inv_w.size()));

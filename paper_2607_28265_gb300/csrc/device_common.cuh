@@ -79,6 +79,14 @@ __device__ __forceinline__ float df_frac(dfl a) {
   return __fadd_rn(__fsub_rn(a.hi, n), a.lo);  // a.hi - n is exact
 }
 
+// Round to the nearest integer on the FP32 add pipe: adding and subtracting
+// 1.5 * 2^23 leaves the nearest integer for |v| < 2^22 (ties to even, as
+// rintf), without occupying the SFU/conversion pipe that the sine and cosine
+// need.
+__device__ __forceinline__ float round_nearest(float v) {
+  return __fsub_rn(__fadd_rn(v, 12582912.0f), 12582912.0f);
+}
+
 __device__ __forceinline__ dfl df_from_double(double x) {
   float h = __double2float_rn(x);
   float l = __double2float_rn(x - (double)h);
@@ -108,8 +116,10 @@ __host__ __device__ inline MassTerms taylorf2_mass_terms(double mc, double q) {
   t.eta = t.m1 * t.m2;                        // q / (1 + q)^2
   const double inv_eta = opq * opq * inv_q;   // 1 / eta
   t.A = (3.0 / (256.0 * kPi)) * inv_eta;      // 3 / (128 eta) in cycles
-  // ln(pi M) = ln(pi T_sun Mc) - (3/5) ln eta;  r = (pi M)^(1/3)
-  t.lpm = log(kPi * kMtsunS * mc) + 0.6 * log(inv_eta);
+  // ln(pi M) = ln(pi T_sun Mc) - (3/5) ln eta = ln((pi T_sun Mc)^5 / eta^3) / 5
+  // (one logarithm);  r = (pi M)^(1/3)
+  const double x = kPi * kMtsunS * mc, x2 = x * x;
+  t.lpm = 0.2 * log(x2 * x2 * x * (inv_eta * inv_eta * inv_eta));
   t.r = exp(t.lpm * (1.0 / 3.0));
   t.ir = 1.0 / t.r;
   return t;
@@ -431,10 +441,9 @@ __device__ inline void setup_projection_det(const LikeConst& L, const double* th
   }
 }
 
-__device__ inline void setup_delay_det(const LikeConst& L, const double* th, int i, EvalRecord* rec) {
-  double sl, cl, sd, cd;
-  sincos(th[9] - L.gmst, &sl, &cl);
-  sincos(th[10], &sd, &cd);
+// Detector i's delay from the sines and cosines of (RA - GMST) and Dec.
+__device__ inline void setup_delay_det_sc(const LikeConst& L, const double* th, int i, double sl, double cl,
+                                          double sd, double cd, EvalRecord* rec) {
   const double n0 = cd * cl * (-1.0 / kCSI), n1 = cd * sl * (-1.0 / kCSI), n2 = sd * (-1.0 / kCSI);
   const double gd = (n0 * L.vertex[i][0] + n1 * L.vertex[i][1] + n2 * L.vertex[i][2]);
   const double tau = th[11] + gd;
@@ -443,6 +452,13 @@ __device__ inline void setup_delay_det(const LikeConst& L, const double* th, int
   dfl tv = df_from_double(tau);
   rec->tau_hi[i] = tv.hi;
   rec->tau_lo[i] = tv.lo;
+}
+
+__device__ inline void setup_delay_det(const LikeConst& L, const double* th, int i, EvalRecord* rec) {
+  double sl, cl, sd, cd;
+  sincos(th[9] - L.gmst, &sl, &cl);
+  sincos(th[10], &sd, &cd);
+  setup_delay_det_sc(L, th, i, sl, cl, sd, cd, rec);
 }
 
 // A move of t_c alone: the record's geocentric delay of detector i is kept,

@@ -43,6 +43,10 @@ struct HetTables {
   const float* nu_wt;
   const float* nu_corr;
   const float2* nu_tw;
+  // chunk anchors (kernels.h HetChunkRow)
+  int n_chunks;
+  const float* chunk;  // [HC_ROWS][n_chunks]
+  const float* dfe;    // [n_chunks][32]
 };
 
 __host__ __device__ inline HetTables het_tables(const DeviceBuffers& B) {
@@ -61,6 +65,9 @@ __host__ __device__ inline HetTables het_tables(const DeviceBuffers& B) {
   H.nu_wt = B.het_nu_wt;
   H.nu_corr = B.het_nu_corr;
   H.nu_tw = B.het_nu_tw;
+  H.n_chunks = B.het_nc;
+  H.chunk = B.het_chunk;
+  H.dfe = B.het_dfe;
   return H;
 }
 
@@ -74,17 +81,49 @@ struct HetPrep {
 };
 
 template <int NDET>
-__device__ inline void het_prepare(const HetTables& H, const EvalRecord& r, HetPrep<NDET>& p) {
+__device__ inline void het_prepare(const LikeConst& L, const HetTables& H, const EvalRecord& r, HetPrep<NDET>& p) {
   const EvalRecord& f0 = *H.fid;
 #pragma unroll
   for (int j = 0; j < NBASIS; ++j) p.dc[j] = df_from_double(r.c[j] - f0.c[j]);
 #pragma unroll
   for (int i = 0; i < NDET; ++i) {
     p.dtau[i] = df_from_double(r.tau[i] - f0.tau[i]);
-    const double den = f0.cre[i] * f0.cre[i] + f0.cim[i] * f0.cim[i];
-    p.rho_re[i] = (float)((r.cre[i] * f0.cre[i] + r.cim[i] * f0.cim[i]) / den);
-    p.rho_im[i] = (float)((r.cim[i] * f0.cre[i] - r.cre[i] * f0.cim[i]) / den);
+    const double iden = L.het_fid_iden[i];
+    p.rho_re[i] = (float)((r.cre[i] * f0.cre[i] + r.cim[i] * f0.cim[i]) * iden);
+    p.rho_im[i] = (float)((r.cim[i] * f0.cre[i] - r.cre[i] * f0.cim[i]) * iden);
   }
+}
+
+// Anchor of chunk q for one evaluation (one thread per chunk; rows of the
+// chunk table are read coalesced across threads): the phase difference
+// dP(f) = sum_j (c_j - c0_j) phi_j(f) at the chunk's first edge f_a in
+// double-float, its scaled derivatives a_1 (double-float sum, stored FP32)
+// and a_2..a_6 (FP32), and per detector frac(dP(f_a) + f_a dtau_i).
+template <int NDET>
+__device__ inline void het_anchor(const HetTables& H, const HetPrep<NDET>& p, int q, float* out) {
+  const int nc = H.n_chunks;
+  const float* T = H.chunk + q;
+  auto row = [&](int r) { return __ldg(T + (size_t)r * nc); };
+  dfl A = {0.0f, 0.0f}, S = {0.0f, 0.0f};
+  float a[kNumPoly];
+#pragma unroll
+  for (int n = 0; n < kNumPoly; ++n) a[n] = 0.0f;
+#pragma unroll
+  for (int j = 0; j < NBASIS; ++j) {
+    const dfl c = p.dc[j];
+    A = df_add(A, df_mul(c, dfl{row(HC_VAL_HI + j), row(HC_VAL_LO + j)}));
+    S = df_add(S, df_mul(c, dfl{row(HC_D1_HI + j), row(HC_D1_LO + j)}));
+#pragma unroll
+    for (int n = 0; n < kNumPoly; ++n) a[n] = fmaf(c.hi, row(HC_POLY + n * NBASIS + j), a[n]);
+  }
+  out[0] = S.hi + S.lo;
+#pragma unroll
+  for (int n = 0; n < kNumPoly; ++n) out[1 + n] = a[n];
+  const dfl fa = {row(HC_FA_HI), row(HC_FA_LO)};
+#pragma unroll
+  for (int i = 0; i < NDET; ++i) out[kHetAncPhase + i] = df_frac(df_add(A, df_mul(fa, p.dtau[i])));
+  out[kHetAncInvS] = row(HC_INV_S);
+  out[kHetAncExact] = row(HC_EXACT);
 }
 
 // Bins [base, base + 31) of the contraction, accumulated into the lane's
@@ -142,6 +181,149 @@ __device__ inline void het_chunk(const HetTables& H, const HetPrep<NDET>& p, int
       zr[i] += a.x * r0r - a.y * r0i + a.z * r1r - a.w * r1i;
       zi[i] += a.x * r0i + a.y * r0r + a.z * r1i + a.w * r1r;
       hh[i] += bb.x * (r0r * r0r + r0i * r0i) + 2.0f * bb.y * (r0r * r1r + r0i * r1i);
+    }
+  }
+}
+
+// Per-lane table data of one chunk step: edge offset, bin width and summary
+// data of the lane's bin (all loads issued together, ahead of the phase
+// arithmetic).
+template <int NDET>
+struct HetBinData {
+  float d, iw;
+  float4 a[NDET];
+  float2 bb[NDET];
+};
+
+template <int NDET>
+__device__ __forceinline__ void het_load_bins(const HetTables& H, int q, int lane, HetBinData<NDET>& t) {
+  const int e = 31 * q + lane, b = e;
+  t.d = e <= H.n_bins ? __ldg(H.dfe + (size_t)q * kHetChunkEdges + lane) : 0.0f;
+  const bool has_bin = lane < 31 && b < H.n_bins;
+  t.iw = has_bin ? __ldg(H.inv_width + b) : 0.0f;
+#pragma unroll
+  for (int i = 0; i < NDET; ++i) {
+    t.a[i] = has_bin ? __ldg(H.coef + (size_t)i * H.n_bins + b) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    t.bb[i] = has_bin ? __ldg(H.coefB + (size_t)i * H.n_bins + b) : make_float2(0.0f, 0.0f);
+  }
+}
+
+// het_chunk with the phase from chunk q's anchor `anc` (het_anchor) and the
+// lane's table data t (het_load_bins): lane l holds edge 31 q + l at
+// x = (f_e - f_a) / S, dP = sum_n a_n x^n (FP32 Horner),
+// phase_i = frac(anchor_i + dP + (f_e - f_a) dtau_i).
+template <int NDET, bool TM = false>
+__device__ inline void het_chunk_anc(const HetTables& H, const HetPrep<NDET>& p, const float* anc, int q, int lane,
+                                     const HetBinData<NDET>& t, float* zr, float* zi, float* hh,
+                                     float2* y = nullptr) {
+  const float twopi = 6.283185307179586f;
+  const int base = 31 * q, e = base + lane;
+  float er[NDET], ei[NDET];
+  if (e <= H.n_bins) {
+    const float x = t.d * anc[kHetAncInvS];
+    float v = anc[kNumPoly];
+#pragma unroll
+    for (int n = kNumPoly - 1; n >= 0; --n) v = fmaf(v, x, anc[n]);
+    v *= x;
+#pragma unroll
+    for (int i = 0; i < NDET; ++i) {
+      float ph = anc[kHetAncPhase + i] + fmaf(t.d, p.dtau[i].hi, v);
+      ph -= round_nearest(ph);
+      float s, co;
+      __sincosf(twopi * ph, &s, &co);  // exp(-2 pi i ph) = co - i s
+      er[i] = p.rho_re[i] * co + p.rho_im[i] * s;
+      ei[i] = p.rho_im[i] * co - p.rho_re[i] * s;
+    }
+    if (TM && (lane < 31 || e == H.n_bins)) {
+      float yr = 0.0f, yi = 0.0f;
+      const size_t ne = (size_t)H.n_bins + 1;
+#pragma unroll
+      for (int i = 0; i < NDET; ++i) {
+        const float2 g = H.tm_g[(size_t)i * ne + e];
+        yr += g.x * er[i] - g.y * ei[i];
+        yi += g.x * ei[i] + g.y * er[i];
+      }
+      y[e] = make_float2(yr, yi);
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < NDET; ++i) er[i] = ei[i] = 0.0f;
+  }
+  const bool has_bin = lane < 31 && base + lane < H.n_bins;
+#pragma unroll
+  for (int i = 0; i < NDET; ++i) {
+    const float nr = __shfl_down_sync(0xffffffffu, er[i], 1);
+    const float ni = __shfl_down_sync(0xffffffffu, ei[i], 1);
+    if (has_bin) {
+      const float r0r = 0.5f * (er[i] + nr), r0i = 0.5f * (ei[i] + ni);
+      const float r1r = (nr - er[i]) * t.iw, r1i = (ni - ei[i]) * t.iw;
+      const float4 a = t.a[i];
+      const float2 bb = t.bb[i];
+      zr[i] += a.x * r0r - a.y * r0i + a.z * r1r - a.w * r1i;
+      zi[i] += a.x * r0i + a.y * r0r + a.z * r1i + a.w * r1r;
+      hh[i] += bb.x * (r0r * r0r + r0i * r0i) + 2.0f * bb.y * (r0r * r1r + r0i * r1i);
+    }
+  }
+}
+
+__device__ __forceinline__ void prefetch_l1(const void* p) { asm volatile("prefetch.global.L1 [%0];" ::"l"(p)); }
+
+// L1 prefetch of chunk q's table data (summary data, bin widths, edge
+// offsets; with TM the time-pass edge weights), one cache line per lane.
+// Every prefetched address lies inside the chunk's rows: line l of a row of
+// `bytes` bytes is prefetched at offset min(128 l, bytes - 1).
+template <int NDET, bool TM>
+__device__ __forceinline__ void het_prefetch_chunk(const HetTables& H, int q, int lane) {
+  const int b0 = 31 * q, nbin = min(31, H.n_bins - b0);
+  const size_t ne = (size_t)H.n_bins + 1;
+  constexpr int kA = 5 * NDET, kB = kA + 3 * NDET, kW = kB + 2, kD = kW + 1, kG = kD + (TM ? 3 * NDET : 0);
+  for (int k = lane; k < kG; k += 32) {
+    const char* base;
+    int bytes, l;
+    if (k < kA) {
+      base = reinterpret_cast<const char*>(H.coef + (size_t)(k / 5) * H.n_bins + b0);
+      bytes = 16 * nbin;
+      l = k % 5;
+    } else if (k < kB) {
+      base = reinterpret_cast<const char*>(H.coefB + (size_t)((k - kA) / 3) * H.n_bins + b0);
+      bytes = 8 * nbin;
+      l = (k - kA) % 3;
+    } else if (k < kW) {
+      base = reinterpret_cast<const char*>(H.inv_width + b0);
+      bytes = 4 * nbin;
+      l = k - kB;
+    } else if (k < kD) {
+      base = reinterpret_cast<const char*>(H.dfe + (size_t)q * kHetChunkEdges);
+      bytes = 4 * kHetChunkEdges;
+      l = 0;
+    } else {
+      const int edges = min(kHetChunkEdges, H.n_bins + 1 - b0);
+      base = reinterpret_cast<const char*>(H.tm_g + (size_t)((k - kD) / 3) * ne + b0);
+      bytes = 8 * edges;
+      l = (k - kD) % 3;
+    }
+    prefetch_l1(base + min(128 * l, bytes - 1));
+  }
+}
+
+// The chunks q = first, first + stride, ... of one evaluation by one warp:
+// anchored chunks (het_chunk_anc) with their table data prefetched into L1
+// two chunk steps ahead, exact chunks edge by edge (het_chunk).
+template <int NDET, bool TM = false>
+__device__ inline void het_chunks_warp(const HetTables& H, const HetPrep<NDET>& p, const float* s_anc, int first,
+                                       int stride, int lane, float* zr, float* zi, float* hh, float2* y = nullptr) {
+  const int nc = H.n_chunks;
+  if (first < nc) het_prefetch_chunk<NDET, TM>(H, first, lane);
+  if (first + stride < nc) het_prefetch_chunk<NDET, TM>(H, first + stride, lane);
+  for (int q = first; q < nc; q += stride) {
+    if (q + 2 * stride < nc) het_prefetch_chunk<NDET, TM>(H, q + 2 * stride, lane);
+    const float* an = s_anc + q * kHetAncStride;
+    if (an[kHetAncExact] != 0.0f) {
+      het_chunk<NDET, TM>(H, p, 31 * q, lane, zr, zi, hh, y);
+    } else {
+      HetBinData<NDET> t;
+      het_load_bins<NDET>(H, q, lane, t);
+      het_chunk_anc<NDET, TM>(H, p, an, q, lane, t, zr, zi, hh, y);
     }
   }
 }
@@ -409,9 +591,10 @@ __device__ inline void het_cache(const LikeConst& L, const EvalRecord& r, int i,
                                  double* kap2, double* vv) {
   const double cr = r.cre[i], ci = r.cim[i], c2 = cr * cr + ci * ci;
   if (c2 > 0.0) {
-    kap2[0] = (zr * cr + zi * ci) / c2 / L.inv_scale[i];
-    kap2[1] = (zi * cr - zr * ci) / c2 / L.inv_scale[i];
-    *vv = hh / c2 * L.amp1 * L.amp1;
+    const double ic2 = 1.0 / c2, k = ic2 / L.inv_scale[i];
+    kap2[0] = (zr * cr + zi * ci) * k;
+    kap2[1] = (zi * cr - zr * ci) * k;
+    *vv = hh * ic2 * (L.amp1 * L.amp1);
   } else {
     kap2[0] = kap2[1] = 0.0;
     *vv = 0.0;
@@ -431,7 +614,7 @@ __device__ inline double het_loglike_warp(const LikeConst& L, const HetTables& H
     return -INFINITY;
   }
   HetPrep<NDET> p;
-  het_prepare<NDET>(H, r, p);
+  het_prepare<NDET>(L, H, r, p);
   float zr[NDET], zi[NDET], hh[NDET];
 #pragma unroll
   for (int i = 0; i < NDET; ++i) zr[i] = zi[i] = hh[i] = 0.0f;

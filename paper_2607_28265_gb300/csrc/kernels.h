@@ -41,6 +41,36 @@ inline size_t het_tm_smem_bytes(int n_bins, int nufft_m = 0) {
   return (((size_t)n_bins + 1) * 2 * sizeof(float) + 15) / 16 * 16 + (size_t)nufft_m * 2 * sizeof(float);
 }
 
+// Heterodyned contraction by chunk anchors.  A warp step covers one chunk of
+// 32 edges (31 bins).  Per chunk the host tabulates, at its first edge f_a,
+// the basis values and first derivative (double-float) and the scaled
+// derivatives of orders 2..kTaylorDeg (float), as rows of a [HC_ROWS][chunks]
+// table; per evaluation the phase difference from the fiducial is anchored
+// there in double-float and carried across the chunk by an FP32 Taylor form
+// in x = (f_e - f_a) / S (S the chunk's span).  A chunk whose Taylor
+// remainder bound over the prior box exceeds the tolerance is flagged exact
+// and evaluated edge by edge in double-float.
+constexpr int kHetChunkEdges = 32;
+enum HetChunkRow {
+  HC_VAL_HI = 0,
+  HC_VAL_LO = NBASIS,
+  HC_D1_HI = 2 * NBASIS,
+  HC_D1_LO = 3 * NBASIS,
+  HC_POLY = 4 * NBASIS,  // HC_POLY + (n - 2) * NBASIS + j: phi_j^(n)(f_a) S^n / n!
+  HC_FA_HI = 4 * NBASIS + kNumPoly * NBASIS,
+  HC_FA_LO,
+  HC_INV_S,
+  HC_EXACT,
+  HC_ROWS
+};
+// Per-evaluation chunk anchor in shared memory: a_1 .. a_kTaylorDeg, then
+// frac(dP(f_a) + f_a dtau_i) per detector, 1 / S and the exact flag.
+constexpr int kHetAncStride = 12;
+constexpr int kHetAncPhase = kNumPoly + 1;
+constexpr int kHetAncInvS = kHetAncPhase + SWIG_MAX_DET;
+constexpr int kHetAncExact = kHetAncInvS + 1;
+static_assert(kHetAncExact < kHetAncStride, "chunk anchor layout");
+
 // Device buffers owned by a context (all allocated with cudaMalloc).
 struct DeviceBuffers {
   // problem data
@@ -64,6 +94,9 @@ struct DeviceBuffers {
   float* het_inv_width = nullptr;   // [N_b]
   float4* het_coef = nullptr;       // [n_det][N_b]
   float2* het_coefB = nullptr;      // [n_det][N_b]
+  int het_nc = 0;                   // chunks of kHetChunkEdges edges
+  float* het_chunk = nullptr;       // [HC_ROWS][het_nc] chunk anchor tables
+  float* het_dfe = nullptr;         // [het_nc][32] f_e - f_a of each chunk's edges
   EvalRecord* het_fid = nullptr;    // fiducial record
   // time marginalisation on the heterodyned bins (t_c marginalised)
   float2* het_tm_g = nullptr;       // [n_det][N_b + 1] edge weights: Z_i = sum_e g_ie r_i(e)

@@ -314,7 +314,7 @@ __global__ void __launch_bounds__(kHetTmThreads, 1)
     return;
   }
   HetPrep<NDET> p;
-  het_prepare<NDET>(H, r, p);
+  het_prepare<NDET>(L, H, r, p);
   float zr[NDET], zi[NDET], hh[NDET];
 #pragma unroll
   for (int i = 0; i < NDET; ++i) zr[i] = zi[i] = hh[i] = 0.0f;

@@ -118,6 +118,8 @@ struct SamplerConst {
   // chain's bracket uses request slot c, the right end slot nrep + c
   int par_out;
   int n_slots;    // request slots: nrep, or 2 nrep with par_out
+  int claim_off;  // byte offset (in the dynamic shared memory after the slice data) of the claim words
+                  // (heterodyned sampler: of the chunk anchors)
 };
 
 struct ChainState {
@@ -626,6 +628,17 @@ __device__ __noinline__ int chain_advance(const LikeConst& L, const SamplerConst
 __device__ __noinline__ void setup_record_warp(const LikeConst& L, const double* th, int fl, bool f32,
                                                EvalRecord* rec, int lane) {
   const bool valid = rec->valid != 0;
+  // a sky move: the two FP64 sines/cosines of the delays on lanes 0 and 1 at
+  // once (one call's latency), shared with the delay lanes
+  double sl = 0.0, cl = 0.0, sd = 0.0, cd = 0.0;
+  if (valid && (fl & BF_SKY)) {  // warp-uniform
+    double sv, cv;
+    sincos((lane & 1) ? th[10] : th[9] - L.gmst, &sv, &cv);
+    sl = __shfl_sync(0xffffffffu, sv, 0);
+    cl = __shfl_sync(0xffffffffu, cv, 0);
+    sd = __shfl_sync(0xffffffffu, sv, 1);
+    cd = __shfl_sync(0xffffffffu, cv, 1);
+  }
   if (valid) {
     if (lane == 0) {
       if (fl & BF_INTR)
@@ -643,7 +656,7 @@ __device__ __noinline__ void setup_record_warp(const LikeConst& L, const double*
       if (fl & BF_PROJ) setup_projection_det(L, th, lane - 2, f32, rec);
     } else if (lane >= 8 && lane < 8 + L.n_det) {
       if (fl & BF_SKY)
-        setup_delay_det(L, th, lane - 8, rec);
+        setup_delay_det_sc(L, th, lane - 8, sl, cl, sd, cd, rec);
       else if (fl & BF_TAU)
         setup_tc_det(th, lane - 8, rec);
     }
@@ -1462,7 +1475,7 @@ __device__ __forceinline__ void wc_publish(const LikeConst& L, const SamplerCons
 // chain is done), CTL_AGAIN (projection-only budget used up: call again) or
 // CTL_EVAL (HET: record set up, evaluate it).
 template <int NDET, bool HET>
-__device__ __noinline__ int control_step_warp(const LikeConst& L, const SamplerConst& S, const DeviceBuffers& B,
+__device__ __forceinline__ int control_step_warp(const LikeConst& L, const SamplerConst& S, const DeviceBuffers& B,
                                  const SamplerPtrs& P, int c, ChainState& ch, EvalRecord& rx, int lane,
                                  double het_ly = 0.0, double het_kap = 0.0, double het_vv = 0.0) {
   NSGlobal* g = P.g;
@@ -1478,19 +1491,22 @@ __device__ __noinline__ int control_step_warp(const LikeConst& L, const SamplerC
   WarpChain w;
   wc_load(ch, w, lane);
   int pend = ch.pending;
-  if (pend && w.phase == PH_OUT) {
-    // the ends whose requests have finished: extend while inside the slice
-    for (int sd = 0; sd < 2; ++sd) {
-      if (!((pend >> sd) & 1)) continue;
-      const int slot = sd ? S.nrep + c : c;
+  // finished requests (one call site for the result, to keep the inlined
+  // control small): an end of a two-ended step-out, or the chain's proposal
+  for (int sd = 0; sd < 2; ++sd) {
+    if (!((pend >> sd) & 1)) continue;
+    const int slot = sd ? S.nrep + c : c;
+    if (w.phase == PH_OUT) {
       int fin = 0;
       if (lane == 0) fin = ld_acquire(&P.done_cnt[slot]) >= target;
       if (!__shfl_sync(kFull, fin, 0)) continue;
-      double kapc, ly;
-      wc_result<NDET>(L, S, B, slot, lane, kapc, ly);
-      pend &= ~(1 << sd);
-      ++w.n_full;
-      ++w.n_evals;
+    }
+    double kapc = het_kap, ly = het_ly;
+    if (!HET) wc_result<NDET>(L, S, B, slot, lane, kapc, ly);
+    pend &= ~(1 << sd);
+    ++w.n_full;
+    ++w.n_evals;
+    if (w.phase == PH_OUT) {  // extend this end while inside the slice
       const bool ok = ly > logl_star;
       if (sd == 0) {
         if (ok) w.lo -= 1.0;
@@ -1499,14 +1515,7 @@ __device__ __noinline__ int control_step_warp(const LikeConst& L, const SamplerC
         if (ok) w.hi += 1.0;
         if (!ok || ++w.n_out_r >= kMaxStepOut) w.side &= ~2;
       }
-    }
-  } else if (pend) {
-    double kapc = het_kap, ly = het_ly;
-    if (!HET) wc_result<NDET>(L, S, B, c, lane, kapc, ly);
-    pend = 0;
-    ++w.n_full;
-    ++w.n_evals;
-    if (wc_apply(S, w, ly, logl_star, g, lane)) {
+    } else if (wc_apply(S, w, ly, logl_star, g, lane)) {
       w.x = w.y;
       w.th = w.thy;
       w.lx = ly;
@@ -1526,49 +1535,46 @@ __device__ __noinline__ int control_step_warp(const LikeConst& L, const SamplerC
   int status = CTL_WAIT;
   for (int guard = 0; guard < 1 << 20 && !w.done; ++guard) {
     const int b = w.block;
+    int sd = 0;  // PH_OUT: the end to issue next (0 left, 1 right)
     if (w.phase == PH_OUT) {
-      // issue the ends that are still stepping and have no request in flight
-      for (int sd = 0; sd < 2; ++sd) {
-        if (!((w.side >> sd) & 1) || ((pend >> sd) & 1)) continue;
-        if (!wc_proposal(S, w, b, sd ? w.hi : w.lo, lane)) {
-          w.side &= ~(1 << sd);  // this end left the unit cube
-          continue;
-        }
-        wc_publish<false>(L, S, B, P, sd ? S.nrep + c : c, b, ch, rx, w, lane);
-        pend |= 1 << sd;
-        if (prof) cnt_setup += 1;
-      }
-      if (pend) break;  // wait for the requests in flight
-      if (w.side == 0) {  // both ends done: shrink
-        w.phase = PH_SHRINK;
+      sd = ((w.side & 1) && !(pend & 1)) ? 0 : ((w.side & 2) && !(pend & 2)) ? 1 : -1;
+      if (sd < 0) {
+        if (pend) break;  // wait for the requests in flight
+        w.phase = PH_SHRINK;  // both ends done
         w.n_shrink = 0;
+        continue;
       }
-      continue;
-    }
-    if (S.block_free[b] && free_left <= 0) {  // resume next round
-      status = CTL_AGAIN;
-      break;
-    }
-    if (w.phase == PH_NEW) {
-      wc_start_step(S, w, P.chol, P.learn_out, c, it, lane);
-      if (prof) {
-        const long long t2 = clock64();
-        acc_step += t2 - tk;
-        cnt_step += 1;
-        tk = t2;
+    } else {
+      if (S.block_free[b] && free_left <= 0) {  // resume next round
+        status = CTL_AGAIN;
+        break;
       }
-      continue;
+      if (w.phase == PH_NEW) {
+        wc_start_step(S, w, P.chol, P.learn_out, c, it, lane);
+        if (prof) {
+          const long long t2 = clock64();
+          acc_step += t2 - tk;
+          cnt_step += 1;
+          tk = t2;
+        }
+        continue;
+      }
     }
     double t;
-    if (w.phase == PH_LEFT)
+    if (w.phase == PH_OUT)
+      t = sd ? w.hi : w.lo;
+    else if (w.phase == PH_LEFT)
       t = w.lo;
     else if (w.phase == PH_RIGHT)
       t = w.hi;
     else
       t = w.lo + (w.hi - w.lo) * wc_uniform(S, w, c, it);
-    w.t = t;
-    if (!wc_proposal(S, w, b, t, lane)) {
-      wc_apply(S, w, -INFINITY, logl_star, g, lane);
+    if (w.phase != PH_OUT) w.t = t;
+    if (!wc_proposal(S, w, b, t, lane)) {  // outside the unit cube
+      if (w.phase == PH_OUT)
+        w.side &= ~(1 << sd);
+      else
+        wc_apply(S, w, -INFINITY, logl_star, g, lane);
       continue;
     }
     if (prof) {
@@ -1576,7 +1582,7 @@ __device__ __noinline__ int control_step_warp(const LikeConst& L, const SamplerC
       acc_prop += t2 - tk;
       tk = t2;
     }
-    if (S.block_free[b]) {
+    if (w.phase != PH_OUT && S.block_free[b]) {
       --free_left;
       ++w.n_evals;
       const double ly = wc_free_loglike<NDET, HET>(L, w, lane);
@@ -1595,14 +1601,17 @@ __device__ __noinline__ int control_step_warp(const LikeConst& L, const SamplerC
       }
       continue;
     }
-    // a full evaluation: published as the chain's next request (slot c)
-    wc_publish<HET>(L, S, B, P, c, b, ch, rx, w, lane);
-    pend = 1;
-    if (HET) status = CTL_EVAL;
+    // a full evaluation: published as a request (slot c, or nrep + c for the
+    // right end of a two-ended step-out)
+    wc_publish<HET>(L, S, B, P, sd == 1 ? S.nrep + c : c, b, ch, rx, w, lane);
+    pend |= sd == 1 ? 2 : 1;
     if (prof) {
       acc_setup += clock64() - tk;
       cnt_setup += 1;
+      tk = clock64();
     }
+    if (w.phase == PH_OUT) continue;  // the other end may go out too
+    if (HET) status = CTL_EVAL;
     break;
   }
   if (lane == 0) {
@@ -1634,7 +1643,6 @@ template <int NDET, bool MIXED>
 __global__ void __launch_bounds__(kFlowThreads, 1)
     k_ns_flow(LikeConst L, SamplerConst S, DeviceBuffers B, SamplerPtrs P) {
   extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ int s_claim[2 * kMaxChains];  // per request slot
   const int slice = blockIdx.x;
   const int b0 = B.slice_begin[slice], b1 = B.slice_begin[slice + 1];
   const int nb = b1 - b0;
@@ -1666,6 +1674,7 @@ __global__ void __launch_bounds__(kFlowThreads, 1)
   __syncthreads();
   unsigned char* dyn = smem + fixed_bytes;  // per-warp records, or sort buffers (boundary)
   EvalRecord* rec = reinterpret_cast<EvalRecord*>(dyn) + warp;
+  int* s_claim = reinterpret_cast<int*>(dyn + S.claim_off);  // per request slot: units this CTA has taken
   float* const arow = MIXED ? s_anc + (size_t)warp * S.max_tiles_slice * kAnchorStride : nullptr;
   const int G = S.flow_parts;
   const int target = S.n_ctas * G;  // units per request: G parts of every slice
@@ -2060,15 +2069,16 @@ __global__ void __launch_bounds__(kFlowThreads, 1)
 // boundaries) and the warps then share the time grid's 32-node chunks
 // (het.cuh tm_pass); there are no projection-only blocks in that mode.
 template <int NDET>
-__device__ __forceinline__ void het_prepare_warp(const HetTables& H, const EvalRecord& r, HetPrep<NDET>& p, int lane) {
+__device__ __forceinline__ void het_prepare_warp(const LikeConst& L, const HetTables& H, const EvalRecord& r,
+                                                 HetPrep<NDET>& p, int lane) {
   const EvalRecord& f0 = *H.fid;
   if (lane < NBASIS) p.dc[lane] = df_from_double(r.c[lane] - f0.c[lane]);
   if (lane >= 16 && lane < 16 + NDET) {
     const int i = lane - 16;
     p.dtau[i] = df_from_double(r.tau[i] - f0.tau[i]);
-    const double den = f0.cre[i] * f0.cre[i] + f0.cim[i] * f0.cim[i];
-    p.rho_re[i] = (float)((r.cre[i] * f0.cre[i] + r.cim[i] * f0.cim[i]) / den);
-    p.rho_im[i] = (float)((r.cim[i] * f0.cre[i] - r.cre[i] * f0.cim[i]) / den);
+    const double iden = L.het_fid_iden[i];
+    p.rho_re[i] = (float)((r.cre[i] * f0.cre[i] + r.cim[i] * f0.cim[i]) * iden);
+    p.rho_im[i] = (float)((r.cim[i] * f0.cre[i] - r.cre[i] * f0.cim[i]) * iden);
   }
   __syncwarp();
 }
@@ -2088,8 +2098,16 @@ __global__ void __launch_bounds__(kHetThreads, 1)
   const int nc = het_chunks(H.n_bins);
   ChainState& ch = *reinterpret_cast<ChainState*>(smem + S.ctl_off);
   EvalRecord& rx = *reinterpret_cast<EvalRecord*>(smem + S.ctl_off + sizeof(ChainState));
+  float* s_anc = reinterpret_cast<float*>(smem + S.claim_off);  // [chunks][kHetAncStride]
   const bool timer = blockIdx.x == 0 && threadIdx.x == 0;
   unsigned long long t0 = gtimer(), t1;
+  // per-CTA cycle counters: contractions, cycles in them (bin pass, time
+  // pass, reductions), cycles the other warps wait on warp 0 (control,
+  // epilogue), and warp 0's cycles in control
+  // (shared memory, one writer each: warp 1's lane 0 and warp 0's lane 0)
+  __shared__ unsigned long long s_prof[5];
+  if (threadIdx.x < 5) s_prof[threadIdx.x] = 0;
+  const bool t_sw = warp == 1 && lane == 0, t_ct = warp == 0 && lane == 0;
   for (;;) {
     if (!grid_sync(g, S.n_ctas, S.spin_limit)) return;
     if (timer) {
@@ -2113,13 +2131,21 @@ __global__ void __launch_bounds__(kHetThreads, 1)
         warp_copy_cg(&ch, &P.chains[c], sizeof(ChainState), lane);
         warp_copy_cg(&rx, &P.recx[c], sizeof(EvalRecord), lane);
       }
+      if (t_sw) s_prof[4] = clock64();
       for (long long guard = 0; guard < (1ll << 24); ++guard) {
         if (warp == 0) {
+          const long long tc = clock64();
           const int st = control_step_warp<NDET, true>(L, S, B, P, c, ch, rx, lane, ly, kapc, vvc);
-          if (st == CTL_EVAL) het_prepare_warp<NDET>(H, B.rec[c], s_prep, lane);
+          if (st == CTL_EVAL) het_prepare_warp<NDET>(L, H, B.rec[c], s_prep, lane);
           if (lane == 0) s_st = st;
+          if (t_ct) s_prof[3] += clock64() - tc;
         }
         __syncthreads();
+        if (t_sw) {
+          const unsigned long long tu = clock64();
+          s_prof[2] += tu - s_prof[4];
+          s_prof[4] = tu;
+        }
         const int st = s_st;
         if (st == CTL_WAIT) break;    // the chain is done
         if (st == CTL_AGAIN) continue;  // projection-only budget used up
@@ -2128,14 +2154,15 @@ __global__ void __launch_bounds__(kHetThreads, 1)
         float zr[NDET], zi[NDET], hh[NDET];
 #pragma unroll
         for (int i = 0; i < NDET; ++i) zr[i] = zi[i] = hh[i] = 0.0f;
-        if (valid) {
-          const HetPrep<NDET> p = s_prep;
-          if (L.tm_n > 0) {
-            float2* y = reinterpret_cast<float2*>(smem);
-            for (int q = warp; q < nc; q += n_warps) het_chunk<NDET, true>(H, p, 31 * q, lane, zr, zi, hh, y);
-          } else {
-            for (int q = warp; q < nc; q += n_warps) het_chunk<NDET>(H, p, 31 * q, lane, zr, zi, hh);
-          }
+        if (valid) {  // block-uniform
+          const HetPrep<NDET>& p = s_prep;  // read from shared memory where used
+          // chunk anchors, one thread per chunk, then the edge pass
+          for (int q = threadIdx.x; q < nc; q += blockDim.x) het_anchor<NDET>(H, p, q, s_anc + q * kHetAncStride);
+          __syncthreads();
+          if (L.tm_n > 0)
+            het_chunks_warp<NDET, true>(H, p, s_anc, warp, n_warps, lane, zr, zi, hh, reinterpret_cast<float2*>(smem));
+          else
+            het_chunks_warp<NDET>(H, p, s_anc, warp, n_warps, lane, zr, zi, hh);
           het_warp_reduce<NDET>(zr, zi, hh);
         }
         if (lane == 0) {
@@ -2159,6 +2186,12 @@ __global__ void __launch_bounds__(kHetThreads, 1)
             s_tm[warp][1] = ws;
           }
           __syncthreads();
+        }
+        if (t_sw) {
+          const unsigned long long tw = clock64();
+          s_prof[0] += 1;
+          s_prof[1] += tw - s_prof[4];
+          s_prof[4] = tw;
         }
         if (warp == 0) {
           // lane i < NDET: detector i's sums over the warps in warp order
@@ -2197,6 +2230,18 @@ __global__ void __launch_bounds__(kHetThreads, 1)
       }
       if (warp == 0) warp_copy(&P.chains[c], &ch, sizeof(ChainState), lane);
       __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+      if (blockIdx.x == 0) {
+        g->f_units += s_prof[0];
+        g->f_unit_cyc += s_prof[1];
+        g->f_idle_cyc += s_prof[2];
+      }
+      if (P.cta_prof) {
+        unsigned long long* cp = P.cta_prof + 4 * (size_t)blockIdx.x;
+        for (int j = 0; j < 4; ++j) cp[j] += s_prof[j];
+      }
+      for (int j = 0; j < 4; ++j) s_prof[j] = 0;
     }
     if (timer) {
       t1 = gtimer();
@@ -2512,7 +2557,10 @@ int run_setup(swig_ctx* c, RunState& R) {
   S.ctl_off = (int)(((het ? het_scratch : std::max(rec_bytes, sort_bytes)) + 15) & ~(size_t)15);
   R.tail = std::max(rec_bytes, sort_bytes);
   const size_t ctl_bytes = (size_t)S.ctl_slots * (sizeof(ChainState) + sizeof(EvalRecord));
-  R.smem = het ? S.ctl_off + ctl_bytes : fixed + flow_tiles + S.ctl_off + ctl_bytes;
+  S.claim_off = (int)((S.ctl_off + ctl_bytes + 15) & ~(size_t)15);
+  // (heterodyned: the per-evaluation chunk anchors at claim_off)
+  R.smem = het ? S.claim_off + sizeof(float) * kHetAncStride * (size_t)c->B.het_nc
+               : fixed + flow_tiles + S.claim_off + sizeof(int) * (size_t)S.n_slots;
   if (R.smem > 220 * 1024) return fail(c, SWIG_E_ARG, "problem too large for the persistent kernel's shared memory");
 
   // buffers

@@ -46,13 +46,6 @@ __device__ inline void compute_anchor(int n_det, const TileInfo& ti, const TileB
   }
 }
 
-// Round to the nearest integer on the FP32 add pipe: adding and subtracting
-// 1.5 * 2^23 leaves the nearest integer for |v| < 2^22 (ties to even, as
-// rintf), without occupying the SFU/conversion pipe that the sine and cosine
-// need.
-__device__ __forceinline__ float round_nearest(float v) {
-  return __fsub_rn(__fadd_rn(v, 12582912.0f), 12582912.0f);
-}
 
 // Anchors of (theta, tile) held in registers by a lane; reloaded only when the
 // lane crosses into the next tile (once per tile for tiles of >= 32 bins).

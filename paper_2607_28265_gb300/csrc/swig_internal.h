@@ -110,6 +110,8 @@ struct LikeConst {
   // of the reference shift tm_dref = tm_t0 + j0 tm_dt
   int tm_M, tm_j0;
   double tm_dref;
+  // heterodyned likelihood: 1 / |C0_i|^2 of the fiducial's projection factors
+  double het_fid_iden[SWIG_MAX_DET];
 };
 
 }  // namespace swig

@@ -12,12 +12,15 @@ Run as a module it executes one small case for a profiler capture::
     python -m paper_2607_28265_gb300.workloads het --batch 1000 --bins 1000
     python -m paper_2607_28265_gb300.workloads sampler-het --max-iter 2 --bins 5000
     python -m paper_2607_28265_gb300.workloads sampler-het --max-iter 2 --bins 5000 --tmarg-nodes 2000
+    python -m paper_2607_28265_gb300.workloads learned --max-iter 2
 
 ``sampler``: the persistent nested-sampling kernel on the 128 s H1/L1/V1
 workload for --max-iter outer iterations (one launch); ``loglike``: one batch
 of the full-grid mixed-precision likelihood; ``het``: one batch of the
 heterodyned likelihood; ``sampler-het``: the heterodyned persistent sampler
-kernel (fiducial at the injection).  ``--tmarg-nodes N`` marginalises t_c over
+kernel (fiducial at the injection); ``learned``: the learned-proposal sampler
+(its first training of the network, then the persistent kernel).
+``--tmarg-nodes N`` marginalises t_c over
 its prior on N grid nodes in the heterodyned cases.  Each case exits non-zero
 on any library error.
 """
@@ -70,7 +73,7 @@ def _prior_draws(ctx, params, n, seed):
 
 def main(argv=None):
     ap = argparse.ArgumentParser(description="small profiling cases on the 128 s three-detector workload")
-    ap.add_argument("case", choices=["sampler", "sampler-het", "loglike", "het"])
+    ap.add_argument("case", choices=["sampler", "sampler-het", "loglike", "het", "learned"])
     ap.add_argument("--max-iter", type=int, default=2)
     ap.add_argument("--batch", type=int, default=1000)
     ap.add_argument("--bins", type=int, default=1000)
@@ -90,6 +93,13 @@ def main(argv=None):
         for _ in range(a.repeat):
             r = ctx.run()
         print(f"sampler: n_iter={r.n_iter} n_evals={r.n_evals} logz={r.logz:.3f}")
+    elif a.case == "learned":
+        ctx.set_sampler(nlive=wl.nlive, nrep=wl.nrep, sweeps=wl.sweeps, steps_per_dim=wl.steps_per_dim,
+                        seed=wl.sampler_seed, precision=swig.PREC_MIXED, max_iter=a.max_iter,
+                        proposal=swig.PROPOSAL_LEARNED, learn_mix=1.0, learn_interval=32, learn_steps=30)
+        for _ in range(a.repeat):
+            r = ctx.run()
+        print(f"learned: n_iter={r.n_iter} n_evals={r.n_evals} logz={r.logz:.3f}")
     elif a.case == "sampler-het":
         ctx.set_sampler(nlive=wl.nlive, nrep=wl.nrep, sweeps=wl.sweeps, steps_per_dim=wl.steps_per_dim,
                         seed=wl.sampler_seed, likelihood=swig.LIKE_HET, het_bins=a.bins, het_fiducial=th,

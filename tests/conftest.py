@@ -11,3 +11,24 @@ if ROOT not in sys.path:
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA device (sm_103a) and the built library")
     config.addinivalue_line("markers", "slow: long-running CPU test")
+
+
+def pytest_terminal_summary(terminalreporter, exitstatus, config):
+    import json
+
+    try:
+        import parity
+    except ImportError:
+        return
+    if not parity.RECORDS:
+        return
+    terminalreporter.write_sep("-", "parity against the oracle (largest error per check)")
+    for r in parity.RECORDS:
+        terminalreporter.write_line(
+            f"{r['name']:<58} n={r['n']:<6} max|err|={r['max_abs']:.3e} max rel={r['max_rel']:.3e} "
+            f"err/tol={r['max_frac_of_tol']:.3f}")
+    path = os.environ.get("SWIG_PARITY_REPORT")
+    if path:
+        with open(path, "w") as f:
+            for r in parity.RECORDS:
+                f.write(json.dumps(r) + "\n")

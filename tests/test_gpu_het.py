@@ -11,6 +11,7 @@ holds with margin (the constant -<d|d>/2 is FP64 on both sides).
 import numpy as np
 import pytest
 
+import parity
 import swig_inputs as si
 from oracle import events
 from oracle import likelihood as L
@@ -65,7 +66,7 @@ def test_het_matches_oracle_cfg1(cfg1, n_bins):
     thetas = _thetas(wl, ev, th, 40, n_bins, 0.002)
     got = ctx.loglike_batch(thetas)
     want = np.array([L.het_loglike(ev, het, t) for t in thetas])
-    assert np.all(np.abs(got - want) <= _tol(want)), np.max(np.abs(got - want))
+    parity.check(f"heterodyned batch (4 s H1, {n_bins} bins)", got, want, 1e-6, 2e-4)
     # at the fiducial itself the heterodyned logL is the full logL up to the
     # FP32 contraction (r = 1 exactly in every bin)
     full = L.loglike(ev, th)
@@ -85,7 +86,7 @@ def test_het_geometric_spacing_and_fiducial_offset(cfg1):
     thetas = _thetas(wl, ev, th, 30, 99, 0.003)
     got = ctx.loglike_batch(thetas)
     want = np.array([L.het_loglike(ev, het, t) for t in thetas])
-    assert np.all(np.abs(got - want) <= _tol(want)), np.max(np.abs(got - want))
+    parity.check("heterodyned batch (4 s H1, geometric, offset fiducial)", got, want, 1e-6, 2e-4)
     ctx.close()
 
 
@@ -100,12 +101,12 @@ def test_het_full_size_three_detectors():
     thetas = _thetas(wl, ev, th, 24, 5, 0.0005)
     got = ctx.loglike_batch(thetas)
     want = np.array([L.het_loglike(ev, het, t) for t in thetas])
-    assert np.all(np.abs(got - want) <= _tol(want)), np.max(np.abs(got - want))
+    parity.check("heterodyned batch (128 s HLV, 5000 bins)", got, want, 1e-6, 2e-4)
     # switching back to the full likelihood re-prepares the context
     ctx.set_sampler(nlive=1000, nrep=100, likelihood=swig.LIKE_FULL)
     full = ctx.loglike_batch(thetas[-4:])
     want_full = np.array([L.loglike(ev, t) for t in thetas[-4:]])
-    assert np.all(np.abs(full - want_full) <= 1e-6 * np.abs(want_full) + 1e-4)
+    parity.check("full-grid batch beside the heterodyned one (128 s HLV)", full, want_full, 1e-6, 1e-4)
     ctx.close()
 
 

@@ -15,6 +15,7 @@ alternate along every chain.
 import numpy as np
 import pytest
 
+import parity
 import swig_inputs as si
 from oracle import events, pp
 from oracle import likelihood as L
@@ -27,9 +28,8 @@ NB = 5000
 ITERS = 40
 
 
-def _tol(want):
-    # the heterodyned parity bound of tests/test_gpu_het.py (FP32 contraction)
-    return 1e-6 * np.abs(want) + 2e-4
+# Parity bound: that of tests/test_gpu_het.py (FP32 contraction), 1e-6
+# relative plus 2e-4 absolute.
 
 
 @pytest.fixture(scope="module")
@@ -61,5 +61,4 @@ def test_full_size_het_dead_points_match_oracle(cfg2, cache_off):
     idx = np.concatenate([rng.choice(len(ll) - 1000, 6, replace=False),
                           len(ll) - 1000 + rng.choice(1000, 10, replace=False)])
     want = np.array([L.het_loglike(ev, het, thd[i]) for i in idx])
-    err = np.abs(ll[idx] - want)
-    assert np.all(err <= _tol(want)), (err.max(), want[np.argmax(err)])
+    parity.check(f"heterodyned sampler dead points (128 s HLV, cache_off={cache_off})", ll[idx], want, 1e-6, 2e-4)

@@ -17,6 +17,7 @@ import os
 import numpy as np
 import pytest
 
+import parity
 import swig_inputs as si
 from oracle import events, pp
 from oracle import likelihood as L
@@ -29,8 +30,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 NB = 450
 
 
-def _tol(want):
-    return 1e-6 * np.abs(want) + 2e-4
+# Parity bound: that of tests/test_gpu_het.py, 1e-6 relative plus 2e-4 absolute.
 
 
 @pytest.fixture(scope="module")
@@ -59,7 +59,7 @@ def test_het_dead_points_match_oracle_and_are_deterministic(cfg1, spacing):
     assert abs(m + math.log(np.sum(np.exp(lw - m))) - r.logz) < 1e-9
     idx = np.linspace(0, len(ll) - 1, 24).astype(int)
     want = np.array([L.het_loglike(ev, het, thd[i]) for i in idx])
-    assert np.all(np.abs(ll[idx] - want) <= _tol(want)), np.max(np.abs(ll[idx] - want))
+    parity.check(f"heterodyned sampler dead points (4 s H1, spacing {spacing})", ll[idx], want, 1e-6, 2e-4)
     r2 = ctx.run()
     thd2, ll2, _ = ctx.get_samples()
     assert r2.logz == r.logz and np.array_equal(ll, ll2) and np.array_equal(thd, thd2)

@@ -8,6 +8,7 @@ import os
 import numpy as np
 import pytest
 
+import parity
 import swig_inputs as si
 from oracle import events, pp
 from oracle import likelihood as L
@@ -45,7 +46,7 @@ def test_learned_dead_points_match_oracle_and_are_deterministic(cfg1):
     assert abs(m + math.log(np.sum(np.exp(lw - m))) - r.logz) < 1e-9
     idx = np.linspace(0, len(ll) - 1, 16).astype(int)
     want = np.array([L.loglike(ev, thd[i]) for i in idx])
-    assert np.all(np.abs(ll[idx] - want) <= 1e-6 * np.abs(want) + 1e-6)
+    parity.check("learned-proposal sampler dead points (4 s H1)", ll[idx], want, 1e-6, 1e-6)
     r2 = ctx.run()
     thd2, ll2, _ = ctx.get_samples()
     assert r2.logz == r.logz and np.array_equal(ll, ll2) and np.array_equal(thd, thd2)

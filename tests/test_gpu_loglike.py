@@ -11,6 +11,7 @@ import math
 import numpy as np
 import pytest
 
+import parity
 import swig_inputs as si
 from oracle import events, physics
 from oracle import likelihood as L
@@ -20,8 +21,7 @@ pytestmark = pytest.mark.gpu
 swig = pytest.importorskip("paper_2607_28265_gb300.swig")
 
 
-def _tol(want):
-    return 1e-6 * np.abs(want) + 1e-6
+# Parity bound: |dlogL| <= 1e-6 |logL| + 1e-6.
 
 
 def _thetas(wl, th_inj, n_prior, n_near, seed):
@@ -73,8 +73,8 @@ def test_cfg1_parity(cfg1, precision):
     thetas = _thetas(wl, th, 48, 48, seed=5)
     got = ctx.loglike_batch(thetas)
     want = np.array([L.loglike(ev, t) for t in thetas])
-    err = np.abs(got - want)
-    assert np.all(err <= _tol(want)), f"max err {err.max():.3e}"
+    err = parity.check(f"full-grid batch (4 s H1, {'fp64' if precision == swig.PREC_FP64 else 'mixed'})", got, want,
+                       1e-6, 1e-6)
     if precision == swig.PREC_FP64:
         assert err.max() < 1e-7
 
@@ -87,8 +87,7 @@ def test_cfg2_full_size_parity(cfg2):
     thetas = _thetas(wl, th, 12, 12, seed=6)
     got = ctx.loglike_batch(thetas)
     want = np.array([L.loglike(ev, t) for t in thetas])
-    err = np.abs(got - want)
-    assert np.all(err <= _tol(want)), f"max err {err.max():.3e}"
+    err = parity.check("full-grid batch (128 s HLV, mixed, prior and near-peak draws)", got, want, 1e-6, 1e-6)
     # the stated bound is 0.78 here (|logL| ~ 7.8e5 from -<d|d>/2); the error
     # on the log-likelihood ratio logL + <d|d>/2 (|.| up to SNR^2 / 2 ~ 300)
     # is what the mixed path controls: FP32 sweep and epilogue, measured
@@ -114,7 +113,7 @@ def test_ragged_multi_tile_grid_two_detectors():
         ctx = swig.context_for_workload(wl, ev.data, ev.psds, ev.gmst)
         ctx.set_sampler(nlive=50, nrep=5, precision=prec)
         got = ctx.loglike_batch(thetas)
-        assert np.all(np.abs(got - want) <= _tol(want)), (prec, np.abs(got - want).max())
+        parity.check(f"full-grid batch (ragged two-detector grid, {prec})", got, want, 1e-6, 1e-6)
 
 
 def test_invalid_theta_empty_batch_and_determinism(cfg1):
@@ -145,7 +144,7 @@ def test_large_batch_is_split_consistently(cfg1):
     assert np.allclose(big[4090:4110], small, rtol=1e-8, atol=1e-4)
     idx = [0, 4095, 4096, 4999]
     want = np.array([L.loglike(ev, thetas[i]) for i in idx])
-    assert np.all(np.abs(big[idx] - want) <= _tol(want))
+    parity.check("full-grid batch (4 s H1, split batch of 10000)", big[idx], want, 1e-6, 1e-6)
 
 
 def test_device_pointer_entry_point(cfg1):

@@ -19,6 +19,7 @@ import pytest
 from scipy import integrate
 from scipy.special import roots_legendre
 
+import parity
 import swig_inputs as si
 from oracle import events, physics, pp
 from oracle import likelihood as L
@@ -30,8 +31,7 @@ swig = pytest.importorskip("paper_2607_28265_gb300.swig")
 HERE = os.path.dirname(os.path.abspath(__file__))
 
 
-def _tol(want):
-    return 1e-6 * np.abs(want) + 1e-6
+# Parity bound of the dead points: |dlogL| <= 1e-6 |logL| + 1e-6.
 
 
 def _fix_all_but(wl, keep, th):
@@ -122,7 +122,7 @@ def test_dead_points_match_oracle_and_runs_are_deterministic(cfg1):
         assert abs(m + math.log(np.sum(np.exp(lw - m))) - r.logz) < 1e-9
         idx = np.linspace(0, len(ll) - 1, 16).astype(int)
         want = np.array([L.loglike(ev, thd[i]) for i in idx])
-        assert np.all(np.abs(ll[idx] - want) <= _tol(want)), prec
+        parity.check(f"sampler dead points (4 s H1, {prec})", ll[idx], want, 1e-6, 1e-6)
         r2 = ctx.run()
         thd2, ll2, lw2 = ctx.get_samples()
         assert r2.logz == r.logz and np.array_equal(ll, ll2) and np.array_equal(thd, thd2)
@@ -173,7 +173,7 @@ def test_full_size_dead_points_match_oracle():
     assert r.n_iter >= 8
     idx = np.random.default_rng(0).choice(len(ll), 8, replace=False)
     want = np.array([L.loglike(ev, thd[i]) for i in idx])
-    assert np.all(np.abs(ll[idx] - want) <= _tol(want))
+    parity.check("sampler dead points (128 s HLV, mixed)", ll[idx], want, 1e-6, 1e-6)
     ctx.close()
 
 
@@ -214,6 +214,6 @@ def test_unblocked_and_multi_sweep_variants(cfg1, variant):
         if seed == 31:
             idx = np.linspace(0, len(ll) - 1, 8).astype(int)
             want = np.array([L.loglike(ev, thd[i]) for i in idx])
-            assert np.all(np.abs(ll[idx] - want) <= _tol(want))
+            parity.check(f"sampler dead points (4 s H1, {variant})", ll[idx], want, 1e-6, 1e-6)
         ctx.close()
     assert abs(np.mean(zs) - logz_true) < 2.0, (zs, logz_true)

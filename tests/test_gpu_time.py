@@ -21,6 +21,7 @@ import os
 import numpy as np
 import pytest
 
+import parity
 import swig_inputs as si
 from oracle import events, physics
 from oracle import likelihood as L
@@ -34,8 +35,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 TC = si.IDX["tc"]
 
 
-def _tol(want):
-    return 1e-6 * np.abs(want) + 2e-4
+# Parity bound: that of the heterodyned likelihood, 1e-6 relative plus 2e-4
+# absolute.
 
 
 def _tm_params(wl, lo=-0.1, hi=0.1, phase_marg=False):
@@ -93,7 +94,7 @@ def test_batched_time_marginal_matches_oracle_cfg1(cfg1, nt, phase_marg):
     thetas = _thetas(params, th, 10, nt, 0.002)
     got = ctx.loglike_batch(thetas)
     want = np.array([L.het_loglike_time_marg(evt, het, t, nt) for t in thetas])
-    assert np.all(np.abs(got - want) <= _tol(want)), np.max(np.abs(got - want))
+    parity.check(f"time-marginal batch (4 s H1, {nt} nodes, phase_marg={phase_marg})", got, want, 1e-6, 2e-4)
     # theta[tc] is ignored
     t2 = thetas.copy()
     t2[:, TC] = 0.05
@@ -113,7 +114,7 @@ def test_batched_time_marginal_full_size_three_detectors():
     thetas = _thetas(params, th, 1, 3, 0.0003)
     got = ctx.loglike_batch(thetas)
     want = np.array([L.het_loglike_time_marg(evt, het, t, 2000) for t in thetas])
-    assert np.all(np.abs(got - want) <= _tol(want)), np.max(np.abs(got - want))
+    parity.check("time-marginal batch (128 s HLV)", got, want, 1e-6, 2e-4)
     ctx.close()
 
 
@@ -157,7 +158,7 @@ def test_sampler_dead_points_time_draws_and_evidence(cfg1):
         if seed == 51:
             idx = np.linspace(0, len(ll) - 1, 8).astype(int)
             want = np.array([L.het_loglike_time_marg(evt, het, thd[i], nt) for i in idx])
-            assert np.all(np.abs(ll[idx] - want) <= _tol(want)), np.max(np.abs(ll[idx] - want))
+            parity.check("time-marginal sampler dead points (4 s H1)", ll[idx], want, 1e-6, 2e-4)
             grid = L.time_grid(params, nt)
             for i in idx:
                 q = _philox_uniform(int(i), seed)
