@@ -49,9 +49,9 @@ SFU_OPS_PER_CLK_SM = 16   # sin/cos results per clock per SM (sm_100-class SFU),
 SFU_OPS_PER_BIN_DET = 2   # one sine and one cosine per bin and detector
 # DRAM bytes (read + write) per logL evaluation inside k_ns_flow (512
 # threads), from one ncu capture of a 2-iteration launch of the 128 s workload
-# (9.45 MB + 1.27 MB over 107,944 evaluations; profiles/
+# (10.03 MB + 0.31 MB over 107,944 evaluations; profiles/
 # k_ns_flow_cfg2_hlv_128s_2iter.md), scaled to a full launch by its evaluations.
-TRAFFIC_B_PER_EVAL = (9.448448e6 + 1.269760e6) / 107944
+TRAFFIC_B_PER_EVAL = (10.032128e6 + 0.309504e6) / 107944
 METRIC = "logL evals/s (128 s 3-det BNS) and wall-s/posterior, plain vs learned+mixed"
 
 # workload name -> (event, sampler options, description)

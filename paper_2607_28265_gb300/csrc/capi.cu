@@ -233,6 +233,8 @@ void free_problem(DeviceBuffers& B) {
   dfree(B.het_nu_wt);
   dfree(B.het_nu_corr);
   dfree(B.het_nu_tw);
+  dfree(B.het_nu_heavy);
+  B.het_nu_nheavy = 0;
   B.het_nb = 0;
 }
 
@@ -380,7 +382,7 @@ void het_summary(const std::vector<double>& f, const std::vector<int>& idx, int 
 // A1.im) per detector and bin, and the rotation exp(-2 pi i f_e dt) of each
 // edge per grid step.  f[idx[q]] is the frequency of edge q.
 void het_tm_tables(const std::vector<double>& a01, const std::vector<double>& f, const std::vector<int>& idx,
-                   int nb, int n_det, double dt, std::vector<float2>& g, std::vector<float2>& w) {
+                   int nb, int n_det, double dt, std::vector<float2>& g, std::vector<float2>& w, double dref = 0.0) {
   const size_t ne = (size_t)nb + 1;
   g.assign((size_t)n_det * ne, make_float2(0.0f, 0.0f));
   w.assign(ne, make_float2(0.0f, 0.0f));
@@ -398,6 +400,14 @@ void het_tm_tables(const std::vector<double>& a01, const std::vector<double>& f,
         const double iw = 1.0 / (f[idx[q]] - f[idx[q - 1]]);
         gr += 0.5 * a[0] + a[2] * iw;
         gi += 0.5 * a[1] + a[3] * iw;
+      }
+      if (dref != 0.0) {  // times exp(-2 pi i f_e dref), the non-uniform FFT's reference rotation
+        double ph = f[idx[q]] * dref;
+        ph -= std::nearbyint(ph);
+        const double cr = std::cos(2.0 * kPi * ph), ci = -std::sin(2.0 * kPi * ph);
+        const double tr = gr * cr - gi * ci;
+        gi = gr * ci + gi * cr;
+        gr = tr;
       }
       g[(size_t)i * ne + q] = make_float2((float)gr, (float)gi);
     }
@@ -557,12 +567,9 @@ int prepare_het(swig_ctx* c) {
   const int nc = (nb + 30) / 31;
   std::vector<float> ct((size_t)HC_ROWS * nc, 0.0f), dfe((size_t)nc * kHetChunkEdges, 0.0f);
   {
-    double cmax[NBASIS];
-    coefficient_bounds(c, cmax);
     const int order = kTaylorDeg + 1;
     double fact = 1.0;
     for (int i = 2; i <= order; ++i) fact *= i;
-    const double eps = 1e-7;  // cycles: Taylor remainder of the phase difference
     for (int q = 0; q < nc; ++q) {
       const int e0 = 31 * q, e1 = std::min(31 * q + 31, nb);
       const double fa = f[idx[e0]], fb = f[idx[e1]], span = fb - fa;
@@ -572,14 +579,11 @@ int prepare_het(swig_ctx* c) {
       put(HC_FA_HI, hi);
       put(HC_FA_LO, lo);
       put(HC_INV_S, span > 0.0 ? 1.0 / span : 0.0);
-      // |c - c0| <= 2 cmax over the prior box
-      double R = 0.0;
-      for (int j = 0; j < NBASIS - 1; ++j)
-        R += 2.0 * cmax[j] * basis_derivative_bound(kBasisPow[j], kBasisLog[j], order, fa, fb);
-      R *= std::pow(span, order) / fact;
-      put(HC_EXACT, R > eps ? 1.0 : 0.0);
       for (int j = 0; j < NBASIS; ++j) {
         const bool one = j == B_ONE;
+        // remainder bound per unit |c_j - c0_j| (the device sums it per evaluation)
+        put(HC_BND + j,
+            one ? 0.0 : basis_derivative_bound(kBasisPow[j], kBasisLog[j], order, fa, fb) * std::pow(span, order) / fact);
         split_df(one ? 1.0 : basis_derivative(kBasisPow[j], kBasisLog[j], 0, fa), &hi, &lo);
         put(HC_VAL_HI + j, hi);
         put(HC_VAL_LO + j, lo);
@@ -618,7 +622,6 @@ int prepare_het(swig_ctx* c) {
                   sizeof(float2) * coefB.size();
   if (L.tm_n > 0) {
     std::vector<float2> g, w;
-    het_tm_tables(a01, f, idx, nb, n_det, L.tm_dt, g, w);
     L.tm_M = 0;
     std::vector<int> ptr, edge;
     std::vector<float> wt, corr;
@@ -630,7 +633,18 @@ int prepare_het(swig_ctx* c) {
       L.tm_dref = L.tm_t0 + (double)L.tm_j0 * L.tm_dt;
       if (ptr.empty()) L.tm_M = 0;
     }
+    // with the non-uniform FFT the edge weights carry the reference rotation,
+    // so the bin pass stores c_e = y_e exp(-2 pi i f_e dt_ref) directly
+    het_tm_tables(a01, f, idx, nb, n_det, L.tm_dt, g, w, L.tm_M > 0 ? L.tm_dref : 0.0);
     if (L.tm_M > 0) {
+      std::vector<int> heavy;
+      for (int l = 0; l < L.tm_M; ++l)
+        if (ptr[l + 1] - ptr[l] > kNufftHeavy) heavy.push_back(l);
+      B.het_nu_nheavy = (int)heavy.size();
+      CUDA_TRY(c, cudaMalloc(&B.het_nu_heavy, sizeof(int) * std::max<size_t>(1, heavy.size())));
+      if (!heavy.empty())
+        CUDA_TRY(c, cudaMemcpy(B.het_nu_heavy, heavy.data(), sizeof(int) * heavy.size(), cudaMemcpyHostToDevice));
+      c->h2d_bytes += sizeof(int) * heavy.size();
       CUDA_TRY(c, cudaMalloc(&B.het_nu_ptr, sizeof(int) * ptr.size()));
       CUDA_TRY(c, cudaMalloc(&B.het_nu_edge, sizeof(int) * std::max<size_t>(1, edge.size())));
       CUDA_TRY(c, cudaMalloc(&B.het_nu_wt, sizeof(float) * std::max<size_t>(1, wt.size())));

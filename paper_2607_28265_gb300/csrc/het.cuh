@@ -43,6 +43,8 @@ struct HetTables {
   const float* nu_wt;
   const float* nu_corr;
   const float2* nu_tw;
+  const int* nu_heavy;
+  int nu_nheavy;
   // chunk anchors (kernels.h HetChunkRow)
   int n_chunks;
   const float* chunk;  // [HC_ROWS][n_chunks]
@@ -65,6 +67,8 @@ __host__ __device__ inline HetTables het_tables(const DeviceBuffers& B) {
   H.nu_wt = B.het_nu_wt;
   H.nu_corr = B.het_nu_corr;
   H.nu_tw = B.het_nu_tw;
+  H.nu_heavy = B.het_nu_heavy;
+  H.nu_nheavy = B.het_nu_nheavy;
   H.n_chunks = B.het_nc;
   H.chunk = B.het_chunk;
   H.dfe = B.het_dfe;
@@ -98,19 +102,22 @@ __device__ inline void het_prepare(const LikeConst& L, const HetTables& H, const
 // chunk table are read coalesced across threads): the phase difference
 // dP(f) = sum_j (c_j - c0_j) phi_j(f) at the chunk's first edge f_a in
 // double-float, its scaled derivatives a_1 (double-float sum, stored FP32)
-// and a_2..a_6 (FP32), and per detector frac(dP(f_a) + f_a dtau_i).
+// and a_2..a_6 (FP32), per detector frac(dP(f_a) + f_a dtau_i), and whether
+// this evaluation's Taylor remainder bound sum_j |c_j - c0_j| HC_BND_j
+// exceeds kHetTaylorEps (then the chunk is taken edge by edge).
 template <int NDET>
 __device__ inline void het_anchor(const HetTables& H, const HetPrep<NDET>& p, int q, float* out) {
   const int nc = H.n_chunks;
   const float* T = H.chunk + q;
   auto row = [&](int r) { return __ldg(T + (size_t)r * nc); };
   dfl A = {0.0f, 0.0f}, S = {0.0f, 0.0f};
-  float a[kNumPoly];
+  float a[kNumPoly], R = 0.0f;
 #pragma unroll
   for (int n = 0; n < kNumPoly; ++n) a[n] = 0.0f;
 #pragma unroll
   for (int j = 0; j < NBASIS; ++j) {
     const dfl c = p.dc[j];
+    R = fmaf(fabsf(c.hi), row(HC_BND + j), R);
     A = df_add(A, df_mul(c, dfl{row(HC_VAL_HI + j), row(HC_VAL_LO + j)}));
     S = df_add(S, df_mul(c, dfl{row(HC_D1_HI + j), row(HC_D1_LO + j)}));
 #pragma unroll
@@ -123,7 +130,7 @@ __device__ inline void het_anchor(const HetTables& H, const HetPrep<NDET>& p, in
 #pragma unroll
   for (int i = 0; i < NDET; ++i) out[kHetAncPhase + i] = df_frac(df_add(A, df_mul(fa, p.dtau[i])));
   out[kHetAncInvS] = row(HC_INV_S);
-  out[kHetAncExact] = row(HC_EXACT);
+  out[kHetAncExact] = R > kHetTaylorEps ? 1.0f : 0.0f;
 }
 
 // Bins [base, base + 31) of the contraction, accumulated into the lane's
@@ -186,8 +193,7 @@ __device__ inline void het_chunk(const HetTables& H, const HetPrep<NDET>& p, int
 }
 
 // Per-lane table data of one chunk step: edge offset, bin width and summary
-// data of the lane's bin (all loads issued together, ahead of the phase
-// arithmetic).
+// data of the lane's bin.
 template <int NDET>
 struct HetBinData {
   float d, iw;
@@ -195,21 +201,8 @@ struct HetBinData {
   float2 bb[NDET];
 };
 
-template <int NDET>
-__device__ __forceinline__ void het_load_bins(const HetTables& H, int q, int lane, HetBinData<NDET>& t) {
-  const int e = 31 * q + lane, b = e;
-  t.d = e <= H.n_bins ? __ldg(H.dfe + (size_t)q * kHetChunkEdges + lane) : 0.0f;
-  const bool has_bin = lane < 31 && b < H.n_bins;
-  t.iw = has_bin ? __ldg(H.inv_width + b) : 0.0f;
-#pragma unroll
-  for (int i = 0; i < NDET; ++i) {
-    t.a[i] = has_bin ? __ldg(H.coef + (size_t)i * H.n_bins + b) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-    t.bb[i] = has_bin ? __ldg(H.coefB + (size_t)i * H.n_bins + b) : make_float2(0.0f, 0.0f);
-  }
-}
-
 // het_chunk with the phase from chunk q's anchor `anc` (het_anchor) and the
-// lane's table data t (het_load_bins): lane l holds edge 31 q + l at
+// lane's table data t (het_read_stage): lane l holds edge 31 q + l at
 // x = (f_e - f_a) / S, dP = sum_n a_n x^n (FP32 Horner),
 // phase_i = frac(anchor_i + dP + (f_e - f_a) dtau_i).
 template <int NDET, bool TM = false>
@@ -266,66 +259,86 @@ __device__ inline void het_chunk_anc(const HetTables& H, const HetPrep<NDET>& p,
   }
 }
 
-__device__ __forceinline__ void prefetch_l1(const void* p) { asm volatile("prefetch.global.L1 [%0];" ::"l"(p)); }
+// Asynchronous global -> shared copies (cp.async, sm_80 and later): the
+// lane's own table entries of a chunk, waited for one chunk later.
+__device__ __forceinline__ unsigned smem_addr(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(smem_addr(dst)), "l"(src), "n"(BYTES) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
-// L1 prefetch of chunk q's table data (summary data, bin widths, edge
-// offsets; with TM the time-pass edge weights), one cache line per lane.
-// Every prefetched address lies inside the chunk's rows: line l of a row of
-// `bytes` bytes is prefetched at offset min(128 l, bytes - 1).
-template <int NDET, bool TM>
-__device__ __forceinline__ void het_prefetch_chunk(const HetTables& H, int q, int lane) {
-  const int b0 = 31 * q, nbin = min(31, H.n_bins - b0);
-  const size_t ne = (size_t)H.n_bins + 1;
-  constexpr int kA = 5 * NDET, kB = kA + 3 * NDET, kW = kB + 2, kD = kW + 1, kG = kD + (TM ? 3 * NDET : 0);
-  for (int k = lane; k < kG; k += 32) {
-    const char* base;
-    int bytes, l;
-    if (k < kA) {
-      base = reinterpret_cast<const char*>(H.coef + (size_t)(k / 5) * H.n_bins + b0);
-      bytes = 16 * nbin;
-      l = k % 5;
-    } else if (k < kB) {
-      base = reinterpret_cast<const char*>(H.coefB + (size_t)((k - kA) / 3) * H.n_bins + b0);
-      bytes = 8 * nbin;
-      l = (k - kA) % 3;
-    } else if (k < kW) {
-      base = reinterpret_cast<const char*>(H.inv_width + b0);
-      bytes = 4 * nbin;
-      l = k - kB;
-    } else if (k < kD) {
-      base = reinterpret_cast<const char*>(H.dfe + (size_t)q * kHetChunkEdges);
-      bytes = 4 * kHetChunkEdges;
-      l = 0;
-    } else {
-      const int edges = min(kHetChunkEdges, H.n_bins + 1 - b0);
-      base = reinterpret_cast<const char*>(H.tm_g + (size_t)((k - kD) / 3) * ne + b0);
-      bytes = 8 * edges;
-      l = (k - kD) % 3;
+// Layout of one stage (kernels.h het_stage_bytes): a[NDET][32] (float4),
+// bb[NDET][32] (float2), iw[32], d[32].
+template <int NDET>
+struct HetStage {
+  float4 a[NDET][32];
+  float2 bb[NDET][32];
+  float iw[32];
+  float d[32];
+};
+
+// Lane l copies the entries of its bin 31 q + l and edge 31 q + l (the
+// entries it reads itself, so no cross-lane ordering is needed).
+template <int NDET>
+__device__ __forceinline__ void het_stage_chunk(const HetTables& H, int q, int lane, HetStage<NDET>* st) {
+  const int b = 31 * q + lane;
+  if (lane < 31 && b < H.n_bins) {
+#pragma unroll
+    for (int i = 0; i < NDET; ++i) {
+      cp_async<16>(&st->a[i][lane], H.coef + (size_t)i * H.n_bins + b);
+      cp_async<8>(&st->bb[i][lane], H.coefB + (size_t)i * H.n_bins + b);
     }
-    prefetch_l1(base + min(128 * l, bytes - 1));
+    cp_async<4>(&st->iw[lane], H.inv_width + b);
+  }
+  if (b <= H.n_bins) cp_async<4>(&st->d[lane], H.dfe + (size_t)q * kHetChunkEdges + lane);
+}
+
+template <int NDET>
+__device__ __forceinline__ void het_read_stage(const HetTables& H, int q, int lane, const HetStage<NDET>* st,
+                                               HetBinData<NDET>& t) {
+  const int b = 31 * q + lane;
+  const bool has_bin = lane < 31 && b < H.n_bins;
+  t.d = b <= H.n_bins ? st->d[lane] : 0.0f;
+  t.iw = has_bin ? st->iw[lane] : 0.0f;
+#pragma unroll
+  for (int i = 0; i < NDET; ++i) {
+    t.a[i] = has_bin ? st->a[i][lane] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    t.bb[i] = has_bin ? st->bb[i][lane] : make_float2(0.0f, 0.0f);
   }
 }
 
 // The chunks q = first, first + stride, ... of one evaluation by one warp:
-// anchored chunks (het_chunk_anc) with their table data prefetched into L1
-// two chunk steps ahead, exact chunks edge by edge (het_chunk).
+// anchored chunks (het_chunk_anc) read their table data from the warp's two
+// shared-memory stages (`stage`, 2 x het_stage_bytes), filled by cp.async one
+// chunk ahead; exact chunks go edge by edge (het_chunk) from global memory.
 template <int NDET, bool TM = false>
 __device__ inline void het_chunks_warp(const HetTables& H, const HetPrep<NDET>& p, const float* s_anc, int first,
-                                       int stride, int lane, float* zr, float* zi, float* hh, float2* y = nullptr) {
+                                       int stride, int lane, unsigned char* stage, float* zr, float* zi, float* hh,
+                                       float2* y = nullptr) {
   const int nc = H.n_chunks;
-  if (first < nc) het_prefetch_chunk<NDET, TM>(H, first, lane);
-  if (first + stride < nc) het_prefetch_chunk<NDET, TM>(H, first + stride, lane);
-  for (int q = first; q < nc; q += stride) {
-    if (q + 2 * stride < nc) het_prefetch_chunk<NDET, TM>(H, q + 2 * stride, lane);
+  HetStage<NDET>* st = reinterpret_cast<HetStage<NDET>*>(stage);
+  if (first < nc) het_stage_chunk<NDET>(H, first, lane, st);
+  cp_async_commit();
+  int buf = 0;
+  for (int q = first; q < nc; q += stride, buf ^= 1) {
+    if (q + stride < nc) het_stage_chunk<NDET>(H, q + stride, lane, st + (buf ^ 1));
+    cp_async_commit();
+    cp_async_wait<1>();  // this lane's copies of chunk q have landed
     const float* an = s_anc + q * kHetAncStride;
     if (an[kHetAncExact] != 0.0f) {
       het_chunk<NDET, TM>(H, p, 31 * q, lane, zr, zi, hh, y);
     } else {
       HetBinData<NDET> t;
-      het_load_bins<NDET>(H, q, lane, t);
+      het_read_stage<NDET>(H, q, lane, st + buf, t);
       het_chunk_anc<NDET, TM>(H, p, an, q, lane, t, zr, zi, hh, y);
     }
   }
+  cp_async_wait<0>();
 }
 
 // Warp-sum of the lane sums (all lanes receive them).
@@ -495,24 +508,20 @@ __device__ inline void tm_pass(const LikeConst& L, const HetTables& H, const flo
 // calls it (it synchronises the CTA).  Cost per evaluation ~W (N_b + 1)
 // multiply-adds for the gather and (M/2) log2 M butterflies, against
 // (N_b + 1) N_t terms for the direct sum.
-__device__ inline void tm_pass_nufft(const LikeConst& L, const HetTables& H, float2* y, float2* g, int warp,
-                                     int n_warps, int lane, float* ell, float& wm, float& ws) {
+__device__ inline void tm_pass_nufft(const LikeConst& L, const HetTables& H, const float2* y, float2* g,
+                                     const float2* tw, int warp, int n_warps, int lane, float* ell, float& wm,
+                                     float& ws) {
   const int tid = threadIdx.x, nt = blockDim.x;
-  const int ne = H.n_bins + 1, M = L.tm_M;
-  const dfl dref = df_from_double(L.tm_dref);
-  for (int e = tid; e < ne; e += nt) {
-    TmEdge d;
-    d.y = y[e];
-    d.f = {H.edge_f[e], H.edge_f[ne + e]};
-    y[e] = tm_start(d, dref);
-  }
-  __syncthreads();
+  const int M = L.tm_M;
+  // y holds c_e (the edge weights carry the reference rotation)
   const int lg = __ffs(M) - 1;
   for (int l = tid; l < M; l += nt) {
     // grid point l gathers the consecutive edges e0, e0 + 1, ... in order;
-    // eight weights' loads are issued together
+    // eight weights' loads are issued together (more than kNufftHeavy
+    // entries: a warp takes the grid point below)
     float br = 0.0f, bi = 0.0f;
-    const int k0 = H.nu_ptr[l], n = H.nu_ptr[l + 1] - k0, e0 = H.nu_edge[l];
+    const int k0 = __ldg(&H.nu_ptr[l]), n = __ldg(&H.nu_ptr[l + 1]) - k0, e0 = __ldg(&H.nu_edge[l]);
+    if (n > kNufftHeavy) continue;
     for (int q0 = 0; q0 < n; q0 += 8) {
       float w[8];
 #pragma unroll
@@ -527,12 +536,46 @@ __device__ inline void tm_pass_nufft(const LikeConst& L, const HetTables& H, flo
     }
     g[__brev((unsigned)l) >> (32 - lg)] = make_float2(br, bi);
   }
+  // the grid points with many entries (low frequencies crowd a few points):
+  // lane-strided entries, fixed-order warp sum
+  for (int h = warp; h < H.nu_nheavy; h += n_warps) {
+    const int l = H.nu_heavy[h];
+    const int k0 = H.nu_ptr[l], n = H.nu_ptr[l + 1] - k0, e0 = H.nu_edge[l];
+    // four lane-strided entries per step in separate sums (fixed order)
+    float br = 0.0f, bi = 0.0f, br1 = 0.0f, bi1 = 0.0f, br2 = 0.0f, bi2 = 0.0f, br3 = 0.0f, bi3 = 0.0f;
+    for (int q = lane; q < n; q += 128) {
+      const float w0 = __ldg(&H.nu_wt[k0 + q]);
+      const float w1 = q + 32 < n ? __ldg(&H.nu_wt[k0 + q + 32]) : 0.0f;
+      const float w2 = q + 64 < n ? __ldg(&H.nu_wt[k0 + q + 64]) : 0.0f;
+      const float w3 = q + 96 < n ? __ldg(&H.nu_wt[k0 + q + 96]) : 0.0f;
+      const float2 c0 = y[e0 + q];
+      const float2 c1 = q + 32 < n ? y[e0 + q + 32] : make_float2(0.0f, 0.0f);
+      const float2 c2 = q + 64 < n ? y[e0 + q + 64] : make_float2(0.0f, 0.0f);
+      const float2 c3 = q + 96 < n ? y[e0 + q + 96] : make_float2(0.0f, 0.0f);
+      br = fmaf(w0, c0.x, br);
+      bi = fmaf(w0, c0.y, bi);
+      br1 = fmaf(w1, c1.x, br1);
+      bi1 = fmaf(w1, c1.y, bi1);
+      br2 = fmaf(w2, c2.x, br2);
+      bi2 = fmaf(w2, c2.y, bi2);
+      br3 = fmaf(w3, c3.x, br3);
+      bi3 = fmaf(w3, c3.y, bi3);
+    }
+    br = (br + br1) + (br2 + br3);
+    bi = (bi + bi1) + (bi2 + bi3);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      br += __shfl_xor_sync(0xffffffffu, br, o);
+      bi += __shfl_xor_sync(0xffffffffu, bi, o);
+    }
+    if (lane == 0) g[__brev((unsigned)l) >> (32 - lg)] = make_float2(br, bi);
+  }
   __syncthreads();
   for (int half = 1; half < M; half <<= 1) {
     const int tstep = M / (2 * half);
     for (int b = tid; b < M / 2; b += nt) {
       const int pos = b & (half - 1), i = ((b - pos) << 1) + pos, j = i + half;
-      const float2 w = H.nu_tw[pos * tstep];
+      const float2 w = tw[pos * tstep];
       const float2 xj = g[j], xi = g[i];
       const float tr = w.x * xj.x - w.y * xj.y, ti = w.x * xj.y + w.y * xj.x;
       g[j] = make_float2(xi.x - tr, xi.y - ti);
@@ -568,9 +611,19 @@ __device__ inline void tm_pass_nufft(const LikeConst& L, const HetTables& H, flo
   ws = S;
 }
 
-// The NUFFT grid's place in shared memory: after the N_b + 1 edge products.
+// The NUFFT grid's place in shared memory: after the N_b + 1 edge products;
+// its M / 2 twiddles follow the grid (tm_nufft_tw).
 __device__ __forceinline__ float2* tm_nufft_grid(unsigned char* smem, int n_bins) {
   return reinterpret_cast<float2*>(smem + ((((size_t)n_bins + 1) * 2 * sizeof(float) + 15) / 16 * 16));
+}
+__device__ __forceinline__ float2* tm_nufft_tw(unsigned char* smem, int n_bins, int M) {
+  return tm_nufft_grid(smem, n_bins) + M;
+}
+// Copy of the twiddle table into shared memory (whole block).
+__device__ __forceinline__ void tm_load_twiddles(const LikeConst& L, const HetTables& H, unsigned char* smem,
+                                                 int n_bins) {
+  float2* tw = tm_nufft_tw(smem, n_bins, L.tm_M);
+  for (int k = threadIdx.x; k < L.tm_M / 2; k += blockDim.x) tw[k] = __ldg(&H.nu_tw[k]);
 }
 
 // Time-marginalised logL from the warps' (max, sum) pairs (warp order) and

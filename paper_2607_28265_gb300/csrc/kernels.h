@@ -37,8 +37,12 @@ constexpr int kMaxTmBins = 16384;
 constexpr int kNufftMinNodes = 64;
 constexpr int kNufftMaxNodes = 4096;
 constexpr int kNufftWidth = 8;
+// grid points gathering more entries than this are summed by a whole warp
+constexpr int kNufftHeavy = 32;
+// (edge products, then the non-uniform FFT's grid of M and twiddles of M / 2
+// complex values)
 inline size_t het_tm_smem_bytes(int n_bins, int nufft_m = 0) {
-  return (((size_t)n_bins + 1) * 2 * sizeof(float) + 15) / 16 * 16 + (size_t)nufft_m * 2 * sizeof(float);
+  return (((size_t)n_bins + 1) * 2 * sizeof(float) + 15) / 16 * 16 + (size_t)nufft_m * 3 * sizeof(float);
 }
 
 // Heterodyned contraction by chunk anchors.  A warp step covers one chunk of
@@ -47,10 +51,12 @@ inline size_t het_tm_smem_bytes(int n_bins, int nufft_m = 0) {
 // derivatives of orders 2..kTaylorDeg (float), as rows of a [HC_ROWS][chunks]
 // table; per evaluation the phase difference from the fiducial is anchored
 // there in double-float and carried across the chunk by an FP32 Taylor form
-// in x = (f_e - f_a) / S (S the chunk's span).  A chunk whose Taylor
-// remainder bound over the prior box exceeds the tolerance is flagged exact
-// and evaluated edge by edge in double-float.
+// in x = (f_e - f_a) / S (S the chunk's span).  Rows HC_BND + j hold the
+// remainder bound of basis j, max |phi_j^(7)| S^7 / 7! over the chunk: an
+// evaluation whose sum_j |c_j - c0_j| HC_BND_j exceeds kHetTaylorEps cycles
+// takes the chunk edge by edge in double-float instead.
 constexpr int kHetChunkEdges = 32;
+constexpr float kHetTaylorEps = 1e-7f;
 enum HetChunkRow {
   HC_VAL_HI = 0,
   HC_VAL_LO = NBASIS,
@@ -60,16 +66,20 @@ enum HetChunkRow {
   HC_FA_HI = 4 * NBASIS + kNumPoly * NBASIS,
   HC_FA_LO,
   HC_INV_S,
-  HC_EXACT,
-  HC_ROWS
+  HC_BND,
+  HC_ROWS = HC_BND + NBASIS
 };
 // Per-evaluation chunk anchor in shared memory: a_1 .. a_kTaylorDeg, then
-// frac(dP(f_a) + f_a dtau_i) per detector, 1 / S and the exact flag.
+// frac(dP(f_a) + f_a dtau_i) per detector, 1 / S and the exact flag of this
+// evaluation.
 constexpr int kHetAncStride = 12;
 constexpr int kHetAncPhase = kNumPoly + 1;
 constexpr int kHetAncInvS = kHetAncPhase + SWIG_MAX_DET;
 constexpr int kHetAncExact = kHetAncInvS + 1;
 static_assert(kHetAncExact < kHetAncStride, "chunk anchor layout");
+// Per-warp shared-memory stage of one chunk's table data (summary data, bin
+// widths, edge offsets), filled by cp.async one chunk ahead: bytes per stage.
+inline size_t het_stage_bytes(int n_det) { return (size_t)n_det * 32 * (16 + 8) + 2 * 32 * 4; }
 
 // Device buffers owned by a context (all allocated with cudaMalloc).
 struct DeviceBuffers {
@@ -108,6 +118,8 @@ struct DeviceBuffers {
   float* het_nu_wt = nullptr;       // [entries]
   float* het_nu_corr = nullptr;     // [N_t]
   float2* het_nu_tw = nullptr;      // [M / 2] exp(2 pi i k / M)
+  int* het_nu_heavy = nullptr;      // grid points with more than kNufftHeavy entries
+  int het_nu_nheavy = 0;
   // scratch for batched evaluation, sized for `cap` thetas
   int cap = 0;
   EvalRecord* rec = nullptr;     // [cap]

@@ -315,6 +315,7 @@ __global__ void __launch_bounds__(kHetTmThreads, 1)
   }
   HetPrep<NDET> p;
   het_prepare<NDET>(L, H, r, p);
+  if (L.tm_M > 0) tm_load_twiddles(L, H, smem, H.n_bins);  // read after the __syncthreads below
   float zr[NDET], zi[NDET], hh[NDET];
 #pragma unroll
   for (int i = 0; i < NDET; ++i) zr[i] = zi[i] = hh[i] = 0.0f;
@@ -327,7 +328,8 @@ __global__ void __launch_bounds__(kHetTmThreads, 1)
   __syncthreads();
   float wm, ws;
   if (L.tm_M > 0)
-    tm_pass_nufft(L, H, y, tm_nufft_grid(smem, H.n_bins), warp, n_warps, lane, ell_th, wm, ws);
+    tm_pass_nufft(L, H, y, tm_nufft_grid(smem, H.n_bins), tm_nufft_tw(smem, H.n_bins, L.tm_M), warp, n_warps, lane,
+                  ell_th, wm, ws);
   else
     tm_pass(L, H, y, warp, n_warps, lane, ell_th, wm, ws);
   if (lane == 0) {

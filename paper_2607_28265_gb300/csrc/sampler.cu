@@ -120,6 +120,7 @@ struct SamplerConst {
   int n_slots;    // request slots: nrep, or 2 nrep with par_out
   int claim_off;  // byte offset (in the dynamic shared memory after the slice data) of the claim words
                   // (heterodyned sampler: of the chunk anchors)
+  int stage_off;  // heterodyned sampler: byte offset of the warps' chunk-table stages
 };
 
 struct ChainState {
@@ -2086,6 +2087,7 @@ __device__ __forceinline__ void het_prepare_warp(const LikeConst& L, const HetTa
 template <int NDET>
 __global__ void __launch_bounds__(kHetThreads, 1)
     k_ns_het(LikeConst L, SamplerConst S, DeviceBuffers B, SamplerPtrs P) {
+  static_assert(sizeof(HetStage<NDET>) == (size_t)NDET * 32 * (16 + 8) + 2 * 32 * 4, "stage layout (kernels.h)");
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ float s_sum[kHetThreads / 32][3 * NDET];
   __shared__ float s_tm[kHetThreads / 32][2];
@@ -2124,6 +2126,10 @@ __global__ void __launch_bounds__(kHetThreads, 1)
       t0 = t1;
     }
     if (*(volatile int*)&g->status != ST_RUNNING) return;
+    if (L.tm_M > 0) {  // the boundary may have used the scratch: twiddles again
+      tm_load_twiddles(L, H, smem, H.n_bins);
+      __syncthreads();
+    }
     for (int c = blockIdx.x; c < S.nrep; c += gridDim.x) {
       // warp 0's copy of the last evaluation's result (see control_step_warp)
       double ly = 0.0, kapc = 0.0, vvc = 0.0;
@@ -2159,10 +2165,12 @@ __global__ void __launch_bounds__(kHetThreads, 1)
           // chunk anchors, one thread per chunk, then the edge pass
           for (int q = threadIdx.x; q < nc; q += blockDim.x) het_anchor<NDET>(H, p, q, s_anc + q * kHetAncStride);
           __syncthreads();
+          unsigned char* stage = smem + S.stage_off + (size_t)warp * 2 * sizeof(HetStage<NDET>);
           if (L.tm_n > 0)
-            het_chunks_warp<NDET, true>(H, p, s_anc, warp, n_warps, lane, zr, zi, hh, reinterpret_cast<float2*>(smem));
+            het_chunks_warp<NDET, true>(H, p, s_anc, warp, n_warps, lane, stage, zr, zi, hh,
+                                        reinterpret_cast<float2*>(smem));
           else
-            het_chunks_warp<NDET>(H, p, s_anc, warp, n_warps, lane, zr, zi, hh);
+            het_chunks_warp<NDET>(H, p, s_anc, warp, n_warps, lane, stage, zr, zi, hh);
           het_warp_reduce<NDET>(zr, zi, hh);
         }
         if (lane == 0) {
@@ -2177,7 +2185,8 @@ __global__ void __launch_bounds__(kHetThreads, 1)
         if (L.tm_n > 0 && valid) {  // block-uniform
           float wm, ws;
           if (L.tm_M > 0)
-            tm_pass_nufft(L, H, reinterpret_cast<float2*>(smem), tm_nufft_grid(smem, H.n_bins), warp, n_warps, lane,
+            tm_pass_nufft(L, H, reinterpret_cast<float2*>(smem), tm_nufft_grid(smem, H.n_bins),
+                          tm_nufft_tw(smem, H.n_bins, L.tm_M), warp, n_warps, lane,
                           nullptr, wm, ws);
           else
             tm_pass(L, H, reinterpret_cast<const float2*>(smem), warp, n_warps, lane, nullptr, wm, ws);
@@ -2558,8 +2567,10 @@ int run_setup(swig_ctx* c, RunState& R) {
   R.tail = std::max(rec_bytes, sort_bytes);
   const size_t ctl_bytes = (size_t)S.ctl_slots * (sizeof(ChainState) + sizeof(EvalRecord));
   S.claim_off = (int)((S.ctl_off + ctl_bytes + 15) & ~(size_t)15);
-  // (heterodyned: the per-evaluation chunk anchors at claim_off)
-  R.smem = het ? S.claim_off + sizeof(float) * kHetAncStride * (size_t)c->B.het_nc
+  // (heterodyned: the per-evaluation chunk anchors at claim_off, then each
+  // warp's two chunk-table stages)
+  S.stage_off = (int)((S.claim_off + sizeof(float) * kHetAncStride * (size_t)c->B.het_nc + 15) & ~(size_t)15);
+  R.smem = het ? S.stage_off + 2 * het_stage_bytes(L.n_det) * (kHetThreads / 32)
                : fixed + flow_tiles + S.claim_off + sizeof(int) * (size_t)S.n_slots;
   if (R.smem > 220 * 1024) return fail(c, SWIG_E_ARG, "problem too large for the persistent kernel's shared memory");
 

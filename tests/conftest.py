@@ -20,15 +20,17 @@ def pytest_terminal_summary(terminalreporter, exitstatus, config):
         import parity
     except ImportError:
         return
-    if not parity.RECORDS:
+    if not parity.RECORDS and not parity.NOTES:
         return
     terminalreporter.write_sep("-", "parity against the oracle (largest error per check)")
     for r in parity.RECORDS:
         terminalreporter.write_line(
             f"{r['name']:<58} n={r['n']:<6} max|err|={r['max_abs']:.3e} max rel={r['max_rel']:.3e} "
             f"err/tol={r['max_frac_of_tol']:.3f}")
+    for r in parity.NOTES:
+        terminalreporter.write_line(json.dumps(r))
     path = os.environ.get("SWIG_PARITY_REPORT")
     if path:
         with open(path, "w") as f:
-            for r in parity.RECORDS:
+            for r in parity.RECORDS + parity.NOTES:
                 f.write(json.dumps(r) + "\n")

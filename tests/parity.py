@@ -5,11 +5,19 @@ check(name, got, want, rtol, atol) asserts |got - want| <= rtol |want| + atol
 element by element and records the largest absolute error, the largest error
 relative to |want| and the largest ratio of error to tolerance.  The summary
 is printed at the end of the pytest session and, when the environment
-variable SWIG_PARITY_REPORT names a file, written there as JSON lines.
+variable SWIG_PARITY_REPORT names a file, written there as JSON lines;
+note(name, **values) records other measured values the same way.
 """
 import numpy as np
 
 RECORDS = []
+NOTES = []
+
+
+def note(name, **values):
+    """Record measured values of a check that is not element-wise (p-values,
+    evidence differences) for the session summary."""
+    NOTES.append(dict(name=name, **values))
 
 
 def check(name, got, want, rtol, atol):

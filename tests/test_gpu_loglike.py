@@ -113,7 +113,8 @@ def test_ragged_multi_tile_grid_two_detectors():
         ctx = swig.context_for_workload(wl, ev.data, ev.psds, ev.gmst)
         ctx.set_sampler(nlive=50, nrep=5, precision=prec)
         got = ctx.loglike_batch(thetas)
-        parity.check(f"full-grid batch (ragged two-detector grid, {prec})", got, want, 1e-6, 1e-6)
+        name = "fp64" if prec == swig.PREC_FP64 else "mixed"
+        parity.check(f"full-grid batch (ragged two-detector grid, {name})", got, want, 1e-6, 1e-6)
 
 
 def test_invalid_theta_empty_batch_and_determinism(cfg1):

@@ -122,7 +122,8 @@ def test_dead_points_match_oracle_and_runs_are_deterministic(cfg1):
         assert abs(m + math.log(np.sum(np.exp(lw - m))) - r.logz) < 1e-9
         idx = np.linspace(0, len(ll) - 1, 16).astype(int)
         want = np.array([L.loglike(ev, thd[i]) for i in idx])
-        parity.check(f"sampler dead points (4 s H1, {prec})", ll[idx], want, 1e-6, 1e-6)
+        name = "fp64" if prec == swig.PREC_FP64 else "mixed"
+        parity.check(f"sampler dead points (4 s H1, {name})", ll[idx], want, 1e-6, 1e-6)
         r2 = ctx.run()
         thd2, ll2, lw2 = ctx.get_samples()
         assert r2.logz == r.logz and np.array_equal(ll, ll2) and np.array_equal(thd, thd2)
