@@ -233,8 +233,8 @@ void free_problem(DeviceBuffers& B) {
   dfree(B.het_nu_wt);
   dfree(B.het_nu_corr);
   dfree(B.het_nu_tw);
-  dfree(B.het_nu_heavy);
-  B.het_nu_nheavy = 0;
+  dfree(B.het_nu_piece);
+  dfree(B.het_nu_point);
   B.het_nb = 0;
 }
 
@@ -567,7 +567,7 @@ int prepare_het(swig_ctx* c) {
   const int nc = (nb + 30) / 31;
   std::vector<float> ct((size_t)HC_ROWS * nc, 0.0f), dfe((size_t)nc * kHetChunkEdges, 0.0f);
   {
-    const int order = kTaylorDeg + 1;
+    const int order = kHetTaylorDeg + 1;
     double fact = 1.0;
     for (int i = 2; i <= order; ++i) fact *= i;
     for (int q = 0; q < nc; ++q) {
@@ -591,7 +591,7 @@ int prepare_het(swig_ctx* c) {
         put(HC_D1_HI + j, hi);
         put(HC_D1_LO + j, lo);
         double nf = 1.0;
-        for (int m = 0; m < kNumPoly; ++m) {
+        for (int m = 0; m < kHetPoly; ++m) {
           const int nn = m + 2;
           nf *= nn;
           put(HC_POLY + m * NBASIS + j,
@@ -623,6 +623,7 @@ int prepare_het(swig_ctx* c) {
   if (L.tm_n > 0) {
     std::vector<float2> g, w;
     L.tm_M = 0;
+    L.tm_pieces = L.tm_points = 0;
     std::vector<int> ptr, edge;
     std::vector<float> wt, corr;
     std::vector<float2> tw;
@@ -637,14 +638,26 @@ int prepare_het(swig_ctx* c) {
     // so the bin pass stores c_e = y_e exp(-2 pi i f_e dt_ref) directly
     het_tm_tables(a01, f, idx, nb, n_det, L.tm_dt, g, w, L.tm_M > 0 ? L.tm_dref : 0.0);
     if (L.tm_M > 0) {
-      std::vector<int> heavy;
-      for (int l = 0; l < L.tm_M; ++l)
-        if (ptr[l + 1] - ptr[l] > kNufftHeavy) heavy.push_back(l);
-      B.het_nu_nheavy = (int)heavy.size();
-      CUDA_TRY(c, cudaMalloc(&B.het_nu_heavy, sizeof(int) * std::max<size_t>(1, heavy.size())));
-      if (!heavy.empty())
-        CUDA_TRY(c, cudaMemcpy(B.het_nu_heavy, heavy.data(), sizeof(int) * heavy.size(), cudaMemcpyHostToDevice));
-      c->h2d_bytes += sizeof(int) * heavy.size();
+      // gather pieces: each grid point's entries in runs of at most
+      // kNufftPiece (summed by one lane each), and the grid points with
+      // entries (their pieces are combined in order)
+      std::vector<int4> piece, point;
+      for (int l = 0; l < L.tm_M; ++l) {
+        const int n = ptr[l + 1] - ptr[l];
+        if (n == 0) continue;
+        point.push_back(make_int4(l, (int)piece.size(), (n + kNufftPiece - 1) / kNufftPiece, 0));
+        for (int o = 0; o < n; o += kNufftPiece)
+          piece.push_back(make_int4(ptr[l] + o, std::min(kNufftPiece, n - o), edge[l] + o, 0));
+      }
+      L.tm_pieces = (int)piece.size();
+      L.tm_points = (int)point.size();
+      CUDA_TRY(c, cudaMalloc(&B.het_nu_piece, sizeof(int4) * std::max<size_t>(1, piece.size())));
+      CUDA_TRY(c, cudaMalloc(&B.het_nu_point, sizeof(int4) * std::max<size_t>(1, point.size())));
+      if (!piece.empty()) {
+        CUDA_TRY(c, cudaMemcpy(B.het_nu_piece, piece.data(), sizeof(int4) * piece.size(), cudaMemcpyHostToDevice));
+        CUDA_TRY(c, cudaMemcpy(B.het_nu_point, point.data(), sizeof(int4) * point.size(), cudaMemcpyHostToDevice));
+      }
+      c->h2d_bytes += sizeof(int4) * (piece.size() + point.size());
       CUDA_TRY(c, cudaMalloc(&B.het_nu_ptr, sizeof(int) * ptr.size()));
       CUDA_TRY(c, cudaMalloc(&B.het_nu_edge, sizeof(int) * std::max<size_t>(1, edge.size())));
       CUDA_TRY(c, cudaMalloc(&B.het_nu_wt, sizeof(float) * std::max<size_t>(1, wt.size())));

@@ -43,8 +43,8 @@ struct HetTables {
   const float* nu_wt;
   const float* nu_corr;
   const float2* nu_tw;
-  const int* nu_heavy;
-  int nu_nheavy;
+  const int4* nu_piece;  // gather pieces (first entry, entries, first edge)
+  const int4* nu_point;  // grid points with entries (point, first piece, pieces)
   // chunk anchors (kernels.h HetChunkRow)
   int n_chunks;
   const float* chunk;  // [HC_ROWS][n_chunks]
@@ -67,8 +67,8 @@ __host__ __device__ inline HetTables het_tables(const DeviceBuffers& B) {
   H.nu_wt = B.het_nu_wt;
   H.nu_corr = B.het_nu_corr;
   H.nu_tw = B.het_nu_tw;
-  H.nu_heavy = B.het_nu_heavy;
-  H.nu_nheavy = B.het_nu_nheavy;
+  H.nu_piece = B.het_nu_piece;
+  H.nu_point = B.het_nu_point;
   H.n_chunks = B.het_nc;
   H.chunk = B.het_chunk;
   H.dfe = B.het_dfe;
@@ -102,7 +102,7 @@ __device__ inline void het_prepare(const LikeConst& L, const HetTables& H, const
 // chunk table are read coalesced across threads): the phase difference
 // dP(f) = sum_j (c_j - c0_j) phi_j(f) at the chunk's first edge f_a in
 // double-float, its scaled derivatives a_1 (double-float sum, stored FP32)
-// and a_2..a_6 (FP32), per detector frac(dP(f_a) + f_a dtau_i), and whether
+// and a_2..a_10 (FP32), per detector frac(dP(f_a) + f_a dtau_i), and whether
 // this evaluation's Taylor remainder bound sum_j |c_j - c0_j| HC_BND_j
 // exceeds kHetTaylorEps (then the chunk is taken edge by edge).
 template <int NDET>
@@ -111,9 +111,9 @@ __device__ inline void het_anchor(const HetTables& H, const HetPrep<NDET>& p, in
   const float* T = H.chunk + q;
   auto row = [&](int r) { return __ldg(T + (size_t)r * nc); };
   dfl A = {0.0f, 0.0f}, S = {0.0f, 0.0f};
-  float a[kNumPoly], R = 0.0f;
+  float a[kHetPoly], R = 0.0f;
 #pragma unroll
-  for (int n = 0; n < kNumPoly; ++n) a[n] = 0.0f;
+  for (int n = 0; n < kHetPoly; ++n) a[n] = 0.0f;
 #pragma unroll
   for (int j = 0; j < NBASIS; ++j) {
     const dfl c = p.dc[j];
@@ -121,11 +121,11 @@ __device__ inline void het_anchor(const HetTables& H, const HetPrep<NDET>& p, in
     A = df_add(A, df_mul(c, dfl{row(HC_VAL_HI + j), row(HC_VAL_LO + j)}));
     S = df_add(S, df_mul(c, dfl{row(HC_D1_HI + j), row(HC_D1_LO + j)}));
 #pragma unroll
-    for (int n = 0; n < kNumPoly; ++n) a[n] = fmaf(c.hi, row(HC_POLY + n * NBASIS + j), a[n]);
+    for (int n = 0; n < kHetPoly; ++n) a[n] = fmaf(c.hi, row(HC_POLY + n * NBASIS + j), a[n]);
   }
   out[0] = S.hi + S.lo;
 #pragma unroll
-  for (int n = 0; n < kNumPoly; ++n) out[1 + n] = a[n];
+  for (int n = 0; n < kHetPoly; ++n) out[1 + n] = a[n];
   const dfl fa = {row(HC_FA_HI), row(HC_FA_LO)};
 #pragma unroll
   for (int i = 0; i < NDET; ++i) out[kHetAncPhase + i] = df_frac(df_add(A, df_mul(fa, p.dtau[i])));
@@ -203,7 +203,7 @@ struct HetBinData {
 
 // het_chunk with the phase from chunk q's anchor `anc` (het_anchor) and the
 // lane's table data t (het_read_stage): lane l holds edge 31 q + l at
-// x = (f_e - f_a) / S, dP = sum_n a_n x^n (FP32 Horner),
+// x = (f_e - f_a) / S, dP = sum_n a_n x^n (degree 10, FP32 Horner),
 // phase_i = frac(anchor_i + dP + (f_e - f_a) dtau_i).
 template <int NDET, bool TM = false>
 __device__ inline void het_chunk_anc(const HetTables& H, const HetPrep<NDET>& p, const float* anc, int q, int lane,
@@ -214,9 +214,9 @@ __device__ inline void het_chunk_anc(const HetTables& H, const HetPrep<NDET>& p,
   float er[NDET], ei[NDET];
   if (e <= H.n_bins) {
     const float x = t.d * anc[kHetAncInvS];
-    float v = anc[kNumPoly];
+    float v = anc[kHetPoly];
 #pragma unroll
-    for (int n = kNumPoly - 1; n >= 0; --n) v = fmaf(v, x, anc[n]);
+    for (int n = kHetPoly - 1; n >= 0; --n) v = fmaf(v, x, anc[n]);
     v *= x;
 #pragma unroll
     for (int i = 0; i < NDET; ++i) {
@@ -498,6 +498,47 @@ __device__ inline void tm_pass(const LikeConst& L, const HetTables& H, const flo
   ws = S;
 }
 
+// The gather's per-piece partial sums follow the grid and its twiddles.
+__device__ __forceinline__ float2* tm_nufft_parts(const LikeConst& L, float2* g) { return g + L.tm_M + L.tm_M / 2; }
+
+// Gather of the non-uniform FFT's grid values b_l = sum_e w_le c_e (the
+// whole block).  A grid point's entries are consecutive edges, cut into
+// pieces of at most kNufftPiece entries; lane t sums pieces t, t + nt, ...
+// (all of a piece's weight loads issued together) into part[], then thread
+// t combines the pieces of grid points t, t + nt, ... in order.  Fixed sum
+// orders: deterministic.  Grid points without entries are zeroed.
+__device__ inline void nufft_gather(const LikeConst& L, const HetTables& H, const float2* y, float2* g,
+                                    float2* part, int lg) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int l = tid; l < L.tm_M; l += nt) g[l] = make_float2(0.0f, 0.0f);
+  for (int p = tid; p < L.tm_pieces; p += nt) {
+    const int4 d = __ldg(&H.nu_piece[p]);
+    float w[kNufftPiece];
+#pragma unroll
+    for (int i = 0; i < kNufftPiece; ++i) w[i] = i < d.y ? __ldg(&H.nu_wt[d.x + i]) : 0.0f;
+    float br = 0.0f, bi = 0.0f;
+#pragma unroll
+    for (int i = 0; i < kNufftPiece; ++i)
+      if (i < d.y) {
+        const float2 c = y[d.z + i];
+        br = fmaf(w[i], c.x, br);
+        bi = fmaf(w[i], c.y, bi);
+      }
+    part[p] = make_float2(br, bi);
+  }
+  __syncthreads();
+  for (int q = tid; q < L.tm_points; q += nt) {
+    const int4 d = __ldg(&H.nu_point[q]);
+    float br = 0.0f, bi = 0.0f;
+    for (int i = 0; i < d.z; ++i) {
+      const float2 v = part[d.y + i];
+      br += v.x;
+      bi += v.y;
+    }
+    g[__brev((unsigned)d.x) >> (32 - lg)] = make_float2(br, bi);
+  }
+}
+
 // The same time pass by non-uniform FFT (tables of het_nufft_tables): the
 // edge products become c_e = y_e exp(-2 pi i f_e dt_ref) (double-float phase;
 // y is overwritten), every grid point gathers its kernel-weighted c_e in a
@@ -515,63 +556,27 @@ __device__ inline void tm_pass_nufft(const LikeConst& L, const HetTables& H, con
   const int M = L.tm_M;
   // y holds c_e (the edge weights carry the reference rotation)
   const int lg = __ffs(M) - 1;
-  for (int l = tid; l < M; l += nt) {
-    // grid point l gathers the consecutive edges e0, e0 + 1, ... in order;
-    // eight weights' loads are issued together (more than kNufftHeavy
-    // entries: a warp takes the grid point below)
-    float br = 0.0f, bi = 0.0f;
-    const int k0 = __ldg(&H.nu_ptr[l]), n = __ldg(&H.nu_ptr[l + 1]) - k0, e0 = __ldg(&H.nu_edge[l]);
-    if (n > kNufftHeavy) continue;
-    for (int q0 = 0; q0 < n; q0 += 8) {
-      float w[8];
+  nufft_gather(L, H, y, g, tm_nufft_parts(L, g), lg);
+  __syncthreads();
+  // radix-2 stages of spans 1..16 inside 32-point blocks in registers (warp
+  // shuffles: no shared-memory bank conflicts, no block barriers), then the
+  // wider spans through shared memory
+  for (int blk = warp; blk < M / 32; blk += n_warps) {
+    const int at = blk * 32 + lane;
+    float2 x = g[at];
 #pragma unroll
-      for (int q = 0; q < 8; ++q) w[q] = q0 + q < n ? __ldg(&H.nu_wt[k0 + q0 + q]) : 0.0f;
-#pragma unroll
-      for (int q = 0; q < 8; ++q)
-        if (q0 + q < n) {
-          const float2 c = y[e0 + q0 + q];
-          br = fmaf(w[q], c.x, br);
-          bi = fmaf(w[q], c.y, bi);
-        }
+    for (int half = 1; half < 32; half <<= 1) {
+      const float2 w = tw[(lane & (half - 1)) * (M / (2 * half))];
+      const float pr = __shfl_xor_sync(0xffffffffu, x.x, half), pi = __shfl_xor_sync(0xffffffffu, x.y, half);
+      if ((lane & half) == 0)  // lower point: x + w partner
+        x = make_float2(x.x + (w.x * pr - w.y * pi), x.y + (w.x * pi + w.y * pr));
+      else  // upper point: partner - w x
+        x = make_float2(pr - (w.x * x.x - w.y * x.y), pi - (w.x * x.y + w.y * x.x));
     }
-    g[__brev((unsigned)l) >> (32 - lg)] = make_float2(br, bi);
-  }
-  // the grid points with many entries (low frequencies crowd a few points):
-  // lane-strided entries, fixed-order warp sum
-  for (int h = warp; h < H.nu_nheavy; h += n_warps) {
-    const int l = H.nu_heavy[h];
-    const int k0 = H.nu_ptr[l], n = H.nu_ptr[l + 1] - k0, e0 = H.nu_edge[l];
-    // four lane-strided entries per step in separate sums (fixed order)
-    float br = 0.0f, bi = 0.0f, br1 = 0.0f, bi1 = 0.0f, br2 = 0.0f, bi2 = 0.0f, br3 = 0.0f, bi3 = 0.0f;
-    for (int q = lane; q < n; q += 128) {
-      const float w0 = __ldg(&H.nu_wt[k0 + q]);
-      const float w1 = q + 32 < n ? __ldg(&H.nu_wt[k0 + q + 32]) : 0.0f;
-      const float w2 = q + 64 < n ? __ldg(&H.nu_wt[k0 + q + 64]) : 0.0f;
-      const float w3 = q + 96 < n ? __ldg(&H.nu_wt[k0 + q + 96]) : 0.0f;
-      const float2 c0 = y[e0 + q];
-      const float2 c1 = q + 32 < n ? y[e0 + q + 32] : make_float2(0.0f, 0.0f);
-      const float2 c2 = q + 64 < n ? y[e0 + q + 64] : make_float2(0.0f, 0.0f);
-      const float2 c3 = q + 96 < n ? y[e0 + q + 96] : make_float2(0.0f, 0.0f);
-      br = fmaf(w0, c0.x, br);
-      bi = fmaf(w0, c0.y, bi);
-      br1 = fmaf(w1, c1.x, br1);
-      bi1 = fmaf(w1, c1.y, bi1);
-      br2 = fmaf(w2, c2.x, br2);
-      bi2 = fmaf(w2, c2.y, bi2);
-      br3 = fmaf(w3, c3.x, br3);
-      bi3 = fmaf(w3, c3.y, bi3);
-    }
-    br = (br + br1) + (br2 + br3);
-    bi = (bi + bi1) + (bi2 + bi3);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      br += __shfl_xor_sync(0xffffffffu, br, o);
-      bi += __shfl_xor_sync(0xffffffffu, bi, o);
-    }
-    if (lane == 0) g[__brev((unsigned)l) >> (32 - lg)] = make_float2(br, bi);
+    g[at] = x;
   }
   __syncthreads();
-  for (int half = 1; half < M; half <<= 1) {
+  for (int half = 32; half < M; half <<= 1) {
     const int tstep = M / (2 * half);
     for (int b = tid; b < M / 2; b += nt) {
       const int pos = b & (half - 1), i = ((b - pos) << 1) + pos, j = i + half;

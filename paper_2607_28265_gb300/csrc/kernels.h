@@ -37,43 +37,48 @@ constexpr int kMaxTmBins = 16384;
 constexpr int kNufftMinNodes = 64;
 constexpr int kNufftMaxNodes = 4096;
 constexpr int kNufftWidth = 8;
-// grid points gathering more entries than this are summed by a whole warp
-constexpr int kNufftHeavy = 32;
+// entries per gather piece (one lane sums a piece)
+constexpr int kNufftPiece = 32;
 // (edge products, then the non-uniform FFT's grid of M and twiddles of M / 2
-// complex values)
-inline size_t het_tm_smem_bytes(int n_bins, int nufft_m = 0) {
-  return (((size_t)n_bins + 1) * 2 * sizeof(float) + 15) / 16 * 16 + (size_t)nufft_m * 3 * sizeof(float);
+// complex values, then the gather's per-piece partial sums)
+inline size_t het_tm_smem_bytes(int n_bins, int nufft_m = 0, int pieces = 0) {
+  return (((size_t)n_bins + 1) * 2 * sizeof(float) + 15) / 16 * 16 + (size_t)nufft_m * 3 * sizeof(float) +
+         (size_t)pieces * 2 * sizeof(float);
 }
 
 // Heterodyned contraction by chunk anchors.  A warp step covers one chunk of
 // 32 edges (31 bins).  Per chunk the host tabulates, at its first edge f_a,
 // the basis values and first derivative (double-float) and the scaled
-// derivatives of orders 2..kTaylorDeg (float), as rows of a [HC_ROWS][chunks]
+// derivatives of orders 2..kHetTaylorDeg (float), as rows of a [HC_ROWS][chunks]
 // table; per evaluation the phase difference from the fiducial is anchored
 // there in double-float and carried across the chunk by an FP32 Taylor form
 // in x = (f_e - f_a) / S (S the chunk's span).  Rows HC_BND + j hold the
-// remainder bound of basis j, max |phi_j^(7)| S^7 / 7! over the chunk: an
+// remainder bound of basis j, max |phi_j^(11)| S^11 / 11! over the chunk: an
 // evaluation whose sum_j |c_j - c0_j| HC_BND_j exceeds kHetTaylorEps cycles
 // takes the chunk edge by edge in double-float instead.
 constexpr int kHetChunkEdges = 32;
 constexpr float kHetTaylorEps = 1e-7f;
+// degree of the chunk Taylor form (wider than the full grid's tiles: a chunk
+// of 31 heterodyned bins spans up to ~10 % of its frequency mid-band)
+constexpr int kHetTaylorDeg = 10;
+constexpr int kHetPoly = kHetTaylorDeg - 1;  // orders 2..kHetTaylorDeg
 enum HetChunkRow {
   HC_VAL_HI = 0,
   HC_VAL_LO = NBASIS,
   HC_D1_HI = 2 * NBASIS,
   HC_D1_LO = 3 * NBASIS,
   HC_POLY = 4 * NBASIS,  // HC_POLY + (n - 2) * NBASIS + j: phi_j^(n)(f_a) S^n / n!
-  HC_FA_HI = 4 * NBASIS + kNumPoly * NBASIS,
+  HC_FA_HI = 4 * NBASIS + kHetPoly * NBASIS,
   HC_FA_LO,
   HC_INV_S,
   HC_BND,
   HC_ROWS = HC_BND + NBASIS
 };
-// Per-evaluation chunk anchor in shared memory: a_1 .. a_kTaylorDeg, then
+// Per-evaluation chunk anchor in shared memory: a_1 .. a_kHetTaylorDeg, then
 // frac(dP(f_a) + f_a dtau_i) per detector, 1 / S and the exact flag of this
 // evaluation.
-constexpr int kHetAncStride = 12;
-constexpr int kHetAncPhase = kNumPoly + 1;
+constexpr int kHetAncStride = 16;
+constexpr int kHetAncPhase = kHetPoly + 1;
 constexpr int kHetAncInvS = kHetAncPhase + SWIG_MAX_DET;
 constexpr int kHetAncExact = kHetAncInvS + 1;
 static_assert(kHetAncExact < kHetAncStride, "chunk anchor layout");
@@ -118,8 +123,8 @@ struct DeviceBuffers {
   float* het_nu_wt = nullptr;       // [entries]
   float* het_nu_corr = nullptr;     // [N_t]
   float2* het_nu_tw = nullptr;      // [M / 2] exp(2 pi i k / M)
-  int* het_nu_heavy = nullptr;      // grid points with more than kNufftHeavy entries
-  int het_nu_nheavy = 0;
+  int4* het_nu_piece = nullptr;     // [pieces] (first entry, entries, first edge, 0)
+  int4* het_nu_point = nullptr;     // [points] (grid point, first piece, pieces, 0)
   // scratch for batched evaluation, sized for `cap` thetas
   int cap = 0;
   EvalRecord* rec = nullptr;     // [cap]

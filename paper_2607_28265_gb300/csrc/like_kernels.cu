@@ -351,7 +351,7 @@ __global__ void __launch_bounds__(kHetTmThreads, 1)
 template <int NDET>
 cudaError_t launch_het_tm(const LikeConst& L, const DeviceBuffers& B, int n, double* out, cudaStream_t st,
                           double* kappa_out, double* vv_out, float* ell) {
-  const size_t bytes = het_tm_smem_bytes(B.het_nb, L.tm_M);
+  const size_t bytes = het_tm_smem_bytes(B.het_nb, L.tm_M, L.tm_M > 0 ? L.tm_pieces : 0);
   cudaError_t e = cudaFuncSetAttribute(k_het_tm<NDET>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   if (e != cudaSuccess) return e;
   k_het_tm<NDET><<<n, kHetTmThreads, bytes, st>>>(L, het_tables(B), B.rec, n, out, kappa_out, vv_out, ell);

@@ -2561,7 +2561,8 @@ int run_setup(swig_ctx* c, RunState& R) {
   // the homed chains' state and records of the warp-parallel control follow
   // the per-warp records / sort buffers
   // (heterodyned: one slot, after the sort buffers / time-pass edge products)
-  const size_t het_scratch = std::max(sort_bytes, L.tm_n > 0 ? het_tm_smem_bytes(c->B.het_nb, L.tm_M) : (size_t)0);
+  const size_t het_scratch =
+      std::max(sort_bytes, L.tm_n > 0 ? het_tm_smem_bytes(c->B.het_nb, L.tm_M, L.tm_M > 0 ? L.tm_pieces : 0) : (size_t)0);
   S.ctl_slots = mixed ? (k + L.n_slices - 1) / L.n_slices : (het ? 1 : 0);
   S.ctl_off = (int)(((het ? het_scratch : std::max(rec_bytes, sort_bytes)) + 15) & ~(size_t)15);
   R.tail = std::max(rec_bytes, sort_bytes);

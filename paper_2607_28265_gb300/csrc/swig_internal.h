@@ -110,6 +110,9 @@ struct LikeConst {
   // of the reference shift tm_dref = tm_t0 + j0 tm_dt
   int tm_M, tm_j0;
   double tm_dref;
+  // the gather's pieces (runs of at most 32 entries of one grid point) and
+  // the grid points with entries
+  int tm_pieces, tm_points;
   // heterodyned likelihood: 1 / |C0_i|^2 of the fiducial's projection factors
   double het_fid_iden[SWIG_MAX_DET];
 };
