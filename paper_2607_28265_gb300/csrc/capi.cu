@@ -228,8 +228,6 @@ void free_problem(DeviceBuffers& B) {
   dfree(B.het_fid);
   dfree(B.het_tm_g);
   dfree(B.het_tm_w);
-  dfree(B.het_nu_ptr);
-  dfree(B.het_nu_edge);
   dfree(B.het_nu_wt);
   dfree(B.het_nu_corr);
   dfree(B.het_nu_tw);
@@ -658,18 +656,19 @@ int prepare_het(swig_ctx* c) {
         CUDA_TRY(c, cudaMemcpy(B.het_nu_point, point.data(), sizeof(int4) * point.size(), cudaMemcpyHostToDevice));
       }
       c->h2d_bytes += sizeof(int4) * (piece.size() + point.size());
-      CUDA_TRY(c, cudaMalloc(&B.het_nu_ptr, sizeof(int) * ptr.size()));
-      CUDA_TRY(c, cudaMalloc(&B.het_nu_edge, sizeof(int) * std::max<size_t>(1, edge.size())));
       CUDA_TRY(c, cudaMalloc(&B.het_nu_wt, sizeof(float) * std::max<size_t>(1, wt.size())));
       CUDA_TRY(c, cudaMalloc(&B.het_nu_corr, sizeof(float) * corr.size()));
+      // twiddles stage by stage (span h: exp(2 pi i p / (2 h)), p < h, at
+      // h - 1 + p) so that a stage reads consecutive entries
+      std::vector<float2> tws(L.tm_M, make_float2(0.0f, 0.0f));
+      for (int h = 1; h < L.tm_M; h <<= 1)
+        for (int q = 0; q < h; ++q) tws[h - 1 + q] = tw[(size_t)q * (L.tm_M / (2 * h))];
+      tw.swap(tws);
       CUDA_TRY(c, cudaMalloc(&B.het_nu_tw, sizeof(float2) * tw.size()));
-      CUDA_TRY(c, cudaMemcpy(B.het_nu_ptr, ptr.data(), sizeof(int) * ptr.size(), cudaMemcpyHostToDevice));
-      CUDA_TRY(c, cudaMemcpy(B.het_nu_edge, edge.data(), sizeof(int) * edge.size(), cudaMemcpyHostToDevice));
       CUDA_TRY(c, cudaMemcpy(B.het_nu_wt, wt.data(), sizeof(float) * wt.size(), cudaMemcpyHostToDevice));
       CUDA_TRY(c, cudaMemcpy(B.het_nu_corr, corr.data(), sizeof(float) * corr.size(), cudaMemcpyHostToDevice));
       CUDA_TRY(c, cudaMemcpy(B.het_nu_tw, tw.data(), sizeof(float2) * tw.size(), cudaMemcpyHostToDevice));
-      c->h2d_bytes += sizeof(int) * (ptr.size() + edge.size()) + sizeof(float) * (wt.size() + corr.size()) +
-                      sizeof(float2) * tw.size();
+      c->h2d_bytes += sizeof(float) * (wt.size() + corr.size()) + sizeof(float2) * tw.size();
     }
     CUDA_TRY(c, cudaMalloc(&B.het_tm_g, sizeof(float2) * g.size()));
     CUDA_TRY(c, cudaMalloc(&B.het_tm_w, sizeof(float2) * w.size()));

@@ -38,8 +38,6 @@ struct HetTables {
   const float2* tm_g;         // [n_det][N_b + 1] time marginalisation: edge weights g_ie
   const float2* tm_w;         // [N_b + 1] exp(-2 pi i f_e dt), one grid step
   // non-uniform FFT form of the time pass (see het_nufft_tables)
-  const int* nu_ptr;
-  const int* nu_edge;
   const float* nu_wt;
   const float* nu_corr;
   const float2* nu_tw;
@@ -62,8 +60,6 @@ __host__ __device__ inline HetTables het_tables(const DeviceBuffers& B) {
   H.fid = B.het_fid;
   H.tm_g = B.het_tm_g;
   H.tm_w = B.het_tm_w;
-  H.nu_ptr = B.het_nu_ptr;
-  H.nu_edge = B.het_nu_edge;
   H.nu_wt = B.het_nu_wt;
   H.nu_corr = B.het_nu_corr;
   H.nu_tw = B.het_nu_tw;
@@ -499,7 +495,7 @@ __device__ inline void tm_pass(const LikeConst& L, const HetTables& H, const flo
 }
 
 // The gather's per-piece partial sums follow the grid and its twiddles.
-__device__ __forceinline__ float2* tm_nufft_parts(const LikeConst& L, float2* g) { return g + L.tm_M + L.tm_M / 2; }
+__device__ __forceinline__ float2* tm_nufft_parts(const LikeConst& L, float2* g) { return g + 2 * L.tm_M; }
 
 // Gather of the non-uniform FFT's grid values b_l = sum_e w_le c_e (the
 // whole block).  A grid point's entries are consecutive edges, cut into
@@ -511,8 +507,18 @@ __device__ inline void nufft_gather(const LikeConst& L, const HetTables& H, cons
                                     float2* part, int lg) {
   const int tid = threadIdx.x, nt = blockDim.x;
   for (int l = tid; l < L.tm_M; l += nt) g[l] = make_float2(0.0f, 0.0f);
-  for (int p = tid; p < L.tm_pieces; p += nt) {
-    const int4 d = __ldg(&H.nu_piece[p]);
+  // the descriptors of this thread's first four pieces, loaded together
+  constexpr int kPre = 4;
+  int4 dp[kPre];
+#pragma unroll
+  for (int r = 0; r < kPre; ++r)
+    dp[r] = tid + r * nt < L.tm_pieces ? __ldg(&H.nu_piece[tid + r * nt]) : make_int4(0, 0, 0, 0);
+  for (int p = tid, r = 0; p < L.tm_pieces; p += nt, ++r) {
+    int4 d = dp[0];
+#pragma unroll
+    for (int u = 1; u < kPre; ++u)
+      if (r == u) d = dp[u];
+    if (r >= kPre) d = __ldg(&H.nu_piece[p]);
     float w[kNufftPiece];
 #pragma unroll
     for (int i = 0; i < kNufftPiece; ++i) w[i] = i < d.y ? __ldg(&H.nu_wt[d.x + i]) : 0.0f;
@@ -566,7 +572,7 @@ __device__ inline void tm_pass_nufft(const LikeConst& L, const HetTables& H, con
     float2 x = g[at];
 #pragma unroll
     for (int half = 1; half < 32; half <<= 1) {
-      const float2 w = tw[(lane & (half - 1)) * (M / (2 * half))];
+      const float2 w = tw[half - 1 + (lane & (half - 1))];
       const float pr = __shfl_xor_sync(0xffffffffu, x.x, half), pi = __shfl_xor_sync(0xffffffffu, x.y, half);
       if ((lane & half) == 0)  // lower point: x + w partner
         x = make_float2(x.x + (w.x * pr - w.y * pi), x.y + (w.x * pi + w.y * pr));
@@ -577,10 +583,9 @@ __device__ inline void tm_pass_nufft(const LikeConst& L, const HetTables& H, con
   }
   __syncthreads();
   for (int half = 32; half < M; half <<= 1) {
-    const int tstep = M / (2 * half);
     for (int b = tid; b < M / 2; b += nt) {
       const int pos = b & (half - 1), i = ((b - pos) << 1) + pos, j = i + half;
-      const float2 w = tw[pos * tstep];
+      const float2 w = tw[half - 1 + pos];
       const float2 xj = g[j], xi = g[i];
       const float tr = w.x * xj.x - w.y * xj.y, ti = w.x * xj.y + w.y * xj.x;
       g[j] = make_float2(xi.x - tr, xi.y - ti);
@@ -617,7 +622,7 @@ __device__ inline void tm_pass_nufft(const LikeConst& L, const HetTables& H, con
 }
 
 // The NUFFT grid's place in shared memory: after the N_b + 1 edge products;
-// its M / 2 twiddles follow the grid (tm_nufft_tw).
+// its M stage-major twiddles follow the grid (tm_nufft_tw).
 __device__ __forceinline__ float2* tm_nufft_grid(unsigned char* smem, int n_bins) {
   return reinterpret_cast<float2*>(smem + ((((size_t)n_bins + 1) * 2 * sizeof(float) + 15) / 16 * 16));
 }
@@ -628,7 +633,7 @@ __device__ __forceinline__ float2* tm_nufft_tw(unsigned char* smem, int n_bins, 
 __device__ __forceinline__ void tm_load_twiddles(const LikeConst& L, const HetTables& H, unsigned char* smem,
                                                  int n_bins) {
   float2* tw = tm_nufft_tw(smem, n_bins, L.tm_M);
-  for (int k = threadIdx.x; k < L.tm_M / 2; k += blockDim.x) tw[k] = __ldg(&H.nu_tw[k]);
+  for (int k = threadIdx.x; k < L.tm_M; k += blockDim.x) tw[k] = __ldg(&H.nu_tw[k]);
 }
 
 // Time-marginalised logL from the warps' (max, sum) pairs (warp order) and

@@ -38,11 +38,12 @@ constexpr int kNufftMinNodes = 64;
 constexpr int kNufftMaxNodes = 4096;
 constexpr int kNufftWidth = 8;
 // entries per gather piece (one lane sums a piece)
-constexpr int kNufftPiece = 32;
-// (edge products, then the non-uniform FFT's grid of M and twiddles of M / 2
-// complex values, then the gather's per-piece partial sums)
+// (odd, so that the pieces of one grid point start in different banks)
+constexpr int kNufftPiece = 31;
+// (edge products, then the non-uniform FFT's grid of M and stage-major
+// twiddle table of M complex values, then the gather's per-piece partial sums)
 inline size_t het_tm_smem_bytes(int n_bins, int nufft_m = 0, int pieces = 0) {
-  return (((size_t)n_bins + 1) * 2 * sizeof(float) + 15) / 16 * 16 + (size_t)nufft_m * 3 * sizeof(float) +
+  return (((size_t)n_bins + 1) * 2 * sizeof(float) + 15) / 16 * 16 + (size_t)nufft_m * 4 * sizeof(float) +
          (size_t)pieces * 2 * sizeof(float);
 }
 
@@ -57,7 +58,7 @@ inline size_t het_tm_smem_bytes(int n_bins, int nufft_m = 0, int pieces = 0) {
 // evaluation whose sum_j |c_j - c0_j| HC_BND_j exceeds kHetTaylorEps cycles
 // takes the chunk edge by edge in double-float instead.
 constexpr int kHetChunkEdges = 32;
-constexpr float kHetTaylorEps = 1e-7f;
+constexpr float kHetTaylorEps = 1e-6f;
 // degree of the chunk Taylor form (wider than the full grid's tiles: a chunk
 // of 31 heterodyned bins spans up to ~10 % of its frequency mid-band)
 constexpr int kHetTaylorDeg = 10;
@@ -116,13 +117,11 @@ struct DeviceBuffers {
   // time marginalisation on the heterodyned bins (t_c marginalised)
   float2* het_tm_g = nullptr;       // [n_det][N_b + 1] edge weights: Z_i = sum_e g_ie r_i(e)
   float2* het_tm_w = nullptr;       // [N_b + 1] exp(-2 pi i f_e dt), the step between grid nodes
-  // ... by non-uniform FFT (L.tm_M > 0): gather list of each of the M grid
-  // points (edge, kernel weight), deconvolution 1 / Phi per node, twiddles
-  int* het_nu_ptr = nullptr;        // [M + 1]
-  int* het_nu_edge = nullptr;       // [entries]
+  // ... by non-uniform FFT (L.tm_M > 0): kernel weight of every (grid point,
+  // edge) entry in grid-point order, deconvolution 1 / Phi per node, twiddles
   float* het_nu_wt = nullptr;       // [entries]
   float* het_nu_corr = nullptr;     // [N_t]
-  float2* het_nu_tw = nullptr;      // [M / 2] exp(2 pi i k / M)
+  float2* het_nu_tw = nullptr;      // [M] stage-major twiddles: span h at h - 1 + p, exp(2 pi i p / (2 h))
   int4* het_nu_piece = nullptr;     // [pieces] (first entry, entries, first edge, 0)
   int4* het_nu_point = nullptr;     // [points] (grid point, first piece, pieces, 0)
   // scratch for batched evaluation, sized for `cap` thetas
