@@ -311,12 +311,34 @@ __device__ __forceinline__ void het_read_stage(const HetTables& H, int q, int la
 // The chunks q = first, first + stride, ... of one evaluation by one warp:
 // anchored chunks (het_chunk_anc) read their table data from the warp's two
 // shared-memory stages (`stage`, 2 x het_stage_bytes), filled by cp.async one
-// chunk ahead; exact chunks go edge by edge (het_chunk) from global memory.
+// chunk ahead, or straight from global memory when there is no room for the
+// stages (stage == nullptr); exact chunks go edge by edge (het_chunk).
 template <int NDET, bool TM = false>
 __device__ inline void het_chunks_warp(const HetTables& H, const HetPrep<NDET>& p, const float* s_anc, int first,
                                        int stride, int lane, unsigned char* stage, float* zr, float* zi, float* hh,
                                        float2* y = nullptr) {
   const int nc = H.n_chunks;
+  if (stage == nullptr) {
+    for (int q = first; q < nc; q += stride) {
+      const float* an = s_anc + q * kHetAncStride;
+      if (an[kHetAncExact] != 0.0f) {
+        het_chunk<NDET, TM>(H, p, 31 * q, lane, zr, zi, hh, y);
+        continue;
+      }
+      const int b = 31 * q + lane;
+      const bool has_bin = lane < 31 && b < H.n_bins;
+      HetBinData<NDET> t;
+      t.d = b <= H.n_bins ? __ldg(H.dfe + (size_t)q * kHetChunkEdges + lane) : 0.0f;
+      t.iw = has_bin ? __ldg(H.inv_width + b) : 0.0f;
+#pragma unroll
+      for (int i = 0; i < NDET; ++i) {
+        t.a[i] = has_bin ? __ldg(H.coef + (size_t)i * H.n_bins + b) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        t.bb[i] = has_bin ? __ldg(H.coefB + (size_t)i * H.n_bins + b) : make_float2(0.0f, 0.0f);
+      }
+      het_chunk_anc<NDET, TM>(H, p, an, q, lane, t, zr, zi, hh, y);
+    }
+    return;
+  }
   HetStage<NDET>* st = reinterpret_cast<HetStage<NDET>*>(stage);
   if (first < nc) het_stage_chunk<NDET>(H, first, lane, st);
   cp_async_commit();

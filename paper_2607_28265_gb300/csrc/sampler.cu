@@ -120,7 +120,7 @@ struct SamplerConst {
   int n_slots;    // request slots: nrep, or 2 nrep with par_out
   int claim_off;  // byte offset (in the dynamic shared memory after the slice data) of the claim words
                   // (heterodyned sampler: of the chunk anchors)
-  int stage_off;  // heterodyned sampler: byte offset of the warps' chunk-table stages
+  int stage_off;  // heterodyned sampler: byte offset of the warps' chunk-table stages (0: none)
 };
 
 struct ChainState {
@@ -2165,7 +2165,8 @@ __global__ void __launch_bounds__(kHetThreads, 1)
           // chunk anchors, one thread per chunk, then the edge pass
           for (int q = threadIdx.x; q < nc; q += blockDim.x) het_anchor<NDET>(H, p, q, s_anc + q * kHetAncStride);
           __syncthreads();
-          unsigned char* stage = smem + S.stage_off + (size_t)warp * 2 * sizeof(HetStage<NDET>);
+          unsigned char* stage =
+              S.stage_off > 0 ? smem + S.stage_off + (size_t)warp * 2 * sizeof(HetStage<NDET>) : nullptr;
           if (L.tm_n > 0)
             het_chunks_warp<NDET, true>(H, p, s_anc, warp, n_warps, lane, stage, zr, zi, hh,
                                         reinterpret_cast<float2*>(smem));
@@ -2573,6 +2574,10 @@ int run_setup(swig_ctx* c, RunState& R) {
   S.stage_off = (int)((S.claim_off + sizeof(float) * kHetAncStride * (size_t)c->B.het_nc + 15) & ~(size_t)15);
   R.smem = het ? S.stage_off + 2 * het_stage_bytes(L.n_det) * (kHetThreads / 32)
                : fixed + flow_tiles + S.claim_off + sizeof(int) * (size_t)S.n_slots;
+  if (het && R.smem > 220 * 1024) {  // no room for the chunk-table stages: direct loads
+    R.smem = S.stage_off;
+    S.stage_off = 0;
+  }
   if (R.smem > 220 * 1024) return fail(c, SWIG_E_ARG, "problem too large for the persistent kernel's shared memory");
 
   // buffers
