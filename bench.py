@@ -273,7 +273,7 @@ def run_campaign(args, rank, world):
         ctx.get_samples()
     torch.cuda.synchronize()
     e2e_ms = (time.perf_counter() - t0) * 1e3
-    e2e_evals = sum(r.n_evals for r in res)
+    e2e_evals = sum(r.n_sweep_evals for r in res)  # full-grid evaluations, as `value`
     h2d = sum(c.profile()["h2d_bytes"] for c in ctxs) - h2d0
     d2h = sum(c.profile()["d2h_bytes"] for c in ctxs) - d2h0
     tmax, tsum = reduce_over_ranks([total_ms, evals, e2e_ms, e2e_evals, full], world)
