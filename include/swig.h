@@ -104,6 +104,14 @@ typedef struct swig_sampler_cfg {
    * see Sec. 3.2 on fast and slow blocks).  A verification switch: the cached
    * and uncached samplers must agree in distribution.  0 = the cache. */
   int cache_off;
+  /* Launch shape of the full-grid mixed-precision sampler (0 selects the
+   * default in brackets; swig_autotune picks them per problem): slice parts,
+   * the number of sweep units each CTA's share of a proposal is split into,
+   * 1..4 [1]; stepout_one_end 1 steps a slice bracket out one end at a time
+   * instead of both ends in flight [0].  Both leave the evaluations and
+   * results the same up to the grouping of the per-part FP32 sums. */
+  int flow_parts;
+  int stepout_one_end;
 } swig_sampler_cfg;
 
 typedef struct swig_result {
@@ -246,6 +254,18 @@ int swig_prior_transform(swig_ctx* ctx, const double* u, int64_t n, double* thet
  * chains per CTA of the persistent kernel.  SWIG_E_TIMEOUT if a bounded
  * device wait expired (the context stays usable). */
 int swig_run(swig_ctx* ctx, swig_result* out);
+/* Launch-shape tuning for this context's problem (grid, detectors, prior,
+ * sampler settings): runs `iters` NS iterations from the configured seed
+ * with each candidate shape (flow_parts, stepout_one_end) in (1, 0), (1, 1),
+ * (2, 0), (3, 0), measures full-grid evaluations per second of the
+ * persistent kernel (CUDA events), and keeps the fastest in the context's
+ * sampler settings for later runs.  out (optional): out[0] the number of
+ * candidates, then per candidate flow_parts, stepout_one_end and the rate
+ * (min(n, 1 + 3 x candidates) values).  Only the full-grid mixed-precision
+ * covariance-proposal sampler has a launch shape: for other settings it
+ * writes out[0] = 0 and changes nothing.  Errors as swig_run; the settings
+ * are restored on an error. */
+int swig_autotune(swig_ctx* ctx, int iters, double* out, int n);
 /* Run nested sampling for a campaign of n_ctx events (config 4), each a
  * context set up as for swig_run; outs[i] receives event i's result and each
  * context keeps its samples.  Events that can share a launch (full grid, mixed

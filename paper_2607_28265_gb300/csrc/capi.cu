@@ -1157,6 +1157,9 @@ int swig_set_sampler(swig_ctx* c, const swig_sampler_cfg* cfg) {
   if (!(cfg->dlogz < 0.0) || cfg->max_iter < 1) return fail(c, SWIG_E_ARG, "need dlogz < 0 and max_iter >= 1");
   if (cfg->tmarg_nodes < 0 || cfg->tmarg_nodes > kMaxTmNodes) return fail(c, SWIG_E_ARG, "tmarg_nodes must be in [0, 65536]");
   if (cfg->cache_off != 0 && cfg->cache_off != 1) return fail(c, SWIG_E_ARG, "cache_off must be 0 or 1");
+  if (cfg->flow_parts < 0 || cfg->flow_parts > 4) return fail(c, SWIG_E_ARG, "flow_parts must be 0..4");
+  if (cfg->stepout_one_end != 0 && cfg->stepout_one_end != 1)
+    return fail(c, SWIG_E_ARG, "stepout_one_end must be 0 or 1");
   if (c->cfg_set && (c->cfg.precision != cfg->precision || c->cfg.likelihood != cfg->likelihood ||
                      c->cfg.het_bins != cfg->het_bins || c->cfg.het_spacing != cfg->het_spacing ||
                      c->cfg.tmarg_nodes != cfg->tmarg_nodes ||

@@ -2522,9 +2522,9 @@ int run_setup(swig_ctx* c, RunState& R) {
   // by up to G sweep warps of the CTA at once; each part has its own partial
   // (fixed places, fixed summation order), at most 4 (the partial buffers
   // hold 4 per slice and theta)
-  S.flow_parts = SWIG_FLOW_PARTS;
+  S.flow_parts = c->cfg.flow_parts > 0 ? c->cfg.flow_parts : SWIG_FLOW_PARTS;
   // two-ended stepping-out: the full-grid mixed-precision dataflow kernel
-  S.par_out = mixed ? SWIG_PAR_OUT : 0;
+  S.par_out = mixed && !c->cfg.stepout_one_end ? SWIG_PAR_OUT : 0;
   S.n_slots = S.par_out ? 2 * k : k;
   // learned proposal: retrain every learn_interval iterations (one launch each)
   R.learned = c->cfg.proposal == SWIG_PROPOSAL_LEARNED;
@@ -3047,6 +3047,44 @@ int run_loop_multi(swig_ctx* const* ctxs, std::vector<RunState>& R, int i0, int 
 }  // namespace
 
 extern "C" {
+
+int swig_autotune(swig_ctx* c, int iters, double* out, int n) {
+  if (!c) return SWIG_E_ARG;
+  if (iters < 1) return fail(c, SWIG_E_ARG, "autotune needs at least one iteration");
+  if (out && n > 0) out[0] = 0.0;
+  const swig_sampler_cfg saved = c->cfg;
+  if (!c->cfg_set) return fail(c, SWIG_E_STATE, "sampler settings not set");
+  if (saved.likelihood != SWIG_LIKE_FULL || saved.precision != SWIG_PREC_MIXED ||
+      saved.proposal != SWIG_PROPOSAL_COV)
+    return SWIG_OK;
+  const int cand[4][2] = {{1, 0}, {1, 1}, {2, 0}, {3, 0}};
+  double rate[4] = {0.0, 0.0, 0.0, 0.0};
+  int best = 0;
+  for (int i = 0; i < 4; ++i) {
+    c->cfg = saved;
+    c->cfg.flow_parts = cand[i][0];
+    c->cfg.stepout_one_end = cand[i][1];
+    c->cfg.max_iter = iters;
+    swig_result r;
+    const int rc = swig_run(c, &r);
+    if (rc != SWIG_OK) {
+      c->cfg = saved;
+      return rc;
+    }
+    rate[i] = c->profile[6] > 0.0 ? (double)r.n_sweep_evals / (c->profile[6] * 1e-3) : 0.0;
+    if (rate[i] > rate[best]) best = i;
+  }
+  c->cfg = saved;
+  c->cfg.flow_parts = cand[best][0];
+  c->cfg.stepout_one_end = cand[best][1];
+  if (out && n > 0) {
+    out[0] = 4.0;
+    for (int i = 0; i < 4; ++i)
+      for (int j = 0; j < 3; ++j)
+        if (1 + 3 * i + j < n) out[1 + 3 * i + j] = j == 0 ? cand[i][0] : j == 1 ? cand[i][1] : rate[i];
+  }
+  return SWIG_OK;
+}
 
 int swig_run(swig_ctx* c, swig_result* out) {
   if (!c) return SWIG_E_ARG;

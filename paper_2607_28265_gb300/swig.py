@@ -40,7 +40,7 @@ class SwigSamplerCfg(ctypes.Structure):
                 ("het_bins", _c_int), ("het_spacing", _c_int), ("dlogz", _c_double), ("max_iter", _c_int),
                 ("het_fiducial", _c_double * N_PARAMS), ("learn_mix", _c_double), ("learn_lr", _c_double),
                 ("learn_steps", _c_int), ("learn_interval", _c_int), ("tmarg_nodes", _c_int),
-                ("cache_off", _c_int)]
+                ("cache_off", _c_int), ("flow_parts", _c_int), ("stepout_one_end", _c_int)]
 
 
 class SwigResult(ctypes.Structure):
@@ -64,6 +64,7 @@ SIGNATURES = {
     "swig_loglike_batch_dev": (_c_int, [_vp, _vp, _c_i64, _vp, _vp]),
     "swig_prior_transform": (_c_int, [_vp, _dp, _c_i64, _dp]),
     "swig_run": (_c_int, [_vp, ctypes.POINTER(SwigResult)]),
+    "swig_autotune": (_c_int, [_vp, _c_int, _dp, _c_int]),
     "swig_set_wait_limit": (_c_int, [_vp, ctypes.c_longlong]),
     "swig_get_profile": (_c_int, [_vp, _dp, _c_int]),
     "swig_set_stream": (_c_int, [_vp, _vp]),
@@ -191,7 +192,7 @@ class Context:
     def set_sampler(self, nlive, nrep, sweeps=1, steps_per_dim=5, seed=0, likelihood=LIKE_FULL,
                     precision=PREC_MIXED, proposal=PROPOSAL_COV, het_bins=0, het_spacing=0, dlogz=-3.0,
                     max_iter=100000, het_fiducial=None, learn_mix=0.0, learn_lr=0.0, learn_steps=0,
-                    learn_interval=0, tmarg_nodes=0, cache_off=0):
+                    learn_interval=0, tmarg_nodes=0, cache_off=0, flow_parts=0, stepout_one_end=0):
         """swig_set_sampler: the fields of swig_sampler_cfg (include/swig.h).
 
         nlive / nrep: live points m and deletions k per iteration; sweeps (M)
@@ -215,6 +216,8 @@ class Context:
         cfg.learn_steps, cfg.learn_interval = int(learn_steps), int(learn_interval)
         cfg.tmarg_nodes = int(tmarg_nodes)
         cfg.cache_off = int(cache_off)
+        cfg.flow_parts = int(flow_parts)
+        cfg.stepout_one_end = int(stepout_one_end)
         self._check(self.lib.swig_set_sampler(self.h, ctypes.byref(cfg)))
 
     # ---- likelihood --------------------------------------------------------
@@ -261,6 +264,21 @@ class Context:
         self._check(self.lib.swig_run(self.h, ctypes.byref(r)))
         return RunResult(r.logz, r.logz_err, r.info, r.ess, r.wall_s, r.n_dead, r.n_iter, r.n_evals,
                          r.n_sweep_evals, r.status)
+
+    def autotune(self, iters=8):
+        """swig_autotune: try the launch shapes for `iters` NS iterations each and
+        keep the fastest.  Returns (candidates, chosen): candidates a list of
+        (flow_parts, stepout_one_end, full-grid evals/s), chosen the kept
+        (flow_parts, stepout_one_end) or None when the settings have no
+        launch shape."""
+        buf = np.zeros(1 + 3 * 8)
+        self._check(self.lib.swig_autotune(self.h, int(iters), buf.ctypes.data_as(_dp), buf.size))
+        n = int(buf[0])
+        cands = [(int(buf[1 + 3 * i]), int(buf[2 + 3 * i]), float(buf[3 + 3 * i])) for i in range(n)]
+        if not cands:
+            return cands, None
+        best = max(cands, key=lambda t: t[2])
+        return cands, (best[0], best[1])
 
     PROFILE_KEYS = ("rounds", "boundary_s", "control_s", "wait_control_s", "sweep_s", "wait_sweep_s",
                     "persistent_ms", "persistent_launches", "kernel_launches", "h2d_bytes", "d2h_bytes",

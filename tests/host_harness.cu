@@ -274,6 +274,7 @@ int main(int argc, char** argv) {
     SWIG_FIELD(swig_sampler_cfg, learn_mix); SWIG_FIELD(swig_sampler_cfg, learn_lr);
     SWIG_FIELD(swig_sampler_cfg, learn_steps); SWIG_FIELD(swig_sampler_cfg, learn_interval);
     SWIG_FIELD(swig_sampler_cfg, tmarg_nodes); SWIG_FIELD(swig_sampler_cfg, cache_off);
+    SWIG_FIELD(swig_sampler_cfg, flow_parts); SWIG_FIELD(swig_sampler_cfg, stepout_one_end);
     first = true;
     std::printf("]}, \"swig_result\": {\"size\": %zu, \"fields\": [", sizeof(swig_result));
     SWIG_FIELD(swig_result, logz); SWIG_FIELD(swig_result, logz_err); SWIG_FIELD(swig_result, info);
