@@ -5,8 +5,10 @@ itself; the oracle forms its own (FP64, numpy).  Both must give the same
 heterodyned logL for the same fiducial, bin count and spacing.  The device
 contraction is FP32 per bin: its rounding error is bounded by a few ulps of
 the sum of the absolute per-bin terms, which here never exceeds ~2x the
-matched-filter SNR^2 plus <h|h>, so 1e-6 relative to |logL| plus 2e-4 absolute
-holds with margin (the constant -<d|d>/2 is FP64 on both sides).
+matched-filter SNR^2 plus <h|h> (the constant -<d|d>/2 is FP64 on both sides).
+The checks use the stated parity bound 1e-6 |logL| + 1e-6: with -<d|d>/2 in
+logL the relative term dominates (~4e-3 on the 4 s grid, where the largest
+measured error is 1.7e-3).
 """
 import numpy as np
 import pytest
@@ -22,6 +24,8 @@ swig = pytest.importorskip("paper_2607_28265_gb300.swig")
 
 
 def _tol(want):
+    # the heterodyne against the full grid at the injection (an approximation
+    # error, not a parity bound)
     return 1e-6 * np.abs(want) + 2e-4
 
 
@@ -66,7 +70,7 @@ def test_het_matches_oracle_cfg1(cfg1, n_bins):
     thetas = _thetas(wl, ev, th, 40, n_bins, 0.002)
     got = ctx.loglike_batch(thetas)
     want = np.array([L.het_loglike(ev, het, t) for t in thetas])
-    parity.check(f"heterodyned batch (4 s H1, {n_bins} bins)", got, want, 1e-6, 2e-4)
+    parity.check(f"heterodyned batch (4 s H1, {n_bins} bins)", got, want, 1e-6, 1e-6)
     # at the fiducial itself the heterodyned logL is the full logL up to the
     # FP32 contraction (r = 1 exactly in every bin)
     full = L.loglike(ev, th)
@@ -86,7 +90,7 @@ def test_het_geometric_spacing_and_fiducial_offset(cfg1):
     thetas = _thetas(wl, ev, th, 30, 99, 0.003)
     got = ctx.loglike_batch(thetas)
     want = np.array([L.het_loglike(ev, het, t) for t in thetas])
-    parity.check("heterodyned batch (4 s H1, geometric, offset fiducial)", got, want, 1e-6, 2e-4)
+    parity.check("heterodyned batch (4 s H1, geometric, offset fiducial)", got, want, 1e-6, 1e-6)
     ctx.close()
 
 
@@ -101,12 +105,12 @@ def test_het_full_size_three_detectors():
     thetas = _thetas(wl, ev, th, 24, 5, 0.0005)
     got = ctx.loglike_batch(thetas)
     want = np.array([L.het_loglike(ev, het, t) for t in thetas])
-    parity.check("heterodyned batch (128 s HLV, 5000 bins)", got, want, 1e-6, 2e-4)
+    parity.check("heterodyned batch (128 s HLV, 5000 bins)", got, want, 1e-6, 1e-6)
     # switching back to the full likelihood re-prepares the context
     ctx.set_sampler(nlive=1000, nrep=100, likelihood=swig.LIKE_FULL)
     full = ctx.loglike_batch(thetas[-4:])
     want_full = np.array([L.loglike(ev, t) for t in thetas[-4:]])
-    parity.check("full-grid batch beside the heterodyned one (128 s HLV)", full, want_full, 1e-6, 1e-4)
+    parity.check("full-grid batch beside the heterodyned one (128 s HLV)", full, want_full, 1e-6, 1e-6)
     ctx.close()
 
 

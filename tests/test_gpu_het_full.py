@@ -28,8 +28,7 @@ NB = 5000
 ITERS = 40
 
 
-# Parity bound: that of tests/test_gpu_het.py (FP32 contraction), 1e-6
-# relative plus 2e-4 absolute.
+# Parity bound: the stated 1e-6 |logL| + 1e-6 (the relative term is ~0.78 here).
 
 
 @pytest.fixture(scope="module")
@@ -61,4 +60,4 @@ def test_full_size_het_dead_points_match_oracle(cfg2, cache_off):
     idx = np.concatenate([rng.choice(len(ll) - 1000, 6, replace=False),
                           len(ll) - 1000 + rng.choice(1000, 10, replace=False)])
     want = np.array([L.het_loglike(ev, het, thd[i]) for i in idx])
-    parity.check(f"heterodyned sampler dead points (128 s HLV, cache_off={cache_off})", ll[idx], want, 1e-6, 2e-4)
+    parity.check(f"heterodyned sampler dead points (128 s HLV, cache_off={cache_off})", ll[idx], want, 1e-6, 1e-6)

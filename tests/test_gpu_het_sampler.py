@@ -30,7 +30,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 NB = 450
 
 
-# Parity bound: that of tests/test_gpu_het.py, 1e-6 relative plus 2e-4 absolute.
+# Parity bound: the stated 1e-6 |logL| + 1e-6 (the relative term is ~4e-3 here;
+# largest measured error 2.4e-3).
 
 
 @pytest.fixture(scope="module")
@@ -59,7 +60,7 @@ def test_het_dead_points_match_oracle_and_are_deterministic(cfg1, spacing):
     assert abs(m + math.log(np.sum(np.exp(lw - m))) - r.logz) < 1e-9
     idx = np.linspace(0, len(ll) - 1, 24).astype(int)
     want = np.array([L.het_loglike(ev, het, thd[i]) for i in idx])
-    parity.check(f"heterodyned sampler dead points (4 s H1, spacing {spacing})", ll[idx], want, 1e-6, 2e-4)
+    parity.check(f"heterodyned sampler dead points (4 s H1, spacing {spacing})", ll[idx], want, 1e-6, 1e-6)
     r2 = ctx.run()
     thd2, ll2, _ = ctx.get_samples()
     assert r2.logz == r.logz and np.array_equal(ll, ll2) and np.array_equal(thd, thd2)
