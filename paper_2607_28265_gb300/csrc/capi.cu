@@ -507,6 +507,73 @@ namespace swig {
 
 // Summary data of the heterodyned likelihood (host FP64 from the device FP64
 // fiducial waveform) and the per-edge basis tables.
+// Gather pieces of the time pass's non-uniform FFT: each grid point's
+// entries (ptr[l] .. ptr[l + 1], consecutive edges from edge[l]) in runs of
+// at most kNufftPiece, piece = (first entry, entries, first edge, 0), and the
+// grid points with entries, point = (grid point, first piece, pieces, 0).
+void nufft_pieces(const std::vector<int>& ptr, const std::vector<int>& edge, int M, std::vector<int4>& piece,
+                  std::vector<int4>& point) {
+  piece.clear();
+  point.clear();
+  for (int l = 0; l < M; ++l) {
+    const int n = ptr[l + 1] - ptr[l];
+    if (n == 0) continue;
+    point.push_back(make_int4(l, (int)piece.size(), (n + kNufftPiece - 1) / kNufftPiece, 0));
+    for (int o = 0; o < n; o += kNufftPiece)
+      piece.push_back(make_int4(ptr[l] + o, std::min(kNufftPiece, n - o), edge[l] + o, 0));
+  }
+}
+
+// Chunk anchor tables of the heterodyned contraction (kernels.h
+// HetChunkRow): chunk q holds edges 31 q .. 31 q + 31 (f[idx[e]]), anchored
+// at its first edge f_a with span S = f_last - f_a; rows: basis values and
+// first derivatives times S (double-float), derivatives of orders
+// 2..kHetTaylorDeg times S^n / n! (float), f_a, 1 / S, and the order-11
+// remainder bound per unit coefficient, max |phi_j^(11)| S^11 / 11! over the
+// chunk.  dfe[32 q + l] = f_e - f_a.  Returns the number of chunks.
+int het_chunk_tables(const std::vector<double>& f, const std::vector<int>& idx, int nb, std::vector<float>& ct,
+                     std::vector<float>& dfe) {
+  const int nc = (nb + 30) / 31;
+  ct.assign((size_t)HC_ROWS * nc, 0.0f);
+  dfe.assign((size_t)nc * kHetChunkEdges, 0.0f);
+  {
+    const int order = kHetTaylorDeg + 1;
+    double fact = 1.0;
+    for (int i = 2; i <= order; ++i) fact *= i;
+    for (int q = 0; q < nc; ++q) {
+      const int e0 = 31 * q, e1 = std::min(31 * q + 31, nb);
+      const double fa = f[idx[e0]], fb = f[idx[e1]], span = fb - fa;
+      auto put = [&](int row, double v) { ct[(size_t)row * nc + q] = (float)v; };
+      float hi, lo;
+      split_df(fa, &hi, &lo);
+      put(HC_FA_HI, hi);
+      put(HC_FA_LO, lo);
+      put(HC_INV_S, span > 0.0 ? 1.0 / span : 0.0);
+      for (int j = 0; j < NBASIS; ++j) {
+        const bool one = j == B_ONE;
+        // remainder bound per unit |c_j - c0_j| (the device sums it per evaluation)
+        put(HC_BND + j,
+            one ? 0.0 : basis_derivative_bound(kBasisPow[j], kBasisLog[j], order, fa, fb) * std::pow(span, order) / fact);
+        split_df(one ? 1.0 : basis_derivative(kBasisPow[j], kBasisLog[j], 0, fa), &hi, &lo);
+        put(HC_VAL_HI + j, hi);
+        put(HC_VAL_LO + j, lo);
+        split_df(one ? 0.0 : basis_derivative(kBasisPow[j], kBasisLog[j], 1, fa) * span, &hi, &lo);
+        put(HC_D1_HI + j, hi);
+        put(HC_D1_LO + j, lo);
+        double nf = 1.0;
+        for (int m = 0; m < kHetPoly; ++m) {
+          const int nn = m + 2;
+          nf *= nn;
+          put(HC_POLY + m * NBASIS + j,
+              one ? 0.0 : basis_derivative(kBasisPow[j], kBasisLog[j], nn, fa) * std::pow(span, nn) / nf);
+        }
+      }
+      for (int l = 0; l < kHetChunkEdges && e0 + l <= nb; ++l) dfe[(size_t)q * kHetChunkEdges + l] = (float)(f[idx[e0 + l]] - fa);
+    }
+  }
+  return nc;
+}
+
 int prepare_het(swig_ctx* c) {
   LikeConst& L = c->L;
   DeviceBuffers& B = c->B;
@@ -560,45 +627,9 @@ int prepare_het(swig_ctx* c) {
     }
     split_df(fe, &ef[q], &ef[ne + q]);
   }
-  // chunk anchor tables (kernels.h HetChunkRow): chunk q holds edges
-  // 31 q .. 31 q + 31, anchored at its first edge
-  const int nc = (nb + 30) / 31;
-  std::vector<float> ct((size_t)HC_ROWS * nc, 0.0f), dfe((size_t)nc * kHetChunkEdges, 0.0f);
-  {
-    const int order = kHetTaylorDeg + 1;
-    double fact = 1.0;
-    for (int i = 2; i <= order; ++i) fact *= i;
-    for (int q = 0; q < nc; ++q) {
-      const int e0 = 31 * q, e1 = std::min(31 * q + 31, nb);
-      const double fa = f[idx[e0]], fb = f[idx[e1]], span = fb - fa;
-      auto put = [&](int row, double v) { ct[(size_t)row * nc + q] = (float)v; };
-      float hi, lo;
-      split_df(fa, &hi, &lo);
-      put(HC_FA_HI, hi);
-      put(HC_FA_LO, lo);
-      put(HC_INV_S, span > 0.0 ? 1.0 / span : 0.0);
-      for (int j = 0; j < NBASIS; ++j) {
-        const bool one = j == B_ONE;
-        // remainder bound per unit |c_j - c0_j| (the device sums it per evaluation)
-        put(HC_BND + j,
-            one ? 0.0 : basis_derivative_bound(kBasisPow[j], kBasisLog[j], order, fa, fb) * std::pow(span, order) / fact);
-        split_df(one ? 1.0 : basis_derivative(kBasisPow[j], kBasisLog[j], 0, fa), &hi, &lo);
-        put(HC_VAL_HI + j, hi);
-        put(HC_VAL_LO + j, lo);
-        split_df(one ? 0.0 : basis_derivative(kBasisPow[j], kBasisLog[j], 1, fa) * span, &hi, &lo);
-        put(HC_D1_HI + j, hi);
-        put(HC_D1_LO + j, lo);
-        double nf = 1.0;
-        for (int m = 0; m < kHetPoly; ++m) {
-          const int nn = m + 2;
-          nf *= nn;
-          put(HC_POLY + m * NBASIS + j,
-              one ? 0.0 : basis_derivative(kBasisPow[j], kBasisLog[j], nn, fa) * std::pow(span, nn) / nf);
-        }
-      }
-      for (int l = 0; l < kHetChunkEdges && e0 + l <= nb; ++l) dfe[(size_t)q * kHetChunkEdges + l] = (float)(f[idx[e0 + l]] - fa);
-    }
-  }
+  // chunk anchor tables (kernels.h HetChunkRow)
+  std::vector<float> ct, dfe;
+  const int nc = het_chunk_tables(f, idx, nb, ct, dfe);
   CUDA_TRY(c, cudaMalloc(&B.het_chunk, sizeof(float) * ct.size()));
   CUDA_TRY(c, cudaMalloc(&B.het_dfe, sizeof(float) * dfe.size()));
   CUDA_TRY(c, cudaMemcpy(B.het_chunk, ct.data(), sizeof(float) * ct.size(), cudaMemcpyHostToDevice));
@@ -640,13 +671,7 @@ int prepare_het(swig_ctx* c) {
       // kNufftPiece (summed by one lane each), and the grid points with
       // entries (their pieces are combined in order)
       std::vector<int4> piece, point;
-      for (int l = 0; l < L.tm_M; ++l) {
-        const int n = ptr[l + 1] - ptr[l];
-        if (n == 0) continue;
-        point.push_back(make_int4(l, (int)piece.size(), (n + kNufftPiece - 1) / kNufftPiece, 0));
-        for (int o = 0; o < n; o += kNufftPiece)
-          piece.push_back(make_int4(ptr[l] + o, std::min(kNufftPiece, n - o), edge[l] + o, 0));
-      }
+      nufft_pieces(ptr, edge, L.tm_M, piece, point);
       L.tm_pieces = (int)piece.size();
       L.tm_points = (int)point.size();
       CUDA_TRY(c, cudaMalloc(&B.het_nu_piece, sizeof(int4) * std::max<size_t>(1, piece.size())));

@@ -23,6 +23,8 @@
 //   host_harness tmtables < NB NDET DT EDGES A01       time-marginalisation edge tables
 //   host_harness hetsum < N NB NDET DF F IDX (DATA PSD H0)xNDET   heterodyne summary data
 //   host_harness weights F_MIN F_MAX DF NDET STRIDE < (DATA PSD)xNDET   full-grid data weights
+//   host_harness hetchunks F_MIN F_MAX DF N_BINS SPACING   heterodyne chunk anchor tables
+//   host_harness nufftpieces NT DT < NE FE...           gather pieces of the time-pass NUFFT
 #include "../paper_2607_28265_gb300/csrc/capi.cu"
 
 #include <cstddef>
@@ -303,6 +305,54 @@ int main(int argc, char** argv) {
     for (size_t q = 0; q < wt.size(); ++q) std::printf("%s%.9g", q ? ", " : "", wt[q]);
     std::printf("], \"corr\": [");
     for (size_t q = 0; q < corr.size(); ++q) std::printf("%s%.9g", q ? ", " : "", corr[q]);
+    std::printf("]}\n");
+    return 0;
+  }
+  if (what == "hetchunks" && argc == 7) {
+    swig_ctx c;
+    if (swig_set_grid(&c, std::atof(argv[2]), std::atof(argv[3]), std::atof(argv[4])) != SWIG_OK) return 3;
+    std::vector<double> f((size_t)c.n_bins);
+    for (int64_t k = 0; k < c.n_bins; ++k) f[(size_t)k] = (double)(c.k_min + k) * c.df;
+    const std::vector<int> idx = het_edge_indices(f, std::atoi(argv[5]), std::atoi(argv[6]));
+    const int nb = (int)idx.size() - 1;
+    std::vector<float> ct, dfe;
+    const int nc = het_chunk_tables(f, idx, nb, ct, dfe);
+    std::printf("{\"nb\": %d, \"nc\": %d, \"rows\": %d, \"nbasis\": %d, \"poly\": %d, \"row\": {\"val_hi\": %d, "
+                "\"val_lo\": %d, \"d1_hi\": %d, \"d1_lo\": %d, \"poly\": %d, \"fa_hi\": %d, \"fa_lo\": %d, \"inv_s\": %d, "
+                "\"bnd\": %d}, \"fe\": [",
+                nb, nc, (int)HC_ROWS, (int)NBASIS, kHetPoly, (int)HC_VAL_HI, (int)HC_VAL_LO, (int)HC_D1_HI,
+                (int)HC_D1_LO, (int)HC_POLY, (int)HC_FA_HI, (int)HC_FA_LO, (int)HC_INV_S, (int)HC_BND);
+    for (int e = 0; e <= nb; ++e) std::printf("%s%.17g", e ? ", " : "", f[idx[e]]);
+    std::printf("], \"ct\": [");
+    for (size_t q = 0; q < ct.size(); ++q) std::printf("%s%.9g", q ? ", " : "", ct[q]);
+    std::printf("], \"dfe\": [");
+    for (size_t q = 0; q < dfe.size(); ++q) std::printf("%s%.9g", q ? ", " : "", dfe[q]);
+    std::printf("]}\n");
+    return 0;
+  }
+  if (what == "nufftpieces" && argc == 4) {
+    int ne = 0;
+    if (std::scanf("%d", &ne) != 1 || ne < 1) return 3;
+    std::vector<double> fe(ne);
+    for (int e = 0; e < ne; ++e)
+      if (std::scanf("%lf", &fe[e]) != 1) return 3;
+    int M = 0, j0 = 0;
+    std::vector<int> ptr, edge;
+    std::vector<float> wt, corr;
+    std::vector<float2> tw;
+    het_nufft_tables(fe, std::atoi(argv[2]), std::atof(argv[3]), kNufftWidth, &M, &j0, ptr, edge, wt, corr, tw);
+    std::vector<int4> piece, point;
+    if (!ptr.empty()) nufft_pieces(ptr, edge, M, piece, point);
+    std::printf("{\"M\": %d, \"max_piece\": %d, \"ptr\": [", M, kNufftPiece);
+    for (size_t q = 0; q < ptr.size(); ++q) std::printf("%s%d", q ? ", " : "", ptr[q]);
+    std::printf("], \"edge\": [");
+    for (size_t q = 0; q < edge.size(); ++q) std::printf("%s%d", q ? ", " : "", edge[q]);
+    std::printf("], \"piece\": [");
+    for (size_t q = 0; q < piece.size(); ++q)
+      std::printf("%s[%d, %d, %d]", q ? ", " : "", piece[q].x, piece[q].y, piece[q].z);
+    std::printf("], \"point\": [");
+    for (size_t q = 0; q < point.size(); ++q)
+      std::printf("%s[%d, %d, %d]", q ? ", " : "", point[q].x, point[q].y, point[q].z);
     std::printf("]}\n");
     return 0;
   }

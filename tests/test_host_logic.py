@@ -407,3 +407,99 @@ def test_time_pass_nufft_tables_reproduce_the_direct_sum(harness, n_t):
     Z = X[(j - j0) % M] * corr
     Zd = np.exp(-2j * np.pi * np.outer(t0 + j * dt, edges)) @ y
     assert np.max(np.abs(Z - Zd)) < 1e-7 * np.sum(np.abs(y))
+
+
+# Basis of the phase in cycles, phi_j(f) (the order of the device's Basis enum):
+# f^-5/3, f^-1, f^-2/3, f^-1/3, ln f, f^1/3, f^1/3 ln f, f^2/3, f^5/3, f^7/3, 1.
+_BASIS_POW = (-5 / 3, -1.0, -2 / 3, -1 / 3, 0.0, 1 / 3, 1 / 3, 2 / 3, 5 / 3, 7 / 3, 0.0)
+_BASIS_LOG = (0, 0, 0, 0, 1, 0, 1, 0, 0, 0, 0)
+
+
+def _basis(f):
+    f = np.asarray(f, dtype=np.float64)
+    out = []
+    for p, lg in zip(_BASIS_POW, _BASIS_LOG):
+        v = f ** p if p != 0.0 else np.ones_like(f)
+        out.append(v * np.log(f) if lg else v)
+    return np.array(out)  # [NBASIS][n]
+
+
+@pytest.mark.parametrize("which,nb,spacing", [("cfg2", 5000, 0), ("cfg1", 450, 1), ("cfg1", 300, 0)])
+def test_het_chunk_taylor_form_within_its_remainder_bound(harness, which, nb, spacing):
+    """The heterodyned contraction's chunk tables: the phase difference
+    sum_j dc_j phi_j(f_e) at every edge, formed from a chunk's anchor values,
+    scaled derivatives and edge offsets as the device forms it (degree-10
+    Taylor form in x = (f_e - f_a) / S), equals the direct basis sum within
+    the chunk's remainder bound sum_j |dc_j| bnd_j (plus the FP32 storage of
+    the table entries).  dc from coefficient differences of real parameter
+    pairs (the library's own coefficient code), near the fiducial and far
+    from it; near it, nearly every chunk stays under the device's 1e-6-cycle
+    threshold."""
+    wl = si.config2() if which == "cfg2" else si.config1()
+    out = _run(harness, "hetchunks", repr(wl.f_min), repr(wl.f_max), repr(wl.df), nb, spacing)
+    nc, nbasis, npoly, rows = out["nc"], out["nbasis"], out["poly"], out["row"]
+    # the tables are FP32: parse the printed values back to the exact floats
+    ct = np.array(out["ct"], dtype=np.float32).astype(np.float64).reshape(out["rows"], nc)
+    dfe = np.array(out["dfe"], dtype=np.float32).astype(np.float64).reshape(nc, 32)
+    fe = np.array(out["fe"])
+    assert nc == (out["nb"] + 30) // 31
+
+    def row(name, j=0):
+        return ct[rows[name] + j]
+
+    val = np.array([row("val_hi", j) + row("val_lo", j) for j in range(nbasis)])  # [j][q]
+    d1 = np.array([row("d1_hi", j) + row("d1_lo", j) for j in range(nbasis)])
+    poly = np.array([[row("poly", m * nbasis + j) for j in range(nbasis)] for m in range(npoly)])  # [m][j][q]
+    bnd = np.array([row("bnd", j) for j in range(nbasis)])
+    inv_s = row("inv_s")
+    fa = row("fa_hi") + row("fa_lo")
+    th0 = (1.975, 0.8, 0.01, -0.02, 300.0, 500.0)
+    pairs = {"near": [(1.975 * (1 + 1e-5), 0.8004, 0.0101, -0.0199, 310.0, 490.0)],
+             "far": [(1.6, 0.55, -0.04, 0.04, 4000.0, 100.0)]}
+    c0 = np.array(_run(harness, "coeffs", *[repr(v) for v in th0])["c"])
+    for kind, ths in pairs.items():
+        for th in ths:
+            dc = np.array(_run(harness, "coeffs", *[repr(v) for v in th])["c"]) - c0
+            R = np.abs(dc) @ bnd  # [q]
+            anchored = 0
+            for q in range(nc):
+                e = np.arange(31 * q, min(31 * q + 31, out["nb"]) + 1)
+                assert abs(fe[e[0]] - fa[q]) <= 1e-9 * fe[e[0]]
+                direct = dc @ _basis(fe[e])
+                x = dfe[q, : e.size] * inv_s[q]
+                assert np.all(x >= -1e-6) and np.all(x <= 1 + 1e-6)
+                a = [dc @ val[:, q], dc @ d1[:, q]] + [dc @ poly[m, :, q] for m in range(npoly)]
+                taylor = a[0] + sum(a[n] * x ** n for n in range(1, npoly + 2))
+                storage = 1e-6 * sum(abs(v) for v in a[1:]) + 1e-12 * abs(a[0]) + 1e-12
+                assert np.all(np.abs(taylor - direct) <= R[q] + storage), (kind, q, np.abs(taylor - direct).max(), R[q])
+                anchored += R[q] <= 1e-6
+            if kind == "near" and which == "cfg2":  # 5,000 narrow bins: the Taylor path nearly everywhere
+                assert anchored >= 0.9 * nc, (anchored, nc)
+
+
+def test_nufft_gather_pieces_cover_every_entry_once(harness):
+    """The time pass's gather pieces: every grid point's entries, in order,
+    cut into runs of at most 31 consecutive edges; the point list names each
+    point with entries once, with its pieces contiguous."""
+    wl = si.config2()
+    edges, _ = L.phase_bound_edges(wl.freqs, 5000)
+    stdin = f"{edges.size}\n" + " ".join(repr(float(v)) for v in edges)
+    r = subprocess.run([harness, "nufftpieces", "2000", repr(0.2 / 2000)], input=stdin, capture_output=True, text=True,
+                       timeout=120)
+    assert r.returncode == 0, r.stderr
+    out = json.loads(r.stdout)
+    ptr, edge, piece, point, M = out["ptr"], out["edge"], out["piece"], out["point"], out["M"]
+    assert len(ptr) == M + 1
+    seen = np.zeros(ptr[-1], dtype=int)
+    nonempty = [l for l in range(M) if ptr[l + 1] > ptr[l]]
+    assert [p[0] for p in point] == nonempty
+    for l, p0, npc in point:
+        k = ptr[l]
+        for p in piece[p0:p0 + npc]:
+            k0, n, e0 = p
+            assert k0 == k and 1 <= n <= out["max_piece"] and e0 == edge[l] + (k0 - ptr[l])
+            seen[k0:k0 + n] += 1
+            k += n
+        assert k == ptr[l + 1]
+    assert np.all(seen == 1)
+    assert sum(npc for _, _, npc in point) == len(piece)
