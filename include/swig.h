@@ -96,7 +96,12 @@ typedef struct swig_sampler_cfg {
    * het_bins <= 16384): nodes of the midpoint grid over the uniform t_c
    * prior [lo, hi], t_j = lo + (j + 1/2)(hi - lo)/tmarg_nodes, 1..65536.
    * The spacing should resolve the t_c posterior (its width is roughly
-   * 1 / (2 pi SNR sigma_f), sigma_f the spread of the signal's frequencies). */
+   * 1 / (2 pi SNR sigma_f), sigma_f the spread of the signal's frequencies).
+   * With 64..4096 nodes the time pass is a non-uniform FFT on M >= 2 nodes
+   * grid points (a power of two) whose grid, twiddles and edge products share
+   * a CTA's shared memory with the sampler's state: about 8 (het_bins + 1) +
+   * 16 M bytes plus ~12 KB must fit in 220 KB, else swig_run returns
+   * SWIG_E_ARG (e.g. 5000 bins: up to 4096 nodes). */
   int tmarg_nodes;
   /* 1: evaluate every proposal in full, also for the blocks that only move
    * the projection factors (d_L, iota, psi, phi_c), which otherwise reuse the
