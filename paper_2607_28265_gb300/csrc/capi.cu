@@ -507,6 +507,17 @@ namespace swig {
 
 // Summary data of the heterodyned likelihood (host FP64 from the device FP64
 // fiducial waveform) and the per-edge basis tables.
+// Twiddles of the time pass's radix-2 FFT stage by stage: span h (1, 2, 4,
+// ..., M / 2) at h - 1 + p for p < h holds exp(2 pi i p / (2 h)), taken from
+// the plain table tw[k] = exp(2 pi i k / M) at k = p M / (2 h), so that every
+// stage reads consecutive entries.  M entries (the last unused).
+std::vector<float2> nufft_stage_twiddles(const std::vector<float2>& tw, int M) {
+  std::vector<float2> tws(M, make_float2(0.0f, 0.0f));
+  for (int h = 1; h < M; h <<= 1)
+    for (int q = 0; q < h; ++q) tws[h - 1 + q] = tw[(size_t)q * (M / (2 * h))];
+  return tws;
+}
+
 // Gather pieces of the time pass's non-uniform FFT: each grid point's
 // entries (ptr[l] .. ptr[l + 1], consecutive edges from edge[l]) in runs of
 // at most kNufftPiece, piece = (first entry, entries, first edge, 0), and the
@@ -683,12 +694,7 @@ int prepare_het(swig_ctx* c) {
       c->h2d_bytes += sizeof(int4) * (piece.size() + point.size());
       CUDA_TRY(c, cudaMalloc(&B.het_nu_wt, sizeof(float) * std::max<size_t>(1, wt.size())));
       CUDA_TRY(c, cudaMalloc(&B.het_nu_corr, sizeof(float) * corr.size()));
-      // twiddles stage by stage (span h: exp(2 pi i p / (2 h)), p < h, at
-      // h - 1 + p) so that a stage reads consecutive entries
-      std::vector<float2> tws(L.tm_M, make_float2(0.0f, 0.0f));
-      for (int h = 1; h < L.tm_M; h <<= 1)
-        for (int q = 0; q < h; ++q) tws[h - 1 + q] = tw[(size_t)q * (L.tm_M / (2 * h))];
-      tw.swap(tws);
+      tw = nufft_stage_twiddles(tw, L.tm_M);
       CUDA_TRY(c, cudaMalloc(&B.het_nu_tw, sizeof(float2) * tw.size()));
       CUDA_TRY(c, cudaMemcpy(B.het_nu_wt, wt.data(), sizeof(float) * wt.size(), cudaMemcpyHostToDevice));
       CUDA_TRY(c, cudaMemcpy(B.het_nu_corr, corr.data(), sizeof(float) * corr.size(), cudaMemcpyHostToDevice));

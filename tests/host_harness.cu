@@ -24,7 +24,8 @@
 //   host_harness hetsum < N NB NDET DF F IDX (DATA PSD H0)xNDET   heterodyne summary data
 //   host_harness weights F_MIN F_MAX DF NDET STRIDE < (DATA PSD)xNDET   full-grid data weights
 //   host_harness hetchunks F_MIN F_MAX DF N_BINS SPACING   heterodyne chunk anchor tables
-//   host_harness nufftpieces NT DT < NE FE...           gather pieces of the time-pass NUFFT
+//   host_harness nufftpieces NT DT < NE FE...           gather pieces and stage-major FFT twiddles of
+//                                                      the time-pass NUFFT
 #include "../paper_2607_28265_gb300/csrc/capi.cu"
 
 #include <cstddef>
@@ -343,7 +344,10 @@ int main(int argc, char** argv) {
     het_nufft_tables(fe, std::atoi(argv[2]), std::atof(argv[3]), kNufftWidth, &M, &j0, ptr, edge, wt, corr, tw);
     std::vector<int4> piece, point;
     if (!ptr.empty()) nufft_pieces(ptr, edge, M, piece, point);
-    std::printf("{\"M\": %d, \"max_piece\": %d, \"ptr\": [", M, kNufftPiece);
+    const std::vector<float2> tws = nufft_stage_twiddles(tw, M);
+    std::printf("{\"M\": %d, \"max_piece\": %d, \"tw\": [", M, kNufftPiece);
+    for (size_t q = 0; q < tws.size(); ++q) std::printf("%s[%.9g, %.9g]", q ? ", " : "", tws[q].x, tws[q].y);
+    std::printf("], \"ptr\": [");
     for (size_t q = 0; q < ptr.size(); ++q) std::printf("%s%d", q ? ", " : "", ptr[q]);
     std::printf("], \"edge\": [");
     for (size_t q = 0; q < edge.size(); ++q) std::printf("%s%d", q ? ", " : "", edge[q]);

@@ -503,3 +503,51 @@ def test_nufft_gather_pieces_cover_every_entry_once(harness):
         assert k == ptr[l + 1]
     assert np.all(seen == 1)
     assert sum(npc for _, _, npc in point) == len(piece)
+
+
+def test_nufft_fft_stage_twiddles_reproduce_the_dft(harness):
+    """The time pass's radix-2 FFT as the device runs it: bit-reversed input,
+    spans 1..16 inside 32-point blocks (each lane pairs with lane ^ h, the
+    lower point adding w x partner, the upper subtracting), then the wider
+    spans in shared memory, twiddles read from the host's stage-major table
+    at h - 1 + p.  Against numpy's inverse-sign DFT of the natural-order
+    input, to FP32 accuracy."""
+    wl = si.config2()
+    edges, _ = L.phase_bound_edges(wl.freqs, 5000)
+    stdin = f"{edges.size}\n" + " ".join(repr(float(v)) for v in edges)
+    r = subprocess.run([harness, "nufftpieces", "2000", repr(0.2 / 2000)], input=stdin, capture_output=True, text=True,
+                       timeout=120)
+    assert r.returncode == 0, r.stderr
+    out = json.loads(r.stdout)
+    M = out["M"]
+    tw = np.array([complex(a, b) for a, b in out["tw"]], dtype=np.complex64)
+    assert tw.size == M
+    lg = M.bit_length() - 1
+    rng = np.random.default_rng(4)
+    nat = (rng.standard_normal(M) + 1j * rng.standard_normal(M)).astype(np.complex64)
+    rev = np.array([int(format(l, f"0{lg}b")[::-1], 2) for l in range(M)])
+    g = np.empty(M, dtype=np.complex64)
+    g[rev] = nat
+    lane = np.arange(32)
+    for blk in range(M // 32):
+        x = g[blk * 32:(blk + 1) * 32].copy()
+        h = 1
+        while h < 32:
+            w = tw[h - 1 + (lane & (h - 1))]
+            p = x[lane ^ h]
+            x = np.where((lane & h) == 0, x + w * p, p - w * x).astype(np.complex64)
+            h <<= 1
+        g[blk * 32:(blk + 1) * 32] = x
+    h = 32
+    while h < M:
+        b = np.arange(M // 2)
+        pos = b & (h - 1)
+        i = ((b - pos) << 1) + pos
+        j = i + h
+        t = tw[h - 1 + pos] * g[j]
+        gi = g[i].copy()
+        g[j] = gi - t
+        g[i] = gi + t
+        h <<= 1
+    want = np.fft.ifft(nat.astype(np.complex128)) * M
+    assert np.abs(g - want).max() <= 2e-6 * np.abs(want).max(), np.abs(g - want).max() / np.abs(want).max()
